@@ -1,0 +1,369 @@
+"""i-NOLF rendering throughput on one GB300 (Mrays/s at 4K).
+
+Workload (default): the full synthetic object -- displaced geodesic sphere,
+200 000 triangles, 16 PSH levels N = 16..2048 (band 2 cells), F = 2 FP32
+features, MLP 48-64-64-4 -- rendered from 64 ring viewpoints at distance 2.5,
+3840x2160 each: one step = one inolf_render call over all 64 views
+(530.8 M primary rays).  Inputs (object tables, cameras) are resident in HBM
+before the timed region; the RGBA output (8.5 GB) is larger than L2, and L2
+is flushed between timed steps as well.
+
+`value` is device-timed Mrays/s of the FP32 path; `e2e` is the same metric
+through the C ABI with host buffers (cameras host->device and the full RGBA
+frame device->host inside the timed region).  Precision variants (BF16/FP8
+MLP on the tensor cores) are reported under `precisions` where built.
+
+`--impl reference` times the FP64 CPU oracle (the only reference this
+project has) on a bounded pixel sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+W4K, H4K, N_VIEWS, RING_R = 3840, 2160, 64, 2.5
+SLOT_SLACK = 1.25
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--small", action="store_true", help="tiny scene, 1 view at 512x512 (profiling)")
+    ap.add_argument("--views", type=int, default=N_VIEWS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precisions", default="fp32,bf16,fp8")
+    return ap.parse_args()
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist_init(n_gpus):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_workload(small: bool, views: int):
+    from paper_2303_04086_gb300 import synth
+    if small:
+        scene = synth.tiny_scene(seed=0)
+        cams = synth.ring_cameras(max(1, min(views, 4)), 3.0)
+        return scene, cams, 512, 512, {"workload": "icosphere-1280tri L4 N16-128, %d view(s) 512x512" % len(cams)}
+    scene = synth.full_scene(seed=0)
+    cams = synth.ring_cameras(views, RING_R)
+    desc = ("displaced geodesic sphere 200k tris, L16 PSH N16-2048 band 2 cells, F2 fp32, "
+            "MLP 48-64-64-4, %d ring views r=2.5 at 3840x2160" % views)
+    return scene, cams, W4K, H4K, {"workload": desc}
+
+
+def algorithmic_bytes_per_hit(scene) -> int:
+    # per hit ray: L levels x 8 corners x (F features + 4-byte Phi entry)
+    fb = 2 if scene.feature_fp16 else 4
+    return scene.n_levels * 8 * (2 * fb + 4)
+
+
+def mlp_flops_per_hit(scene) -> int:
+    return 2 * (64 * scene.d_in + 64 * 64 + 4 * 64)
+
+
+def cpu_baseline(scene, cams, W, H, budget_s=12.0):
+    """The FP64 oracle as it stands, on a seeded pixel sample of view 0."""
+    import oracle
+    oracle.build()
+    orc = oracle.Oracle(scene)
+    rng = np.random.default_rng(0)
+    n = 2000
+    spent = 0.0
+    total_rays = 0
+    while spent < budget_s and n <= W * H:
+        pix = np.sort(rng.choice(W * H, n, replace=False)).astype(np.int64)
+        t0 = time.perf_counter()
+        orc.render_pixels(cams[0], W, H, pix)
+        dt = time.perf_counter() - t0
+        spent += dt
+        total_rays += n
+        if dt < 0.5 * (budget_s - spent):
+            n = min(W * H, n * 4)
+    rate = total_rays / spent
+    return {"value": rate / 1e6, "unit": "Mrays/s", "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"{total_rays} seeded random pixels of view 0 ({W}x{H}), FP64 oracle, "
+                      f"{spent:.1f} s of CPU work"}
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    scene, cams, W, H, cfg = make_workload(a.small, a.views)
+    per_step = []
+    import oracle
+    oracle.build()
+    orc = oracle.Oracle(scene)
+    rng = np.random.default_rng(0)
+    n = 20000 if not a.small else 20000
+    for s in range(a.warmup + a.steps):
+        pix = np.sort(rng.choice(W * H, min(n, W * H), replace=False)).astype(np.int64)
+        t0 = time.perf_counter()
+        orc.render_pixels(cams[s % len(cams)], W, H, pix)
+        dt = time.perf_counter() - t0
+        if s >= a.warmup:
+            per_step.append((len(pix), dt))
+    rays = sum(r for r, _ in per_step)
+    secs = sum(t for _, t in per_step)
+    val = rays / secs / 1e6
+    cfg = dict(cfg)
+    cfg["sample"] = f"{n} seeded random pixels per step of the 4K views"
+    out = {"impl": "reference", "metric": "i-NOLF Mrays/s at 4K (FP32 plain)", "value": val, "unit": "Mrays/s",
+           "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * secs / a.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": cfg,
+           "cpu_baseline": {"value": val, "unit": "Mrays/s", "cores": oracle.max_threads(), "kind": "oracle",
+                            "sample": cfg["sample"]},
+           "e2e": {"value": val, "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def run_native(a):
+    import torch
+    from paper_2303_04086_gb300 import build, inolf, synth
+    rank, world, local = _dist_init(a.gpus)
+    build.build()
+    scene, cams, W, H, cfg = make_workload(a.small, a.views)
+    t0 = time.time()
+    hashes = inolf.build_hashes(scene, slot_slack=1.0 if a.small else SLOT_SLACK)
+    obj = inolf.object_create(scene, hashes)
+    prep_s = time.time() - t0
+    nv = len(cams)
+    n_rays = nv * W * H
+    dev = torch.device("cuda", torch.cuda.current_device())
+    rgba = torch.empty((nv, H, W, 4), dtype=torch.float32, device=dev)
+    ws = torch.empty((inolf.render_workspace_bytes(n_rays) + 15) // 16 * 4, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+    peaks = _peaks()
+
+    def step(prec):
+        inolf.render(obj, cams, W, H, prec, rgba_out=rgba, workspace=ws, stream=stream)
+
+    # hit count (for per-hit algorithmic work)
+    tri = torch.empty((nv, H, W), dtype=torch.int32, device=dev)
+    inolf.render(obj, cams, W, H, "fp32", rgba_out=rgba, tri_out=tri, workspace=ws)
+    torch.cuda.synchronize()
+    n_hit = int((tri >= 0).sum().item())
+    del tri
+
+    def timed(prec, steps, warmup, with_stats=False):
+        for _ in range(warmup):
+            step(prec)
+        torch.cuda.synchronize()
+        _barrier(world)
+        inolf.stats_reset()
+        inolf.stats_enable(with_stats)
+        evs = []
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(prec)
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        _barrier(world)
+        inolf.stats_enable(False)
+        ms = sum(e0.elapsed_time(e1) for e0, e1 in evs)
+        return ms, inolf.stats_read()
+
+    with ClockSampler(local) as clk:
+        ms, stats = timed("fp32", a.steps, a.warmup, with_stats=True)
+    ms = _max_over_ranks(ms, world)
+    clocks = clk.summary()
+    rays_all = n_rays * a.steps * world
+    value = rays_all / (ms / 1e3) / 1e6
+
+    # precision variants
+    precisions = {}
+    for prec in [p for p in a.precisions.split(",") if p and p != "fp32"]:
+        try:
+            if prec == "fp8" and hasattr(inolf, "calibrate_fp8"):
+                inolf.calibrate_fp8(obj, cams[:1], W, H)
+            pms, _ = timed(prec, a.steps, 1)
+            pms = _max_over_ranks(pms, world)
+            precisions[prec] = {"value": n_rays * a.steps * world / (pms / 1e3) / 1e6, "unit": "Mrays/s",
+                                "ms_per_step": pms / a.steps}
+        except inolf.InolfError as e:
+            precisions[prec] = {"unavailable": str(e)}
+
+    # end to end through the C ABI with host buffers: the cameras go from
+    # host memory into the launch, the full RGBA frame comes back to pinned
+    # host memory inside the timed region
+    host_out = torch.empty((nv, H, W, 4), dtype=torch.float32, pin_memory=True)
+    host_cams = np.ascontiguousarray(cams, np.float32)
+    e2e_steps = max(1, min(a.steps, 3))
+
+    def e2e_step():
+        inolf.render(obj, host_cams, W, H, "fp32", rgba_out=rgba, workspace=ws, stream=stream)
+        host_out.copy_(rgba, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    _barrier(world)
+    t_e = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = _max_over_ranks(time.perf_counter() - t_e, world)
+    e2e = {"value": n_rays * e2e_steps * world / e2e_s / 1e6, "unit": "Mrays/s",
+           "h2d_bytes_per_step": int(host_cams.nbytes), "d2h_bytes_per_step": int(host_out.numel() * 4)}
+    del host_out
+
+    # roofline of the dominant kernel (from CUDA events around each launch)
+    top = max(stats, key=lambda k: stats[k]["ms"]) if stats else None
+    roof = None
+    if top:
+        st = stats[top]
+        avg_s = st["ms"] / 1e3 / st["launches"]
+        hits_per_launch = n_hit / max(1, st["launches"] // a.steps) if a.steps else n_hit
+        if top.startswith("k_shade"):
+            byt = algorithmic_bytes_per_hit(scene) * hits_per_launch + 16 * hits_per_launch + 8 * hits_per_launch
+            achieved = byt / avg_s / 1e9
+            peak = peaks.get("hbm_gbs", 6800.0)
+            roof = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "mlp_tflops": mlp_flops_per_hit(scene) * hits_per_launch / avg_s / 1e12}
+        else:
+            rays_per_launch = n_rays / max(1, st["launches"] // a.steps)
+            byt = 16 * rays_per_launch + 8 * hits_per_launch
+            achieved = byt / avg_s / 1e9
+            peak = peaks.get("hbm_gbs", 6800.0)
+            roof = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": None}
+
+    base = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        base = cpu_baseline(scene, cams, W, H)
+
+    cfg = dict(cfg)
+    cfg.update({"l2": "flushed between timed steps (256 MB write); output 8.5 GB > L2" if not a.small else
+                "flushed between timed steps", "rays_per_step": n_rays, "hit_rays_per_step": n_hit,
+                "prep_s": round(prep_s, 1), "slot_slack": 1.0 if a.small else SLOT_SLACK})
+    out = {"metric": "i-NOLF Mrays/s at 4K (FP32 plain)", "value": value, "unit": "Mrays/s", "n_gpus": world,
+           "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
+           "e2e": e2e, "gpu_launches": int(sum(s["launches"] for s in stats.values())),
+           "kernels": stats, "roofline": roof, "cpu_baseline": base, "clocks": clocks,
+           "precisions": precisions, "hit_mrays_per_s": n_hit * a.steps * world / (ms / 1e3) / 1e6}
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_native(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,218 @@
+/*
+ * inolf.h -- C ABI of libinolf.so, the GB300 (sm_103a) implementation of the
+ * i-NOLF per-ray hot path of "NEPHELE: A Neural Platform for Highly Realistic
+ * Cloud Radiance Rendering" (arXiv 2303.04086):
+ *
+ *   one network query per ray (Sec. 4.2, Eqs. 2-3): the ray's first hit on a
+ *   triangle-mesh geometry proxy, a multi-level perfect-spatial-hash feature
+ *   fetch h(p) = h0(p) + Phi[h1(p)] (Sec. 4.1, Eq. 1) with trilinear
+ *   interpolation, and a fused MLP F_s mapping the features plus a spherical
+ *   harmonics encoding of the view direction to RGBA.
+ *
+ * Conventions for every call:
+ *   - Every call returns an inolf_status; no C++ exception crosses the ABI.
+ *     On error, inolf_last_error() returns a message (thread-local).
+ *   - Dimension and pointer errors return INOLF_E_INVALID before any launch.
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *     global memory of the current device (e.g. a PyTorch CUDA tensor).
+ *   - Callers own every buffer they pass in; the library owns the handles it
+ *     returns (inolf_hash, inolf_object, inolf_server) and frees them in the
+ *     matching *_free / *_destroy call.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Device work is enqueued on it and the call returns without
+ *     synchronising unless stated otherwise.
+ *
+ * Geometry conventions (shared with the synthetic scene records):
+ *   - object frame: the scene cube [lo, lo + 1/scale]^3; grid level l has
+ *     N_l cells per axis and vertices at integer coordinates 0..N_l;
+ *   - a hit point P maps to x = (P - lo) * scale, u = N_l * x,
+ *     c = clamp(floor(u), 0, N_l - 1), f = u - c (all FP32, Sec. 4.1);
+ *   - camera record: 13 floats eye[3], right[3], up[3], fwd[3], tan(fovy/2);
+ *     pixel (i, j), row 0 at the top, looks along
+ *     normalize(((2i+1)/W - 1) tan W/H right + (1 - (2j+1)/H) tan up + fwd);
+ *   - MLP input: level-major features (F per level) then 16 real SH values of
+ *     the unit view direction, index l*l + l + m, no Condon-Shortley phase;
+ *     hidden layers 64 wide with ReLU, output 4 with sigmoid, no biases;
+ *     weights row-major [out][in].
+ */
+#ifndef INOLF_H
+#define INOLF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int inolf_status;
+
+#define INOLF_OK 0
+#define INOLF_PENDING 1            /* serve_poll: the request is still in flight */
+#define INOLF_E_INVALID (-1)       /* bad argument: nothing was launched */
+#define INOLF_E_OOM (-2)           /* host or device allocation failed */
+#define INOLF_E_CUDA (-3)          /* a CUDA runtime call failed */
+#define INOLF_E_BUDGET (-4)        /* serving admission refused: HBM budget or slots exhausted */
+#define INOLF_E_TIMEOUT (-5)       /* a bounded wait ran out */
+#define INOLF_E_HASH_FAILED (-6)   /* perfect hash construction failed after max_retries */
+#define INOLF_E_UNKNOWN_TICKET (-7) /* serve_poll: no such request */
+#define INOLF_E_UNSUPPORTED (-8)   /* valid request this build cannot serve */
+
+#define INOLF_MAX_LEVELS 16
+#define INOLF_HIDDEN 64
+#define INOLF_OUT 4
+#define INOLF_N_SH 16
+
+typedef enum {
+  INOLF_FP32 = 0, /* FP32 SIMT MLP */
+  INOLF_BF16 = 1, /* BF16 weights/activations, FP32 accumulation (tensor cores) */
+  INOLF_FP8 = 2   /* FP8 e4m3 weights/activations with per-tensor scales, FP32 accumulation */
+} inolf_precision;
+
+/* Message of the last error raised on the calling thread ("" if none). */
+const char* inolf_last_error(void);
+
+/* Library version string. */
+const char* inolf_version(void);
+
+/* ------------------------------------------------------------------------ */
+/* Perfect spatial hash (Sec. 4.1, Eq. 1; construction after Lefebvre and    */
+/* Hoppe 2006, which the paper cites for Phi).                               */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  double sigma;        /* offset-table size r^3 ~ sigma * n (default 1/6) */
+  double slot_slack;   /* hash-table size m^3 >= slot_slack * n (default 1.0) */
+  int32_t max_retries; /* growth steps of r (then m) before INOLF_E_HASH_FAILED */
+  uint64_t seed;       /* start of the offset search */
+} inolf_hash_params;
+
+typedef struct {
+  int32_t m;          /* hash-table side: m^3 slots, m <= 1024 */
+  int32_t r;          /* offset-table side: r^3 entries, gcd(m, r) = 1, m r > extent */
+  int64_t n;          /* number of hashed points */
+  uint32_t* phi;      /* host, r^3 entries, offset (x, y, z) packed x | y << 10 | z << 20 */
+  uint32_t* slot_of;  /* host, n entries: h(p_i) linearised x + m (y + m z) */
+} inolf_hash;
+
+/* Host-only, pure.  Builds a collision-free hash of n distinct integer points
+ * coords[n][3] (host, int32, each in [0, grid_extent]): h0(p) = p mod m,
+ * h1(p) = p mod r per axis, h(p) = (h0(p) + Phi[h1(p)]) mod m per axis.
+ * Offsets of 6-neighbouring Phi entries are tried first so that adjacent
+ * points tend to land in adjacent slots (the coherence the paper's
+ * Sec. 4.1 / Fig. 3 relies on).  Deterministic for given inputs and params
+ * (params may be NULL for the defaults).  On success *out is a new handle that
+ * the caller releases with inolf_hash_free.  Errors: INOLF_E_INVALID (bad
+ * pointer, n < 0, coordinates out of range, duplicate points, m > 1024),
+ * INOLF_E_OOM, INOLF_E_HASH_FAILED. */
+inolf_status inolf_build_hash(const int32_t* coords, int64_t n, int32_t grid_extent,
+                              const inolf_hash_params* params, inolf_hash** out);
+void inolf_hash_free(inolf_hash* h);
+
+/* ------------------------------------------------------------------------ */
+/* Object: proxy mesh + per-level hashes and feature tables + MLP weights.   */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  /* geometry proxy (host): n_vertices x 3 FP32, n_triangles x 3 int32 */
+  int32_t n_vertices, n_triangles;
+  const float* vertices;
+  const int32_t* triangles;
+  /* encoder levels (Sec. 4.1 grid + Eq. 1 hash per level) */
+  int32_t n_levels;                 /* 1..INOLF_MAX_LEVELS */
+  int32_t n_features;               /* F, must be 2 */
+  const int32_t* resolution;        /* host [n_levels]: N_l */
+  const inolf_hash* const* hashes;  /* host [n_levels]: hash of level l's vertex set */
+  const float* const* features;     /* host [n_levels]: n_l x F FP32, row i belongs to the
+                                       point i given to inolf_build_hash */
+  int32_t features_fp16;            /* 1: tables stored as FP16 on the device */
+  /* MLP F_s: d_in = n_levels * F + 16, hidden 64, out 4 (host, row-major) */
+  const float* w1;                  /* [64][d_in] */
+  const float* w2;                  /* [64][64] */
+  const float* w3;                  /* [4][64] */
+  /* FP8 activation scales (amax / 448) of the MLP inputs of layers 1, 2, 3;
+     0 = calibrate later with inolf_object_set_fp8_scales */
+  float fp8_act_scale[3];
+  /* object frame */
+  float domain_lo;                  /* lo (same on all axes), e.g. -1.5 */
+  float domain_scale;               /* scale = 1 / side, e.g. (float)(1/3) */
+} inolf_object_desc;
+
+typedef struct inolf_object inolf_object;
+
+/* Copies the description into library-owned device memory on the current
+ * device (BVH built on the host, feature rows scattered into slot order).
+ * Synchronous with respect to `stream` (returns after the uploads finish).
+ * Errors: INOLF_E_INVALID, INOLF_E_OOM, INOLF_E_CUDA. */
+inolf_status inolf_object_create(const inolf_object_desc* desc, void* stream, inolf_object** out);
+void inolf_object_destroy(inolf_object* obj);
+
+/* Device bytes held by the object (tables, Phi, BVH, weights). */
+inolf_status inolf_object_bytes(const inolf_object* obj, size_t* bytes);
+
+/* Sets the FP8 activation scales (amax / 448 of the inputs of layers 1-3). */
+inolf_status inolf_object_set_fp8_scales(inolf_object* obj, const float scales[3]);
+
+/* Reads back the object's device feature tables (slot order) and weights into
+ * host buffers: table_l has m_l^3 x F floats (FP16 tables are widened). */
+inolf_status inolf_object_read_params(const inolf_object* obj, float* const* tables, float* w1, float* w2,
+                                      float* w3);
+
+/* Number of slots m_l^3 of level l (size of its feature table in rows). */
+inolf_status inolf_object_table_rows(const inolf_object* obj, int32_t level, int64_t* rows);
+
+/* ------------------------------------------------------------------------ */
+/* Forward rendering (Sec. 4.2, one query per ray).                          */
+/* ------------------------------------------------------------------------ */
+
+/* Workspace bytes inolf_render / inolf_render_rays need for n_rays rays. */
+size_t inolf_render_workspace_bytes(int64_t n_rays);
+
+/* Renders n_views pinhole views of W x H pixels.
+ *   cams       host, n_views x 13 floats (camera records)
+ *   rgba_out   device, [n_views][H][W][4] FP32, straight alpha; rays that miss
+ *              the proxy get (0, 0, 0, 0)
+ *   tri_out    device [n_views][H][W] int32 closest triangle (-1 = miss), or NULL
+ *   t_out      device [n_views][H][W] FP32 hit distance (0 on miss), or NULL
+ *   workspace  device, >= inolf_render_workspace_bytes(n_views * W * H) bytes,
+ *              16-byte aligned, owned by the caller; contents undefined after
+ * Calls on one workspace must not overlap in time. */
+inolf_status inolf_render(const inolf_object* obj, const float* cams, int32_t n_views, int32_t W, int32_t H,
+                          inolf_precision prec, float* rgba_out, int32_t* tri_out, float* t_out,
+                          void* workspace, size_t workspace_bytes, void* stream);
+
+/* Renders n explicit rays: o, d device [n][3] FP32 (d unit length, object
+ * frame).  rgba_out device [n][4]; tri_out / t_out optional [n]. */
+inolf_status inolf_render_rays(const inolf_object* obj, const float* o, const float* d, int64_t n,
+                               inolf_precision prec, float* rgba_out, int32_t* tri_out, float* t_out,
+                               void* workspace, size_t workspace_bytes, void* stream);
+
+/* Stage outputs for parity checks of the encoder: for each ray that hits,
+ * slots_out[n][L][8] uint32 (corner (dx,dy,dz), x fastest) and
+ * feat_out[n][L*F] FP32 interpolated features; rows of missing rays are left
+ * untouched.  Device buffers; workspace as for inolf_render_rays. */
+inolf_status inolf_encode_rays(const inolf_object* obj, const float* o, const float* d, int64_t n,
+                               uint32_t* slots_out, float* feat_out, void* workspace, size_t workspace_bytes,
+                               void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Launch statistics (measurement support, no paper counterpart).           */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  char name[32];     /* kernel name */
+  int64_t launches;  /* launches since the last reset */
+  double ms;         /* summed device time between the events around each launch */
+} inolf_kernel_stat;
+
+/* When on != 0, every kernel launch of the library is bracketed by two CUDA
+ * events recorded on its stream (process-wide switch). */
+inolf_status inolf_stats_enable(int32_t on);
+/* Drops all recorded launches. */
+inolf_status inolf_stats_reset(void);
+/* Waits for the recorded events and returns per-kernel totals: up to `max`
+ * entries in out (host), the number of kernels in *n. */
+inolf_status inolf_stats_read(inolf_kernel_stat* out, int32_t max, int32_t* n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* INOLF_H */

@@ -1,0 +1,90 @@
+// Internal declarations shared by the translation units of libinolf.so.
+#pragma once
+
+#include <cstdint>
+#include <cstddef>
+#include <string>
+
+#include "../../include/inolf.h"
+
+namespace inolf {
+
+// Thread-local error message + status helper.
+inolf_status fail(inolf_status st, const std::string& msg);
+void clear_error();
+
+// Per-level encoder description as the kernels see it.
+struct LevelDev {
+  int32_t N;              // cells per axis
+  int32_t m;              // hash-table side
+  int32_t r;              // offset-table side
+  float N_f;              // (float)N
+  float inv_m;            // 1/m rounded to FP32 (fast exact modulo, see kernels)
+  float inv_r;            // 1/r rounded to FP32
+  const uint32_t* phi;    // r^3 packed offsets
+  const void* table;      // m^3 rows of F=2 features: float2 (FP32) or __half2 (FP16)
+};
+
+// Device-resident object (all pointers are device memory unless noted).
+struct Object {
+  int device = 0;
+  int L = 0, F = 2, d_in = 0;
+  int fp16 = 0;
+  float lo = -1.5f, scale = 1.0f / 3.0f;
+  LevelDev lv[INOLF_MAX_LEVELS] = {};
+  int64_t rows[INOLF_MAX_LEVELS] = {};
+  // BVH: nodes are 4 x float4 (child boxes x, y, z + child refs), triangles
+  // 3 x float4 (v0 + id bits, e1, e2)
+  void* nodes = nullptr;
+  int32_t n_nodes = 0;
+  void* tris = nullptr;
+  int32_t n_tris = 0;
+  // FP32 weights packed for the SIMT MLP: W1T [d_in][64], W2 [64][64], W3T [64][4]
+  float* w_f32 = nullptr;
+  // BF16 / FP8 operands for the tensor-core MLP (K-major rows, see mlp kernels)
+  void* w_bf16 = nullptr;
+  void* w_fp8 = nullptr;
+  float fp8_w_scale[3] = {0, 0, 0};
+  float fp8_act_scale[3] = {0, 0, 0};
+  size_t bytes = 0;
+};
+
+// Brackets one kernel launch with CUDA events when statistics are enabled
+// (stats.cpp).
+class LaunchTimer {
+ public:
+  LaunchTimer(const char* name, struct CUstream_st* st);
+  ~LaunchTimer();
+
+ private:
+  const char* name_;
+  struct CUstream_st* st_;
+  void* a_ = nullptr;
+  void* b_ = nullptr;
+  bool active_ = false;
+};
+
+// Launch helpers (render.cu).
+struct RayBatch {
+  int mode;                // 0 = pinhole views, 1 = explicit rays
+  const float* cams;       // device [n_views][13] (mode 0)
+  int32_t n_views, W, H;
+  const float* o;          // device [n][3] (mode 1)
+  const float* d;
+  int64_t n;               // total rays
+};
+
+inolf_status launch_render(const Object& obj, const RayBatch& rays, inolf_precision prec, float* rgba,
+                           int32_t* tri_out, float* t_out, uint32_t* slots_out, float* feat_out,
+                           void* workspace, size_t workspace_bytes, void* stream);
+
+size_t workspace_bytes(int64_t n_rays);
+
+// Weight repacking for the tensor-core paths (mlp_tc.cu).
+inolf_status prepare_tc_weights(Object& obj, const float* w1, const float* w2, const float* w3, void* stream);
+
+}  // namespace inolf
+
+struct inolf_object {
+  inolf::Object o;
+};

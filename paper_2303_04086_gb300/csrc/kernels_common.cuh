@@ -1,0 +1,339 @@
+// Device building blocks of the i-NOLF per-ray path, shared by the forward,
+// tensor-core and backward kernels of libinolf.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cmath>
+#include <cstdint>
+
+#include "inolf_internal.h"
+
+namespace inolf {
+
+static constexpr int kMaxViewsPerLaunch = 64;
+static constexpr int kStackDepth = 64;
+
+struct Params {
+  // geometry proxy
+  const float4* nodes;
+  const float4* tris;
+  // rays of this launch
+  int32_t mode;             // 0 = pinhole views (cams), 1 = explicit rays (ro, rd)
+  int32_t W, H;
+  int64_t n_rays;
+  int64_t ray_base;         // global index of this launch's first ray (outputs)
+  const float* ro;
+  const float* rd;
+  float cams[13 * kMaxViewsPerLaunch];
+  // encoder
+  int32_t L;
+  int32_t fp16;
+  float lo, scale;
+  LevelDev lv[INOLF_MAX_LEVELS];
+  // MLP
+  int32_t d_in;
+  const float* w_f32;
+  const void* w_bf16;
+  const void* w_fp8;
+  float fp8_w_scale[3];
+  float fp8_act_scale[3];
+  float shc[10];
+  // outputs
+  float4* rgba;
+  int32_t* tri_out;
+  float* t_out;
+  uint32_t* slots_out;
+  float* feat_out;
+  // workspace
+  uint32_t* counter;   // [0] hit count, [1] error flags
+  uint2* hits;         // (ray index in launch, t bits)
+};
+
+// Real SH constants of bands 0..3 (no Condon-Shortley phase), from
+// Y_l^m = K_l^m P_l^|m|(cos th) {sqrt2 cos(m ph), 1, sqrt2 sin(|m| ph)} with
+// K_l^m = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!) written as polynomials of the
+// unit direction (x, y, z):
+//   Y00 = c0;  Y1,-1 = c1 y, Y10 = c1 z, Y11 = c1 x
+//   Y2,-2 = c2a x y, Y2,-1 = c2a y z, Y20 = c2b (3 z^2 - 1), Y21 = c2a x z, Y22 = c2c (x^2 - y^2)
+//   Y3,-3 = c3a y (3 x^2 - y^2), Y3,-2 = c3b x y z, Y3,-1 = c3d y (5 z^2 - 1), Y30 = c3e z (5 z^2 - 3),
+//   Y31 = c3d x (5 z^2 - 1), Y32 = c3c z (x^2 - y^2), Y33 = c3a x (x^2 - 3 y^2)
+inline void sh_constants(float c[10]) {
+  const double pi = 3.14159265358979323846;
+  c[0] = (float)(0.5 / std::sqrt(pi));             // c0
+  c[1] = (float)std::sqrt(3.0 / (4.0 * pi));       // c1
+  c[2] = (float)std::sqrt(15.0 / (4.0 * pi));      // c2a
+  c[3] = (float)std::sqrt(5.0 / (16.0 * pi));      // c2b
+  c[4] = (float)std::sqrt(15.0 / (16.0 * pi));     // c2c
+  c[5] = (float)std::sqrt(35.0 / (32.0 * pi));     // c3a
+  c[6] = (float)std::sqrt(105.0 / (4.0 * pi));     // c3b
+  c[7] = (float)std::sqrt(105.0 / (16.0 * pi));    // c3c
+  c[8] = (float)std::sqrt(21.0 / (32.0 * pi));     // c3d
+  c[9] = (float)std::sqrt(7.0 / (16.0 * pi));      // c3e
+}
+
+__device__ __forceinline__ void sh16(const Params& p, const float d[3], float y[16]) {
+  const float x = d[0], yy = d[1], z = d[2];
+  const float* c = p.shc;
+  const float x2 = x * x, y2 = yy * yy, z2 = z * z;
+  y[0] = c[0];
+  y[1] = c[1] * yy;
+  y[2] = c[1] * z;
+  y[3] = c[1] * x;
+  y[4] = c[2] * x * yy;
+  y[5] = c[2] * yy * z;
+  y[6] = c[3] * (3.0f * z2 - 1.0f);
+  y[7] = c[2] * x * z;
+  y[8] = c[4] * (x2 - y2);
+  y[9] = c[5] * yy * (3.0f * x2 - y2);
+  y[10] = c[6] * x * yy * z;
+  y[11] = c[8] * yy * (5.0f * z2 - 1.0f);
+  y[12] = c[9] * z * (5.0f * z2 - 3.0f);
+  y[13] = c[8] * x * (5.0f * z2 - 1.0f);
+  y[14] = c[7] * z * (x2 - y2);
+  y[15] = c[5] * x * (x2 - 3.0f * y2);
+}
+
+__device__ __forceinline__ float sigmoidf_(float z) { return 1.0f / (1.0f + expf(-z)); }
+
+// Pinhole ray of pixel (i, j), row 0 at the top (exact FP32 operation order):
+//   tx = (tan * W) / H, a = (2i+1)/W - 1, b = 1 - (2j+1)/H
+//   v = ((a tx) right + (b tan) up) + fwd, d = v * (1 / sqrt((vx^2 + vy^2) + vz^2))
+__device__ __forceinline__ void make_ray(const float* cam, int W, int H, int i, int j, float o[3], float d[3]) {
+  const float th = cam[12];
+  const float fW = __int2float_rn(W), fH = __int2float_rn(H);
+  const float tx = __fdiv_rn(__fmul_rn(th, fW), fH);
+  const float a = __fsub_rn(__fdiv_rn(__int2float_rn(2 * i + 1), fW), 1.0f);
+  const float b = __fsub_rn(1.0f, __fdiv_rn(__int2float_rn(2 * j + 1), fH));
+  const float px = __fmul_rn(a, tx), py = __fmul_rn(b, th);
+  float v[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) v[k] = __fadd_rn(__fadd_rn(__fmul_rn(px, cam[3 + k]), __fmul_rn(py, cam[6 + k])), cam[9 + k]);
+  const float len2 = __fadd_rn(__fadd_rn(__fmul_rn(v[0], v[0]), __fmul_rn(v[1], v[1])), __fmul_rn(v[2], v[2]));
+  const float inv = __fdiv_rn(1.0f, __fsqrt_rn(len2));
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    o[k] = cam[k];
+    d[k] = __fmul_rn(v[k], inv);
+  }
+}
+
+__device__ __forceinline__ void ray_of(const Params& p, int64_t ray, float o[3], float d[3]) {
+  if (p.mode == 0) {
+    const int64_t per_view = (int64_t)p.W * p.H;
+    const int view = (int)(ray / per_view);
+    const int64_t pix = ray - (int64_t)view * per_view;
+    const int j = (int)(pix / p.W), i = (int)(pix - (int64_t)j * p.W);
+    make_ray(p.cams + 13 * view, p.W, p.H, i, j, o, d);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { o[k] = p.ro[3 * ray + k]; d[k] = p.rd[3 * ray + k]; }
+  }
+}
+
+// Moller-Trumbore, two-sided, exact FP32 operation order; accepts when
+// det != 0, u >= 0, v >= 0, u + v <= 1, t > 1e-6.
+__device__ __forceinline__ bool mt_hit(const float o[3], const float d[3], const float4 v0, const float4 e1,
+                                       const float4 e2, float& t_out) {
+  const float p0 = __fsub_rn(__fmul_rn(d[1], e2.z), __fmul_rn(d[2], e2.y));
+  const float p1 = __fsub_rn(__fmul_rn(d[2], e2.x), __fmul_rn(d[0], e2.z));
+  const float p2 = __fsub_rn(__fmul_rn(d[0], e2.y), __fmul_rn(d[1], e2.x));
+  const float det = __fadd_rn(__fadd_rn(__fmul_rn(e1.x, p0), __fmul_rn(e1.y, p1)), __fmul_rn(e1.z, p2));
+  if (det == 0.0f) return false;
+  const float inv = __fdiv_rn(1.0f, det);
+  const float s0 = __fsub_rn(o[0], v0.x), s1 = __fsub_rn(o[1], v0.y), s2 = __fsub_rn(o[2], v0.z);
+  const float u = __fmul_rn(__fadd_rn(__fadd_rn(__fmul_rn(s0, p0), __fmul_rn(s1, p1)), __fmul_rn(s2, p2)), inv);
+  if (!(u >= 0.0f) || !(u <= 1.0f)) return false;  // u > 1 implies u + v > 1 or v < 0
+  const float q0 = __fsub_rn(__fmul_rn(s1, e1.z), __fmul_rn(s2, e1.y));
+  const float q1 = __fsub_rn(__fmul_rn(s2, e1.x), __fmul_rn(s0, e1.z));
+  const float q2 = __fsub_rn(__fmul_rn(s0, e1.y), __fmul_rn(s1, e1.x));
+  const float v = __fmul_rn(__fadd_rn(__fadd_rn(__fmul_rn(d[0], q0), __fmul_rn(d[1], q1)), __fmul_rn(d[2], q2)), inv);
+  if (!(v >= 0.0f) || !(__fadd_rn(u, v) <= 1.0f)) return false;
+  const float t = __fmul_rn(__fadd_rn(__fadd_rn(__fmul_rn(e2.x, q0), __fmul_rn(e2.y, q1)), __fmul_rn(e2.z, q2)), inv);
+  if (!(t > 1e-6f)) return false;
+  t_out = t;
+  return true;
+}
+
+// Slab test of a padded box; returns entry distance or +inf.
+__device__ __forceinline__ float box_enter(float lox, float hix, float loy, float hiy, float loz, float hiz,
+                                           const float o[3], const float inv[3], float tmax) {
+  const float ax = (lox - o[0]) * inv[0], bx = (hix - o[0]) * inv[0];
+  const float ay = (loy - o[1]) * inv[1], by = (hiy - o[1]) * inv[1];
+  const float az = (loz - o[2]) * inv[2], bz = (hiz - o[2]) * inv[2];
+  const float t0 = fmaxf(fmaxf(fminf(ax, bx), fminf(ay, by)), fmaxf(fminf(az, bz), 0.0f));
+  const float t1 = fminf(fminf(fmaxf(ax, bx), fmaxf(ay, by)), fminf(fmaxf(az, bz), tmax));
+  return t0 <= t1 ? t0 : INFINITY;
+}
+
+// Closest hit over the proxy: lexicographic minimum of (t, triangle id).  A
+// subtree is skipped only when its padded box is entered after the current
+// best t plus a relative slack, which never drops an equal-or-better hit.
+__device__ __forceinline__ void closest_hit(const Params& p, const float o[3], const float d[3], int32_t& best_id,
+                                            float& best_t) {
+  float inv[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float dk = fabsf(d[k]) < 1e-20f ? copysignf(1e-20f, d[k]) : d[k];
+    inv[k] = 1.0f / dk;
+  }
+  best_id = -1;
+  best_t = INFINITY;
+  int32_t st_idx[kStackDepth];
+  int32_t st_cnt[kStackDepth];
+  float st_t[kStackDepth];
+  int sp = 0;
+  int32_t cur = 0, cur_cnt = 0;  // inner node 0
+  // every step visits a new node of a finite tree; the bound only guards
+  // against a malformed node array (flagged, traversal stops)
+  for (int32_t guard = 0;; ++guard) {
+    if (guard > (1 << 22)) {
+      atomicOr(p.counter + 1, 2u);
+      break;
+    }
+    const float lim = best_id < 0 ? INFINITY : best_t * 1.00002f + 1e-5f;
+    if (cur_cnt == 0) {
+      const float4 nx = __ldg(p.nodes + 4 * cur + 0);
+      const float4 ny = __ldg(p.nodes + 4 * cur + 1);
+      const float4 nz = __ldg(p.nodes + 4 * cur + 2);
+      const int4 meta = __ldg(reinterpret_cast<const int4*>(p.nodes) + 4 * cur + 3);
+      const float tl = box_enter(nx.x, nx.y, ny.x, ny.y, nz.x, nz.y, o, inv, lim);
+      const float tr = box_enter(nx.z, nx.w, ny.z, ny.w, nz.z, nz.w, o, inv, lim);
+      // a child with index < 0 and count 0 is empty
+      const bool hl = tl != INFINITY && (meta.x >= 0), hr = tr != INFINITY && (meta.z >= 0);
+      if (hl && hr) {
+        const bool lfirst = tl <= tr;
+        if (sp < kStackDepth) {
+          st_idx[sp] = lfirst ? meta.z : meta.x;
+          st_cnt[sp] = lfirst ? meta.w : meta.y;
+          st_t[sp] = lfirst ? tr : tl;
+          ++sp;
+        } else {
+          atomicOr(p.counter + 1, 1u);  // stack overflow: flagged, subtree skipped
+        }
+        cur = lfirst ? meta.x : meta.z;
+        cur_cnt = lfirst ? meta.y : meta.w;
+        continue;
+      } else if (hl || hr) {
+        cur = hl ? meta.x : meta.z;
+        cur_cnt = hl ? meta.y : meta.w;
+        continue;
+      }
+    } else {
+      for (int32_t k = 0; k < cur_cnt; ++k) {
+        const float4 a = __ldg(p.tris + 3 * (cur + k) + 0);
+        const float4 b = __ldg(p.tris + 3 * (cur + k) + 1);
+        const float4 c = __ldg(p.tris + 3 * (cur + k) + 2);
+        float t;
+        if (mt_hit(o, d, a, b, c, t)) {
+          const int32_t id = __float_as_int(a.w);
+          if (t < best_t || (t == best_t && id < best_id)) { best_t = t; best_id = id; }
+        }
+      }
+    }
+    // pop the next subtree that can still hold a better hit
+    bool found = false;
+    while (sp > 0) {
+      --sp;
+      const float lim2 = best_id < 0 ? INFINITY : best_t * 1.00002f + 1e-5f;
+      if (st_t[sp] <= lim2) {
+        cur = st_idx[sp];
+        cur_cnt = st_cnt[sp];
+        found = true;
+        break;
+      }
+    }
+    if (!found) break;
+  }
+  if (best_id < 0) best_t = 0.0f;
+}
+
+// Scene-unit coordinates of the hit point: P = o + t d, x = (P - lo) * scale.
+__device__ __forceinline__ void hit_unit_coords(const Params& p, const float o[3], const float d[3], float t,
+                                                float x[3]) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float P = __fadd_rn(o[k], __fmul_rn(t, d[k]));
+    x[k] = __fmul_rn(__fsub_rn(P, p.lo), p.scale);
+  }
+}
+
+// a mod m for 0 <= a < 2^21 and m <= 2^10, with a float quotient estimate
+// (error < 0.25) corrected once in each direction.
+__device__ __forceinline__ int32_t mod_small(int32_t a, int32_t m, float inv_m) {
+  const int32_t q = __float2int_rz(__int2float_rn(a) * inv_m);
+  int32_t r = a - q * m;
+  r += (r < 0) ? m : 0;
+  r -= (r >= m) ? m : 0;
+  return r;
+}
+
+// Cell of level `lv` (Sec. 4.1, p = floor(N x)): c = clamp(floor(u), 0, N-1),
+// f = u - c with u = N x, all in FP32.
+__device__ __forceinline__ void cell_of(const LevelDev& lv, const float x[3], int32_t c[3], float f[3]) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float u = __fmul_rn(lv.N_f, x[k]);
+    int32_t ci = (int32_t)floorf(u);
+    ci = ci < 0 ? 0 : (ci > lv.N - 1 ? lv.N - 1 : ci);
+    c[k] = ci;
+    f[k] = __fsub_rn(u, __int2float_rn(ci));
+  }
+}
+
+// Eq. 1 slots of the 8 corners c + (dx, dy, dz) (x fastest) and the
+// trilinearly interpolated F = 2 features.
+__device__ __forceinline__ void encode_level(const LevelDev& lv, int fp16, const float x[3], uint32_t slots[8],
+                                             float& e0, float& e1) {
+  int32_t c[3];
+  float f[3];
+  cell_of(lv, x, c, f);
+  const int32_t m = lv.m, r = lv.r;
+  int32_t h0[3], h0n[3], h1[3], h1n[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    h0[k] = mod_small(c[k], m, lv.inv_m);
+    h0n[k] = h0[k] + 1 == m ? 0 : h0[k] + 1;
+    h1[k] = mod_small(c[k], r, lv.inv_r);
+    h1n[k] = h1[k] + 1 == r ? 0 : h1[k] + 1;
+  }
+  uint32_t ph[8];
+#pragma unroll
+  for (int cc = 0; cc < 8; ++cc) {
+    const int32_t qx = (cc & 1) ? h1n[0] : h1[0];
+    const int32_t qy = (cc & 2) ? h1n[1] : h1[1];
+    const int32_t qz = (cc & 4) ? h1n[2] : h1[2];
+    ph[cc] = __ldg(lv.phi + (qx + r * (qy + r * qz)));
+  }
+#pragma unroll
+  for (int cc = 0; cc < 8; ++cc) {
+    int32_t sx = ((cc & 1) ? h0n[0] : h0[0]) + (int32_t)(ph[cc] & 1023u);
+    int32_t sy = ((cc & 2) ? h0n[1] : h0[1]) + (int32_t)((ph[cc] >> 10) & 1023u);
+    int32_t sz = ((cc & 4) ? h0n[2] : h0[2]) + (int32_t)((ph[cc] >> 20) & 1023u);
+    sx -= sx >= m ? m : 0;
+    sy -= sy >= m ? m : 0;
+    sz -= sz >= m ? m : 0;
+    slots[cc] = (uint32_t)(sx + m * (sy + m * sz));
+  }
+  float2 v[8];
+  if (fp16) {
+    const __half2* tb = reinterpret_cast<const __half2*>(lv.table);
+#pragma unroll
+    for (int cc = 0; cc < 8; ++cc) v[cc] = __half22float2(__ldg(tb + slots[cc]));
+  } else {
+    const float2* tb = reinterpret_cast<const float2*>(lv.table);
+#pragma unroll
+    for (int cc = 0; cc < 8; ++cc) v[cc] = __ldg(tb + slots[cc]);
+  }
+  const float gx = 1.0f - f[0], gy = 1.0f - f[1], gz = 1.0f - f[2];
+  e0 = 0.0f;
+  e1 = 0.0f;
+#pragma unroll
+  for (int cc = 0; cc < 8; ++cc) {
+    const float w = ((cc & 1) ? f[0] : gx) * ((cc & 2) ? f[1] : gy) * ((cc & 4) ? f[2] : gz);
+    e0 += w * v[cc].x;
+    e1 += w * v[cc].y;
+  }
+}
+
+}  // namespace inolf

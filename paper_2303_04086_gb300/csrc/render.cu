@@ -1,0 +1,374 @@
+// Forward i-NOLF rendering on sm_103a: one network query per ray (Sec. 4.2).
+//
+// Two kernels per batch of rays:
+//   k_trace  one thread per ray: pinhole ray generation, closest-hit BVH
+//            traversal of the proxy mesh (FP32 Moller-Trumbore, closest =
+//            lexicographic (t, triangle id) minimum), then warp-ballot
+//            compaction of the hitting rays into a dense hit list
+//            (one global atomic per CTA).  Misses write RGBA = 0.
+//   k_shade  persistent over the hit list, one thread per hit ray: the
+//            Sec. 4.1 grid vertex of the hit point on every level, Eq. 1
+//            perfect-hash slots of the 8 voxel corners, feature gather,
+//            trilinear interpolation, SH view encoding and the MLP F_s of
+//            Eq. 3 with weights resident in shared memory.  Tensor-core
+//            variants of the MLP live in mlp_tc.cu.
+//
+// The FP32 steps that decide integers (ray generation, triangle test, hit
+// point, cell index) are written with explicit round-to-nearest intrinsics
+// so that no multiply-add is contracted and every result is the IEEE result
+// of the stated operation order.
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+#include <vector>
+
+#include "inolf_internal.h"
+#include "kernels_common.cuh"
+
+namespace inolf {
+
+// ---------------------------------------------------------------------------
+// k_trace
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_trace(const __grid_constant__ Params p, int32_t tiles_x, int32_t tiles_y) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int64_t ray;       // index within this chunk
+  bool valid;
+  float o[3], d[3];
+  if (p.mode == 0) {
+    // 16 x 16 pixel tile per CTA, each warp an 8 x 4 block of pixels
+    const int64_t tiles = (int64_t)tiles_x * tiles_y;
+    const int view = (int)(blockIdx.x / tiles);
+    const int64_t tr = blockIdx.x - (int64_t)view * tiles;
+    const int ty = (int)(tr / tiles_x), tx = (int)(tr - (int64_t)ty * tiles_x);
+    const int i = tx * 16 + (warp & 1) * 8 + (lane & 7);
+    const int j = ty * 16 + (warp >> 1) * 4 + (lane >> 3);
+    valid = (i < p.W) && (j < p.H);
+    ray = (int64_t)view * p.W * p.H + (int64_t)j * p.W + i;
+    if (valid) make_ray(p.cams + 13 * view, p.W, p.H, i, j, o, d);
+  } else {
+    ray = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    valid = ray < p.n_rays;
+    if (valid) {
+      for (int k = 0; k < 3; ++k) { o[k] = p.ro[3 * ray + k]; d[k] = p.rd[3 * ray + k]; }
+    }
+  }
+  int32_t tri = -1;
+  float t = 0.0f;
+  if (valid) closest_hit(p, o, d, tri, t);
+  const bool hit = valid && tri >= 0;
+
+  // compaction: warp ballot + per-CTA prefix + one global atomic per CTA
+  __shared__ uint32_t s_warp[8];
+  __shared__ uint32_t s_base;
+  const uint32_t mask = __ballot_sync(0xffffffffu, hit);
+  if (lane == 0) s_warp[warp] = __popc(mask);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t acc = 0;
+    for (int w = 0; w < 8; ++w) { uint32_t c = s_warp[w]; s_warp[w] = acc; acc += c; }
+    s_base = acc ? atomicAdd(p.counter, acc) : 0u;
+  }
+  __syncthreads();
+  if (valid) {
+    const int64_t g = p.ray_base + ray;
+    if (hit) {
+      const uint32_t pos = s_base + s_warp[warp] + __popc(mask & ((1u << lane) - 1u));
+      p.hits[pos] = make_uint2((uint32_t)ray, __float_as_uint(t));
+    } else if (p.rgba) {
+      p.rgba[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (p.tri_out) p.tri_out[g] = tri;
+    if (p.t_out) p.t_out[g] = hit ? t : 0.0f;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_shade (FP32 SIMT MLP) and k_encode (stage outputs for parity checks)
+// ---------------------------------------------------------------------------
+template <bool kEncodeOnly>
+__global__ void __launch_bounds__(128) k_shade_f32(const __grid_constant__ Params p) {
+  extern __shared__ float4 smem4[];
+  float* sw = reinterpret_cast<float*>(smem4);
+  const int din = p.d_in;
+  const int nw = din * 64 + 64 * 64 + 64 * 4;
+  if (!kEncodeOnly) {
+    for (int k = threadIdx.x; k < nw / 4; k += blockDim.x)
+      smem4[k] = reinterpret_cast<const float4*>(p.w_f32)[k];
+    __syncthreads();
+  }
+  const float4* W1T = smem4;                       // [din][16] float4
+  const float4* W2 = smem4 + din * 16;             // [64][16]
+  const float4* W3T = smem4 + din * 16 + 64 * 16;  // [64] float4
+  const uint32_t total = *p.counter;
+  for (uint32_t h = blockIdx.x * blockDim.x + threadIdx.x; h < total; h += gridDim.x * blockDim.x) {
+    const uint2 rec = p.hits[h];
+    const int64_t ray = rec.x;
+    const float t = __uint_as_float(rec.y);
+    float o[3], d[3];
+    ray_of(p, ray, o, d);
+    float x[3];
+    hit_unit_coords(p, o, d, t, x);
+    float h1[64];
+    if (!kEncodeOnly) {
+#pragma unroll
+      for (int j = 0; j < 64; ++j) h1[j] = 0.0f;
+    }
+    for (int l = 0; l < p.L; ++l) {
+      uint32_t slots[8];
+      float e0, e1;
+      encode_level(p.lv[l], p.fp16, x, slots, e0, e1);
+      if (kEncodeOnly) {
+        const int64_t g = p.ray_base + ray;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) p.slots_out[(g * p.L + l) * 8 + c] = slots[c];
+        p.feat_out[(g * p.L + l) * 2 + 0] = e0;
+        p.feat_out[(g * p.L + l) * 2 + 1] = e1;
+      } else {
+        const float4* r0 = W1T + (2 * l) * 16;
+        const float4* r1 = r0 + 16;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const float4 a = r0[q], b = r1[q];
+          h1[4 * q + 0] += a.x * e0 + b.x * e1;
+          h1[4 * q + 1] += a.y * e0 + b.y * e1;
+          h1[4 * q + 2] += a.z * e0 + b.z * e1;
+          h1[4 * q + 3] += a.w * e0 + b.w * e1;
+        }
+      }
+    }
+    if (kEncodeOnly) continue;
+    float sh[16];
+    sh16(p, d, sh);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const float4* r = W1T + (2 * p.L + k) * 16;
+      const float s = sh[k];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const float4 a = r[q];
+        h1[4 * q + 0] += a.x * s;
+        h1[4 * q + 1] += a.y * s;
+        h1[4 * q + 2] += a.z * s;
+        h1[4 * q + 3] += a.w * s;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 64; ++j) h1[j] = fmaxf(h1[j], 0.0f);
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 2
+    for (int j = 0; j < 64; ++j) {
+      const float4* r = W2 + j * 16;
+      float z = 0.0f;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const float4 a = r[q];
+        z += a.x * h1[4 * q + 0];
+        z += a.y * h1[4 * q + 1];
+        z += a.z * h1[4 * q + 2];
+        z += a.w * h1[4 * q + 3];
+      }
+      z = fmaxf(z, 0.0f);
+      const float4 w3 = W3T[j];
+      acc.x += w3.x * z;
+      acc.y += w3.y * z;
+      acc.z += w3.z * z;
+      acc.w += w3.w * z;
+    }
+    p.rgba[p.ray_base + ray] = make_float4(sigmoidf_(acc.x), sigmoidf_(acc.y), sigmoidf_(acc.z), sigmoidf_(acc.w));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static constexpr size_t kWsHeader = 256;
+
+size_t workspace_bytes(int64_t n_rays) { return kWsHeader + (size_t)std::max<int64_t>(n_rays, 1) * 8; }
+
+static int sm_count() {
+  static int n = 0;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  });
+  return n;
+}
+
+static void fill_common(const Object& obj, Params& p) {
+  p.nodes = (const float4*)obj.nodes;
+  p.tris = (const float4*)obj.tris;
+  p.L = obj.L;
+  p.lo = obj.lo;
+  p.scale = obj.scale;
+  p.fp16 = obj.fp16;
+  for (int l = 0; l < obj.L; ++l) p.lv[l] = obj.lv[l];
+  p.d_in = obj.d_in;
+  p.w_f32 = obj.w_f32;
+  p.w_bf16 = obj.w_bf16;
+  p.w_fp8 = obj.w_fp8;
+  for (int k = 0; k < 3; ++k) {
+    p.fp8_w_scale[k] = obj.fp8_w_scale[k];
+    p.fp8_act_scale[k] = obj.fp8_act_scale[k];
+  }
+  sh_constants(p.shc);
+}
+
+static inolf_status check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(INOLF_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return INOLF_OK;
+}
+
+inolf_status launch_shade_tc(const Params& p, inolf_precision prec, cudaStream_t st);  // mlp_tc.cu
+
+inolf_status launch_render(const Object& obj, const RayBatch& rays, inolf_precision prec, float* rgba,
+                           int32_t* tri_out, float* t_out, uint32_t* slots_out, float* feat_out,
+                           void* workspace, size_t ws_bytes, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!workspace || ws_bytes < workspace_bytes(1) || ((uintptr_t)workspace & 15))
+    return fail(INOLF_E_INVALID, "render: workspace missing, too small or not 16-byte aligned");
+  const bool encode = slots_out != nullptr;
+  if (!encode && prec != INOLF_FP32 && prec != INOLF_BF16 && prec != INOLF_FP8)
+    return fail(INOLF_E_INVALID, "render: unknown precision");
+  if (!encode && prec == INOLF_FP8 && !(obj.fp8_act_scale[0] > 0))
+    return fail(INOLF_E_INVALID, "render: FP8 needs activation scales (inolf_object_set_fp8_scales)");
+  const int64_t cap = (int64_t)((ws_bytes - kWsHeader) / 8);
+  uint32_t* counter = (uint32_t*)workspace;
+  uint2* hits = (uint2*)((char*)workspace + kWsHeader);
+
+  Params p{};
+  fill_common(obj, p);
+  p.mode = rays.mode;
+  p.rgba = (float4*)rgba;
+  p.tri_out = tri_out;
+  p.t_out = t_out;
+  p.slots_out = slots_out;
+  p.feat_out = feat_out;
+  p.counter = counter;
+  p.hits = hits;
+
+  const size_t smem_f32 = (size_t)(obj.d_in * 64 + 64 * 64 + 64 * 4) * sizeof(float);
+  static std::once_flag attr_once;
+  std::call_once(attr_once, [&] {
+    cudaFuncSetAttribute(k_shade_f32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+  });
+  const int shade_grid = sm_count() * 8;
+
+  auto run_chunk = [&](int64_t n_chunk, int32_t tiles_x, int32_t tiles_y, int64_t trace_blocks) -> inolf_status {
+    if (cudaMemsetAsync(counter, 0, 8, st) != cudaSuccess) return fail(INOLF_E_CUDA, "cudaMemsetAsync failed");
+    (void)n_chunk;
+    {
+      LaunchTimer lt("k_trace", st);
+      k_trace<<<(unsigned)trace_blocks, 256, 0, st>>>(p, tiles_x, tiles_y);
+    }
+    inolf_status s = check_launch("k_trace");
+    if (s != INOLF_OK) return s;
+    if (encode) {
+      LaunchTimer lt("k_encode", st);
+      k_shade_f32<true><<<shade_grid, 128, 0, st>>>(p);
+      return check_launch("k_encode");
+    }
+    if (prec == INOLF_FP32) {
+      {
+        LaunchTimer lt("k_shade_f32", st);
+        k_shade_f32<false><<<shade_grid, 128, smem_f32, st>>>(p);
+      }
+      return check_launch("k_shade_f32");
+    }
+    return launch_shade_tc(p, prec, st);
+  };
+
+  if (rays.mode == 0) {
+    const int64_t per_view = (int64_t)rays.W * rays.H;
+    if (per_view > 0xFFFFFFFFll) return fail(INOLF_E_INVALID, "render: view too large");
+    int64_t vpc = std::min<int64_t>(kMaxViewsPerLaunch, cap / per_view);
+    vpc = std::min<int64_t>(vpc, (int64_t)0xFFFFFFFFll / per_view);
+    if (vpc < 1) return fail(INOLF_E_INVALID, "render: workspace smaller than one view's hit list");
+    p.W = rays.W;
+    p.H = rays.H;
+    const int32_t tx = (rays.W + 15) / 16, ty = (rays.H + 15) / 16;
+    for (int32_t v0 = 0; v0 < rays.n_views; v0 += (int32_t)vpc) {
+      const int32_t nv = (int32_t)std::min<int64_t>(vpc, rays.n_views - v0);
+      for (int k = 0; k < 13 * nv; ++k) p.cams[k] = rays.cams[13 * v0 + k];
+      p.ray_base = (int64_t)v0 * per_view;
+      p.n_rays = (int64_t)nv * per_view;
+      inolf_status s = run_chunk(p.n_rays, tx, ty, (int64_t)nv * tx * ty);
+      if (s != INOLF_OK) return s;
+    }
+  } else {
+    int64_t chunk = std::min<int64_t>(cap, 0xFFFFFFFFll);
+    for (int64_t r0 = 0; r0 < rays.n; r0 += chunk) {
+      const int64_t nr = std::min(chunk, rays.n - r0);
+      p.ro = rays.o + 3 * r0;
+      p.rd = rays.d + 3 * r0;
+      p.ray_base = r0;
+      p.n_rays = nr;
+      // outputs are indexed by ray_base + local index; inputs by local index
+      inolf_status s = run_chunk(nr, 0, 0, (nr + 255) / 256);
+      if (s != INOLF_OK) return s;
+    }
+  }
+  return INOLF_OK;
+}
+
+}  // namespace inolf
+
+using namespace inolf;
+
+extern "C" size_t inolf_render_workspace_bytes(int64_t n_rays) { return inolf::workspace_bytes(n_rays); }
+
+extern "C" inolf_status inolf_render(const inolf_object* obj, const float* cams, int32_t n_views, int32_t W,
+                                     int32_t H, inolf_precision prec, float* rgba_out, int32_t* tri_out,
+                                     float* t_out, void* workspace, size_t workspace_bytes, void* stream) {
+  clear_error();
+  if (!obj || !cams || !rgba_out || n_views < 0 || W <= 0 || H <= 0)
+    return fail(INOLF_E_INVALID, "inolf_render: bad argument");
+  if (n_views == 0) return INOLF_OK;
+  RayBatch rb{};
+  rb.mode = 0;
+  rb.cams = cams;
+  rb.n_views = n_views;
+  rb.W = W;
+  rb.H = H;
+  rb.n = (int64_t)n_views * W * H;
+  return launch_render(obj->o, rb, prec, rgba_out, tri_out, t_out, nullptr, nullptr, workspace, workspace_bytes,
+                       stream);
+}
+
+extern "C" inolf_status inolf_render_rays(const inolf_object* obj, const float* o, const float* d, int64_t n,
+                                          inolf_precision prec, float* rgba_out, int32_t* tri_out, float* t_out,
+                                          void* workspace, size_t workspace_bytes, void* stream) {
+  clear_error();
+  if (!obj || n < 0 || (n > 0 && (!o || !d || !rgba_out))) return fail(INOLF_E_INVALID, "inolf_render_rays: bad argument");
+  if (n == 0) return INOLF_OK;
+  RayBatch rb{};
+  rb.mode = 1;
+  rb.o = o;
+  rb.d = d;
+  rb.n = n;
+  return launch_render(obj->o, rb, prec, rgba_out, tri_out, t_out, nullptr, nullptr, workspace, workspace_bytes,
+                       stream);
+}
+
+extern "C" inolf_status inolf_encode_rays(const inolf_object* obj, const float* o, const float* d, int64_t n,
+                                          uint32_t* slots_out, float* feat_out, void* workspace,
+                                          size_t workspace_bytes, void* stream) {
+  clear_error();
+  if (!obj || n < 0 || (n > 0 && (!o || !d || !slots_out || !feat_out)))
+    return fail(INOLF_E_INVALID, "inolf_encode_rays: bad argument");
+  if (n == 0) return INOLF_OK;
+  RayBatch rb{};
+  rb.mode = 1;
+  rb.o = o;
+  rb.d = d;
+  rb.n = n;
+  return launch_render(obj->o, rb, INOLF_FP32, nullptr, nullptr, nullptr, slots_out, feat_out, workspace,
+                       workspace_bytes, stream);
+}

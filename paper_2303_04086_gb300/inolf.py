@@ -1,0 +1,315 @@
+"""Thin Python binding of libinolf.so (ctypes).  Argument marshalling only:
+every step of the per-ray path runs in the library's CUDA kernels.  PyTorch
+supplies device memory and the current stream.
+
+Names follow the C ABI in include/inolf.h: build_hash, object_create,
+render, render_rays, encode_rays, ...
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from concurrent.futures import ThreadPoolExecutor
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libinolf.so")
+
+OK, PENDING = 0, 1
+E_INVALID, E_OOM, E_CUDA, E_BUDGET, E_TIMEOUT, E_HASH_FAILED, E_UNKNOWN_TICKET, E_UNSUPPORTED = range(-1, -9, -1)
+FP32, BF16, FP8 = 0, 1, 2
+PRECISIONS = {"fp32": FP32, "bf16": BF16, "fp8": FP8}
+MAX_LEVELS = 16
+
+_lib = None
+
+
+class InolfError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"inolf status {status}: {msg}")
+        self.status = status
+
+
+class HashParams(ctypes.Structure):
+    _fields_ = [("sigma", ctypes.c_double), ("slot_slack", ctypes.c_double),
+                ("max_retries", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+class HashStruct(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int32), ("r", ctypes.c_int32), ("n", ctypes.c_int64),
+                ("phi", ctypes.POINTER(ctypes.c_uint32)), ("slot_of", ctypes.POINTER(ctypes.c_uint32))]
+
+
+class ObjectDesc(ctypes.Structure):
+    _fields_ = [("n_vertices", ctypes.c_int32), ("n_triangles", ctypes.c_int32),
+                ("vertices", ctypes.c_void_p), ("triangles", ctypes.c_void_p),
+                ("n_levels", ctypes.c_int32), ("n_features", ctypes.c_int32),
+                ("resolution", ctypes.c_void_p), ("hashes", ctypes.c_void_p), ("features", ctypes.c_void_p),
+                ("features_fp16", ctypes.c_int32),
+                ("w1", ctypes.c_void_p), ("w2", ctypes.c_void_p), ("w3", ctypes.c_void_p),
+                ("fp8_act_scale", ctypes.c_float * 3),
+                ("domain_lo", ctypes.c_float), ("domain_scale", ctypes.c_float)]
+
+
+def lib():
+    """Load libinolf.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2303_04086_gb300.build.build() "
+                           "(there is no CPU fallback)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+    L.inolf_last_error.restype = ctypes.c_char_p
+    L.inolf_version.restype = ctypes.c_char_p
+    L.inolf_build_hash.argtypes = [vp, i64, i32, ctypes.POINTER(HashParams), ctypes.POINTER(ctypes.POINTER(HashStruct))]
+    L.inolf_hash_free.argtypes = [ctypes.POINTER(HashStruct)]
+    L.inolf_hash_free.restype = None
+    L.inolf_object_create.argtypes = [ctypes.POINTER(ObjectDesc), vp, ctypes.POINTER(vp)]
+    L.inolf_object_destroy.argtypes = [vp]
+    L.inolf_object_destroy.restype = None
+    L.inolf_object_bytes.argtypes = [vp, ctypes.POINTER(sz)]
+    L.inolf_object_set_fp8_scales.argtypes = [vp, vp]
+    L.inolf_object_read_params.argtypes = [vp, vp, vp, vp, vp]
+    L.inolf_object_table_rows.argtypes = [vp, i32, ctypes.POINTER(i64)]
+    L.inolf_render_workspace_bytes.argtypes = [i64]
+    L.inolf_render_workspace_bytes.restype = sz
+    L.inolf_render.argtypes = [vp, vp, i32, i32, i32, i32, vp, vp, vp, vp, sz, vp]
+    L.inolf_render_rays.argtypes = [vp, vp, vp, i64, i32, vp, vp, vp, vp, sz, vp]
+    L.inolf_encode_rays.argtypes = [vp, vp, vp, i64, vp, vp, vp, sz, vp]
+    _lib = L
+    return L
+
+
+def last_error() -> str:
+    return lib().inolf_last_error().decode()
+
+
+def _check(st: int):
+    if st < 0:
+        raise InolfError(st, last_error())
+    return st
+
+
+def _ptr(t) -> Optional[int]:
+    """Device/host address of a torch tensor or numpy array (None -> NULL)."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+# ---------------------------------------------------------------------------
+# perfect spatial hash (Sec. 4.1, Eq. 1)
+# ---------------------------------------------------------------------------
+class Hash:
+    """Handle of one level's hash; m, r, phi (r^3) and slot_of (n) as numpy views."""
+
+    def __init__(self, handle):
+        self._h = handle
+        h = handle.contents
+        self.m, self.r, self.n = h.m, h.r, h.n
+        self.phi = np.ctypeslib.as_array(h.phi, shape=(h.r ** 3,))
+        self.slot_of = np.ctypeslib.as_array(h.slot_of, shape=(max(h.n, 1),))[: h.n]
+
+    def __del__(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.inolf_hash_free(self._h)
+            self._h = None
+
+
+def build_hash(coords: np.ndarray, grid_extent: int, sigma: float = 1.0 / 6.0, slot_slack: float = 1.0,
+               max_retries: int = 8, seed: int = 0) -> Hash:
+    coords = np.ascontiguousarray(coords, np.int32).reshape(-1, 3)
+    out = ctypes.POINTER(HashStruct)()
+    prm = HashParams(sigma, slot_slack, max_retries, seed)
+    _check(lib().inolf_build_hash(ctypes.c_void_p(coords.ctypes.data), len(coords), grid_extent,
+                                  ctypes.byref(prm), ctypes.byref(out)))
+    return Hash(out)
+
+
+# ---------------------------------------------------------------------------
+# objects
+# ---------------------------------------------------------------------------
+class Object:
+    """A device-resident i-NOLF object (inolf_object handle)."""
+
+    def __init__(self, handle, L, d_in, hashes):
+        self._h = handle
+        self.L = L
+        self.d_in = d_in
+        self.hashes = hashes
+
+    @property
+    def handle(self):
+        return self._h
+
+    def bytes(self) -> int:
+        b = ctypes.c_size_t()
+        _check(lib().inolf_object_bytes(self._h, ctypes.byref(b)))
+        return b.value
+
+    def table_rows(self, level: int) -> int:
+        r = ctypes.c_int64()
+        _check(lib().inolf_object_table_rows(self._h, level, ctypes.byref(r)))
+        return r.value
+
+    def set_fp8_scales(self, scales: Sequence[float]):
+        s = np.ascontiguousarray(scales, np.float32)
+        _check(lib().inolf_object_set_fp8_scales(self._h, ctypes.c_void_p(s.ctypes.data)))
+
+    def read_params(self):
+        tables = [np.empty((self.table_rows(l), 2), np.float32) for l in range(self.L)]
+        tp = (ctypes.c_void_p * self.L)(*[t.ctypes.data for t in tables])
+        w1 = np.empty((64, self.d_in), np.float32)
+        w2 = np.empty((64, 64), np.float32)
+        w3 = np.empty((4, 64), np.float32)
+        _check(lib().inolf_object_read_params(self._h, tp, w1.ctypes.data, w2.ctypes.data, w3.ctypes.data))
+        return tables, w1, w2, w3
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.inolf_object_destroy(self._h)
+            self._h = None
+
+
+def build_hashes(scene, threads: int = 0, **kw) -> List[Hash]:
+    """inolf_build_hash for every level of a synth.Scene, levels in parallel
+    (ctypes releases the GIL during the call)."""
+    from .synth import unpack_keys
+
+    def one(l):
+        return build_hash(unpack_keys(scene.keys[l]), scene.resolutions[l], **kw)
+
+    n = threads or min(len(scene.keys), os.cpu_count() or 1)
+    with ThreadPoolExecutor(max_workers=n) as ex:
+        return list(ex.map(one, range(scene.n_levels)))
+
+
+def object_create(scene, hashes: Optional[List[Hash]] = None, fp16: Optional[bool] = None,
+                  fp8_act_scale=(0.0, 0.0, 0.0), stream=None) -> Object:
+    """Upload a synth.Scene (mesh, per-level hash + features, MLP weights)."""
+    if hashes is None:
+        hashes = build_hashes(scene)
+    L = scene.n_levels
+    V = np.ascontiguousarray(scene.vertices, np.float32)
+    F = np.ascontiguousarray(scene.triangles, np.int32)
+    res = np.ascontiguousarray(scene.resolutions, np.int32)
+    feats = [np.ascontiguousarray(f, np.float32) for f in scene.features]
+    w1 = np.ascontiguousarray(scene.w1, np.float32)
+    w2 = np.ascontiguousarray(scene.w2, np.float32)
+    w3 = np.ascontiguousarray(scene.w3, np.float32)
+    hp = (ctypes.POINTER(HashStruct) * L)(*[h._h for h in hashes])
+    fp = (ctypes.c_void_p * L)(*[f.ctypes.data for f in feats])
+    d = ObjectDesc()
+    d.n_vertices, d.n_triangles = len(V), len(F)
+    d.vertices, d.triangles = V.ctypes.data, F.ctypes.data
+    d.n_levels, d.n_features = L, 2
+    d.resolution = res.ctypes.data
+    d.hashes = ctypes.cast(hp, ctypes.c_void_p)
+    d.features = ctypes.cast(fp, ctypes.c_void_p)
+    d.features_fp16 = int(scene.feature_fp16 if fp16 is None else fp16)
+    d.w1, d.w2, d.w3 = w1.ctypes.data, w2.ctypes.data, w3.ctypes.data
+    for k in range(3):
+        d.fp8_act_scale[k] = float(fp8_act_scale[k])
+    d.domain_lo = float(scene.domain_lo)
+    d.domain_scale = float(np.float32(1.0 / scene.domain_side))
+    out = ctypes.c_void_p()
+    _check(lib().inolf_object_create(ctypes.byref(d), _stream(stream), ctypes.byref(out)))
+    return Object(out.value, L, scene.d_in, hashes)
+
+
+# ---------------------------------------------------------------------------
+# rendering
+# ---------------------------------------------------------------------------
+def render_workspace_bytes(n_rays: int) -> int:
+    return int(lib().inolf_render_workspace_bytes(int(n_rays)))
+
+
+def _workspace(n_rays, device):
+    import torch
+    nb = render_workspace_bytes(n_rays)
+    return torch.empty((nb + 15) // 16 * 4, dtype=torch.int32, device=device)
+
+
+def render(obj: Object, cams: np.ndarray, W: int, H: int, prec="fp32", rgba_out=None, tri_out=None, t_out=None,
+           workspace=None, stream=None):
+    """Render pinhole views (cams: host [n_views, 13] float32).  Returns rgba
+    [n_views, H, W, 4] (a new CUDA tensor unless rgba_out is given)."""
+    import torch
+    cams = np.ascontiguousarray(cams, np.float32).reshape(-1, 13)
+    nv = len(cams)
+    if rgba_out is None:
+        rgba_out = torch.empty((nv, H, W, 4), dtype=torch.float32, device="cuda")
+    if workspace is None:
+        workspace = _workspace(nv * W * H, rgba_out.device)
+    p = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+    _check(lib().inolf_render(obj.handle, cams.ctypes.data, nv, W, H, p, _ptr(rgba_out), _ptr(tri_out),
+                              _ptr(t_out), _ptr(workspace), workspace.numel() * workspace.element_size(),
+                              _stream(stream)))
+    return rgba_out
+
+
+def render_rays(obj: Object, o, d, prec="fp32", rgba_out=None, tri_out=None, t_out=None, workspace=None,
+                stream=None):
+    """Render explicit rays (o, d: CUDA float32 [n, 3])."""
+    import torch
+    n = o.shape[0]
+    if rgba_out is None:
+        rgba_out = torch.empty((n, 4), dtype=torch.float32, device=o.device)
+    if workspace is None:
+        workspace = _workspace(n, o.device)
+    p = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+    _check(lib().inolf_render_rays(obj.handle, _ptr(o), _ptr(d), n, p, _ptr(rgba_out), _ptr(tri_out),
+                                   _ptr(t_out), _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                   _stream(stream)))
+    return rgba_out
+
+
+def encode_rays(obj: Object, o, d, slots_out, feat_out, workspace=None, stream=None):
+    """Stage outputs: per hit ray and level the 8 corner slots and the
+    interpolated features (rows of missing rays untouched)."""
+    n = o.shape[0]
+    if workspace is None:
+        workspace = _workspace(n, o.device)
+    _check(lib().inolf_encode_rays(obj.handle, _ptr(o), _ptr(d), n, _ptr(slots_out), _ptr(feat_out),
+                                   _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                   _stream(stream)))
+
+
+# ---------------------------------------------------------------------------
+# launch statistics (CUDA events around every library kernel launch)
+# ---------------------------------------------------------------------------
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("ms", ctypes.c_double)]
+
+
+def stats_enable(on: bool = True):
+    lib().inolf_stats_enable.argtypes = [ctypes.c_int32]
+    _check(lib().inolf_stats_enable(int(bool(on))))
+
+
+def stats_reset():
+    _check(lib().inolf_stats_reset())
+
+
+def stats_read() -> dict:
+    """{kernel name: {"launches": n, "ms": summed device ms}} since the last reset."""
+    L = lib()
+    arr = (KernelStat * 64)()
+    n = ctypes.c_int32()
+    L.inolf_stats_read.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+    _check(L.inolf_stats_read(ctypes.cast(arr, ctypes.c_void_p), 64, ctypes.byref(n)))
+    return {arr[i].name.decode(): {"launches": int(arr[i].launches), "ms": float(arr[i].ms)}
+            for i in range(min(n.value, 64))}
