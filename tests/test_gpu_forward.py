@@ -85,8 +85,9 @@ def _random_rays(n, seed, inside_frac=0.1):
     tgt = rng.uniform(-1.1, 1.1, size=(n, 3))
     d = tgt - eye
     # a few axis-aligned directions (zero components)
-    d[k:k + 6] = [[1, 0, 0], [0, -1, 0], [0, 0, 1], [-1, 0, 0], [0, 1, 0], [0, 0, -1]]
-    eye[k:k + 6] = [[-3, 0.1, 0.2], [0.05, 3, -0.1], [0.3, 0.2, -3], [3, 0, 0], [0, -3, 0], [0, 0, 3]]
+    if n >= k + 6:
+        d[k:k + 6] = [[1, 0, 0], [0, -1, 0], [0, 0, 1], [-1, 0, 0], [0, 1, 0], [0, 0, -1]]
+        eye[k:k + 6] = [[-3, 0.1, 0.2], [0.05, 3, -0.1], [0.3, 0.2, -3], [3, 0, 0], [0, -3, 0], [0, 0, 3]]
     d /= np.linalg.norm(d, axis=1, keepdims=True)
     return eye.astype(np.float32), d.astype(np.float32)
 
