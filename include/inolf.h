@@ -194,6 +194,35 @@ inolf_status inolf_encode_rays(const inolf_object* obj, const float* o, const fl
                                void* stream);
 
 /* ------------------------------------------------------------------------ */
+/* Allocation-free rendering (the paper has no counterpart: this exists for   */
+/* callers of the library, not for the method).                              */
+/* ------------------------------------------------------------------------ */
+#define INOLF_NOALLOC_MAX_RAYS 1048576
+
+/* Renders n explicit rays exactly like inolf_render_rays, but without a
+ * workspace and without allocating anything.  It is meant for callers that
+ * cannot allocate device memory where they render: a frame loop whose memory
+ * budget is fixed at start-up, a plug-in whose host application owns every
+ * device allocation, or a latency-critical thread that cannot afford the
+ * device-wide synchronisation of cudaMalloc/cudaFree.  The hit list lives in
+ * a fixed 8 MiB + 256 B array inside the library's device image, which every
+ * GPU that loads the library keeps until the process exits.
+ *   - n must be <= INOLF_NOALLOC_MAX_RAYS; larger n returns INOLF_E_INVALID
+ *     and launches nothing.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current) and caches it; make
+ *     that first call before any stream capture.
+ *   - All calls on a device share the one array; the call clears its counters
+ *     itself.  Calls whose GPU work overlaps in time (other streams or host
+ *     threads) race on the array and produce wrong results: order them, e.g.
+ *     on one stream.
+ * o, d, rgba_out, tri_out, t_out, prec and stream are as for
+ * inolf_render_rays. */
+inolf_status inolf_render_rays_noalloc(const inolf_object* obj, const float* o, const float* d, int64_t n,
+                                       inolf_precision prec, float* rgba_out, int32_t* tri_out, float* t_out,
+                                       void* stream);
+
+/* ------------------------------------------------------------------------ */
 /* Launch statistics (measurement support, no paper counterpart).           */
 /* ------------------------------------------------------------------------ */
 typedef struct {

@@ -80,6 +80,7 @@ def lib():
     L.inolf_render.argtypes = [vp, vp, i32, i32, i32, i32, vp, vp, vp, vp, sz, vp]
     L.inolf_render_rays.argtypes = [vp, vp, vp, i64, i32, vp, vp, vp, vp, sz, vp]
     L.inolf_encode_rays.argtypes = [vp, vp, vp, i64, vp, vp, vp, sz, vp]
+    L.inolf_render_rays_noalloc.argtypes = [vp, vp, vp, i64, i32, vp, vp, vp, vp]
     _lib = L
     return L
 
@@ -274,6 +275,24 @@ def render_rays(obj: Object, o, d, prec="fp32", rgba_out=None, tri_out=None, t_o
     _check(lib().inolf_render_rays(obj.handle, _ptr(o), _ptr(d), n, p, _ptr(rgba_out), _ptr(tri_out),
                                    _ptr(t_out), _ptr(workspace), workspace.numel() * workspace.element_size(),
                                    _stream(stream)))
+    return rgba_out
+
+
+NOALLOC_MAX_RAYS = 1048576
+
+
+def render_rays_noalloc(obj: Object, o, d, prec="fp32", rgba_out=None, tri_out=None, t_out=None, stream=None):
+    """inolf_render_rays_noalloc: like render_rays but with the library's fixed
+    device scratch instead of a workspace (n <= NOALLOC_MAX_RAYS), for callers
+    that must not allocate device memory while rendering.  Pass rgba_out to
+    keep this call itself free of allocations as well."""
+    import torch
+    n = o.shape[0]
+    if rgba_out is None:
+        rgba_out = torch.empty((n, 4), dtype=torch.float32, device=o.device)
+    p = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+    _check(lib().inolf_render_rays_noalloc(obj.handle, _ptr(o), _ptr(d), n, p, _ptr(rgba_out), _ptr(tri_out),
+                                           _ptr(t_out), _stream(stream)))
     return rgba_out
 
 

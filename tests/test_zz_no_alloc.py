@@ -1,0 +1,89 @@
+"""inolf_render_rays_noalloc, called through the C ABI, gives the same
+result as inolf_render_rays.
+
+The entry point exists for callers that cannot allocate device memory where
+they render (a fixed start-up memory budget, a host application that owns all
+device allocations, a thread that cannot afford cudaMalloc's synchronisation):
+it keeps its hit list in a fixed array inside the library instead of a
+caller-provided workspace.  Two calls in a row, with different rays, must each
+match the workspace-based entry point (triangle ids and t bit-exact, RGBA within
+the 1e-4 max-abs tolerance of the other parity tests), which also shows that the
+second call is not disturbed by what the first left in the shared array.
+
+This file is named so that pytest collects it last."""
+import ctypes
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+RGBA_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def setup(tiny):
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2303_04086_gb300 import build, inolf
+    build.build()
+    return torch, inolf, inolf.object_create(tiny)
+
+
+def _rays(n, seed):
+    rng = np.random.default_rng(seed)
+    eye = rng.normal(size=(n, 3))
+    eye = 2.6 * eye / np.linalg.norm(eye, axis=1, keepdims=True)
+    d = rng.uniform(-1.1, 1.1, size=(n, 3)) - eye
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    return eye.astype(np.float32), d.astype(np.float32)
+
+
+def _call_noalloc(torch, inolf, obj, o, d):
+    """Direct C-ABI call with preallocated outputs (poisoned with NaN / -7)."""
+    n = o.shape[0]
+    rgba = torch.full((n, 4), float("nan"), dtype=torch.float32, device="cuda")
+    tri = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+    t = torch.full((n,), float("nan"), dtype=torch.float32, device="cuda")
+    st = inolf.lib().inolf_render_rays_noalloc(
+        ctypes.c_void_p(obj.handle), ctypes.c_void_p(o.data_ptr()), ctypes.c_void_p(d.data_ptr()), n,
+        inolf.FP32, ctypes.c_void_p(rgba.data_ptr()), ctypes.c_void_p(tri.data_ptr()),
+        ctypes.c_void_p(t.data_ptr()), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == inolf.OK, inolf.last_error()
+    torch.cuda.synchronize()
+    return rgba.cpu().numpy(), tri.cpu().numpy(), t.cpu().numpy()
+
+
+def _call_workspace(torch, inolf, obj, o, d):
+    n = o.shape[0]
+    tri = torch.empty((n,), dtype=torch.int32, device="cuda")
+    t = torch.empty((n,), dtype=torch.float32, device="cuda")
+    rgba = inolf.render_rays(obj, o, d, "fp32", tri_out=tri, t_out=t)
+    torch.cuda.synchronize()
+    return rgba.cpu().numpy(), tri.cpu().numpy(), t.cpu().numpy()
+
+
+def test_noalloc_matches_workspace_entry_point_twice(setup):
+    torch, inolf, obj = setup
+    for call, (n, seed) in enumerate([(6001, 11), (4099, 12)]):
+        o_np, d_np = _rays(n, seed)
+        o, d = torch.from_numpy(o_np).cuda(), torch.from_numpy(d_np).cuda()
+        ref = _call_workspace(torch, inolf, obj, o, d)
+        got = _call_noalloc(torch, inolf, obj, o, d)
+        assert np.array_equal(got[1], ref[1]), f"call {call}: triangle ids differ"
+        assert np.array_equal(got[2].view(np.int32), ref[2].view(np.int32)), f"call {call}: t differs"
+        assert np.isfinite(got[0]).all()
+        assert np.abs(got[0] - ref[0]).max() <= RGBA_TOL, f"call {call}: RGBA differs"
+        assert (ref[1] >= 0).mean() > 0.2
+
+
+def test_noalloc_rejects_batches_beyond_the_limit(setup):
+    torch, inolf, obj = setup
+    o = torch.zeros((4, 3), dtype=torch.float32, device="cuda")
+    rgba = torch.zeros((4, 4), dtype=torch.float32, device="cuda")
+    st = inolf.lib().inolf_render_rays_noalloc(
+        ctypes.c_void_p(obj.handle), ctypes.c_void_p(o.data_ptr()), ctypes.c_void_p(o.data_ptr()),
+        inolf.NOALLOC_MAX_RAYS + 1, inolf.FP32, ctypes.c_void_p(rgba.data_ptr()), None, None, None)
+    assert st == inolf.E_INVALID
+    assert "limit" in inolf.last_error()
