@@ -185,6 +185,17 @@ inolf_status inolf_render_rays(const inolf_object* obj, const float* o, const fl
                                inolf_precision prec, float* rgba_out, int32_t* tri_out, float* t_out,
                                void* workspace, size_t workspace_bytes, void* stream);
 
+/* FP8 calibration (per-tensor activation scales): renders the given views
+ * with the FP32 path, records the largest |input| of each MLP layer and sets
+ * the object's activation scales to amax / 448 (the e4m3 maximum).  Weight
+ * scales are set from the weights at inolf_object_create.  Synchronises
+ * `stream`.  workspace as for inolf_render. */
+inolf_status inolf_calibrate_fp8(inolf_object* obj, const float* cams, int32_t n_views, int32_t W, int32_t H,
+                                 void* workspace, size_t workspace_bytes, void* stream);
+
+/* Current FP8 scales: act[3] of the inputs of layers 1-3, weight[3] of W1-W3. */
+inolf_status inolf_object_get_fp8_scales(const inolf_object* obj, float act[3], float weight[3]);
+
 /* Stage outputs for parity checks of the encoder: for each ray that hits,
  * slots_out[n][L][8] uint32 (corner (dx,dy,dz), x fastest) and
  * feat_out[n][L*F] FP32 interpolated features; rows of missing rays are left

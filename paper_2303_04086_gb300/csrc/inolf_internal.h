@@ -44,6 +44,8 @@ struct Object {
   // BF16 / FP8 operands for the tensor-core MLP (K-major rows, see mlp kernels)
   void* w_bf16 = nullptr;
   void* w_fp8 = nullptr;
+  int32_t tc_k1_bf16 = 0, tc_k1_fp8 = 0;
+  uint32_t tc_bytes_bf16 = 0, tc_bytes_fp8 = 0;
   float fp8_w_scale[3] = {0, 0, 0};
   float fp8_act_scale[3] = {0, 0, 0};
   size_t bytes = 0;
@@ -76,7 +78,7 @@ struct RayBatch {
 
 inolf_status launch_render(const Object& obj, const RayBatch& rays, inolf_precision prec, float* rgba,
                            int32_t* tri_out, float* t_out, uint32_t* slots_out, float* feat_out,
-                           void* workspace, size_t workspace_bytes, void* stream);
+                           void* workspace, size_t workspace_bytes, void* stream, bool amax = false);
 
 size_t workspace_bytes(int64_t n_rays);
 

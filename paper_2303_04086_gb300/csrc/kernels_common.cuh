@@ -36,6 +36,11 @@ struct Params {
   const float* w_f32;
   const void* w_bf16;
   const void* w_fp8;
+  int32_t tc_k1_bf16, tc_k1_fp8;      // padded input width of the tensor-core layer 1
+  uint32_t tc_bytes_bf16, tc_bytes_fp8;
+  const void* tc_w;                   // blob used by this launch
+  int32_t tc_k1;
+  uint32_t tc_wbytes;
   float fp8_w_scale[3];
   float fp8_act_scale[3];
   float shc[10];
@@ -46,7 +51,7 @@ struct Params {
   uint32_t* slots_out;
   float* feat_out;
   // workspace
-  uint32_t* counter;   // [0] hit count, [1] error flags
+  uint32_t* counter;   // [0] hit count, [1] error flags, [4..6] activation amax bits
   uint2* hits;         // (ray index in launch, t bits)
 };
 

@@ -1,20 +1,353 @@
-// Tensor-core MLP variants of the shade step (BF16 / FP8 e4m3 operands, FP32
-// accumulation in tensor memory).
+// Tensor-core shade kernel: the gather of k_shade_f32 followed by the MLP F_s
+// (Eq. 3) on the 5th-generation tensor cores, with BF16 or FP8-e4m3 operands
+// and FP32 accumulation in tensor memory.
+//
+// One CTA = 256 threads = two tiles of 128 hit rays.  Per tile pair:
+//   1. every thread gathers its ray's encoding (Sec. 4.1: 16 corner features
+//      of the PSH levels, trilinear) and SH view encoding, quantises it and
+//      writes its row of the A operand (K-major, 8x16-byte core matrices);
+//   2. one thread issues D1 = A1 W1^T (M = 128, N = 64) for both tiles into
+//      tensor memory (64 FP32 columns per tile) and commits to an mbarrier;
+//   3. each warp reads its 32 rows of D1 (tcgen05.ld), applies ReLU and the
+//      quantisation of the next layer's input and writes A2 in place of A1;
+//   4. D2 = A2 W2^T on the tensor cores;
+//   5. each thread reads its row of D2, applies ReLU, quantises, multiplies by
+//      W3 (4 x 64, CUDA cores: N = 4 is below the tensor-core minimum) and
+//      writes sigmoid(.) as RGBA.
+// The weights of all three layers are staged once per CTA into shared memory
+// by one bulk (TMA) copy from a blob laid out on the host in the operand
+// format.  Every mbarrier wait is bounded by a global-timer limit; on expiry
+// the CTA flags an error in the workspace header, frees its tensor memory and
+// returns.
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
 
 #include "inolf_internal.h"
 #include "kernels_common.cuh"
+#include "tc_ptx.cuh"
 
 namespace inolf {
 
+static constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s: MMAs of a tile take microseconds
+static constexpr int kTcThreads = 256;
+static constexpr uint32_t kTmemCols = 128;  // 2 tiles x 64 FP32 columns
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+__device__ __forceinline__ uint16_t pack_fp8(float a, float b) {
+  return (uint16_t)__nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+}
+__device__ __forceinline__ float round_bf16(float a) { return __bfloat162float(__float2bfloat16_rn(a)); }
+__device__ __forceinline__ float round_fp8(float a) {
+  __half_raw h = __nv_cvt_fp8_to_halfraw(__nv_cvt_float_to_fp8(a, __NV_SATFINITE, __NV_E4M3), __NV_E4M3);
+  return __half2float(__half(h));
+}
+
+// stores the pair (a, b) of input column k (even) of row `row`
+template <bool kFP8>
+__device__ __forceinline__ void store_pair(uint8_t* A, uint32_t row, uint32_t k, uint32_t chunks, float a, float b,
+                                           float inv_scale) {
+  if (kFP8) {
+    const uint32_t off = tc::core_off(row, k >> 4, chunks) + (k & 15u);
+    *reinterpret_cast<uint16_t*>(A + off) = pack_fp8(a * inv_scale, b * inv_scale);
+  } else {
+    const uint32_t off = tc::core_off(row, k >> 3, chunks) + (k & 7u) * 2u;
+    *reinterpret_cast<uint32_t*>(A + off) = pack_bf16(a, b);
+  }
+}
+
+template <bool kFP8>
+__global__ void __launch_bounds__(kTcThreads, 1) k_shade_tc(const __grid_constant__ Params p) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  constexpr uint32_t ES = kFP8 ? 1u : 2u;  // operand element bytes
+  constexpr uint32_t KSTEP_CHUNKS = 2;     // one MMA consumes 32 bytes of K per row
+  const uint32_t K1 = (uint32_t)p.tc_k1;
+  const uint32_t chunks1 = K1 * ES / 16u, chunks2 = 64u * ES / 16u;
+  const uint32_t wbytes = p.tc_wbytes;
+  uint8_t* sB1 = smem;
+  uint8_t* sB2 = smem + 64u * K1 * ES;
+  const float* sW3 = reinterpret_cast<const float*>(sB2 + 64u * 64u * ES);
+  uint8_t* sA = smem + ((wbytes + 1023u) & ~1023u);
+  constexpr uint32_t tile_bytes = 128u * 64u * ES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + 2 * tile_bytes);  // [0] weights, [1] MMA
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2);
+
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (tid == 0) {
+    tc::mbar_init(&bars[0], 1);
+    tc::mbar_init(&bars[1], 1);
+    tc::fence_mbar_init();
+  }
+  __syncthreads();
+  if (warp == 0) tc::tmem_alloc(tslot, kTmemCols);
+  if (tid == 0) {
+    tc::mbar_arrive_expect_tx(&bars[0], wbytes);
+    tc::bulk_g2s(smem, p.tc_w, wbytes, &bars[0]);
+  }
+  bool ok = tc::mbar_wait(&bars[0], 0, kWaitLimitNs);
+  tc::fence_before();
+  bool bad = __syncthreads_or(!ok);
+  tc::fence_after();
+  const uint32_t tmem = *tslot;
+
+  // precision-dependent scales (FP8: per-tensor, amax / 448)
+  const float inv_sx = kFP8 ? 1.0f / p.fp8_act_scale[0] : 1.0f;
+  const float mul1 = kFP8 ? p.fp8_act_scale[0] * p.fp8_w_scale[0] : 1.0f;
+  const float inv_sh1 = kFP8 ? 1.0f / p.fp8_act_scale[1] : 1.0f;
+  const float mul2 = kFP8 ? p.fp8_act_scale[1] * p.fp8_w_scale[1] : 1.0f;
+  const float sh2 = kFP8 ? p.fp8_act_scale[2] : 1.0f;
+  const float inv_sh2 = kFP8 ? 1.0f / p.fp8_act_scale[2] : 1.0f;
+  const uint32_t id = tc::idesc(128, 64, kFP8 ? 0u : 1u);
+  const uint32_t t = (uint32_t)tid >> 7, row = (uint32_t)tid & 127u;
+  uint8_t* A = sA + t * tile_bytes;
+  const uint32_t lane_base = ((uint32_t)(warp & 3) * 32u) << 16;
+  const int din = p.d_in;
+  uint32_t phase = 0;
+  const uint32_t total = *p.counter;
+
+  for (uint32_t base = blockIdx.x * kTcThreads; !bad && base < total; base += gridDim.x * kTcThreads) {
+    const uint32_t h = base + (uint32_t)tid;
+    const bool valid = h < total;
+    int64_t ray = 0;
+    // ---- 1. gather + encode -> A1 row ----
+    if (valid) {
+      const uint2 rec = p.hits[h];
+      ray = rec.x;
+      float o[3], d[3], x[3];
+      ray_of(p, ray, o, d);
+      hit_unit_coords(p, o, d, __uint_as_float(rec.y), x);
+      for (int l = 0; l < p.L; ++l) {
+        uint32_t slots[8];
+        float e0, e1;
+        encode_level(p.lv[l], p.fp16, x, slots, e0, e1);
+        store_pair<kFP8>(A, row, 2u * l, chunks1, e0, e1, inv_sx);
+      }
+      float sh[16];
+      sh16(p, d, sh);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) store_pair<kFP8>(A, row, 2u * p.L + 2u * i, chunks1, sh[2 * i], sh[2 * i + 1], inv_sx);
+      for (uint32_t k = (uint32_t)din; k < K1; k += 2) store_pair<kFP8>(A, row, k, chunks1, 0.f, 0.f, 1.f);
+    } else {
+      for (uint32_t c = 0; c < chunks1; ++c)
+        *reinterpret_cast<uint4*>(A + tc::core_off(row, c, chunks1)) = make_uint4(0, 0, 0, 0);
+    }
+    tc::fence_async_smem();
+    __syncthreads();
+    // ---- 2. D1 = A1 W1^T ----
+    if (tid == 0) {
+      tc::fence_after();
+      for (uint32_t tt = 0; tt < 2; ++tt) {
+        const uint32_t a0 = tc::smem_u32(sA + tt * tile_bytes), b0 = tc::smem_u32(sB1);
+        for (uint32_t s = 0; s < chunks1 / KSTEP_CHUNKS; ++s) {
+          const uint64_t ad = tc::desc_kmajor(a0 + s * 256u, 128u, chunks1 * 128u);
+          const uint64_t bd = tc::desc_kmajor(b0 + s * 256u, 128u, chunks1 * 128u);
+          if (kFP8) tc::mma_fp8(tmem + tt * 64u, ad, bd, id, s > 0);
+          else tc::mma_bf16(tmem + tt * 64u, ad, bd, id, s > 0);
+        }
+      }
+      tc::mma_commit(&bars[1]);
+    }
+    ok = tc::mbar_wait(&bars[1], phase, kWaitLimitNs);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) { bad = true; break; }
+    tc::fence_after();
+    // ---- 3. ReLU, quantise -> A2 row ----
+#pragma unroll 1
+    for (uint32_t c = 0; c < 4; ++c) {
+      float v[16];
+      tc::tmem_ld16(tmem + lane_base + t * 64u + c * 16u, v);
+      if (kFP8) {
+        uint32_t w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float a0 = fmaxf(v[4 * q + 0] * mul1, 0.f) * inv_sh1, a1 = fmaxf(v[4 * q + 1] * mul1, 0.f) * inv_sh1;
+          const float a2 = fmaxf(v[4 * q + 2] * mul1, 0.f) * inv_sh1, a3 = fmaxf(v[4 * q + 3] * mul1, 0.f) * inv_sh1;
+          w[q] = (uint32_t)pack_fp8(a0, a1) | ((uint32_t)pack_fp8(a2, a3) << 16);
+        }
+        *reinterpret_cast<uint4*>(A + tc::core_off(row, c, chunks2)) = make_uint4(w[0], w[1], w[2], w[3]);
+      } else {
+        uint32_t w[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) w[q] = pack_bf16(fmaxf(v[2 * q], 0.f), fmaxf(v[2 * q + 1], 0.f));
+        *reinterpret_cast<uint4*>(A + tc::core_off(row, 2 * c, chunks2)) = make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4*>(A + tc::core_off(row, 2 * c + 1, chunks2)) = make_uint4(w[4], w[5], w[6], w[7]);
+      }
+    }
+    tc::fence_before();
+    tc::fence_async_smem();
+    __syncthreads();
+    // ---- 4. D2 = A2 W2^T ----
+    if (tid == 0) {
+      tc::fence_after();
+      for (uint32_t tt = 0; tt < 2; ++tt) {
+        const uint32_t a0 = tc::smem_u32(sA + tt * tile_bytes), b0 = tc::smem_u32(sB2);
+        for (uint32_t s = 0; s < chunks2 / KSTEP_CHUNKS; ++s) {
+          const uint64_t ad = tc::desc_kmajor(a0 + s * 256u, 128u, chunks2 * 128u);
+          const uint64_t bd = tc::desc_kmajor(b0 + s * 256u, 128u, chunks2 * 128u);
+          if (kFP8) tc::mma_fp8(tmem + tt * 64u, ad, bd, id, s > 0);
+          else tc::mma_bf16(tmem + tt * 64u, ad, bd, id, s > 0);
+        }
+      }
+      tc::mma_commit(&bars[1]);
+    }
+    ok = tc::mbar_wait(&bars[1], phase, kWaitLimitNs);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) { bad = true; break; }
+    tc::fence_after();
+    // ---- 5. ReLU, quantise, W3, sigmoid ----
+    float out0 = 0.f, out1 = 0.f, out2 = 0.f, out3 = 0.f;
+#pragma unroll 1
+    for (uint32_t c = 0; c < 4; ++c) {
+      float v[16];
+      tc::tmem_ld16(tmem + lane_base + t * 64u + c * 16u, v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        float a = fmaxf(v[j] * mul2, 0.f);
+        a = kFP8 ? round_fp8(a * inv_sh2) * sh2 : round_bf16(a);
+        const uint32_t col = c * 16u + (uint32_t)j;
+        out0 += sW3[0 * 64 + col] * a;
+        out1 += sW3[1 * 64 + col] * a;
+        out2 += sW3[2 * 64 + col] * a;
+        out3 += sW3[3 * 64 + col] * a;
+      }
+    }
+    if (valid) p.rgba[p.ray_base + ray] = make_float4(sigmoidf_(out0), sigmoidf_(out1), sigmoidf_(out2), sigmoidf_(out3));
+    tc::fence_before();
+    __syncthreads();
+  }
+  if (bad) {
+    if (tid == 0) atomicOr(p.counter + 1, 4u);
+    tc::mbar_wait(&bars[1], phase, kWaitLimitNs);  // let MMAs still in flight finish
+  }
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after();
+    tc::tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static uint32_t round_up(uint32_t v, uint32_t m) { return (v + m - 1) / m * m; }
+
+// Weight blob in the operand layout (K-major core matrices, rows = output
+// neurons): [W1: 64 x K1][W2: 64 x 64][W3: 4 x 64 FP32 of the quantised values]
 inolf_status prepare_tc_weights(Object& obj, const float* w1, const float* w2, const float* w3, void* stream) {
-  (void)obj; (void)w1; (void)w2; (void)w3; (void)stream;
+  const int din = obj.d_in, H = INOLF_HIDDEN, O = INOLF_OUT;
+  cudaStream_t st = (cudaStream_t)stream;
+  auto amax = [](const float* w, size_t n) {
+    float m = 0.f;
+    for (size_t i = 0; i < n; ++i) m = std::max(m, std::fabs(w[i]));
+    return m;
+  };
+  // ---- BF16 ----
+  {
+    const uint32_t K1 = round_up((uint32_t)din, 16), ch1 = K1 / 8, ch2 = 8;
+    std::vector<uint8_t> blob((size_t)H * K1 * 2 + (size_t)H * H * 2 + (size_t)O * H * 4, 0);
+    for (int n = 0; n < H; ++n)
+      for (int k = 0; k < din; ++k) {
+        __nv_bfloat16 v = __float2bfloat16_rn(w1[(size_t)n * din + k]);
+        std::memcpy(&blob[tc::core_off(n, k / 8, ch1) + (k % 8) * 2], &v, 2);
+      }
+    uint8_t* b2 = blob.data() + (size_t)H * K1 * 2;
+    for (int n = 0; n < H; ++n)
+      for (int k = 0; k < H; ++k) {
+        __nv_bfloat16 v = __float2bfloat16_rn(w2[(size_t)n * H + k]);
+        std::memcpy(&b2[tc::core_off(n, k / 8, ch2) + (k % 8) * 2], &v, 2);
+      }
+    float* b3 = reinterpret_cast<float*>(b2 + (size_t)H * H * 2);
+    for (int i = 0; i < O * H; ++i) b3[i] = __bfloat162float(__float2bfloat16_rn(w3[i]));
+    if (cudaMalloc(&obj.w_bf16, blob.size()) != cudaSuccess) return fail(INOLF_E_OOM, "cudaMalloc bf16 weights");
+    if (cudaMemcpyAsync(obj.w_bf16, blob.data(), blob.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return fail(INOLF_E_CUDA, "upload bf16 weights");
+    obj.tc_k1_bf16 = (int32_t)K1;
+    obj.tc_bytes_bf16 = (uint32_t)blob.size();
+    obj.bytes += blob.size();
+  }
+  // ---- FP8 e4m3, per-tensor scales amax / 448 ----
+  {
+    const uint32_t K1 = round_up((uint32_t)din, 32), ch1 = K1 / 16, ch2 = 4;
+    const float s1 = amax(w1, (size_t)H * din), s2 = amax(w2, (size_t)H * H), s3 = amax(w3, (size_t)O * H);
+    obj.fp8_w_scale[0] = s1 > 0 ? s1 / 448.0f : 1.0f;
+    obj.fp8_w_scale[1] = s2 > 0 ? s2 / 448.0f : 1.0f;
+    obj.fp8_w_scale[2] = s3 > 0 ? s3 / 448.0f : 1.0f;
+    auto q = [](float v, float s) { return (uint8_t)__nv_cvt_float_to_fp8(v / s, __NV_SATFINITE, __NV_E4M3); };
+    auto dq = [](uint8_t b) {
+      __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)b, __NV_E4M3);
+      return __half2float(__half(h));
+    };
+    std::vector<uint8_t> blob((size_t)H * K1 + (size_t)H * H + (size_t)O * H * 4, 0);
+    for (int n = 0; n < H; ++n)
+      for (int k = 0; k < din; ++k)
+        blob[tc::core_off(n, k / 16, ch1) + (k % 16)] = q(w1[(size_t)n * din + k], obj.fp8_w_scale[0]);
+    uint8_t* b2 = blob.data() + (size_t)H * K1;
+    for (int n = 0; n < H; ++n)
+      for (int k = 0; k < H; ++k) b2[tc::core_off(n, k / 16, ch2) + (k % 16)] = q(w2[(size_t)n * H + k], obj.fp8_w_scale[1]);
+    float* b3 = reinterpret_cast<float*>(b2 + (size_t)H * H);
+    for (int i = 0; i < O * H; ++i) b3[i] = dq(q(w3[i], obj.fp8_w_scale[2])) * obj.fp8_w_scale[2];
+    if (cudaMalloc(&obj.w_fp8, blob.size()) != cudaSuccess) return fail(INOLF_E_OOM, "cudaMalloc fp8 weights");
+    if (cudaMemcpyAsync(obj.w_fp8, blob.data(), blob.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return fail(INOLF_E_CUDA, "upload fp8 weights");
+    obj.tc_k1_fp8 = (int32_t)K1;
+    obj.tc_bytes_fp8 = (uint32_t)blob.size();
+    obj.bytes += blob.size();
+  }
   return INOLF_OK;
 }
 
-inolf_status launch_shade_tc(const Params& p, inolf_precision prec, cudaStream_t st) {
-  (void)p; (void)prec; (void)st;
-  return fail(INOLF_E_UNSUPPORTED, "tensor-core MLP not built yet");
+static size_t tc_smem_bytes(uint32_t wbytes, bool fp8) {
+  const size_t tile = 128u * 64u * (fp8 ? 1u : 2u);
+  return ((wbytes + 1023u) & ~1023u) + 2 * tile + 64;
+}
+
+inolf_status launch_shade_tc(const Params& p_in, inolf_precision prec, cudaStream_t st) {
+  const bool fp8 = prec == INOLF_FP8;
+  Params p = p_in;
+  p.tc_w = fp8 ? p.w_fp8 : p.w_bf16;
+  p.tc_k1 = fp8 ? p.tc_k1_fp8 : p.tc_k1_bf16;
+  p.tc_wbytes = fp8 ? p.tc_bytes_fp8 : p.tc_bytes_bf16;
+  if (!p.tc_w || p.tc_wbytes == 0 || (p.tc_wbytes & 15u)) return fail(INOLF_E_INVALID, "tensor-core weights missing");
+  const size_t smem = tc_smem_bytes(p.tc_wbytes, fp8);
+  static int grid_bf16 = 0, grid_fp8 = 0;
+  static std::once_flag once;
+  std::call_once(once, [&] {
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t sb = tc_smem_bytes(16384, false), sf = tc_smem_bytes(16384, true);
+    cudaFuncSetAttribute(k_shade_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
+    cudaFuncSetAttribute(k_shade_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf);
+    int ob = 1, of = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ob, k_shade_tc<false>, kTcThreads, sb);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&of, k_shade_tc<true>, kTcThreads, sf);
+    // each CTA holds kTmemCols of the SM's 512 tensor-memory columns
+    const int tmem_cap = 512 / (int)kTmemCols;
+    grid_bf16 = sms * std::max(1, std::min(ob, tmem_cap));
+    grid_fp8 = sms * std::max(1, std::min(of, tmem_cap));
+  });
+  if (smem > (size_t)tc_smem_bytes(16384, fp8)) return fail(INOLF_E_INVALID, "tensor-core weights too large");
+  const int grid = fp8 ? grid_fp8 : grid_bf16;
+  {
+    LaunchTimer lt(fp8 ? "k_shade_tc_fp8" : "k_shade_tc_bf16", st);
+    if (fp8) k_shade_tc<true><<<grid, kTcThreads, smem, st>>>(p);
+    else k_shade_tc<false><<<grid, kTcThreads, smem, st>>>(p);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(INOLF_E_CUDA, std::string("k_shade_tc: ") + cudaGetErrorString(e));
+  return INOLF_OK;
 }
 
 }  // namespace inolf

@@ -22,6 +22,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <mutex>
 #include <vector>
 
@@ -87,13 +88,23 @@ __global__ void __launch_bounds__(256) k_trace(const __grid_constant__ Params p,
 }
 
 // ---------------------------------------------------------------------------
-// k_shade (FP32 SIMT MLP) and k_encode (stage outputs for parity checks)
+// k_shade (FP32 SIMT MLP), k_encode (stage outputs for parity checks) and
+// the FP8 calibration pass (FP32 shade that records the largest |input| of
+// each MLP layer instead of writing RGBA)
 // ---------------------------------------------------------------------------
-template <bool kEncodeOnly>
+enum ShadeMode { kShade = 0, kEncode = 1, kAmax = 2 };
+
+__device__ __forceinline__ void atomic_max_nonneg(uint32_t* addr, float v) {
+  // non-negative floats order like their bit patterns
+  atomicMax(addr, __float_as_uint(v));
+}
+
+template <int kMode>
 __global__ void __launch_bounds__(128) k_shade_f32(const __grid_constant__ Params p) {
+  constexpr bool kEncodeOnly = kMode == kEncode;
   extern __shared__ float4 smem4[];
-  float* sw = reinterpret_cast<float*>(smem4);
   const int din = p.d_in;
+  float amax_x = 0.f, amax_h1 = 0.f, amax_h2 = 0.f;
   const int nw = din * 64 + 64 * 64 + 64 * 4;
   if (!kEncodeOnly) {
     for (int k = threadIdx.x; k < nw / 4; k += blockDim.x)
@@ -128,6 +139,7 @@ __global__ void __launch_bounds__(128) k_shade_f32(const __grid_constant__ Param
         p.feat_out[(g * p.L + l) * 2 + 0] = e0;
         p.feat_out[(g * p.L + l) * 2 + 1] = e1;
       } else {
+        if (kMode == kAmax) amax_x = fmaxf(amax_x, fmaxf(fabsf(e0), fabsf(e1)));
         const float4* r0 = W1T + (2 * l) * 16;
         const float4* r1 = r0 + 16;
 #pragma unroll
@@ -147,6 +159,7 @@ __global__ void __launch_bounds__(128) k_shade_f32(const __grid_constant__ Param
     for (int k = 0; k < 16; ++k) {
       const float4* r = W1T + (2 * p.L + k) * 16;
       const float s = sh[k];
+      if (kMode == kAmax) amax_x = fmaxf(amax_x, fabsf(s));
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
         const float4 a = r[q];
@@ -157,7 +170,10 @@ __global__ void __launch_bounds__(128) k_shade_f32(const __grid_constant__ Param
       }
     }
 #pragma unroll
-    for (int j = 0; j < 64; ++j) h1[j] = fmaxf(h1[j], 0.0f);
+    for (int j = 0; j < 64; ++j) {
+      h1[j] = fmaxf(h1[j], 0.0f);
+      if (kMode == kAmax) amax_h1 = fmaxf(amax_h1, h1[j]);
+    }
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll 2
     for (int j = 0; j < 64; ++j) {
@@ -172,13 +188,28 @@ __global__ void __launch_bounds__(128) k_shade_f32(const __grid_constant__ Param
         z += a.w * h1[4 * q + 3];
       }
       z = fmaxf(z, 0.0f);
+      if (kMode == kAmax) amax_h2 = fmaxf(amax_h2, z);
       const float4 w3 = W3T[j];
       acc.x += w3.x * z;
       acc.y += w3.y * z;
       acc.z += w3.z * z;
       acc.w += w3.w * z;
     }
-    p.rgba[p.ray_base + ray] = make_float4(sigmoidf_(acc.x), sigmoidf_(acc.y), sigmoidf_(acc.z), sigmoidf_(acc.w));
+    if (kMode == kShade)
+      p.rgba[p.ray_base + ray] = make_float4(sigmoidf_(acc.x), sigmoidf_(acc.y), sigmoidf_(acc.z), sigmoidf_(acc.w));
+  }
+  if (kMode == kAmax) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      amax_x = fmaxf(amax_x, __shfl_xor_sync(0xffffffffu, amax_x, o));
+      amax_h1 = fmaxf(amax_h1, __shfl_xor_sync(0xffffffffu, amax_h1, o));
+      amax_h2 = fmaxf(amax_h2, __shfl_xor_sync(0xffffffffu, amax_h2, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomic_max_nonneg(p.counter + 4, amax_x);
+      atomic_max_nonneg(p.counter + 5, amax_h1);
+      atomic_max_nonneg(p.counter + 6, amax_h2);
+    }
   }
 }
 
@@ -188,6 +219,7 @@ __global__ void __launch_bounds__(128) k_shade_f32(const __grid_constant__ Param
 static constexpr size_t kWsHeader = 256;
 
 size_t workspace_bytes(int64_t n_rays) { return kWsHeader + (size_t)std::max<int64_t>(n_rays, 1) * 8; }
+static size_t workspace_bytes_min() { return workspace_bytes(1); }
 
 static int sm_count() {
   static int n = 0;
@@ -213,6 +245,10 @@ static void fill_common(const Object& obj, Params& p) {
   p.w_f32 = obj.w_f32;
   p.w_bf16 = obj.w_bf16;
   p.w_fp8 = obj.w_fp8;
+  p.tc_k1_bf16 = obj.tc_k1_bf16;
+  p.tc_k1_fp8 = obj.tc_k1_fp8;
+  p.tc_bytes_bf16 = obj.tc_bytes_bf16;
+  p.tc_bytes_fp8 = obj.tc_bytes_fp8;
   for (int k = 0; k < 3; ++k) {
     p.fp8_w_scale[k] = obj.fp8_w_scale[k];
     p.fp8_act_scale[k] = obj.fp8_act_scale[k];
@@ -230,7 +266,7 @@ inolf_status launch_shade_tc(const Params& p, inolf_precision prec, cudaStream_t
 
 inolf_status launch_render(const Object& obj, const RayBatch& rays, inolf_precision prec, float* rgba,
                            int32_t* tri_out, float* t_out, uint32_t* slots_out, float* feat_out,
-                           void* workspace, size_t ws_bytes, void* stream) {
+                           void* workspace, size_t ws_bytes, void* stream, bool amax) {
   cudaStream_t st = (cudaStream_t)stream;
   if (!workspace || ws_bytes < workspace_bytes(1) || ((uintptr_t)workspace & 15))
     return fail(INOLF_E_INVALID, "render: workspace missing, too small or not 16-byte aligned");
@@ -257,7 +293,8 @@ inolf_status launch_render(const Object& obj, const RayBatch& rays, inolf_precis
   const size_t smem_f32 = (size_t)(obj.d_in * 64 + 64 * 64 + 64 * 4) * sizeof(float);
   static std::once_flag attr_once;
   std::call_once(attr_once, [&] {
-    cudaFuncSetAttribute(k_shade_f32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    cudaFuncSetAttribute(k_shade_f32<kShade>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    cudaFuncSetAttribute(k_shade_f32<kAmax>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
   });
   const int shade_grid = sm_count() * 8;
 
@@ -272,13 +309,18 @@ inolf_status launch_render(const Object& obj, const RayBatch& rays, inolf_precis
     if (s != INOLF_OK) return s;
     if (encode) {
       LaunchTimer lt("k_encode", st);
-      k_shade_f32<true><<<shade_grid, 128, 0, st>>>(p);
+      k_shade_f32<kEncode><<<shade_grid, 128, 0, st>>>(p);
       return check_launch("k_encode");
+    }
+    if (amax) {
+      LaunchTimer lt("k_shade_amax", st);
+      k_shade_f32<kAmax><<<shade_grid, 128, smem_f32, st>>>(p);
+      return check_launch("k_shade_amax");
     }
     if (prec == INOLF_FP32) {
       {
         LaunchTimer lt("k_shade_f32", st);
-        k_shade_f32<false><<<shade_grid, 128, smem_f32, st>>>(p);
+        k_shade_f32<kShade><<<shade_grid, 128, smem_f32, st>>>(p);
       }
       return check_launch("k_shade_f32");
     }
@@ -355,6 +397,45 @@ extern "C" inolf_status inolf_render_rays(const inolf_object* obj, const float* 
   rb.n = n;
   return launch_render(obj->o, rb, prec, rgba_out, tri_out, t_out, nullptr, nullptr, workspace, workspace_bytes,
                        stream);
+}
+
+extern "C" inolf_status inolf_calibrate_fp8(inolf_object* obj, const float* cams, int32_t n_views, int32_t W,
+                                            int32_t H, void* workspace, size_t workspace_bytes, void* stream) {
+  clear_error();
+  if (!obj || !cams || n_views <= 0 || W <= 0 || H <= 0 || !workspace || workspace_bytes < workspace_bytes_min())
+    return fail(INOLF_E_INVALID, "inolf_calibrate_fp8: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  uint32_t* hdr = (uint32_t*)workspace;
+  if (cudaMemsetAsync(hdr, 0, 32, st) != cudaSuccess) return fail(INOLF_E_CUDA, "cudaMemsetAsync failed");
+  RayBatch rb{};
+  rb.mode = 0;
+  rb.cams = cams;
+  rb.n_views = n_views;
+  rb.W = W;
+  rb.H = H;
+  rb.n = (int64_t)n_views * W * H;
+  inolf_status s = launch_render(obj->o, rb, INOLF_FP32, nullptr, nullptr, nullptr, nullptr, nullptr, workspace,
+                                 workspace_bytes, stream, true);
+  if (s != INOLF_OK) return s;
+  uint32_t bits[3];
+  if (cudaMemcpyAsync(bits, hdr + 4, sizeof(bits), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return fail(INOLF_E_CUDA, "inolf_calibrate_fp8: readback failed");
+  for (int k = 0; k < 3; ++k) {
+    float a;
+    std::memcpy(&a, &bits[k], 4);
+    obj->o.fp8_act_scale[k] = a > 0 ? a / 448.0f : 1.0f;
+  }
+  return INOLF_OK;
+}
+
+extern "C" inolf_status inolf_object_get_fp8_scales(const inolf_object* obj, float act[3], float weight[3]) {
+  if (!obj || !act || !weight) return fail(INOLF_E_INVALID, "inolf_object_get_fp8_scales: NULL argument");
+  for (int k = 0; k < 3; ++k) {
+    act[k] = obj->o.fp8_act_scale[k];
+    weight[k] = obj->o.fp8_w_scale[k];
+  }
+  return INOLF_OK;
 }
 
 extern "C" inolf_status inolf_encode_rays(const inolf_object* obj, const float* o, const float* d, int64_t n,

@@ -81,6 +81,8 @@ def lib():
     L.inolf_render_rays.argtypes = [vp, vp, vp, i64, i32, vp, vp, vp, vp, sz, vp]
     L.inolf_encode_rays.argtypes = [vp, vp, vp, i64, vp, vp, vp, sz, vp]
     L.inolf_render_rays_noalloc.argtypes = [vp, vp, vp, i64, i32, vp, vp, vp, vp]
+    L.inolf_calibrate_fp8.argtypes = [vp, vp, i32, i32, i32, vp, sz, vp]
+    L.inolf_object_get_fp8_scales.argtypes = [vp, vp, vp]
     _lib = L
     return L
 
@@ -169,6 +171,13 @@ class Object:
     def set_fp8_scales(self, scales: Sequence[float]):
         s = np.ascontiguousarray(scales, np.float32)
         _check(lib().inolf_object_set_fp8_scales(self._h, ctypes.c_void_p(s.ctypes.data)))
+
+    def fp8_scales(self):
+        """(activation scales of layers 1-3, weight scales of W1-W3)."""
+        a = np.zeros(3, np.float32)
+        w = np.zeros(3, np.float32)
+        _check(lib().inolf_object_get_fp8_scales(self._h, a.ctypes.data, w.ctypes.data))
+        return a, w
 
     def read_params(self):
         tables = [np.empty((self.table_rows(l), 2), np.float32) for l in range(self.L)]
@@ -276,6 +285,17 @@ def render_rays(obj: Object, o, d, prec="fp32", rgba_out=None, tri_out=None, t_o
                                    _ptr(t_out), _ptr(workspace), workspace.numel() * workspace.element_size(),
                                    _stream(stream)))
     return rgba_out
+
+
+def calibrate_fp8(obj: Object, cams: np.ndarray, W: int, H: int, workspace=None, stream=None):
+    """Per-tensor FP8 activation scales (amax / 448) from the FP32 path on the
+    given views; frozen in the object until the next calibration."""
+    cams = np.ascontiguousarray(cams, np.float32).reshape(-1, 13)
+    if workspace is None:
+        workspace = _workspace(len(cams) * W * H, "cuda")
+    _check(lib().inolf_calibrate_fp8(obj.handle, cams.ctypes.data, len(cams), W, H, _ptr(workspace),
+                                     workspace.numel() * workspace.element_size(), _stream(stream)))
+    return obj.fp8_scales()
 
 
 NOALLOC_MAX_RAYS = 1048576

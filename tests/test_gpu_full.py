@@ -1,0 +1,104 @@
+"""Full-size parity: the benchmark's launch (one inolf_render of 64 ring views
+at 3840x2160 of the 200 000-triangle, 16-level scene) checked against the FP64
+oracle on sampled pixels -- triangle ids and t bit-exact (also against brute
+force), Eq. 1 slots bit-exact on all 16 levels, RGBA within 1e-4."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2303_04086_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+W, H, NV = 3840, 2160, 64
+SLOT_SLACK = 1.25   # as in bench.py
+RGBA_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def full():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2303_04086_gb300 import build, inolf
+    build.build()
+    scene = synth.full_scene(seed=0)
+    hashes = inolf.build_hashes(scene, slot_slack=SLOT_SLACK)
+    obj = inolf.object_create(scene, hashes)
+    cams = synth.ring_cameras(NV, 2.5)
+    return torch, inolf, scene, obj, cams
+
+
+@pytest.fixture(scope="module")
+def rendered(full):
+    torch, inolf, scene, obj, cams = full
+    tri = torch.empty((NV, H, W), dtype=torch.int32, device="cuda")
+    t = torch.empty((NV, H, W), dtype=torch.float32, device="cuda")
+    rgba = inolf.render(obj, cams, W, H, "fp32", tri_out=tri, t_out=t)
+    torch.cuda.synchronize()
+    return rgba, tri, t
+
+
+@pytest.fixture(scope="module")
+def full_oracle(full):
+    return oracle.Oracle(full[2])
+
+
+def _sample(view, n, seed):
+    rng = np.random.default_rng(seed)
+    pix = rng.choice(W * H, n, replace=False)
+    # plus a 48 x 48 patch across the silhouette on the right of the image
+    j0, i0 = H // 2 - 24, int(W / 2 + 0.4 * H) - 24
+    jj, ii = np.meshgrid(np.arange(j0, j0 + 48), np.arange(i0, i0 + 48), indexing="ij")
+    return np.unique(np.concatenate([pix, (jj * W + ii).ravel()])).astype(np.int64)
+
+
+@pytest.mark.parametrize("view", [0, 17, 40, 63])
+def test_full_views_sampled(full, rendered, full_oracle, view):
+    torch, inolf, scene, obj, cams = full
+    rgba, tri, t = rendered
+    pix = _sample(view, 3000, view)
+    ref = full_oracle.render_pixels(cams[view], W, H, pix)
+    assert ref["missing"] == 0
+    pt = torch.from_numpy(pix).cuda()
+    g_tri = tri[view].reshape(-1)[pt].cpu().numpy()
+    g_t = t[view].reshape(-1)[pt].cpu().numpy()
+    g_rgba = rgba[view].reshape(-1, 4)[pt].cpu().numpy()
+    assert np.array_equal(g_tri, ref["tri"])
+    assert np.array_equal(g_t.view(np.int32), ref["t"].view(np.int32))
+    assert np.abs(g_rgba - ref["rgba"]).max() <= RGBA_TOL
+    hit = ref["tri"] >= 0
+    assert 0.2 < hit.mean() < 0.9 and np.all(g_rgba[~hit] == 0)
+
+
+def test_full_hits_against_brute_force(full, rendered):
+    torch, inolf, scene, obj, cams = full
+    _, tri, t = rendered
+    pix = _sample(5, 200, 5)
+    o, d = oracle.raygen(cams[5], W, H, pix)
+    bt, btt, _ = oracle.hit_brute(scene.vertices, scene.triangles, o, d)
+    pt = torch.from_numpy(pix).cuda()
+    assert np.array_equal(tri[5].reshape(-1)[pt].cpu().numpy(), bt)
+    assert np.array_equal(t[5].reshape(-1)[pt].cpu().numpy().view(np.int32), btt.view(np.int32))
+
+
+def test_full_slots_all_levels(full, full_oracle):
+    torch, inolf, scene, obj, cams = full
+    pix = _sample(9, 2000, 9)
+    o, d = oracle.raygen(cams[9], W, H, pix)
+    r = full_oracle.render_rays(o, d, with_E=True)
+    hit = np.nonzero(r["tri"] >= 0)[0]
+    o, d = o[hit], d[hit]
+    n, L = len(o), scene.n_levels
+    slots = torch.zeros((n, L, 8), dtype=torch.int32, device="cuda")
+    feats = torch.zeros((n, 2 * L), dtype=torch.float32, device="cuda")
+    inolf.encode_rays(obj, torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda(), slots, feats)
+    slots = slots.cpu().numpy().view(np.uint32).astype(np.int64)
+    idx, _ = full_oracle.corners(o, d, r["t"][hit])
+    assert np.all(idx >= 0)
+    for l in range(L):
+        h = obj.hashes[l]
+        coords = synth.unpack_keys(scene.keys[l][idx[:, l, :].ravel()])
+        expect = oracle.psh_slots(h.phi, h.m, h.r, coords).reshape(n, 8)
+        assert np.array_equal(slots[:, l, :], expect), l
+    assert np.abs(feats.cpu().numpy() - r["E"][hit, :2 * L]).max() <= 1e-6
