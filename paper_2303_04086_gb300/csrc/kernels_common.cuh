@@ -286,35 +286,51 @@ __device__ __forceinline__ void cell_of(const LevelDev& lv, const float x[3], in
   }
 }
 
-// Eq. 1 slots of the 8 corners c + (dx, dy, dz) (x fastest) and the
-// trilinearly interpolated F = 2 features.
-__device__ __forceinline__ void encode_level(const LevelDev& lv, int fp16, const float x[3], uint32_t slots[8],
-                                             float& e0, float& e1) {
-  int32_t c[3];
+// Per-level state between the two dependent loads of the gather: the 8 Phi
+// entries (in flight), the wrapped h0 coordinates and the cell fractions.
+struct LevelFetch {
+  uint32_t ph[8];
+  int32_t h0[3], h0n[3];
   float f[3];
-  cell_of(lv, x, c, f);
+};
+
+// Cell of the level, h0 / h1 coordinates of the 8 corners c + (dx, dy, dz)
+// (x fastest), and the loads of their Phi entries (Eq. 1, first half).
+__device__ __forceinline__ void fetch_phi(const LevelDev& lv, const float x[3], LevelFetch& s) {
+  int32_t c[3];
+  cell_of(lv, x, c, s.f);
   const int32_t m = lv.m, r = lv.r;
-  int32_t h0[3], h0n[3], h1[3], h1n[3];
+  int32_t qx[2], qy[2], qz[2];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    h0[k] = mod_small(c[k], m, lv.inv_m);
-    h0n[k] = h0[k] + 1 == m ? 0 : h0[k] + 1;
-    h1[k] = mod_small(c[k], r, lv.inv_r);
-    h1n[k] = h1[k] + 1 == r ? 0 : h1[k] + 1;
+    s.h0[k] = mod_small(c[k], m, lv.inv_m);
+    s.h0n[k] = s.h0[k] + 1 == m ? 0 : s.h0[k] + 1;
   }
-  uint32_t ph[8];
+  {
+    const int32_t a = mod_small(c[0], r, lv.inv_r);
+    qx[0] = a;
+    qx[1] = a + 1 == r ? 0 : a + 1;
+    const int32_t b = mod_small(c[1], r, lv.inv_r);
+    qy[0] = b * r;
+    qy[1] = (b + 1 == r ? 0 : b + 1) * r;
+    const int32_t z = mod_small(c[2], r, lv.inv_r);
+    qz[0] = z * r * r;
+    qz[1] = (z + 1 == r ? 0 : z + 1) * r * r;
+  }
+#pragma unroll
+  for (int cc = 0; cc < 8; ++cc) s.ph[cc] = __ldg(lv.phi + (qx[cc & 1] + qy[(cc >> 1) & 1] + qz[cc >> 2]));
+}
+
+// Second half of Eq. 1: slots (h0 + phi) mod m of the 8 corners, the feature
+// gather and the trilinear interpolation of the F = 2 features.
+__device__ __forceinline__ void finish_level(const LevelDev& lv, int fp16, const LevelFetch& s, uint32_t slots[8],
+                                             float& e0, float& e1) {
+  const int32_t m = lv.m;
 #pragma unroll
   for (int cc = 0; cc < 8; ++cc) {
-    const int32_t qx = (cc & 1) ? h1n[0] : h1[0];
-    const int32_t qy = (cc & 2) ? h1n[1] : h1[1];
-    const int32_t qz = (cc & 4) ? h1n[2] : h1[2];
-    ph[cc] = __ldg(lv.phi + (qx + r * (qy + r * qz)));
-  }
-#pragma unroll
-  for (int cc = 0; cc < 8; ++cc) {
-    int32_t sx = ((cc & 1) ? h0n[0] : h0[0]) + (int32_t)(ph[cc] & 1023u);
-    int32_t sy = ((cc & 2) ? h0n[1] : h0[1]) + (int32_t)((ph[cc] >> 10) & 1023u);
-    int32_t sz = ((cc & 4) ? h0n[2] : h0[2]) + (int32_t)((ph[cc] >> 20) & 1023u);
+    int32_t sx = ((cc & 1) ? s.h0n[0] : s.h0[0]) + (int32_t)(s.ph[cc] & 1023u);
+    int32_t sy = ((cc & 2) ? s.h0n[1] : s.h0[1]) + (int32_t)((s.ph[cc] >> 10) & 1023u);
+    int32_t sz = ((cc & 4) ? s.h0n[2] : s.h0[2]) + (int32_t)((s.ph[cc] >> 20) & 1023u);
     sx -= sx >= m ? m : 0;
     sy -= sy >= m ? m : 0;
     sz -= sz >= m ? m : 0;
@@ -330,6 +346,7 @@ __device__ __forceinline__ void encode_level(const LevelDev& lv, int fp16, const
 #pragma unroll
     for (int cc = 0; cc < 8; ++cc) v[cc] = __ldg(tb + slots[cc]);
   }
+  const float* f = s.f;
   const float gx = 1.0f - f[0], gy = 1.0f - f[1], gz = 1.0f - f[2];
   e0 = 0.0f;
   e1 = 0.0f;
@@ -338,6 +355,32 @@ __device__ __forceinline__ void encode_level(const LevelDev& lv, int fp16, const
     const float w = ((cc & 1) ? f[0] : gx) * ((cc & 2) ? f[1] : gy) * ((cc & 4) ? f[2] : gz);
     e0 += w * v[cc].x;
     e1 += w * v[cc].y;
+  }
+}
+
+// Eq. 1 slots of the 8 corners and the interpolated features of one level.
+__device__ __forceinline__ void encode_level(const LevelDev& lv, int fp16, const float x[3], uint32_t slots[8],
+                                             float& e0, float& e1) {
+  LevelFetch s;
+  fetch_phi(lv, x, s);
+  finish_level(lv, fp16, s, slots, e0, e1);
+}
+
+// All levels of one hit point, with the Phi loads of level l + 1 issued
+// before the feature loads of level l are consumed (two dependent load
+// rounds per level overlap across levels).  emit(l, e0, e1, slots) receives
+// each level's result in order.
+template <class Emit>
+__device__ __forceinline__ void encode_all_levels(const Params& p, const float x[3], Emit&& emit) {
+  LevelFetch cur, nxt;
+  fetch_phi(p.lv[0], x, cur);
+  for (int l = 0; l < p.L; ++l) {
+    if (l + 1 < p.L) fetch_phi(p.lv[l + 1], x, nxt);
+    uint32_t slots[8];
+    float e0, e1;
+    finish_level(p.lv[l], p.fp16, cur, slots, e0, e1);
+    emit(l, e0, e1, slots);
+    cur = nxt;
   }
 }
 

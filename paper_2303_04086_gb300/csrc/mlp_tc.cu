@@ -25,6 +25,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -67,7 +68,7 @@ __device__ __forceinline__ void store_pair(uint8_t* A, uint32_t row, uint32_t k,
 }
 
 template <bool kFP8>
-__global__ void __launch_bounds__(kTcThreads, 1) k_shade_tc(const __grid_constant__ Params p) {
+__global__ void __launch_bounds__(kTcThreads, 4) k_shade_tc(const __grid_constant__ Params p) {
   extern __shared__ __align__(1024) uint8_t smem[];
   constexpr uint32_t ES = kFP8 ? 1u : 2u;  // operand element bytes
   constexpr uint32_t KSTEP_CHUNKS = 2;     // one MMA consumes 32 bytes of K per row
@@ -126,12 +127,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_shade_tc(const __grid_constan
       float o[3], d[3], x[3];
       ray_of(p, ray, o, d);
       hit_unit_coords(p, o, d, __uint_as_float(rec.y), x);
-      for (int l = 0; l < p.L; ++l) {
-        uint32_t slots[8];
-        float e0, e1;
-        encode_level(p.lv[l], p.fp16, x, slots, e0, e1);
+      encode_all_levels(p, x, [&](int l, float e0, float e1, const uint32_t*) {
         store_pair<kFP8>(A, row, 2u * l, chunks1, e0, e1, inv_sx);
-      }
+      });
       float sh[16];
       sh16(p, d, sh);
 #pragma unroll
@@ -324,19 +322,30 @@ inolf_status launch_shade_tc(const Params& p_in, inolf_precision prec, cudaStrea
   static int grid_bf16 = 0, grid_fp8 = 0;
   static std::once_flag once;
   std::call_once(once, [&] {
-    int dev = 0, sms = 1;
+    int dev = 0, sms = 1, regs_sm = 65536, smem_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t sb = tc_smem_bytes(16384, false), sf = tc_smem_bytes(16384, true);
-    cudaFuncSetAttribute(k_shade_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
-    cudaFuncSetAttribute(k_shade_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf);
-    int ob = 1, of = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ob, k_shade_tc<false>, kTcThreads, sb);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&of, k_shade_tc<true>, kTcThreads, sf);
-    // each CTA holds kTmemCols of the SM's 512 tensor-memory columns
-    const int tmem_cap = 512 / (int)kTmemCols;
-    grid_bf16 = sms * std::max(1, std::min(ob, tmem_cap));
-    grid_fp8 = sms * std::max(1, std::min(of, tmem_cap));
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    auto ctas_per_sm = [&](const void* fn, size_t smem_b) {
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b);
+      cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      cudaFuncAttributes fa{};
+      cudaFuncGetAttributes(&fa, fn);
+      // registers are allocated per warp in units of 256
+      const int regs_warp = ((std::max(fa.numRegs, 1) * 32 + 255) / 256) * 256;
+      const int by_regs = regs_sm / (regs_warp * (kTcThreads / 32));
+      const int by_smem = (int)(smem_sm / (smem_b + fa.sharedSizeBytes + 1024));
+      const int by_tmem = 512 / (int)kTmemCols;  // each CTA holds kTmemCols of 512 TMEM columns
+      int n = std::min(std::min(by_regs, by_smem), by_tmem);
+      // optional cap (tuning knob): fewer resident CTAs leave more of the
+      // unified L1/shared storage to the L1 cache that the gather relies on
+      if (const char* e = std::getenv("INOLF_TC_CTAS_PER_SM")) n = std::min(n, std::atoi(e));
+      return std::max(1, n);
+    };
+    grid_bf16 = sms * ctas_per_sm((const void*)k_shade_tc<false>, tc_smem_bytes(16384, false));
+    grid_fp8 = sms * ctas_per_sm((const void*)k_shade_tc<true>, tc_smem_bytes(16384, true));
+    cudaGetLastError();
   });
   if (smem > (size_t)tc_smem_bytes(16384, fp8)) return fail(INOLF_E_INVALID, "tensor-core weights too large");
   const int grid = fp8 ? grid_fp8 : grid_bf16;

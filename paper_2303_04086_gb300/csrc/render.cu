@@ -128,10 +128,7 @@ __global__ void __launch_bounds__(128) k_shade_f32(const __grid_constant__ Param
 #pragma unroll
       for (int j = 0; j < 64; ++j) h1[j] = 0.0f;
     }
-    for (int l = 0; l < p.L; ++l) {
-      uint32_t slots[8];
-      float e0, e1;
-      encode_level(p.lv[l], p.fp16, x, slots, e0, e1);
+    encode_all_levels(p, x, [&](int l, float e0, float e1, const uint32_t* slots) {
       if (kEncodeOnly) {
         const int64_t g = p.ray_base + ray;
 #pragma unroll
@@ -151,7 +148,7 @@ __global__ void __launch_bounds__(128) k_shade_f32(const __grid_constant__ Param
           h1[4 * q + 3] += a.w * e0 + b.w * e1;
         }
       }
-    }
+    });
     if (kEncodeOnly) continue;
     float sh[16];
     sh16(p, d, sh);
@@ -294,6 +291,7 @@ inolf_status launch_render(const Object& obj, const RayBatch& rays, inolf_precis
   static std::once_flag attr_once;
   std::call_once(attr_once, [&] {
     cudaFuncSetAttribute(k_shade_f32<kShade>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    cudaFuncSetAttribute(k_shade_f32<kShade>, cudaFuncAttributePreferredSharedMemoryCarveout, 50);
     cudaFuncSetAttribute(k_shade_f32<kAmax>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
   });
   const int shade_grid = sm_count() * 8;
