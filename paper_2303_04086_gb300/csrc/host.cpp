@@ -286,11 +286,13 @@ struct Builder {
   std::vector<float> cen;
   std::vector<int32_t> idx;
   std::vector<float> nodes;  // 16 floats per node
+  int max_depth = 0;
   static constexpr int kBins = 16;
   static constexpr int kMaxLeaf = 8;
 
-  ChildRef make(int32_t first, int32_t count) {
+  ChildRef make(int32_t first, int32_t count, int depth = 0) {
     ChildRef ref;
+    max_depth = std::max(max_depth, depth);
     Box cb;
     for (int32_t i = first; i < first + count; ++i) {
       ref.box.grow(tb[idx[i]]);
@@ -352,8 +354,8 @@ struct Builder {
     }
     int32_t node = (int32_t)(nodes.size() / 16);
     nodes.resize(nodes.size() + 16);
-    ChildRef l = make(first, mid - first);
-    ChildRef r = make(mid, first + count - mid);
+    ChildRef l = make(first, mid - first, depth + 1);
+    ChildRef r = make(mid, first + count - mid, depth + 1);
     write_node(node, l, r);
     ref.index = node;
     ref.count = 0;
@@ -467,6 +469,12 @@ extern "C" inolf_status inolf_object_create(const inolf_object_desc* desc, void*
     }
   }
   o.n_nodes = (int32_t)(b.nodes.size() / 16);
+  // the traversal keeps at most one deferred child per level on its stack
+  if (b.max_depth >= 48) {
+    destroy_object(o);
+    delete obj;
+    return fail(INOLF_E_UNSUPPORTED, "inolf_object_create: BVH deeper than the traversal stack (48)");
+  }
   std::vector<float> tri(12 * (size_t)nF);
   for (int32_t s = 0; s < nF; ++s) {
     const int32_t t = b.idx[s];

@@ -12,7 +12,7 @@
 namespace inolf {
 
 static constexpr int kMaxViewsPerLaunch = 64;
-static constexpr int kStackDepth = 64;
+static constexpr int kStackDepth = 48;  // >= BVH depth (checked at object creation)
 
 struct Params {
   // geometry proxy
@@ -137,35 +137,61 @@ __device__ __forceinline__ void ray_of(const Params& p, int64_t ray, float o[3],
 }
 
 // Moller-Trumbore, two-sided, exact FP32 operation order; accepts when
-// det != 0, u >= 0, v >= 0, u + v <= 1, t > 1e-6.
+// det != 0, u >= 0, v >= 0, u + v <= 1, t > 1e-6 and, when best_id >= 0,
+// (t, id) can still win over (best_t, best_id).
+//
+// The result equals evaluating every quantity with its IEEE operations in the
+// stated order.  Before paying for the division, tests that are implied by
+// the numerators alone reject early: with n/det of opposite signs and
+// neither value near the underflow or overflow range, RN(n * RN(1/det)) is
+// strictly negative; with |n| > |det| (1 + 2^-16) it is strictly above 1 (or
+// above best_t for t), since the three roundings change the quotient by less
+// than 2^-22 relative.  These early exits reject only triangles the exact
+// test rejects.
 __device__ __forceinline__ bool mt_hit(const float o[3], const float d[3], const float4 v0, const float4 e1,
-                                       const float4 e2, float& t_out) {
+                                       const float4 e2, float best_t, bool have_best, float& t_out) {
   const float p0 = __fsub_rn(__fmul_rn(d[1], e2.z), __fmul_rn(d[2], e2.y));
   const float p1 = __fsub_rn(__fmul_rn(d[2], e2.x), __fmul_rn(d[0], e2.z));
   const float p2 = __fsub_rn(__fmul_rn(d[0], e2.y), __fmul_rn(d[1], e2.x));
   const float det = __fadd_rn(__fadd_rn(__fmul_rn(e1.x, p0), __fmul_rn(e1.y, p1)), __fmul_rn(e1.z, p2));
   if (det == 0.0f) return false;
-  const float inv = __fdiv_rn(1.0f, det);
   const float s0 = __fsub_rn(o[0], v0.x), s1 = __fsub_rn(o[1], v0.y), s2 = __fsub_rn(o[2], v0.z);
-  const float u = __fmul_rn(__fadd_rn(__fadd_rn(__fmul_rn(s0, p0), __fmul_rn(s1, p1)), __fmul_rn(s2, p2)), inv);
-  if (!(u >= 0.0f) || !(u <= 1.0f)) return false;  // u > 1 implies u + v > 1 or v < 0
+  const float nu = __fadd_rn(__fadd_rn(__fmul_rn(s0, p0), __fmul_rn(s1, p1)), __fmul_rn(s2, p2));
+  const float adet = fabsf(det);
+  const bool safe = adet < 1e12f && adet > 1e-30f;
+  const float lim1 = adet * 1.0000153f;  // |det| (1 + 2^-16)
+  const bool neg_det = det < 0.0f;
+  if (safe && fabsf(nu) > 1e-30f && ((nu < 0.0f) != neg_det)) return false;  // u < 0
+  if (safe && fabsf(nu) > lim1) return false;                                // |u| > 1
   const float q0 = __fsub_rn(__fmul_rn(s1, e1.z), __fmul_rn(s2, e1.y));
   const float q1 = __fsub_rn(__fmul_rn(s2, e1.x), __fmul_rn(s0, e1.z));
   const float q2 = __fsub_rn(__fmul_rn(s0, e1.y), __fmul_rn(s1, e1.x));
-  const float v = __fmul_rn(__fadd_rn(__fadd_rn(__fmul_rn(d[0], q0), __fmul_rn(d[1], q1)), __fmul_rn(d[2], q2)), inv);
+  const float nv = __fadd_rn(__fadd_rn(__fmul_rn(d[0], q0), __fmul_rn(d[1], q1)), __fmul_rn(d[2], q2));
+  if (safe && fabsf(nv) > 1e-30f && ((nv < 0.0f) != neg_det)) return false;  // v < 0
+  if (safe && fabsf(nv) > lim1) return false;                                // v > 1 (so u + v > 1)
+  const float nt = __fadd_rn(__fadd_rn(__fmul_rn(e2.x, q0), __fmul_rn(e2.y, q1)), __fmul_rn(e2.z, q2));
+  if (safe && fabsf(nt) > 1e-30f && ((nt < 0.0f) != neg_det)) return false;  // t < 0
+  if (safe && have_best && fabsf(nt) > adet * best_t * 1.0000153f) return false;  // t > best_t
+  const float inv = __fdiv_rn(1.0f, det);
+  const float u = __fmul_rn(nu, inv);
+  if (!(u >= 0.0f) || !(u <= 1.0f)) return false;  // u > 1 implies u + v > 1 or v < 0
+  const float v = __fmul_rn(nv, inv);
   if (!(v >= 0.0f) || !(__fadd_rn(u, v) <= 1.0f)) return false;
-  const float t = __fmul_rn(__fadd_rn(__fadd_rn(__fmul_rn(e2.x, q0), __fmul_rn(e2.y, q1)), __fmul_rn(e2.z, q2)), inv);
+  const float t = __fmul_rn(nt, inv);
   if (!(t > 1e-6f)) return false;
   t_out = t;
   return true;
 }
 
-// Slab test of a padded box; returns entry distance or +inf.
+// Slab test of a padded box; returns entry distance or +inf.  oi = o * inv
+// per axis, so each plane distance is one fused multiply-add (the boxes are
+// padded and the comparison against the best hit has slack, so the rounding
+// of this test never decides a result).
 __device__ __forceinline__ float box_enter(float lox, float hix, float loy, float hiy, float loz, float hiz,
-                                           const float o[3], const float inv[3], float tmax) {
-  const float ax = (lox - o[0]) * inv[0], bx = (hix - o[0]) * inv[0];
-  const float ay = (loy - o[1]) * inv[1], by = (hiy - o[1]) * inv[1];
-  const float az = (loz - o[2]) * inv[2], bz = (hiz - o[2]) * inv[2];
+                                           const float oi[3], const float inv[3], float tmax) {
+  const float ax = fmaf(lox, inv[0], -oi[0]), bx = fmaf(hix, inv[0], -oi[0]);
+  const float ay = fmaf(loy, inv[1], -oi[1]), by = fmaf(hiy, inv[1], -oi[1]);
+  const float az = fmaf(loz, inv[2], -oi[2]), bz = fmaf(hiz, inv[2], -oi[2]);
   const float t0 = fmaxf(fmaxf(fminf(ax, bx), fminf(ay, by)), fmaxf(fminf(az, bz), 0.0f));
   const float t1 = fminf(fminf(fmaxf(ax, bx), fmaxf(ay, by)), fminf(fmaxf(az, bz), tmax));
   return t0 <= t1 ? t0 : INFINITY;
@@ -176,11 +202,12 @@ __device__ __forceinline__ float box_enter(float lox, float hix, float loy, floa
 // best t plus a relative slack, which never drops an equal-or-better hit.
 __device__ __forceinline__ void closest_hit(const Params& p, const float o[3], const float d[3], int32_t& best_id,
                                             float& best_t) {
-  float inv[3];
+  float inv[3], oi[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const float dk = fabsf(d[k]) < 1e-20f ? copysignf(1e-20f, d[k]) : d[k];
     inv[k] = 1.0f / dk;
+    oi[k] = o[k] * inv[k];
   }
   best_id = -1;
   best_t = INFINITY;
@@ -202,8 +229,8 @@ __device__ __forceinline__ void closest_hit(const Params& p, const float o[3], c
       const float4 ny = __ldg(p.nodes + 4 * cur + 1);
       const float4 nz = __ldg(p.nodes + 4 * cur + 2);
       const int4 meta = __ldg(reinterpret_cast<const int4*>(p.nodes) + 4 * cur + 3);
-      const float tl = box_enter(nx.x, nx.y, ny.x, ny.y, nz.x, nz.y, o, inv, lim);
-      const float tr = box_enter(nx.z, nx.w, ny.z, ny.w, nz.z, nz.w, o, inv, lim);
+      const float tl = box_enter(nx.x, nx.y, ny.x, ny.y, nz.x, nz.y, oi, inv, lim);
+      const float tr = box_enter(nx.z, nx.w, ny.z, ny.w, nz.z, nz.w, oi, inv, lim);
       // a child with index < 0 and count 0 is empty
       const bool hl = tl != INFINITY && (meta.x >= 0), hr = tr != INFINITY && (meta.z >= 0);
       if (hl && hr) {
@@ -230,7 +257,7 @@ __device__ __forceinline__ void closest_hit(const Params& p, const float o[3], c
         const float4 b = __ldg(p.tris + 3 * (cur + k) + 1);
         const float4 c = __ldg(p.tris + 3 * (cur + k) + 2);
         float t;
-        if (mt_hit(o, d, a, b, c, t)) {
+        if (mt_hit(o, d, a, b, c, best_t, best_id >= 0, t)) {
           const int32_t id = __float_as_int(a.w);
           if (t < best_t || (t == best_t && id < best_id)) { best_t = t; best_id = id; }
         }
