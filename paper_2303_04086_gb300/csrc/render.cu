@@ -211,6 +211,130 @@ __global__ void __launch_bounds__(128) k_shade_f32(const __grid_constant__ Param
 }
 
 // ---------------------------------------------------------------------------
+// k_shade_f32_tiled: FP32 SIMT shade over tiles of 128 hit rays per 256-thread
+// CTA.  Gather: two threads per ray, each taking every other level (halving
+// the chain of dependent Phi -> feature loads per thread); features and SH go
+// to a shared [k][ray] FP32 tile.  MLP: each thread computes a 4-ray x
+// 8-neuron block of a layer from shared memory (32 accumulators), the
+// activations of the tile are exchanged through one 32 KB shared buffer, and
+// layer 3 (64 -> 4) plus the sigmoid are computed per ray.
+// ---------------------------------------------------------------------------
+static constexpr int kF32Tile = 128;
+static constexpr int kF32Threads = 256;
+
+__device__ __forceinline__ void block_gemm_4x8(const float* __restrict__ act, const float* __restrict__ wT, int K,
+                                               int r0, int c0, float acc[4][8]) {
+  // act: [K][kF32Tile] (ray fastest), wT: [K][64] (neuron fastest)
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+#pragma unroll 4
+  for (int k = 0; k < K; ++k) {
+    const float4 a = *reinterpret_cast<const float4*>(act + k * kF32Tile + r0);
+    const float4 w0 = *reinterpret_cast<const float4*>(wT + k * 64 + c0);
+    const float4 w1 = *reinterpret_cast<const float4*>(wT + k * 64 + c0 + 4);
+    const float av[4] = {a.x, a.y, a.z, a.w};
+    const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], wv[j], acc[i][j]);
+  }
+}
+
+__global__ void __launch_bounds__(kF32Threads, 3) k_shade_f32_tiled(const __grid_constant__ Params p) {
+  extern __shared__ float4 smem4[];
+  float* sm = reinterpret_cast<float*>(smem4);
+  const int din = p.d_in;
+  float* W1T = sm;                 // [din][64]
+  float* W2T = W1T + din * 64;     // [64][64]  (W2 transposed: [in][out])
+  float* W3 = W2T + 64 * 64;       // [4][64]
+  float* act = W3 + 4 * 64;        // [64][kF32Tile] activations of the tile
+  const int tid = threadIdx.x;
+  // stage weights: W1T as packed on the host, W2 transposed here, W3 from W3T
+  {
+    const float* g = p.w_f32;
+    for (int k = tid; k < din * 64; k += kF32Threads) W1T[k] = g[k];
+    const float* g2 = g + din * 64;  // W2 [out][in]
+    for (int k = tid; k < 64 * 64; k += kF32Threads) W2T[(k & 63) * 64 + (k >> 6)] = g2[k];
+    const float* g3 = g2 + 64 * 64;  // W3T [in][4]
+    for (int k = tid; k < 64 * 4; k += kF32Threads) W3[(k & 3) * 64 + (k >> 2)] = g3[k];
+  }
+  __syncthreads();
+  const uint32_t total = *p.counter;
+  const int ray_slot = tid & (kF32Tile - 1), half = tid >> 7;
+  // MLP block of this thread: rays r0..r0+3, neurons c0..c0+7
+  const int r0 = (tid & 31) * 4, c0 = (tid >> 5) * 8;
+  for (uint32_t base = blockIdx.x * kF32Tile; base < total; base += gridDim.x * kF32Tile) {
+    const uint32_t h = base + (uint32_t)ray_slot;
+    const bool valid = h < total;
+    int64_t ray = 0;
+    float o[3], d[3];
+    if (valid) {
+      const uint2 rec = p.hits[h];
+      ray = rec.x;
+      float x[3];
+      ray_of(p, ray, o, d);
+      hit_unit_coords(p, o, d, __uint_as_float(rec.y), x);
+      // levels half, half + 2, ... with the next level's Phi loads in flight
+      LevelFetch cur, nxt;
+      if (half < p.L) fetch_phi(p.lv[half], x, cur);
+      for (int l = half; l < p.L; l += 2) {
+        if (l + 2 < p.L) fetch_phi(p.lv[l + 2], x, nxt);
+        uint32_t slots[8];
+        float e0, e1;
+        finish_level(p.lv[l], p.fp16, cur, slots, e0, e1);
+        act[(2 * l) * kF32Tile + ray_slot] = e0;
+        act[(2 * l + 1) * kF32Tile + ray_slot] = e1;
+        cur = nxt;
+      }
+      if (half == 1) {
+        float sh[16];
+        sh16(p, d, sh);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) act[(2 * p.L + k) * kF32Tile + ray_slot] = sh[k];
+      }
+    } else {
+      for (int k = half; k < din; k += 2) act[k * kF32Tile + ray_slot] = 0.0f;
+    }
+    __syncthreads();
+    float acc[4][8];
+    block_gemm_4x8(act, W1T, din, r0, c0, acc);
+    __syncthreads();  // every thread has read the inputs
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      *reinterpret_cast<float4*>(act + (c0 + j) * kF32Tile + r0) =
+          make_float4(fmaxf(acc[0][j], 0.f), fmaxf(acc[1][j], 0.f), fmaxf(acc[2][j], 0.f), fmaxf(acc[3][j], 0.f));
+    __syncthreads();
+    block_gemm_4x8(act, W2T, 64, r0, c0, acc);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      *reinterpret_cast<float4*>(act + (c0 + j) * kF32Tile + r0) =
+          make_float4(fmaxf(acc[0][j], 0.f), fmaxf(acc[1][j], 0.f), fmaxf(acc[2][j], 0.f), fmaxf(acc[3][j], 0.f));
+    __syncthreads();
+    // layer 3: output channel pair (2 half, 2 half + 1) of ray ray_slot
+    {
+      float z0 = 0.f, z1 = 0.f;
+      const float* w0 = W3 + (2 * half) * 64;
+      const float* w1 = w0 + 64;
+#pragma unroll 8
+      for (int j = 0; j < 64; ++j) {
+        const float a = act[j * kF32Tile + ray_slot];
+        z0 = fmaf(w0[j], a, z0);
+        z1 = fmaf(w1[j], a, z1);
+      }
+      if (valid) {
+        float* out = reinterpret_cast<float*>(p.rgba + (p.ray_base + ray));
+        *reinterpret_cast<float2*>(out + 2 * half) = make_float2(sigmoidf_(z0), sigmoidf_(z1));
+      }
+    }
+    __syncthreads();  // before the next tile overwrites the activations
+  }
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 static constexpr size_t kWsHeader = 256;
@@ -295,6 +419,17 @@ inolf_status launch_render(const Object& obj, const RayBatch& rays, inolf_precis
     cudaFuncSetAttribute(k_shade_f32<kAmax>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
   });
   const int shade_grid = sm_count() * 8;
+  const size_t smem_f32_tiled = (size_t)(obj.d_in * 64 + 64 * 64 + 4 * 64 + 64 * kF32Tile) * sizeof(float);
+  static std::once_flag tiled_once;
+  static int f32_ctas = 1;
+  std::call_once(tiled_once, [&] {
+    const size_t mx = (size_t)(48 * 64 + 64 * 64 + 4 * 64 + 64 * kF32Tile) * sizeof(float);
+    cudaFuncSetAttribute(k_shade_f32_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&f32_ctas, k_shade_f32_tiled, kF32Threads, mx);
+    if (f32_ctas < 1) f32_ctas = 1;
+    cudaGetLastError();
+  });
+  const int f32_grid = sm_count() * f32_ctas;
 
   auto run_chunk = [&](int64_t n_chunk, int32_t tiles_x, int32_t tiles_y, int64_t trace_blocks) -> inolf_status {
     if (cudaMemsetAsync(counter, 0, 8, st) != cudaSuccess) return fail(INOLF_E_CUDA, "cudaMemsetAsync failed");
@@ -318,7 +453,7 @@ inolf_status launch_render(const Object& obj, const RayBatch& rays, inolf_precis
     if (prec == INOLF_FP32) {
       {
         LaunchTimer lt("k_shade_f32", st);
-        k_shade_f32<kShade><<<shade_grid, 128, smem_f32, st>>>(p);
+        k_shade_f32_tiled<<<f32_grid, kF32Threads, smem_f32_tiled, st>>>(p);
       }
       return check_launch("k_shade_f32");
     }
