@@ -185,6 +185,32 @@ inolf_status inolf_render_rays(const inolf_object* obj, const float* o, const fl
                                inolf_precision prec, float* rgba_out, int32_t* tri_out, float* t_out,
                                void* workspace, size_t workspace_bytes, void* stream);
 
+/* ------------------------------------------------------------------------ */
+/* Training (Sec. 4.2 "Training", Eq. 8).                                     */
+/* ------------------------------------------------------------------------ */
+
+/* Backward of the FP32 per-ray path for n explicit rays (o, d device [n][3]):
+ * given d_rgba (device [n][4], dLoss/dRGBA), ACCUMULATES (+=) the gradients
+ * of the feature tables into grad_tables (host array of n_levels device
+ * pointers, each m_l^3 x 2 FP32 in slot order, see inolf_object_table_rows)
+ * and of the weights into grad_w1 [64][d_in], grad_w2 [64][64], grad_w3
+ * [4][64] (device FP32, row-major).  Activations are recomputed from the
+ * object's current parameters; rays that miss contribute nothing.  Feature
+ * gradients are scattered with atomics, weight gradients are reduced per
+ * CTA first.  workspace as for inolf_render_rays. */
+inolf_status inolf_backward(const inolf_object* obj, const float* o, const float* d, int64_t n,
+                            const float* d_rgba, float* const* grad_tables, float* grad_w1, float* grad_w2,
+                            float* grad_w3, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Replaces the object's parameters from DEVICE buffers (e.g. after an
+ * optimiser step): tables_dev (host array of n_levels device pointers, each
+ * m_l^3 x 2 FP32 in slot order; NULL array or NULL entries keep a level) and
+ * the three weight matrices (all or none; row-major FP32).  Tables are copied
+ * on `stream`; new weights are read back, repacked for every precision
+ * (FP8 weight scales recomputed) and uploaded, which synchronises `stream`. */
+inolf_status inolf_object_load_params(inolf_object* obj, const float* const* tables_dev, const float* w1_dev,
+                                      const float* w2_dev, const float* w3_dev, void* stream);
+
 /* FP8 calibration (per-tensor activation scales): renders the given views
  * with the FP32 path, records the largest |input| of each MLP layer and sets
  * the object's activation scales to amax / 448 (the e4m3 maximum).  Weight

@@ -399,6 +399,29 @@ struct Builder {
     }                                                                                      \
   } while (0)
 
+// FP32 weights packed for the SIMT kernels (W1T [d_in][64], W2 [64][64],
+// W3T [64][4]) and the tensor-core blobs, into existing buffers when present.
+namespace inolf {
+inolf_status upload_weights(Object& o, const float* w1, const float* w2, const float* w3, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  const int din = o.d_in, H = INOLF_HIDDEN, O = INOLF_OUT;
+  std::vector<float> w((size_t)din * H + H * H + H * O);
+  for (int j = 0; j < H; ++j)
+    for (int i = 0; i < din; ++i) w[(size_t)i * H + j] = w1[(size_t)j * din + i];
+  std::memcpy(&w[(size_t)din * H], w2, sizeof(float) * H * H);
+  for (int j = 0; j < O; ++j)
+    for (int i = 0; i < H; ++i) w[(size_t)din * H + H * H + (size_t)i * O + j] = w3[(size_t)j * H + i];
+  if (!o.w_f32) {
+    if (cudaMalloc(&o.w_f32, w.size() * sizeof(float)) != cudaSuccess) return fail(INOLF_E_OOM, "cudaMalloc weights");
+    o.bytes += w.size() * sizeof(float);
+  }
+  if (cudaMemcpyAsync(o.w_f32, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return fail(INOLF_E_CUDA, "upload weights");
+  return prepare_tc_weights(o, w1, w2, w3, stream);
+}
+}  // namespace inolf
+
 static void destroy_object(Object& o) {
   auto f = [](void* p) { if (p) cudaFree(p); };
   f(o.nodes); f(o.tris); f(o.w_f32); f(o.w_bf16); f(o.w_fp8);
@@ -537,22 +560,8 @@ extern "C" inolf_status inolf_object_create(const inolf_object_desc* desc, void*
     o.bytes += sizeof(uint32_t) * R3 + table.size();
   }
 
-  // --- FP32 MLP weights: W1T [d_in][64], W2 [64][64], W3T [64][4] ---
-  {
-    const int din = o.d_in, H = INOLF_HIDDEN, O = INOLF_OUT;
-    std::vector<float> w((size_t)din * H + H * H + H * O);
-    for (int j = 0; j < H; ++j)
-      for (int i = 0; i < din; ++i) w[(size_t)i * H + j] = D.w1[(size_t)j * din + i];
-    std::memcpy(&w[(size_t)din * H], D.w2, sizeof(float) * H * H);
-    for (int j = 0; j < O; ++j)
-      for (int i = 0; i < H; ++i) w[(size_t)din * H + H * H + (size_t)i * O + j] = D.w3[(size_t)j * H + i];
-    CUDA_TRY(cudaMalloc(&o.w_f32, w.size() * sizeof(float)));
-    CUDA_TRY(cudaMemcpyAsync(o.w_f32, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice, st));
-    CUDA_TRY(cudaStreamSynchronize(st));
-    o.bytes += w.size() * sizeof(float);
-  }
-  inolf_status ts = prepare_tc_weights(o, D.w1, D.w2, D.w3, stream);
-  if (ts != INOLF_OK) { destroy_object(o); delete obj; return ts; }
+  inolf_status ws = upload_weights(o, D.w1, D.w2, D.w3, stream);
+  if (ws != INOLF_OK) { destroy_object(o); delete obj; return ws; }
   *out = obj;
   return INOLF_OK;
 }
@@ -622,3 +631,4 @@ extern "C" inolf_status inolf_object_read_params(const inolf_object* obj, float*
   }
   return INOLF_OK;
 }
+

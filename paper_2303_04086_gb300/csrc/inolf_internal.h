@@ -82,8 +82,15 @@ inolf_status launch_render(const Object& obj, const RayBatch& rays, inolf_precis
 
 size_t workspace_bytes(int64_t n_rays);
 
-// Weight repacking for the tensor-core paths (mlp_tc.cu).
+// Weight repacking for the tensor-core paths (mlp_tc.cu) and the upload of
+// all weight formats (host.cpp); both reuse existing device buffers.
 inolf_status prepare_tc_weights(Object& obj, const float* w1, const float* w2, const float* w3, void* stream);
+inolf_status upload_weights(Object& obj, const float* w1, const float* w2, const float* w3, void* stream);
+
+// Backward over explicit rays (render.cu + backward.cu).
+inolf_status launch_backward_rays(const Object& obj, const float* o, const float* d, int64_t n, const float* d_rgba,
+                                  float* const* grad_tables, float* gw1, float* gw2, float* gw3, void* workspace,
+                                  size_t workspace_bytes, void* stream);
 
 }  // namespace inolf
 

@@ -55,6 +55,15 @@ struct Params {
   uint2* hits;         // (ray index in launch, t bits)
 };
 
+// Backward-pass arguments (passed by value: every pointer is device memory).
+struct BwdParams {
+  float* gtab[INOLF_MAX_LEVELS];  // per level: m^3 x 2 FP32 gradient table (slot order)
+  float* gw1;                     // [64][d_in]
+  float* gw2;                     // [64][64]
+  float* gw3;                     // [4][64]
+  const float* d_rgba;            // [n][4] upstream gradient
+};
+
 // Real SH constants of bands 0..3 (no Condon-Shortley phase), from
 // Y_l^m = K_l^m P_l^|m|(cos th) {sqrt2 cos(m ph), 1, sqrt2 sin(|m| ph)} with
 // K_l^m = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!) written as polynomials of the

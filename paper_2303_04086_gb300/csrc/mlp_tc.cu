@@ -266,13 +266,15 @@ inolf_status prepare_tc_weights(Object& obj, const float* w1, const float* w2, c
       }
     float* b3 = reinterpret_cast<float*>(b2 + (size_t)H * H * 2);
     for (int i = 0; i < O * H; ++i) b3[i] = __bfloat162float(__float2bfloat16_rn(w3[i]));
-    if (cudaMalloc(&obj.w_bf16, blob.size()) != cudaSuccess) return fail(INOLF_E_OOM, "cudaMalloc bf16 weights");
+    if (!obj.w_bf16) {
+      if (cudaMalloc(&obj.w_bf16, blob.size()) != cudaSuccess) return fail(INOLF_E_OOM, "cudaMalloc bf16 weights");
+      obj.bytes += blob.size();
+    }
     if (cudaMemcpyAsync(obj.w_bf16, blob.data(), blob.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
       return fail(INOLF_E_CUDA, "upload bf16 weights");
     obj.tc_k1_bf16 = (int32_t)K1;
     obj.tc_bytes_bf16 = (uint32_t)blob.size();
-    obj.bytes += blob.size();
   }
   // ---- FP8 e4m3, per-tensor scales amax / 448 ----
   {
@@ -295,13 +297,15 @@ inolf_status prepare_tc_weights(Object& obj, const float* w1, const float* w2, c
       for (int k = 0; k < H; ++k) b2[tc::core_off(n, k / 16, ch2) + (k % 16)] = q(w2[(size_t)n * H + k], obj.fp8_w_scale[1]);
     float* b3 = reinterpret_cast<float*>(b2 + (size_t)H * H);
     for (int i = 0; i < O * H; ++i) b3[i] = dq(q(w3[i], obj.fp8_w_scale[2])) * obj.fp8_w_scale[2];
-    if (cudaMalloc(&obj.w_fp8, blob.size()) != cudaSuccess) return fail(INOLF_E_OOM, "cudaMalloc fp8 weights");
+    if (!obj.w_fp8) {
+      if (cudaMalloc(&obj.w_fp8, blob.size()) != cudaSuccess) return fail(INOLF_E_OOM, "cudaMalloc fp8 weights");
+      obj.bytes += blob.size();
+    }
     if (cudaMemcpyAsync(obj.w_fp8, blob.data(), blob.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
       return fail(INOLF_E_CUDA, "upload fp8 weights");
     obj.tc_k1_fp8 = (int32_t)K1;
     obj.tc_bytes_fp8 = (uint32_t)blob.size();
-    obj.bytes += blob.size();
   }
   return INOLF_OK;
 }

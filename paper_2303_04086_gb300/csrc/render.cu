@@ -5,7 +5,7 @@
 //            traversal of the proxy mesh (FP32 Moller-Trumbore, closest =
 //            lexicographic (t, triangle id) minimum), then warp-ballot
 //            compaction of the hitting rays into a dense hit list
-//            (one global atomic per CTA).  Misses write RGBA = 0.
+//            (one global atomic per warp).  Misses write RGBA = 0.
 //   k_shade  persistent over the hit list, one thread per hit ray: the
 //            Sec. 4.1 grid vertex of the hit point on every level, Eq. 1
 //            perfect-hash slots of the 8 voxel corners, feature gather,
@@ -62,22 +62,16 @@ __global__ void __launch_bounds__(256) k_trace(const __grid_constant__ Params p,
   if (valid) closest_hit(p, o, d, tri, t);
   const bool hit = valid && tri >= 0;
 
-  // compaction: warp ballot + per-CTA prefix + one global atomic per CTA
-  __shared__ uint32_t s_warp[8];
-  __shared__ uint32_t s_base;
+  // compaction: warp ballot + one global atomic per warp (no CTA barrier, so
+  // a warp whose rays finish early does not wait for the slowest warp)
   const uint32_t mask = __ballot_sync(0xffffffffu, hit);
-  if (lane == 0) s_warp[warp] = __popc(mask);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t acc = 0;
-    for (int w = 0; w < 8; ++w) { uint32_t c = s_warp[w]; s_warp[w] = acc; acc += c; }
-    s_base = acc ? atomicAdd(p.counter, acc) : 0u;
-  }
-  __syncthreads();
+  uint32_t wbase = 0;
+  if (lane == 0 && mask) wbase = atomicAdd(p.counter, (uint32_t)__popc(mask));
+  wbase = __shfl_sync(0xffffffffu, wbase, 0);
   if (valid) {
     const int64_t g = p.ray_base + ray;
     if (hit) {
-      const uint32_t pos = s_base + s_warp[warp] + __popc(mask & ((1u << lane) - 1u));
+      const uint32_t pos = wbase + __popc(mask & ((1u << lane) - 1u));
       p.hits[pos] = make_uint2((uint32_t)ray, __float_as_uint(t));
     } else if (p.rgba) {
       p.rgba[g] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -493,9 +487,63 @@ inolf_status launch_render(const Object& obj, const RayBatch& rays, inolf_precis
   return INOLF_OK;
 }
 
+inolf_status launch_backward(const Params& p, const BwdParams& b, cudaStream_t st);  // backward.cu
+
+inolf_status launch_backward_rays(const Object& obj, const float* o, const float* d, int64_t n, const float* d_rgba,
+                                  float* const* grad_tables, float* gw1, float* gw2, float* gw3, void* workspace,
+                                  size_t ws_bytes, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!workspace || ws_bytes < workspace_bytes(1) || ((uintptr_t)workspace & 15))
+    return fail(INOLF_E_INVALID, "backward: workspace missing, too small or not 16-byte aligned");
+  const int64_t cap = (int64_t)((ws_bytes - kWsHeader) / 8);
+  Params p{};
+  fill_common(obj, p);
+  p.mode = 1;
+  p.counter = (uint32_t*)workspace;
+  p.hits = (uint2*)((char*)workspace + kWsHeader);
+  BwdParams b{};
+  for (int l = 0; l < obj.L; ++l) b.gtab[l] = grad_tables[l];
+  b.gw1 = gw1;
+  b.gw2 = gw2;
+  b.gw3 = gw3;
+  b.d_rgba = d_rgba;
+  const int64_t chunk = std::min<int64_t>(cap, 0xFFFFFFFFll);
+  for (int64_t r0 = 0; r0 < n; r0 += chunk) {
+    const int64_t nr = std::min(chunk, n - r0);
+    p.ro = o + 3 * r0;
+    p.rd = d + 3 * r0;
+    p.ray_base = r0;
+    p.n_rays = nr;
+    if (cudaMemsetAsync(p.counter, 0, 8, st) != cudaSuccess) return fail(INOLF_E_CUDA, "cudaMemsetAsync failed");
+    {
+      LaunchTimer lt("k_trace", st);
+      k_trace<<<(unsigned)((nr + 255) / 256), 256, 0, st>>>(p, 0, 0);
+    }
+    inolf_status s = check_launch("k_trace");
+    if (s != INOLF_OK) return s;
+    s = launch_backward(p, b, st);
+    if (s != INOLF_OK) return s;
+  }
+  return INOLF_OK;
+}
+
 }  // namespace inolf
 
 using namespace inolf;
+
+extern "C" inolf_status inolf_backward(const inolf_object* obj, const float* o, const float* d, int64_t n,
+                                       const float* d_rgba, float* const* grad_tables, float* grad_w1,
+                                       float* grad_w2, float* grad_w3, void* workspace, size_t workspace_bytes,
+                                       void* stream) {
+  clear_error();
+  if (!obj || n < 0 || (n > 0 && (!o || !d || !d_rgba || !grad_tables || !grad_w1 || !grad_w2 || !grad_w3)))
+    return fail(INOLF_E_INVALID, "inolf_backward: bad argument");
+  for (int l = 0; n > 0 && l < obj->o.L; ++l)
+    if (!grad_tables[l]) return fail(INOLF_E_INVALID, "inolf_backward: missing gradient table");
+  if (n == 0) return INOLF_OK;
+  return launch_backward_rays(obj->o, o, d, n, d_rgba, grad_tables, grad_w1, grad_w2, grad_w3, workspace,
+                              workspace_bytes, stream);
+}
 
 extern "C" size_t inolf_render_workspace_bytes(int64_t n_rays) { return inolf::workspace_bytes(n_rays); }
 

@@ -82,6 +82,8 @@ def lib():
     L.inolf_encode_rays.argtypes = [vp, vp, vp, i64, vp, vp, vp, sz, vp]
     L.inolf_render_rays_noalloc.argtypes = [vp, vp, vp, i64, i32, vp, vp, vp, vp]
     L.inolf_calibrate_fp8.argtypes = [vp, vp, i32, i32, i32, vp, sz, vp]
+    L.inolf_backward.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, sz, vp]
+    L.inolf_object_load_params.argtypes = [vp, vp, vp, vp, vp, vp]
     L.inolf_object_get_fp8_scales.argtypes = [vp, vp, vp]
     _lib = L
     return L
@@ -352,3 +354,80 @@ def stats_read() -> dict:
     _check(L.inolf_stats_read(ctypes.cast(arr, ctypes.c_void_p), 64, ctypes.byref(n)))
     return {arr[i].name.decode(): {"launches": int(arr[i].launches), "ms": float(arr[i].ms)}
             for i in range(min(n.value, 64))}
+
+
+# ---------------------------------------------------------------------------
+# training: backward, parameter updates, autograd
+# ---------------------------------------------------------------------------
+def backward(obj: Object, o, d, d_rgba, grad_tables, gw1, gw2, gw3, workspace=None, stream=None):
+    """inolf_backward: accumulate (+=) dLoss/d(tables, W1, W2, W3) for rays
+    (o, d) given dLoss/dRGBA; all tensors on the device, FP32."""
+    n = o.shape[0]
+    if workspace is None:
+        workspace = _workspace(n, o.device)
+    tp = (ctypes.c_void_p * obj.L)(*[t.data_ptr() for t in grad_tables])
+    _check(lib().inolf_backward(obj.handle, _ptr(o), _ptr(d), n, _ptr(d_rgba), ctypes.cast(tp, ctypes.c_void_p),
+                                _ptr(gw1), _ptr(gw2), _ptr(gw3), _ptr(workspace),
+                                workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
+def load_params(obj: Object, tables=None, w1=None, w2=None, w3=None, stream=None):
+    """inolf_object_load_params from device tensors (tables slot-ordered [m^3, 2])."""
+    tp = None
+    keep = []
+    if tables is not None:
+        arr = (ctypes.c_void_p * obj.L)(*[(t.data_ptr() if t is not None else None) for t in tables])
+        tp = ctypes.cast(arr, ctypes.c_void_p)
+        keep.append(arr)
+    _check(lib().inolf_object_load_params(obj.handle, tp, _ptr(w1), _ptr(w2), _ptr(w3), _stream(stream)))
+
+
+def _render_fn():
+    import torch
+
+    class _RenderRays(torch.autograd.Function):
+        """Forward through inolf_render_rays, backward through inolf_backward
+        (FP32 recompute).  The object's parameters are loaded from the given
+        tensors before the forward."""
+
+        @staticmethod
+        def forward(ctx, o, d, field, prec, w1, w2, w3, *tables):
+            load_params(field.obj, tables, w1, w2, w3)
+            rgba = render_rays(field.obj, o, d, prec)
+            ctx.save_for_backward(o, d)
+            ctx.field = field
+            return rgba
+
+        @staticmethod
+        def backward(ctx, g):
+            o, d = ctx.saved_tensors
+            f = ctx.field
+            gt = [torch.zeros_like(t) for t in f.tables]
+            g1, g2, g3 = torch.zeros_like(f.w1), torch.zeros_like(f.w2), torch.zeros_like(f.w3)
+            backward(f.obj, o, d, g.contiguous(), gt, g1, g2, g3)
+            return (None, None, None, None, g1, g2, g3, *gt)
+
+    return _RenderRays
+
+
+class Field:
+    """A trainable i-NOLF object: the feature tables (slot order) and MLP
+    weights are torch CUDA tensors with requires_grad; ``render(o, d)`` is
+    differentiable with respect to all of them."""
+
+    def __init__(self, scene, hashes=None, fp16: bool = False):
+        import torch
+        self.obj = object_create(scene, hashes, fp16=fp16)
+        tables, w1, w2, w3 = self.obj.read_params()
+        dev = torch.device("cuda")
+        self.tables = [torch.from_numpy(t).to(dev).requires_grad_() for t in tables]
+        self.w1 = torch.from_numpy(w1).to(dev).requires_grad_()
+        self.w2 = torch.from_numpy(w2).to(dev).requires_grad_()
+        self.w3 = torch.from_numpy(w3).to(dev).requires_grad_()
+        self._fn = _render_fn()
+
+    def parameters(self):
+        return [self.w1, self.w2, self.w3] + list(self.tables)
+
+    def render(self, o, d, prec="fp32"):
+        return self._fn.apply(o, d, self, prec, self.w1, self.w2, self.w3, *self.tables)
