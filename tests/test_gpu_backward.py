@@ -127,8 +127,9 @@ def test_backward_accumulates(env, tiny, tiny_oracle):
     inolf.backward(obj, to, td, tg, gt, *gw)
     once = [t.clone() for t in gw]
     inolf.backward(obj, to, td, tg, gt, *gw)
+    # atomics add the per-CTA partials in any order: equal up to FP32 rounding
     for a, b in zip(gw, once):
-        assert torch.allclose(a, 2 * b, rtol=1e-5, atol=1e-9)
+        assert float((a - 2 * b).norm() / (2 * b).norm()) < 1e-5
 
 
 def test_load_params_round_trip(env, tiny):
