@@ -57,6 +57,7 @@ typedef int inolf_status;
 #define INOLF_E_HASH_FAILED (-6)   /* perfect hash construction failed after max_retries */
 #define INOLF_E_UNKNOWN_TICKET (-7) /* serve_poll: no such request */
 #define INOLF_E_UNSUPPORTED (-8)   /* valid request this build cannot serve */
+#define INOLF_E_CANCELLED (-9)     /* serve_poll: the request was cancelled */
 
 #define INOLF_MAX_LEVELS 16
 #define INOLF_HIDDEN 64
@@ -229,6 +230,73 @@ inolf_status inolf_object_get_fp8_scales(const inolf_object* obj, float act[3], 
 inolf_status inolf_encode_rays(const inolf_object* obj, const float* o, const float* d, int64_t n,
                                uint32_t* slots_out, float* feat_out, void* workspace, size_t workspace_bytes,
                                void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Serving: continuous batching of many viewers over resident objects (the   */
+/* render farm + frame composer of Sec. 5-6 on one GPU).                     */
+/* ------------------------------------------------------------------------ */
+typedef struct inolf_server inolf_server;
+
+typedef struct {
+  size_t hbm_budget;       /* device bytes for served frames (admission budget), default 4 GiB */
+  int32_t max_slots;       /* requests admitted at once (1..256), default 48 */
+  int32_t max_width, max_height; /* largest admitted frame, default 3840 x 2160 */
+  int32_t max_hits;        /* K: hits composited per ray (1..4), default 4 */
+  int64_t wait_limit_ns;   /* bound of the device wait for a request descriptor, default 1 s */
+  int64_t idle_limit_ns;   /* the persistent kernel exits after this long without work, default 20 ms */
+  int32_t ctas_per_sm;     /* persistent CTAs per SM, 0 = as many as fit */
+} inolf_serve_params;
+
+#define INOLF_REQ_TEST_DROP_DESCRIPTOR 1u /* fault injection: the request descriptor is never published */
+
+typedef struct {
+  float camera[13];        /* camera record (world frame) */
+  int32_t width, height;
+  inolf_precision precision; /* INOLF_FP32 */
+  uint32_t viewer_id;
+  uint32_t flags;          /* 0, or INOLF_REQ_TEST_DROP_DESCRIPTOR in fault tests */
+} inolf_request;
+
+typedef struct {
+  const float* frame;      /* device [height][width][4] straight RGBA, valid until inolf_serve_release */
+  int32_t width, height;
+  int64_t latency_ns;      /* submission to the first poll that saw the request complete */
+  int64_t rays;
+} inolf_result;
+
+/* Creates a server on the current device: a frame arena of hbm_budget bytes,
+ * mapped host memory for the request ring, and its own stream on which the
+ * persistent kernel runs.  params may be NULL (defaults). */
+inolf_status inolf_serve_create(const inolf_serve_params* params, inolf_server** out);
+
+/* Makes an object resident in the scene at a translation (object frame =
+ * world - translation).  Up to 16 objects; only while no request is in
+ * flight.  The object must outlive the server. */
+inolf_status inolf_serve_add_object(inolf_server* srv, const inolf_object* obj, const float translation[3]);
+
+/* Admits a request (INOLF_E_BUDGET when every slot is busy or the frame
+ * does not fit the HBM budget: nothing is queued, retry later) and publishes
+ * its 16x16 tiles to the running kernel (launching it if idle).  Each pixel
+ * composites, front to back by (t, object id), up to max_hits hits over all
+ * resident objects with the straight-alpha over operator and stores
+ * (C / A, A).  *ticket identifies the request. */
+inolf_status inolf_serve_submit(inolf_server* srv, const inolf_request* req, uint64_t* ticket);
+
+/* INOLF_PENDING while in flight (and relaunches the kernel if it went idle);
+ * INOLF_OK with *result filled when complete; INOLF_E_TIMEOUT or
+ * INOLF_E_CANCELLED for requests that ended so; INOLF_E_UNKNOWN_TICKET. */
+inolf_status inolf_serve_poll(inolf_server* srv, uint64_t ticket, inolf_result* result);
+
+/* Asks the device to skip the remaining tiles of a request; poll then
+ * returns INOLF_E_CANCELLED once its tiles have drained. */
+inolf_status inolf_serve_cancel(inolf_server* srv, uint64_t ticket);
+
+/* Returns the frame memory and the slot of a completed request. */
+inolf_status inolf_serve_release(inolf_server* srv, uint64_t ticket);
+
+/* Stops the persistent kernel (it finishes the tiles it holds) and frees
+ * everything. */
+inolf_status inolf_serve_destroy(inolf_server* srv);
 
 /* ------------------------------------------------------------------------ */
 /* Allocation-free rendering (the paper has no counterpart: this exists for   */

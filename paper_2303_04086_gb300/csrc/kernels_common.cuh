@@ -86,9 +86,8 @@ inline void sh_constants(float c[10]) {
   c[9] = (float)std::sqrt(7.0 / (16.0 * pi));      // c3e
 }
 
-__device__ __forceinline__ void sh16(const Params& p, const float d[3], float y[16]) {
+__device__ __forceinline__ void sh16c(const float* c, const float d[3], float y[16]) {
   const float x = d[0], yy = d[1], z = d[2];
-  const float* c = p.shc;
   const float x2 = x * x, y2 = yy * yy, z2 = z * z;
   y[0] = c[0];
   y[1] = c[1] * yy;
@@ -107,6 +106,8 @@ __device__ __forceinline__ void sh16(const Params& p, const float d[3], float y[
   y[14] = c[7] * z * (x2 - y2);
   y[15] = c[5] * x * (x2 - 3.0f * y2);
 }
+
+__device__ __forceinline__ void sh16(const Params& p, const float d[3], float y[16]) { sh16c(p.shc, d, y); }
 
 __device__ __forceinline__ float sigmoidf_(float z) { return 1.0f / (1.0f + expf(-z)); }
 
@@ -209,8 +210,9 @@ __device__ __forceinline__ float box_enter(float lox, float hix, float loy, floa
 // Closest hit over the proxy: lexicographic minimum of (t, triangle id).  A
 // subtree is skipped only when its padded box is entered after the current
 // best t plus a relative slack, which never drops an equal-or-better hit.
-__device__ __forceinline__ void closest_hit(const Params& p, const float o[3], const float d[3], int32_t& best_id,
-                                            float& best_t) {
+__device__ __forceinline__ void closest_hit_bvh(const float4* __restrict__ nodes, const float4* __restrict__ tris,
+                                                uint32_t* err, const float o[3], const float d[3], int32_t& best_id,
+                                                float& best_t) {
   float inv[3], oi[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
@@ -229,15 +231,15 @@ __device__ __forceinline__ void closest_hit(const Params& p, const float o[3], c
   // against a malformed node array (flagged, traversal stops)
   for (int32_t guard = 0;; ++guard) {
     if (guard > (1 << 22)) {
-      atomicOr(p.counter + 1, 2u);
+      atomicOr(err, 2u);
       break;
     }
     const float lim = best_id < 0 ? INFINITY : best_t * 1.00002f + 1e-5f;
     if (cur_cnt == 0) {
-      const float4 nx = __ldg(p.nodes + 4 * cur + 0);
-      const float4 ny = __ldg(p.nodes + 4 * cur + 1);
-      const float4 nz = __ldg(p.nodes + 4 * cur + 2);
-      const int4 meta = __ldg(reinterpret_cast<const int4*>(p.nodes) + 4 * cur + 3);
+      const float4 nx = __ldg(nodes + 4 * cur + 0);
+      const float4 ny = __ldg(nodes + 4 * cur + 1);
+      const float4 nz = __ldg(nodes + 4 * cur + 2);
+      const int4 meta = __ldg(reinterpret_cast<const int4*>(nodes) + 4 * cur + 3);
       const float tl = box_enter(nx.x, nx.y, ny.x, ny.y, nz.x, nz.y, oi, inv, lim);
       const float tr = box_enter(nx.z, nx.w, ny.z, ny.w, nz.z, nz.w, oi, inv, lim);
       // a child with index < 0 and count 0 is empty
@@ -250,7 +252,7 @@ __device__ __forceinline__ void closest_hit(const Params& p, const float o[3], c
           st_t[sp] = lfirst ? tr : tl;
           ++sp;
         } else {
-          atomicOr(p.counter + 1, 1u);  // stack overflow: flagged, subtree skipped
+          atomicOr(err, 1u);  // stack overflow: flagged, subtree skipped
         }
         cur = lfirst ? meta.x : meta.z;
         cur_cnt = lfirst ? meta.y : meta.w;
@@ -262,9 +264,9 @@ __device__ __forceinline__ void closest_hit(const Params& p, const float o[3], c
       }
     } else {
       for (int32_t k = 0; k < cur_cnt; ++k) {
-        const float4 a = __ldg(p.tris + 3 * (cur + k) + 0);
-        const float4 b = __ldg(p.tris + 3 * (cur + k) + 1);
-        const float4 c = __ldg(p.tris + 3 * (cur + k) + 2);
+        const float4 a = __ldg(tris + 3 * (cur + k) + 0);
+        const float4 b = __ldg(tris + 3 * (cur + k) + 1);
+        const float4 c = __ldg(tris + 3 * (cur + k) + 2);
         float t;
         if (mt_hit(o, d, a, b, c, best_t, best_id >= 0, t)) {
           const int32_t id = __float_as_int(a.w);
@@ -289,14 +291,23 @@ __device__ __forceinline__ void closest_hit(const Params& p, const float o[3], c
   if (best_id < 0) best_t = 0.0f;
 }
 
+__device__ __forceinline__ void closest_hit(const Params& p, const float o[3], const float d[3], int32_t& best_id,
+                                            float& best_t) {
+  closest_hit_bvh(p.nodes, p.tris, p.counter + 1, o, d, best_id, best_t);
+}
+
 // Scene-unit coordinates of the hit point: P = o + t d, x = (P - lo) * scale.
-__device__ __forceinline__ void hit_unit_coords(const Params& p, const float o[3], const float d[3], float t,
-                                                float x[3]) {
+__device__ __forceinline__ void hit_unit_coords_ls(float lo, float scale, const float o[3], const float d[3], float t,
+                                                   float x[3]) {
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const float P = __fadd_rn(o[k], __fmul_rn(t, d[k]));
-    x[k] = __fmul_rn(__fsub_rn(P, p.lo), p.scale);
+    x[k] = __fmul_rn(__fsub_rn(P, lo), scale);
   }
+}
+__device__ __forceinline__ void hit_unit_coords(const Params& p, const float o[3], const float d[3], float t,
+                                                float x[3]) {
+  hit_unit_coords_ls(p.lo, p.scale, o, d, t, x);
 }
 
 // a mod m for 0 <= a < 2^21 and m <= 2^10, with a float quotient estimate

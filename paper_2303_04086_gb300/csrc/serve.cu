@@ -1,0 +1,681 @@
+// Continuous-batching request loop for many viewers over several resident
+// i-NOLF objects on one GPU (the paper's render farm and frame composer,
+// Sec. 5-6, collapsed onto a single device).
+//
+// A persistent kernel (one or a few CTAs per SM) claims work units -- 16x16
+// pixel tiles of any live request -- from a ring that the host publishes in
+// mapped host memory.  Requests that arrive while others are being rendered
+// are published into the same ring, so their tiles interleave with the
+// earlier requests' tiles on the device: there is no per-request launch and
+// no waiting for a batch to drain.  For every pixel of a tile the CTA
+//   1. generates the viewer's pinhole ray (world frame);
+//   2. intersects every resident object's proxy in that object's local frame
+//      (translation-only placement) and keeps the K nearest hits, ordered by
+//      (t, object id);
+//   3. shades each hit with its object's encoding and MLP (one query per hit,
+//      Sec. 4.2), the object's weights staged in shared memory;
+//   4. composites the hits front to back with the straight-alpha "over"
+//      operator (depth-ordered fusion, the frame composer of Sec. 5.1):
+//      C += (1 - A) a c, A += (1 - A) a, and writes (C / A, A).
+// The last tile of a request publishes its completion to mapped host memory.
+// Admission is by slot count and by an arena of device memory for the
+// frames (the HBM budget).  Every device-side wait is bounded by the global
+// timer: an idle kernel exits after idle_limit_ns (the host relaunches it on
+// the next submission), and a tile whose request descriptor does not appear
+// within wait_limit_ns completes with INOLF_E_TIMEOUT.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "inolf_internal.h"
+#include "kernels_common.cuh"
+
+namespace inolf {
+
+static constexpr int kServeMaxObjects = 16;
+static constexpr int kServeMaxK = 4;
+static constexpr int kServeTile = 16;
+static constexpr int kServeThreads = kServeTile * kServeTile;
+static constexpr int kServeMaxSlots = 256;
+static constexpr int kServeMaxDin = 2 * INOLF_MAX_LEVELS + INOLF_N_SH;
+
+struct ServeObj {
+  const float4* nodes;
+  const float4* tris;
+  const float* w_f32;
+  int32_t L, fp16, d_in, pad;
+  float lo, scale;
+  float T[3];  // object placement: local = world - T
+  LevelDev lv[INOLF_MAX_LEVELS];
+};
+
+struct ServeSlot {  // mapped host memory, written by the host at submission
+  uint32_t gen;
+  int32_t W, H, prec;
+  float* out;
+  float cam[13];
+  uint32_t tiles_x, tiles_total;
+  uint32_t cancelled;
+};
+
+struct ServeTile {  // ring entry, mapped host memory
+  uint32_t slot, gen, tx, ty, tiles_total, pad;
+};
+
+struct ServeDone {  // completion record, mapped host memory, written by the device
+  uint32_t gen;
+  int32_t status;
+};
+
+struct ServeCtl {  // mapped host memory
+  unsigned long long published;  // tiles published so far (host)
+  uint32_t stop;                 // host asks the kernel to exit
+  uint32_t pad;
+};
+
+struct ServeDevState {  // device memory
+  unsigned long long head;           // tiles claimed so far
+  unsigned long long last_activity;  // global timer of the last claim
+  uint32_t tiles_done[kServeMaxSlots];
+  int32_t status[kServeMaxSlots];
+  uint32_t err;
+};
+
+struct ServeKParams {
+  const ServeObj* objs;
+  int32_t n_objs;
+  int32_t K;
+  ServeCtl* ctl;
+  ServeDone* done;
+  const ServeSlot* slots;
+  const ServeTile* ring;
+  unsigned long long ring_cap;
+  ServeDevState* st;
+  unsigned long long wait_limit_ns;
+  unsigned long long idle_limit_ns;
+  float shc[10];
+};
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned long long ld_acq_sys_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_acq_sys_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_vol_u32(const uint32_t* p) { return *(const volatile uint32_t*)p; }
+__device__ __forceinline__ float ld_vol_f32(const float* p) { return *(const volatile float*)p; }
+__device__ __forceinline__ void st_rel_sys_u32(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// FP32 MLP F_s of one hit from shared-memory weights (W1T [d_in][64],
+// W2 [64][64], W3T [64][4]); x = features (2L) followed by 16 SH values.
+__device__ __forceinline__ float4 mlp_f32(const float4* W1T, const float4* W2, const float4* W3T, const float* x,
+                                          int din) {
+  float h1[64];
+#pragma unroll
+  for (int j = 0; j < 64; ++j) h1[j] = 0.0f;
+  for (int i = 0; i < din; ++i) {
+    const float v = x[i];
+    const float4* r = W1T + i * 16;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const float4 a = r[q];
+      h1[4 * q + 0] += a.x * v;
+      h1[4 * q + 1] += a.y * v;
+      h1[4 * q + 2] += a.z * v;
+      h1[4 * q + 3] += a.w * v;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 64; ++j) h1[j] = fmaxf(h1[j], 0.0f);
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 2
+  for (int j = 0; j < 64; ++j) {
+    const float4* r = W2 + j * 16;
+    float z = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const float4 a = r[q];
+      z += a.x * h1[4 * q + 0] + a.y * h1[4 * q + 1] + a.z * h1[4 * q + 2] + a.w * h1[4 * q + 3];
+    }
+    z = fmaxf(z, 0.0f);
+    const float4 w3 = W3T[j];
+    acc.x += w3.x * z;
+    acc.y += w3.y * z;
+    acc.z += w3.z * z;
+    acc.w += w3.w * z;
+  }
+  return make_float4(sigmoidf_(acc.x), sigmoidf_(acc.y), sigmoidf_(acc.z), sigmoidf_(acc.w));
+}
+
+__global__ void __launch_bounds__(kServeThreads) k_serve(const __grid_constant__ ServeKParams kp) {
+  extern __shared__ float4 smem4[];  // FP32 weights of the object being shaded
+  __shared__ int s_cmd;
+  __shared__ unsigned long long s_idx;
+  __shared__ uint32_t s_slot, s_gen, s_tx, s_ty, s_tiles_total;
+  __shared__ int s_W, s_H, s_status, s_skip;
+  __shared__ float* s_out;
+  __shared__ float s_cam[13];
+  __shared__ uint32_t s_obj_hits[kServeMaxObjects];
+  const int tid = threadIdx.x;
+  const unsigned long long t_start = gtimer();
+
+  while (true) {
+    // ---- claim one published tile (thread 0), bounded idle wait ----
+    if (tid == 0) {
+      int cmd = 1;
+      while (true) {
+        if (ld_vol_u32(&kp.ctl->stop)) break;
+        const unsigned long long pub = ld_acq_sys_u64(&kp.ctl->published);
+        const unsigned long long h = atomicAdd(&kp.st->head, 0ull);
+        if (h < pub) {
+          if (atomicCAS(&kp.st->head, h, h + 1) == h) {
+            s_idx = h;
+            cmd = 0;
+            atomicMax(&kp.st->last_activity, gtimer());
+            break;
+          }
+          continue;
+        }
+        const unsigned long long now = gtimer();
+        const unsigned long long last = max((unsigned long long)atomicAdd(&kp.st->last_activity, 0ull), t_start);
+        if (now > last + kp.idle_limit_ns) break;  // idle: exit, the host relaunches on new work
+        __nanosleep(1000);
+      }
+      s_cmd = cmd;
+      if (cmd == 0) {
+        const ServeTile* e = kp.ring + (s_idx % kp.ring_cap);
+        s_slot = ld_vol_u32(&e->slot);
+        s_gen = ld_vol_u32(&e->gen);
+        s_tx = ld_vol_u32(&e->tx);
+        s_ty = ld_vol_u32(&e->ty);
+        s_tiles_total = ld_vol_u32(&e->tiles_total);
+        const ServeSlot* sl = kp.slots + s_slot;
+        // bounded wait for the request descriptor of this generation
+        int status = 0;
+        const unsigned long long t0 = gtimer();
+        while (ld_acq_sys_u32(&sl->gen) != s_gen) {
+          if (gtimer() - t0 > kp.wait_limit_ns) {
+            status = INOLF_E_TIMEOUT;
+            break;
+          }
+          __nanosleep(500);
+        }
+        s_status = status;
+        s_skip = status != 0;
+        if (!status) {
+          if (ld_vol_u32(&sl->cancelled)) {
+            s_status = INOLF_E_CANCELLED;
+            s_skip = 1;
+          }
+          s_W = (int)ld_vol_u32((const uint32_t*)&sl->W);
+          s_H = (int)ld_vol_u32((const uint32_t*)&sl->H);
+          s_out = *(float* const volatile*)&sl->out;
+          for (int k = 0; k < 13; ++k) s_cam[k] = ld_vol_f32(&sl->cam[k]);
+        }
+      }
+    }
+    if (tid < kServeMaxObjects) s_obj_hits[tid] = 0;
+    __syncthreads();
+    if (s_cmd) break;
+
+    // ---- trace every object, keep the K nearest hits of this pixel ----
+    float ht[kServeMaxK];
+    int hk[kServeMaxK];
+    int nh = 0;
+    const int i = (int)s_tx * kServeTile + (tid & 15), j = (int)s_ty * kServeTile + (tid >> 4);
+    const bool valid = !s_skip && i < s_W && j < s_H;
+    float o[3], d[3];
+    if (valid) {
+      make_ray(s_cam, s_W, s_H, i, j, o, d);
+      for (int k = 0; k < kp.n_objs; ++k) {
+        const ServeObj& ob = kp.objs[k];
+        float ol[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) ol[a] = __fsub_rn(o[a], ob.T[a]);
+        int32_t id;
+        float t;
+        closest_hit_bvh(ob.nodes, ob.tris, &kp.st->err, ol, d, id, t);
+        if (id < 0) continue;
+        // insert (t, k) into the sorted list (ties by object id: k increases)
+        int pos = nh < kp.K ? nh : kp.K;
+        while (pos > 0 && ht[pos - 1] > t) {
+          if (pos < kp.K) { ht[pos] = ht[pos - 1]; hk[pos] = hk[pos - 1]; }
+          --pos;
+        }
+        if (pos < kp.K) {
+          ht[pos] = t;
+          hk[pos] = k;
+          if (nh < kp.K) ++nh;
+        }
+      }
+      for (int q = 0; q < nh; ++q) atomicOr(&s_obj_hits[hk[q]], 1u);
+    }
+    __syncthreads();
+
+    // ---- shade the hits object by object (weights staged in shared memory) ----
+    float4 rgba[kServeMaxK];
+    for (int k = 0; k < kp.n_objs; ++k) {
+      if (!s_obj_hits[k]) continue;  // uniform: no pixel of the tile hits object k
+      const ServeObj& ob = kp.objs[k];
+      const int din = ob.d_in;
+      const int nw4 = (din * 64 + 64 * 64 + 64 * 4) / 4;
+      for (int q = tid; q < nw4; q += kServeThreads) smem4[q] = reinterpret_cast<const float4*>(ob.w_f32)[q];
+      __syncthreads();
+      for (int q = 0; q < nh; ++q) {
+        if (hk[q] != k) continue;
+        float ol[3], x3[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) ol[a] = __fsub_rn(o[a], ob.T[a]);
+        hit_unit_coords_ls(ob.lo, ob.scale, ol, d, ht[q], x3);
+        float x[kServeMaxDin];
+        for (int l = 0; l < ob.L; ++l) {
+          uint32_t slots[8];
+          float e0, e1;
+          encode_level(ob.lv[l], ob.fp16, x3, slots, e0, e1);
+          x[2 * l] = e0;
+          x[2 * l + 1] = e1;
+        }
+        sh16c(kp.shc, d, x + 2 * ob.L);
+        rgba[q] = mlp_f32(smem4, smem4 + din * 16, smem4 + din * 16 + 64 * 16, x, din);
+      }
+      __syncthreads();
+    }
+
+    // ---- composite front to back, straight alpha out ----
+    if (valid) {
+      float C0 = 0.f, C1 = 0.f, C2 = 0.f, A = 0.f;
+      for (int q = 0; q < nh; ++q) {
+        const float w = (1.0f - A) * rgba[q].w;
+        C0 += w * rgba[q].x;
+        C1 += w * rgba[q].y;
+        C2 += w * rgba[q].z;
+        A += w;
+      }
+      const float4 px = A > 0.f ? make_float4(C0 / A, C1 / A, C2 / A, A) : make_float4(0.f, 0.f, 0.f, 0.f);
+      reinterpret_cast<float4*>(s_out)[(size_t)j * s_W + i] = px;
+    }
+    __threadfence_system();
+    __syncthreads();
+    // ---- tile done; the last tile of the request publishes its completion ----
+    if (tid == 0) {
+      const uint32_t slot = s_slot;
+      if (s_status) atomicCAS(&kp.st->status[slot], 0, s_status);
+      const uint32_t n = atomicAdd(&kp.st->tiles_done[slot], 1u) + 1u;
+      if (n == s_tiles_total) {
+        const int status = atomicExch(&kp.st->status[slot], 0);
+        kp.st->tiles_done[slot] = 0;
+        __threadfence_system();
+        *(volatile int32_t*)&kp.done[slot].status = status;
+        st_rel_sys_u32(&kp.done[slot].gen, s_gen);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace inolf
+
+// ===========================================================================
+// host side
+// ===========================================================================
+using namespace inolf;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct SlotMeta {
+  bool busy = false;
+  bool done_seen = false;
+  uint64_t ticket = 0;
+  uint32_t gen = 0;
+  size_t off = 0, bytes = 0;
+  int W = 0, H = 0;
+  Clock::time_point submitted;
+  int64_t latency_ns = 0;
+  int32_t status = 0;
+};
+
+}  // namespace
+
+struct inolf_server {
+  std::mutex mu;
+  int device = 0;
+  inolf_serve_params prm{};
+  cudaStream_t stream = nullptr;
+  cudaEvent_t kernel_done = nullptr;
+  bool launched = false;
+  int grid = 0;
+  // objects
+  std::vector<ServeObj> objs;
+  ServeObj* d_objs = nullptr;
+  bool objs_dirty = true;
+  // mapped host memory
+  ServeCtl* h_ctl = nullptr;
+  ServeCtl* d_ctl = nullptr;
+  ServeDone* h_done = nullptr;
+  ServeDone* d_done = nullptr;
+  ServeSlot* h_slots = nullptr;
+  ServeSlot* d_slots = nullptr;
+  ServeTile* h_ring = nullptr;
+  ServeTile* d_ring = nullptr;
+  unsigned long long ring_cap = 0;
+  unsigned long long published = 0;
+  // device state and frame arena
+  ServeDevState* d_st = nullptr;
+  uint8_t* arena = nullptr;
+  std::map<size_t, size_t> free_blocks;  // offset -> size
+  std::vector<SlotMeta> slots;
+  std::vector<uint32_t> slot_gen;  // last generation issued per slot
+  std::map<uint64_t, int> by_ticket;
+  uint64_t next_ticket = 1;
+};
+
+static bool arena_alloc(inolf_server* s, size_t bytes, size_t* off) {
+  for (auto it = s->free_blocks.begin(); it != s->free_blocks.end(); ++it) {
+    if (it->second >= bytes) {
+      *off = it->first;
+      const size_t rest = it->second - bytes;
+      const size_t noff = it->first + bytes;
+      s->free_blocks.erase(it);
+      if (rest) s->free_blocks[noff] = rest;
+      return true;
+    }
+  }
+  return false;
+}
+
+static void arena_free(inolf_server* s, size_t off, size_t bytes) {
+  auto it = s->free_blocks.emplace(off, bytes).first;
+  auto nx = std::next(it);
+  if (nx != s->free_blocks.end() && it->first + it->second == nx->first) {
+    it->second += nx->second;
+    s->free_blocks.erase(nx);
+  }
+  if (it != s->free_blocks.begin()) {
+    auto pv = std::prev(it);
+    if (pv->first + pv->second == it->first) {
+      pv->second += it->second;
+      s->free_blocks.erase(it);
+    }
+  }
+}
+
+static void serve_free(inolf_server* s) {
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  if (s->kernel_done) cudaEventDestroy(s->kernel_done);
+  if (s->stream) cudaStreamDestroy(s->stream);
+  if (s->h_ctl) cudaFreeHost(s->h_ctl);
+  if (s->h_done) cudaFreeHost(s->h_done);
+  if (s->h_slots) cudaFreeHost(s->h_slots);
+  if (s->h_ring) cudaFreeHost(s->h_ring);
+  if (s->d_st) cudaFree(s->d_st);
+  if (s->d_objs) cudaFree(s->d_objs);
+  if (s->arena) cudaFree(s->arena);
+  delete s;
+}
+
+static size_t serve_smem_bytes() { return (size_t)(48 * 64 + 64 * 64 + 64 * 4) * sizeof(float); }
+
+// Launches the persistent kernel if it is not running (must hold s->mu).
+static inolf_status ensure_running(inolf_server* s) {
+  if (s->launched) {
+    const cudaError_t q = cudaEventQuery(s->kernel_done);
+    if (q == cudaErrorNotReady) return INOLF_OK;
+    if (q != cudaSuccess) return fail(INOLF_E_CUDA, std::string("serve kernel: ") + cudaGetErrorString(q));
+    s->launched = false;
+  }
+  if (s->objs_dirty) {
+    if (cudaMemcpyAsync(s->d_objs, s->objs.data(), sizeof(ServeObj) * s->objs.size(), cudaMemcpyHostToDevice,
+                        s->stream) != cudaSuccess)
+      return fail(INOLF_E_CUDA, "serve: object table upload failed");
+    s->objs_dirty = false;
+  }
+  ServeKParams kp{};
+  kp.objs = s->d_objs;
+  kp.n_objs = (int32_t)s->objs.size();
+  kp.K = s->prm.max_hits;
+  kp.ctl = s->d_ctl;
+  kp.done = s->d_done;
+  kp.slots = s->d_slots;
+  kp.ring = s->d_ring;
+  kp.ring_cap = s->ring_cap;
+  kp.st = s->d_st;
+  kp.wait_limit_ns = (unsigned long long)s->prm.wait_limit_ns;
+  kp.idle_limit_ns = (unsigned long long)s->prm.idle_limit_ns;
+  sh_constants(kp.shc);
+  {
+    LaunchTimer lt("k_serve", s->stream);
+    k_serve<<<s->grid, kServeThreads, serve_smem_bytes(), s->stream>>>(kp);
+  }
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(INOLF_E_CUDA, std::string("k_serve launch: ") + cudaGetErrorString(e));
+  cudaEventRecord(s->kernel_done, s->stream);
+  s->launched = true;
+  return INOLF_OK;
+}
+
+extern "C" inolf_status inolf_serve_create(const inolf_serve_params* prm, inolf_server** out) {
+  clear_error();
+  if (!out) return fail(INOLF_E_INVALID, "inolf_serve_create: out is NULL");
+  *out = nullptr;
+  inolf_serve_params p{};
+  p.hbm_budget = (size_t)4 << 30;
+  p.max_slots = 48;
+  p.max_width = 3840;
+  p.max_height = 2160;
+  p.max_hits = 4;
+  p.wait_limit_ns = 1000000000;
+  p.idle_limit_ns = 20000000;
+  p.ctas_per_sm = 0;
+  if (prm) p = *prm;
+  if (p.hbm_budget < 4096 || p.max_slots < 1 || p.max_slots > kServeMaxSlots || p.max_width < 1 ||
+      p.max_height < 1 || p.max_width > 16384 || p.max_height > 16384 || p.max_hits < 1 ||
+      p.max_hits > kServeMaxK || p.wait_limit_ns <= 0 || p.idle_limit_ns <= 0 || p.ctas_per_sm < 0)
+    return fail(INOLF_E_INVALID, "inolf_serve_create: bad parameters");
+  inolf_server* s = new (std::nothrow) inolf_server();
+  if (!s) return fail(INOLF_E_OOM, "inolf_serve_create: oom");
+  s->prm = p;
+  cudaGetDevice(&s->device);
+  const unsigned long long tiles_max = (unsigned long long)((p.max_width + kServeTile - 1) / kServeTile) *
+                                       ((p.max_height + kServeTile - 1) / kServeTile);
+  s->ring_cap = tiles_max * (unsigned long long)p.max_slots;
+  auto bad = [&](const char* what) {
+    serve_free(s);
+    return fail(INOLF_E_OOM, std::string("inolf_serve_create: ") + what);
+  };
+  if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) return bad("stream");
+  if (cudaEventCreateWithFlags(&s->kernel_done, cudaEventDisableTiming) != cudaSuccess) return bad("event");
+  const unsigned fl = cudaHostAllocMapped | cudaHostAllocPortable;
+  if (cudaHostAlloc((void**)&s->h_ctl, sizeof(ServeCtl), fl) != cudaSuccess) return bad("control block");
+  if (cudaHostAlloc((void**)&s->h_done, sizeof(ServeDone) * p.max_slots, fl) != cudaSuccess) return bad("done");
+  if (cudaHostAlloc((void**)&s->h_slots, sizeof(ServeSlot) * p.max_slots, fl) != cudaSuccess) return bad("slots");
+  if (cudaHostAlloc((void**)&s->h_ring, sizeof(ServeTile) * s->ring_cap, fl) != cudaSuccess) return bad("ring");
+  std::memset(s->h_ctl, 0, sizeof(ServeCtl));
+  std::memset(s->h_done, 0, sizeof(ServeDone) * p.max_slots);
+  std::memset(s->h_slots, 0, sizeof(ServeSlot) * p.max_slots);
+  if (cudaHostGetDevicePointer((void**)&s->d_ctl, s->h_ctl, 0) != cudaSuccess ||
+      cudaHostGetDevicePointer((void**)&s->d_done, s->h_done, 0) != cudaSuccess ||
+      cudaHostGetDevicePointer((void**)&s->d_slots, s->h_slots, 0) != cudaSuccess ||
+      cudaHostGetDevicePointer((void**)&s->d_ring, s->h_ring, 0) != cudaSuccess)
+    return bad("mapped pointers");
+  if (cudaMalloc(&s->d_st, sizeof(ServeDevState)) != cudaSuccess) return bad("device state");
+  if (cudaMemset(s->d_st, 0, sizeof(ServeDevState)) != cudaSuccess) return bad("device state");
+  if (cudaMalloc(&s->d_objs, sizeof(ServeObj) * kServeMaxObjects) != cudaSuccess) return bad("object table");
+  if (cudaMalloc(&s->arena, p.hbm_budget) != cudaSuccess) return bad("frame arena (HBM budget)");
+  s->free_blocks[0] = p.hbm_budget;
+  s->slots.resize(p.max_slots);
+  s->slot_gen.assign(p.max_slots, 0);
+  int sms = 1, occ = 1;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+  cudaFuncSetAttribute(k_serve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)serve_smem_bytes());
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_serve, kServeThreads, serve_smem_bytes());
+  occ = std::max(1, occ);
+  if (p.ctas_per_sm > 0) occ = std::min(occ, p.ctas_per_sm);
+  s->grid = sms * occ;
+  cudaGetLastError();
+  *out = s;
+  return INOLF_OK;
+}
+
+extern "C" inolf_status inolf_serve_add_object(inolf_server* s, const inolf_object* obj, const float translation[3]) {
+  clear_error();
+  if (!s || !obj || !translation) return fail(INOLF_E_INVALID, "inolf_serve_add_object: NULL argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  for (auto& m : s->slots)
+    if (m.busy) return fail(INOLF_E_INVALID, "inolf_serve_add_object: requests are in flight");
+  if ((int)s->objs.size() >= kServeMaxObjects) return fail(INOLF_E_INVALID, "inolf_serve_add_object: 16 objects max");
+  const Object& o = obj->o;
+  ServeObj so{};
+  so.nodes = (const float4*)o.nodes;
+  so.tris = (const float4*)o.tris;
+  so.w_f32 = o.w_f32;
+  so.L = o.L;
+  so.fp16 = o.fp16;
+  so.d_in = o.d_in;
+  so.lo = o.lo;
+  so.scale = o.scale;
+  for (int k = 0; k < 3; ++k) so.T[k] = translation[k];
+  for (int l = 0; l < o.L; ++l) so.lv[l] = o.lv[l];
+  s->objs.push_back(so);
+  s->objs_dirty = true;
+  return INOLF_OK;
+}
+
+extern "C" inolf_status inolf_serve_submit(inolf_server* s, const inolf_request* r, uint64_t* ticket) {
+  clear_error();
+  if (!s || !r || !ticket) return fail(INOLF_E_INVALID, "inolf_serve_submit: NULL argument");
+  if (r->width < 1 || r->height < 1 || r->width > s->prm.max_width || r->height > s->prm.max_height)
+    return fail(INOLF_E_INVALID, "inolf_serve_submit: resolution outside (0, max]");
+  if (r->precision != INOLF_FP32) return fail(INOLF_E_UNSUPPORTED, "inolf_serve_submit: only FP32 shading is served");
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->objs.empty()) return fail(INOLF_E_INVALID, "inolf_serve_submit: no objects");
+  int slot = -1;
+  for (int k = 0; k < (int)s->slots.size(); ++k)
+    if (!s->slots[k].busy) { slot = k; break; }
+  if (slot < 0) return fail(INOLF_E_BUDGET, "inolf_serve_submit: all request slots are in use");
+  const size_t bytes = ((size_t)r->width * r->height * 16 + 255) & ~(size_t)255;
+  size_t off = 0;
+  if (!arena_alloc(s, bytes, &off)) return fail(INOLF_E_BUDGET, "inolf_serve_submit: HBM budget exhausted");
+  SlotMeta& m = s->slots[slot];
+  m = SlotMeta();
+  m.busy = true;
+  m.ticket = s->next_ticket++;
+  m.gen = ++s->slot_gen[slot];
+  if (m.gen == 0) m.gen = s->slot_gen[slot] = 1;
+  m.off = off;
+  m.bytes = bytes;
+  m.W = r->width;
+  m.H = r->height;
+  m.submitted = Clock::now();
+  s->by_ticket[m.ticket] = slot;
+  const uint32_t tx = (uint32_t)((r->width + kServeTile - 1) / kServeTile);
+  const uint32_t ty = (uint32_t)((r->height + kServeTile - 1) / kServeTile);
+  ServeSlot& hs = s->h_slots[slot];
+  hs.W = r->width;
+  hs.H = r->height;
+  hs.prec = r->precision;
+  hs.out = reinterpret_cast<float*>(s->arena + off);
+  std::memcpy(hs.cam, r->camera, sizeof(hs.cam));
+  hs.tiles_x = tx;
+  hs.tiles_total = tx * ty;
+  __atomic_store_n(&hs.cancelled, 0u, __ATOMIC_RELAXED);
+  // the generation is written last: the device reads the descriptor once it
+  // sees this generation (the test-only flag leaves it out)
+  if (!(r->flags & INOLF_REQ_TEST_DROP_DESCRIPTOR)) __atomic_store_n(&hs.gen, m.gen, __ATOMIC_RELEASE);
+  for (uint32_t y = 0; y < ty; ++y)
+    for (uint32_t x = 0; x < tx; ++x) {
+      ServeTile& e = s->h_ring[(s->published + (unsigned long long)y * tx + x) % s->ring_cap];
+      e.slot = (uint32_t)slot;
+      e.gen = m.gen;
+      e.tx = x;
+      e.ty = y;
+      e.tiles_total = tx * ty;
+    }
+  s->published += (unsigned long long)tx * ty;
+  __atomic_store_n(&s->h_ctl->published, s->published, __ATOMIC_RELEASE);
+  *ticket = m.ticket;
+  return ensure_running(s);
+}
+
+extern "C" inolf_status inolf_serve_poll(inolf_server* s, uint64_t ticket, inolf_result* res) {
+  clear_error();
+  if (!s) return fail(INOLF_E_INVALID, "inolf_serve_poll: NULL server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->by_ticket.find(ticket);
+  if (it == s->by_ticket.end()) return fail(INOLF_E_UNKNOWN_TICKET, "inolf_serve_poll: unknown ticket");
+  SlotMeta& m = s->slots[it->second];
+  if (!m.done_seen) {
+    const uint32_t g = __atomic_load_n(&s->h_done[it->second].gen, __ATOMIC_ACQUIRE);
+    if (g != m.gen) {
+      const inolf_status e = ensure_running(s);  // relaunch if the kernel went idle
+      return e != INOLF_OK ? e : INOLF_PENDING;
+    }
+    m.done_seen = true;
+    m.status = __atomic_load_n(&s->h_done[it->second].status, __ATOMIC_ACQUIRE);
+    m.latency_ns = std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now() - m.submitted).count();
+  }
+  if (res) {
+    res->frame = reinterpret_cast<const float*>(s->arena + m.off);
+    res->width = m.W;
+    res->height = m.H;
+    res->latency_ns = m.latency_ns;
+    res->rays = (int64_t)m.W * m.H;
+  }
+  if (m.status == INOLF_E_TIMEOUT) return fail(INOLF_E_TIMEOUT, "request descriptor did not arrive in time");
+  if (m.status == INOLF_E_CANCELLED) return fail(INOLF_E_CANCELLED, "request cancelled");
+  return INOLF_OK;
+}
+
+extern "C" inolf_status inolf_serve_cancel(inolf_server* s, uint64_t ticket) {
+  clear_error();
+  if (!s) return fail(INOLF_E_INVALID, "inolf_serve_cancel: NULL server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->by_ticket.find(ticket);
+  if (it == s->by_ticket.end()) return fail(INOLF_E_UNKNOWN_TICKET, "inolf_serve_cancel: unknown ticket");
+  __atomic_store_n(&s->h_slots[it->second].cancelled, 1u, __ATOMIC_RELEASE);
+  return INOLF_OK;
+}
+
+extern "C" inolf_status inolf_serve_release(inolf_server* s, uint64_t ticket) {
+  clear_error();
+  if (!s) return fail(INOLF_E_INVALID, "inolf_serve_release: NULL server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->by_ticket.find(ticket);
+  if (it == s->by_ticket.end()) return fail(INOLF_E_UNKNOWN_TICKET, "inolf_serve_release: unknown ticket");
+  SlotMeta& m = s->slots[it->second];
+  if (!m.done_seen) return fail(INOLF_E_INVALID, "inolf_serve_release: request not complete (poll first)");
+  arena_free(s, m.off, m.bytes);
+  m.busy = false;
+  s->by_ticket.erase(it);
+  return INOLF_OK;
+}
+
+extern "C" inolf_status inolf_serve_destroy(inolf_server* s) {
+  clear_error();
+  if (!s) return INOLF_OK;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    __atomic_store_n(&s->h_ctl->stop, 1u, __ATOMIC_RELEASE);
+  }
+  serve_free(s);
+  return INOLF_OK;
+}

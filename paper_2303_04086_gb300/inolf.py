@@ -18,7 +18,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libinolf.so")
 
 OK, PENDING = 0, 1
-E_INVALID, E_OOM, E_CUDA, E_BUDGET, E_TIMEOUT, E_HASH_FAILED, E_UNKNOWN_TICKET, E_UNSUPPORTED = range(-1, -9, -1)
+(E_INVALID, E_OOM, E_CUDA, E_BUDGET, E_TIMEOUT, E_HASH_FAILED, E_UNKNOWN_TICKET, E_UNSUPPORTED,
+ E_CANCELLED) = range(-1, -10, -1)
+REQ_TEST_DROP_DESCRIPTOR = 1
 FP32, BF16, FP8 = 0, 1, 2
 PRECISIONS = {"fp32": FP32, "bf16": BF16, "fp8": FP8}
 MAX_LEVELS = 16
@@ -431,3 +433,119 @@ class Field:
 
     def render(self, o, d, prec="fp32"):
         return self._fn.apply(o, d, self, prec, self.w1, self.w2, self.w3, *self.tables)
+
+
+# ---------------------------------------------------------------------------
+# serving
+# ---------------------------------------------------------------------------
+class ServeParams(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_size_t), ("max_slots", ctypes.c_int32), ("max_width", ctypes.c_int32),
+                ("max_height", ctypes.c_int32), ("max_hits", ctypes.c_int32), ("wait_limit_ns", ctypes.c_int64),
+                ("idle_limit_ns", ctypes.c_int64), ("ctas_per_sm", ctypes.c_int32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("camera", ctypes.c_float * 13), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("viewer_id", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("frame", ctypes.c_void_p), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("latency_ns", ctypes.c_int64), ("rays", ctypes.c_int64)]
+
+
+_cudart = None
+
+
+def _device_copy(dst_ptr: int, src_ptr: int, nbytes: int):
+    """cudaMemcpy (default kind) through the CUDA runtime the library uses."""
+    global _cudart
+    if _cudart is None:
+        for cand in ("/usr/local/cuda/lib64/libcudart.so.13", "libcudart.so.13", "libcudart.so"):
+            try:
+                _cudart = ctypes.CDLL(cand)
+                break
+            except OSError:
+                continue
+        _cudart.cudaMemcpy.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]
+    st = _cudart.cudaMemcpy(ctypes.c_void_p(dst_ptr), ctypes.c_void_p(src_ptr), nbytes, 4)  # cudaMemcpyDefault
+    if st != 0:
+        raise RuntimeError(f"cudaMemcpy failed ({st})")
+
+
+class Server:
+    """inolf_server: persistent-kernel request loop over resident objects."""
+
+    def __init__(self, hbm_budget=4 << 30, max_slots=48, max_width=3840, max_height=2160, max_hits=4,
+                 wait_limit_ns=1_000_000_000, idle_limit_ns=20_000_000, ctas_per_sm=0):
+        L = lib()
+        vp = ctypes.c_void_p
+        L.inolf_serve_create.argtypes = [ctypes.POINTER(ServeParams), ctypes.POINTER(vp)]
+        L.inolf_serve_add_object.argtypes = [vp, vp, vp]
+        L.inolf_serve_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
+        L.inolf_serve_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(Result)]
+        L.inolf_serve_cancel.argtypes = [vp, ctypes.c_uint64]
+        L.inolf_serve_release.argtypes = [vp, ctypes.c_uint64]
+        L.inolf_serve_destroy.argtypes = [vp]
+        prm = ServeParams(hbm_budget, max_slots, max_width, max_height, max_hits, wait_limit_ns, idle_limit_ns,
+                          ctas_per_sm)
+        h = vp()
+        _check(L.inolf_serve_create(ctypes.byref(prm), ctypes.byref(h)))
+        self._h = h.value
+        self.objects = []
+
+    def add_object(self, obj: Object, translation=(0.0, 0.0, 0.0)):
+        t = np.ascontiguousarray(translation, np.float32)
+        _check(lib().inolf_serve_add_object(self._h, obj.handle, t.ctypes.data))
+        self.objects.append(obj)
+
+    def submit(self, camera, width: int, height: int, prec="fp32", viewer_id: int = 0, flags: int = 0) -> int:
+        r = Request()
+        cam = np.ascontiguousarray(camera, np.float32).ravel()
+        for k in range(13):
+            r.camera[k] = float(cam[k])
+        r.width, r.height = width, height
+        r.precision = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+        r.viewer_id, r.flags = viewer_id, flags
+        t = ctypes.c_uint64()
+        _check(lib().inolf_serve_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket: int):
+        """(status, Result): status is OK, PENDING or a negative error code."""
+        res = Result()
+        st = lib().inolf_serve_poll(self._h, ticket, ctypes.byref(res))
+        return st, res
+
+    def wait(self, ticket: int, timeout_s: float = 60.0):
+        import time
+        t0 = time.monotonic()
+        while True:
+            st, res = self.poll(ticket)
+            if st != PENDING:
+                return st, res
+            if time.monotonic() - t0 > timeout_s:
+                raise TimeoutError(f"request {ticket} still pending after {timeout_s} s")
+            time.sleep(0.0002)
+
+    def frame(self, res: Result):
+        """Copy a completed frame into a new CUDA tensor [H, W, 4]."""
+        import torch
+        out = torch.empty((res.height, res.width, 4), dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        _device_copy(out.data_ptr(), res.frame, res.height * res.width * 16)
+        return out
+
+    def cancel(self, ticket: int):
+        _check(lib().inolf_serve_cancel(self._h, ticket))
+
+    def release(self, ticket: int):
+        _check(lib().inolf_serve_release(self._h, ticket))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().inolf_serve_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()

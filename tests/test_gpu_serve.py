@@ -1,0 +1,193 @@
+"""Serving (continuous batching in a persistent kernel) through the C ABI:
+one object == inolf_render; each request's frame is the same alone and in a
+mix of concurrent requests; multi-object depth compositing against the FP64
+oracle; admission by slots and HBM budget; bounded device waits (a dropped
+request descriptor ends in INOLF_E_TIMEOUT); cancel; idle exit and relaunch."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2303_04086_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2303_04086_gb300 import build, inolf
+    build.build()
+    scenes = [synth.tiny_scene(seed=s) for s in range(4)]
+    objs = [inolf.object_create(sc) for sc in scenes]
+    return torch, inolf, scenes, objs
+
+
+PLACES = [(0.0, 0.0, 0.0), (2.2, 0.3, -1.0), (-1.9, -0.4, -2.5), (0.4, 1.8, 1.2)]
+
+
+def _done(srv, t):
+    st, res = srv.wait(t)
+    return st, res
+
+
+def test_single_object_equals_render(env):
+    torch, inolf, scenes, objs = env
+    srv = inolf.Server(hbm_budget=64 << 20, max_slots=4, max_width=512, max_height=512)
+    srv.add_object(objs[0], (0.0, 0.0, 0.0))
+    cam = synth.camera((0.3, 0.2, 3.0))
+    for W, H in [(128, 128), (37, 23)]:
+        t = srv.submit(cam, W, H)
+        st, res = _done(srv, t)
+        assert st == inolf.OK
+        got = srv.frame(res).cpu().numpy()
+        ref = inolf.render(objs[0], cam[None], W, H).cpu().numpy()[0]
+        assert np.abs(got - ref).max() <= TOL
+        assert res.latency_ns > 0 and res.rays == W * H
+        srv.release(t)
+    srv.close()
+
+
+def _multi_server(inolf, objs, **kw):
+    srv = inolf.Server(**kw)
+    for o, p in zip(objs, PLACES):
+        srv.add_object(o, p)
+    return srv
+
+
+def test_alone_equals_in_the_mix(env):
+    torch, inolf, scenes, objs = env
+    srv = _multi_server(inolf, objs, hbm_budget=512 << 20, max_slots=32, max_width=1024, max_height=1024)
+    cam = synth.camera((1.0, 2.0, 9.0), target=(0.0, 0.0, -0.5))
+    t = srv.submit(cam, 320, 200)
+    st, res = _done(srv, t)
+    assert st == inolf.OK
+    alone = srv.frame(res).cpu().numpy()
+    srv.release(t)
+    assert (alone[..., 3] > 0).mean() > 0.05
+    # the same request submitted among 24 others of mixed sizes and cameras
+    rng = np.random.default_rng(0)
+    tickets, mine = [], None
+    for k in range(25):
+        if k == 12:
+            mine = srv.submit(cam, 320, 200)
+            tickets.append(mine)
+            continue
+        e = rng.normal(size=3)
+        e = 9.0 * e / np.linalg.norm(e)
+        W, H = [(64, 64), (256, 144), (400, 300), (1024, 576)][k % 4]
+        tickets.append(srv.submit(synth.camera(tuple(e)), W, H))
+    frames = {}
+    for t in tickets:
+        st, res = _done(srv, t)
+        assert st == inolf.OK
+        if t == mine:
+            frames[t] = srv.frame(res).cpu().numpy()
+        srv.release(t)
+    assert np.abs(frames[mine] - alone).max() <= TOL
+    srv.close()
+
+
+def test_multi_object_composite_matches_oracle(env):
+    torch, inolf, scenes, objs = env
+    srv = _multi_server(inolf, objs, hbm_budget=64 << 20, max_slots=4, max_width=256, max_height=256)
+    cam = synth.camera((0.5, 1.0, 8.0), target=(0.2, 0.3, -0.8))
+    W = H = 160
+    t = srv.submit(cam, W, H)
+    st, res = _done(srv, t)
+    assert st == inolf.OK
+    got = srv.frame(res).cpu().numpy().reshape(-1, 4)
+    srv.release(t)
+    srv.close()
+    # FP64 reference: every object in its local frame, (t, id)-ordered over
+    o, d = oracle.raygen(cam, W, H)
+    per = []
+    for sc, pl in zip(scenes, PLACES):
+        ol = (o - np.float32(pl)).astype(np.float32)   # the same FP32 subtraction
+        r = oracle.Oracle(sc).render_rays(ol, d)
+        per.append(r)
+    ref = np.zeros((W * H, 4))
+    nhit = 0
+    for px in range(W * H):
+        hits = sorted((per[k]["t"][px], k) for k in range(len(per)) if per[k]["tri"][px] >= 0)[:4]
+        C, A = np.zeros(3), 0.0
+        for _, k in hits:
+            c = per[k]["rgba"][px]
+            w = (1 - A) * c[3]
+            C += w * c[:3]
+            A += w
+        if A > 0:
+            ref[px, :3] = C / A
+            ref[px, 3] = A
+        nhit += len(hits) > 1
+    assert nhit > 20  # some pixels see more than one object
+    assert np.abs(got - ref).max() <= TOL
+
+
+def test_admission_by_budget_and_slots(env):
+    torch, inolf, scenes, objs = env
+    frame = 256 * 256 * 16
+    srv = inolf.Server(hbm_budget=2 * frame + 1024, max_slots=3, max_width=256, max_height=256)
+    srv.add_object(objs[0])
+    cam = synth.camera((0.0, 0.0, 3.0))
+    a = srv.submit(cam, 256, 256)
+    b = srv.submit(cam, 256, 256)
+    with pytest.raises(inolf.InolfError) as e:
+        srv.submit(cam, 256, 256)      # frame does not fit the budget
+    assert e.value.status == inolf.E_BUDGET
+    c = srv.submit(cam, 16, 16)        # a small one still fits
+    with pytest.raises(inolf.InolfError) as e:
+        srv.submit(cam, 8, 8)          # no slot left
+    assert e.value.status == inolf.E_BUDGET
+    for t in (a, b, c):
+        assert _done(srv, t)[0] == inolf.OK
+        srv.release(t)
+    t = srv.submit(cam, 256, 256)      # admitted again after release
+    assert _done(srv, t)[0] == inolf.OK
+    srv.release(t)
+    with pytest.raises(inolf.InolfError) as e:
+        srv.release(12345)
+    assert e.value.status == inolf.E_UNKNOWN_TICKET
+    assert srv.poll(777)[0] == inolf.E_UNKNOWN_TICKET
+    srv.close()
+
+
+def test_dropped_descriptor_times_out(env):
+    torch, inolf, scenes, objs = env
+    srv = inolf.Server(hbm_budget=16 << 20, max_slots=2, max_width=64, max_height=64, wait_limit_ns=2_000_000)
+    srv.add_object(objs[0])
+    cam = synth.camera((0.0, 0.0, 3.0))
+    bad = srv.submit(cam, 32, 32, flags=inolf.REQ_TEST_DROP_DESCRIPTOR)
+    st, _ = srv.wait(bad, timeout_s=30)
+    assert st == inolf.E_TIMEOUT
+    srv.release(bad)
+    good = srv.submit(cam, 32, 32)     # the server keeps working
+    assert srv.wait(good)[0] == inolf.OK
+    srv.release(good)
+    srv.close()
+
+
+def test_cancel_and_idle_relaunch(env):
+    torch, inolf, scenes, objs = env
+    srv = inolf.Server(hbm_budget=256 << 20, max_slots=4, max_width=2048, max_height=2048,
+                       idle_limit_ns=5_000_000)
+    srv.add_object(objs[0])
+    cam = synth.camera((0.0, 0.0, 3.0))
+    t = srv.submit(cam, 2048, 2048)
+    srv.cancel(t)
+    st, _ = srv.wait(t)
+    assert st in (inolf.E_CANCELLED, inolf.OK)
+    srv.release(t)
+    time.sleep(0.05)                   # longer than the idle limit: the kernel has exited
+    t = srv.submit(cam, 64, 64)
+    st, res = srv.wait(t)
+    assert st == inolf.OK
+    ref = inolf.render(objs[0], cam[None], 64, 64).cpu().numpy()[0]
+    assert np.abs(srv.frame(res).cpu().numpy() - ref).max() <= TOL
+    srv.release(t)
+    srv.close()
