@@ -132,7 +132,7 @@ def test_multi_object_composite_matches_oracle(env):
 def test_admission_by_budget_and_slots(env):
     torch, inolf, scenes, objs = env
     frame = 256 * 256 * 16
-    srv = inolf.Server(hbm_budget=2 * frame + 1024, max_slots=3, max_width=256, max_height=256)
+    srv = inolf.Server(hbm_budget=2 * frame + 16 * 16 * 16, max_slots=3, max_width=256, max_height=256)
     srv.add_object(objs[0])
     cam = synth.camera((0.0, 0.0, 3.0))
     a = srv.submit(cam, 256, 256)
