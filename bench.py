@@ -47,6 +47,8 @@ def _args():
     ap.add_argument("--views", type=int, default=N_VIEWS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precisions", default="fp32,bf16,fp8")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-seconds", type=float, default=10.0)
     return ap.parse_args()
 
 
@@ -188,6 +190,137 @@ def cpu_baseline(scene, cams, W, H, budget_s=12.0, orc=None):
     return {"value": rate / 1e6, "unit": "Mrays/s", "cores": oracle.max_threads(), "kind": "oracle",
             "sample": f"{total_rays} rays: seeded random pixel subsets (2000, x4 per round) of view 0 "
                       f"({W}x{H}), FP64 oracle, {spent:.1f} s of CPU work"}
+
+
+def serving_workload(seed: int = 0):
+    """12 tiny-scene objects (seeds 0-11) placed without bounding-sphere
+    overlap in a 10 m cube; 32 viewers on a 12 m sphere around the cube
+    centre, each with its resolution drawn from 720p / 1080p / 4K."""
+    from paper_2303_04086_gb300 import synth
+    rng = np.random.default_rng(seed)
+    places = []
+    while len(places) < 12:
+        p = rng.uniform(-4.0, 4.0, size=3)  # centres keep the r = 1.1 proxies inside the 10 m cube
+        if all(np.linalg.norm(p - q) > 2.3 for q in places):
+            places.append(p)
+    scenes = [synth.tiny_scene(seed=s) for s in range(12)]
+    res = [(1280, 720), (1920, 1080), (3840, 2160)]
+    viewers = []
+    for v in range(32):
+        d = rng.normal(size=3)
+        viewers.append({"dir": d / np.linalg.norm(d), "res": res[rng.integers(0, 3)]})
+    return scenes, [tuple(map(float, p)) for p in places], viewers
+
+
+def run_serving(seconds=10.0, warmup=1.0, rate_hz=50.0, seed=0):
+    """Poisson frame requests of 32 viewers against the persistent request
+    loop; returns p50/p99 submit->complete latency, throughput, refusals."""
+    import heapq
+    from paper_2303_04086_gb300 import inolf, synth
+    scenes, places, viewers = serving_workload(seed)
+    srv = inolf.Server(hbm_budget=8 << 30, max_slots=64, max_width=3840, max_height=2160, max_hits=4)
+    objs = [inolf.object_create(sc) for sc in scenes]
+    for o, p in zip(objs, places):
+        srv.add_object(o, p)
+    rng = np.random.default_rng(seed + 1)
+    events = [(rng.exponential(1.0 / rate_hz), v) for v in range(len(viewers))]
+    heapq.heapify(events)
+    inflight = {}
+    lat, rays_done, frames, refused, submitted = [], 0, 0, 0, 0
+    t0 = time.perf_counter()
+    end = warmup + seconds
+    frame_no = [0] * len(viewers)
+    while True:
+        now = time.perf_counter() - t0
+        while events and events[0][0] <= now and events[0][0] < end:
+            ta, v = heapq.heappop(events)
+            vw = viewers[v]
+            frame_no[v] += 1
+            ang = 0.02 * frame_no[v]  # small orbit per frame
+            axis = np.cross(vw["dir"], [0.0, 1.0, 0.0])
+            axis = axis / (np.linalg.norm(axis) + 1e-12)
+            dv = vw["dir"] * np.cos(ang) + np.cross(axis, vw["dir"]) * np.sin(ang)
+            cam = synth.camera(tuple(12.0 * dv))
+            W, H = vw["res"]
+            try:
+                t = srv.submit(cam, W, H, "fp32", viewer_id=v)
+                inflight[t] = (ta, W * H)
+                submitted += 1
+            except inolf.InolfError as e:
+                if e.status != inolf.E_BUDGET:
+                    raise
+                if ta >= warmup:
+                    refused += 1
+            heapq.heappush(events, (ta + rng.exponential(1.0 / rate_hz), v))
+        for t in list(inflight):
+            st, res = srv.poll(t)
+            if st == inolf.PENDING:
+                continue
+            ta, npx = inflight.pop(t)
+            done_t = time.perf_counter() - t0
+            if ta >= warmup and st == inolf.OK:
+                lat.append(done_t - ta)
+                rays_done += npx
+                frames += 1
+            srv.release(t)
+        if now >= end and not inflight:
+            break
+        time.sleep(0.0002)
+    wall = time.perf_counter() - t0 - warmup
+    srv.close()
+    lat_ms = np.array(lat) * 1e3
+    return {"viewers": len(viewers), "objects": len(objs), "rate_hz_per_viewer": rate_hz, "seconds": seconds,
+            "frames": frames, "frames_per_s": frames / wall, "mrays_per_s": rays_done / wall / 1e6,
+            "p50_ms": float(np.percentile(lat_ms, 50)) if len(lat_ms) else None,
+            "p99_ms": float(np.percentile(lat_ms, 99)) if len(lat_ms) else None,
+            "refused": refused, "submitted": submitted, "precision": "fp32",
+            "note": "latency = arrival time -> completion seen by the poller; refused = admission (slots/HBM "
+                    "budget) full at arrival"}
+
+
+def run_training(steps=40, batch=1 << 18, n_views=100, res=800, prec="bf16"):
+    """Differentiation workload: a teacher object (seed 1) renders 100 target
+    views at 800x800; a student (seed 2) trains toward them with batches of
+    2^18 random (view, pixel) rays, L2 loss (Eq. 8), Adam lr 1e-2, forward MLP
+    in `prec`, FP32 backward with atomic scatter into the feature tables."""
+    import torch
+    from paper_2303_04086_gb300 import inolf, synth
+    teacher = inolf.object_create(synth.tiny_scene(seed=1))
+    field = inolf.Field(synth.tiny_scene(seed=2))
+    cams = synth.fibonacci_cameras(n_views, 3.0)
+    tgt = inolf.render(teacher, cams, res, res).reshape(-1, 4)
+    # rays of all target pixels (inputs: any FP32 rays will do)
+    c = torch.from_numpy(np.ascontiguousarray(cams)).cuda()
+    jj, ii = torch.meshgrid(torch.arange(res, device="cuda"), torch.arange(res, device="cuda"), indexing="ij")
+    a = ((2 * ii + 1).float() / res - 1).reshape(-1) * c[:, 12:13]
+    b = (1 - (2 * jj + 1).float() / res).reshape(-1) * c[:, 12:13]
+    d = a[..., None] * c[:, None, 3:6] + b[..., None] * c[:, None, 6:9] + c[:, None, 9:12]
+    d = (d / d.norm(dim=-1, keepdim=True)).reshape(-1, 3).contiguous()
+    o = c[:, None, 0:3].expand(-1, res * res, -1).reshape(-1, 3).contiguous()
+    opt = torch.optim.Adam(field.parameters(), lr=1e-2, betas=(0.9, 0.99), eps=1e-15)
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    losses = []
+
+    def one():
+        idx = torch.randint(0, o.shape[0], (batch,), device="cuda", generator=gen)
+        pred = field.render(o[idx], d[idx], prec)
+        loss = ((pred - tgt[idx]) ** 2).sum(1).mean()
+        opt.zero_grad()
+        loss.backward()
+        opt.step()
+        return loss
+
+    for _ in range(3):
+        losses.append(float(one().detach()))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        losses.append(float(one().detach()))
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"steps_per_s": steps / dt, "rays_per_step": batch, "mrays_per_s": steps * batch / dt / 1e6,
+            "loss_first": losses[0], "loss_last": losses[-1], "forward": prec, "backward": "fp32",
+            "views": n_views, "res": res}
 
 
 def run_reference(a):
@@ -376,6 +509,11 @@ def run_native(a):
            "precisions": precisions, "hit_mrays_per_s": n_hit * a.steps * world / (ms / 1e3) / 1e6}
     if fp32_acc is not None:
         out["accuracy_vs_oracle"] = fp32_acc
+    if rank == 0 and not a.no_serving and not a.small:
+        del rgba, ws
+        torch.cuda.empty_cache()
+        out["serving"] = run_serving(seconds=a.serving_seconds)
+        out["training"] = run_training()
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
