@@ -155,6 +155,14 @@ def make_workload(small: bool, views: int):
     return scene, cams, W4K, H4K, {"workload": desc}
 
 
+# DRAM bytes (read + write) per hit ray of the current shade kernels, from one
+# ncu capture of a one-view launch of the full workload (cold L2), see
+# profiles/k_shade_f32_tiled_full_1view.md: 1.357 GB + 0.070 GB for 4 010 637
+# hit rays.  Traffic grows in proportion to the hit rays rendered, so a launch's
+# traffic is this figure times its hit rays.  None once the kernel changes.
+DRAM_BYTES_PER_HIT = {"k_shade_f32": (1.357024e9 + 69.943808e6) / 4010637}
+
+
 def algorithmic_bytes_per_hit(scene) -> int:
     # per hit ray: L levels x 8 corners x (F features + 4-byte Phi entry)
     fb = 2 if scene.feature_fp16 else 4
@@ -462,9 +470,12 @@ def run_native(a):
             byt = algorithmic_bytes_per_hit(scene) * hits_per_launch + 16 * hits_per_launch + 8 * hits_per_launch
             achieved = byt / avg_s / 1e9
             peak = peaks.get("hbm_gbs", 6800.0)
+            tpb = DRAM_BYTES_PER_HIT.get(top) if not a.small else None
             roof = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak, "traffic": None,
-                    "mlp_tflops": mlp_flops_per_hit(scene) * hits_per_launch / avg_s / 1e12}
+                    "frac": achieved / peak, "traffic": tpb * hits_per_launch if tpb else None,
+                    "algorithmic_bytes_per_launch": byt,
+                    "mlp_tflops": mlp_flops_per_hit(scene) * hits_per_launch / avg_s / 1e12,
+                    "mlp_frac_of_fp32_peak": mlp_flops_per_hit(scene) * hits_per_launch / avg_s / 80.5e12}
         else:
             rays_per_launch = n_rays / max(1, st["launches"] // a.steps)
             byt = 16 * rays_per_launch + 8 * hits_per_launch
