@@ -220,7 +220,7 @@ def serving_workload(seed: int = 0):
     return scenes, [tuple(map(float, p)) for p in places], viewers
 
 
-def run_serving(seconds=10.0, warmup=1.0, rate_hz=50.0, seed=0):
+def run_serving(seconds=10.0, warmup=1.0, rate_hz=50.0, seed=0, prec="bf16"):
     """Poisson frame requests of 32 viewers against the persistent request
     loop; returns p50/p99 submit->complete latency, throughput, refusals."""
     import heapq
@@ -251,7 +251,7 @@ def run_serving(seconds=10.0, warmup=1.0, rate_hz=50.0, seed=0):
             cam = synth.camera(tuple(12.0 * dv))
             W, H = vw["res"]
             try:
-                t = srv.submit(cam, W, H, "fp32", viewer_id=v)
+                t = srv.submit(cam, W, H, prec, viewer_id=v)
                 inflight[t] = (ta, W * H)
                 submitted += 1
             except inolf.InolfError as e:
@@ -281,7 +281,7 @@ def run_serving(seconds=10.0, warmup=1.0, rate_hz=50.0, seed=0):
             "frames": frames, "frames_per_s": frames / wall, "mrays_per_s": rays_done / wall / 1e6,
             "p50_ms": float(np.percentile(lat_ms, 50)) if len(lat_ms) else None,
             "p99_ms": float(np.percentile(lat_ms, 99)) if len(lat_ms) else None,
-            "refused": refused, "submitted": submitted, "precision": "fp32",
+            "refused": refused, "submitted": submitted, "precision": prec,
             "note": "latency = arrival time -> completion seen by the poller; refused = admission (slots/HBM "
                     "budget) full at arrival"}
 

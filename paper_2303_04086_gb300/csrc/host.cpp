@@ -463,6 +463,27 @@ extern "C" inolf_status inolf_object_create(const inolf_object_desc* desc, void*
   o.scale = D.domain_scale;
   for (int k = 0; k < 3; ++k) o.fp8_act_scale[k] = D.fp8_act_scale[k];
 
+  // --- bounding sphere of the proxy (box centre, farthest vertex), padded
+  //     so that FP32 rounding of the ray-sphere test never culls a hit ---
+  {
+    double lo3[3] = {1e300, 1e300, 1e300}, hi3[3] = {-1e300, -1e300, -1e300};
+    for (int32_t v = 0; v < D.n_vertices; ++v)
+      for (int k = 0; k < 3; ++k) {
+        lo3[k] = std::min(lo3[k], (double)D.vertices[3 * v + k]);
+        hi3[k] = std::max(hi3[k], (double)D.vertices[3 * v + k]);
+      }
+    double c[3], r2 = 0.0;
+    for (int k = 0; k < 3; ++k) c[k] = 0.5 * (lo3[k] + hi3[k]);
+    for (int32_t v = 0; v < D.n_vertices; ++v) {
+      double q = 0.0;
+      for (int k = 0; k < 3; ++k) q += (D.vertices[3 * v + k] - c[k]) * (D.vertices[3 * v + k] - c[k]);
+      r2 = std::max(r2, q);
+    }
+    const double r = std::sqrt(r2);
+    for (int k = 0; k < 3; ++k) o.bsphere[k] = (float)c[k];
+    o.bsphere[3] = (float)(r * 1.001 + 1e-3 * (1.0 + std::fabs(c[0]) + std::fabs(c[1]) + std::fabs(c[2]) + r));
+  }
+
   // --- BVH ---
   Builder b;
   b.V = D.vertices;

@@ -31,6 +31,7 @@ struct Object {
   int L = 0, F = 2, d_in = 0;
   int fp16 = 0;
   float lo = -1.5f, scale = 1.0f / 3.0f;
+  float bsphere[4] = {0, 0, 0, 0};  // proxy bounding sphere (centre, padded radius), object frame
   LevelDev lv[INOLF_MAX_LEVELS] = {};
   int64_t rows[INOLF_MAX_LEVELS] = {};
   // BVH: nodes are 4 x float4 (child boxes x, y, z + child refs), triangles

@@ -34,46 +34,19 @@
 #include "inolf_internal.h"
 #include "kernels_common.cuh"
 #include "tc_ptx.cuh"
+#include "tc_mlp.cuh"
 
 namespace inolf {
 
-static constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s: MMAs of a tile take microseconds
 static constexpr int kTcThreads = 256;
 static constexpr uint32_t kTmemCols = 128;  // 2 tiles x 64 FP32 columns
-
-__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
-  __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
-  return *reinterpret_cast<uint32_t*>(&v);
-}
-__device__ __forceinline__ uint16_t pack_fp8(float a, float b) {
-  return (uint16_t)__nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
-}
-__device__ __forceinline__ float round_bf16(float a) { return __bfloat162float(__float2bfloat16_rn(a)); }
-__device__ __forceinline__ float round_fp8(float a) {
-  __half_raw h = __nv_cvt_fp8_to_halfraw(__nv_cvt_float_to_fp8(a, __NV_SATFINITE, __NV_E4M3), __NV_E4M3);
-  return __half2float(__half(h));
-}
-
-// stores the pair (a, b) of input column k (even) of row `row`
-template <bool kFP8>
-__device__ __forceinline__ void store_pair(uint8_t* A, uint32_t row, uint32_t k, uint32_t chunks, float a, float b,
-                                           float inv_scale) {
-  if (kFP8) {
-    const uint32_t off = tc::core_off(row, k >> 4, chunks) + (k & 15u);
-    *reinterpret_cast<uint16_t*>(A + off) = pack_fp8(a * inv_scale, b * inv_scale);
-  } else {
-    const uint32_t off = tc::core_off(row, k >> 3, chunks) + (k & 7u) * 2u;
-    *reinterpret_cast<uint32_t*>(A + off) = pack_bf16(a, b);
-  }
-}
 
 template <bool kFP8>
 __global__ void __launch_bounds__(kTcThreads, 4) k_shade_tc(const __grid_constant__ Params p) {
   extern __shared__ __align__(1024) uint8_t smem[];
   constexpr uint32_t ES = kFP8 ? 1u : 2u;  // operand element bytes
-  constexpr uint32_t KSTEP_CHUNKS = 2;     // one MMA consumes 32 bytes of K per row
   const uint32_t K1 = (uint32_t)p.tc_k1;
-  const uint32_t chunks1 = K1 * ES / 16u, chunks2 = 64u * ES / 16u;
+  const uint32_t chunks1 = K1 * ES / 16u;
   const uint32_t wbytes = p.tc_wbytes;
   uint8_t* sB1 = smem;
   uint8_t* sB2 = smem + 64u * K1 * ES;
@@ -101,17 +74,10 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_shade_tc(const __grid_constan
   tc::fence_after();
   const uint32_t tmem = *tslot;
 
-  // precision-dependent scales (FP8: per-tensor, amax / 448)
-  const float inv_sx = kFP8 ? 1.0f / p.fp8_act_scale[0] : 1.0f;
-  const float mul1 = kFP8 ? p.fp8_act_scale[0] * p.fp8_w_scale[0] : 1.0f;
-  const float inv_sh1 = kFP8 ? 1.0f / p.fp8_act_scale[1] : 1.0f;
-  const float mul2 = kFP8 ? p.fp8_act_scale[1] * p.fp8_w_scale[1] : 1.0f;
-  const float sh2 = kFP8 ? p.fp8_act_scale[2] : 1.0f;
-  const float inv_sh2 = kFP8 ? 1.0f / p.fp8_act_scale[2] : 1.0f;
-  const uint32_t id = tc::idesc(128, 64, kFP8 ? 0u : 1u);
+  const TcScales sc = TcScales::make(kFP8, p.fp8_act_scale, p.fp8_w_scale);
+  const float inv_sx = sc.inv_sx;
   const uint32_t t = (uint32_t)tid >> 7, row = (uint32_t)tid & 127u;
   uint8_t* A = sA + t * tile_bytes;
-  const uint32_t lane_base = ((uint32_t)(warp & 3) * 32u) << 16;
   const int din = p.d_in;
   uint32_t phase = 0;
   const uint32_t total = *p.counter;
@@ -139,89 +105,12 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_shade_tc(const __grid_constan
       for (uint32_t c = 0; c < chunks1; ++c)
         *reinterpret_cast<uint4*>(A + tc::core_off(row, c, chunks1)) = make_uint4(0, 0, 0, 0);
     }
-    tc::fence_async_smem();
-    __syncthreads();
-    // ---- 2. D1 = A1 W1^T ----
-    if (tid == 0) {
-      tc::fence_after();
-      for (uint32_t tt = 0; tt < 2; ++tt) {
-        const uint32_t a0 = tc::smem_u32(sA + tt * tile_bytes), b0 = tc::smem_u32(sB1);
-        for (uint32_t s = 0; s < chunks1 / KSTEP_CHUNKS; ++s) {
-          const uint64_t ad = tc::desc_kmajor(a0 + s * 256u, 128u, chunks1 * 128u);
-          const uint64_t bd = tc::desc_kmajor(b0 + s * 256u, 128u, chunks1 * 128u);
-          if (kFP8) tc::mma_fp8(tmem + tt * 64u, ad, bd, id, s > 0);
-          else tc::mma_bf16(tmem + tt * 64u, ad, bd, id, s > 0);
-        }
-      }
-      tc::mma_commit(&bars[1]);
+    float4 rgba;
+    if (!tc_mlp_run<kFP8>(sA, sB1, sB2, sW3, K1, tmem, &bars[1], phase, sc, rgba)) {
+      bad = true;
+      break;
     }
-    ok = tc::mbar_wait(&bars[1], phase, kWaitLimitNs);
-    phase ^= 1u;
-    if (__syncthreads_or(!ok)) { bad = true; break; }
-    tc::fence_after();
-    // ---- 3. ReLU, quantise -> A2 row ----
-#pragma unroll 1
-    for (uint32_t c = 0; c < 4; ++c) {
-      float v[16];
-      tc::tmem_ld16(tmem + lane_base + t * 64u + c * 16u, v);
-      if (kFP8) {
-        uint32_t w[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float a0 = fmaxf(v[4 * q + 0] * mul1, 0.f) * inv_sh1, a1 = fmaxf(v[4 * q + 1] * mul1, 0.f) * inv_sh1;
-          const float a2 = fmaxf(v[4 * q + 2] * mul1, 0.f) * inv_sh1, a3 = fmaxf(v[4 * q + 3] * mul1, 0.f) * inv_sh1;
-          w[q] = (uint32_t)pack_fp8(a0, a1) | ((uint32_t)pack_fp8(a2, a3) << 16);
-        }
-        *reinterpret_cast<uint4*>(A + tc::core_off(row, c, chunks2)) = make_uint4(w[0], w[1], w[2], w[3]);
-      } else {
-        uint32_t w[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) w[q] = pack_bf16(fmaxf(v[2 * q], 0.f), fmaxf(v[2 * q + 1], 0.f));
-        *reinterpret_cast<uint4*>(A + tc::core_off(row, 2 * c, chunks2)) = make_uint4(w[0], w[1], w[2], w[3]);
-        *reinterpret_cast<uint4*>(A + tc::core_off(row, 2 * c + 1, chunks2)) = make_uint4(w[4], w[5], w[6], w[7]);
-      }
-    }
-    tc::fence_before();
-    tc::fence_async_smem();
-    __syncthreads();
-    // ---- 4. D2 = A2 W2^T ----
-    if (tid == 0) {
-      tc::fence_after();
-      for (uint32_t tt = 0; tt < 2; ++tt) {
-        const uint32_t a0 = tc::smem_u32(sA + tt * tile_bytes), b0 = tc::smem_u32(sB2);
-        for (uint32_t s = 0; s < chunks2 / KSTEP_CHUNKS; ++s) {
-          const uint64_t ad = tc::desc_kmajor(a0 + s * 256u, 128u, chunks2 * 128u);
-          const uint64_t bd = tc::desc_kmajor(b0 + s * 256u, 128u, chunks2 * 128u);
-          if (kFP8) tc::mma_fp8(tmem + tt * 64u, ad, bd, id, s > 0);
-          else tc::mma_bf16(tmem + tt * 64u, ad, bd, id, s > 0);
-        }
-      }
-      tc::mma_commit(&bars[1]);
-    }
-    ok = tc::mbar_wait(&bars[1], phase, kWaitLimitNs);
-    phase ^= 1u;
-    if (__syncthreads_or(!ok)) { bad = true; break; }
-    tc::fence_after();
-    // ---- 5. ReLU, quantise, W3, sigmoid ----
-    float out0 = 0.f, out1 = 0.f, out2 = 0.f, out3 = 0.f;
-#pragma unroll 1
-    for (uint32_t c = 0; c < 4; ++c) {
-      float v[16];
-      tc::tmem_ld16(tmem + lane_base + t * 64u + c * 16u, v);
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        float a = fmaxf(v[j] * mul2, 0.f);
-        a = kFP8 ? round_fp8(a * inv_sh2) * sh2 : round_bf16(a);
-        const uint32_t col = c * 16u + (uint32_t)j;
-        out0 += sW3[0 * 64 + col] * a;
-        out1 += sW3[1 * 64 + col] * a;
-        out2 += sW3[2 * 64 + col] * a;
-        out3 += sW3[3 * 64 + col] * a;
-      }
-    }
-    if (valid) p.rgba[p.ray_base + ray] = make_float4(sigmoidf_(out0), sigmoidf_(out1), sigmoidf_(out2), sigmoidf_(out3));
-    tc::fence_before();
-    __syncthreads();
+    if (valid) p.rgba[p.ray_base + ray] = rgba;
   }
   if (bad) {
     if (tid == 0) atomicOr(p.counter + 1, 4u);

@@ -36,6 +36,8 @@
 
 #include "inolf_internal.h"
 #include "kernels_common.cuh"
+#include "tc_mlp.cuh"
+#include "tc_ptx.cuh"
 
 namespace inolf {
 
@@ -45,14 +47,19 @@ static constexpr int kServeTile = 16;
 static constexpr int kServeThreads = kServeTile * kServeTile;
 static constexpr int kServeMaxSlots = 256;
 static constexpr int kServeMaxDin = 2 * INOLF_MAX_LEVELS + INOLF_N_SH;
+static constexpr unsigned long long kServeClaim = 16;  // tiles claimed per atomic
 
 struct ServeObj {
   const float4* nodes;
   const float4* tris;
   const float* w_f32;
+  const void* w_bf16;      // tensor-core operand blob (BF16)
+  int32_t tc_k1_bf16;
+  uint32_t tc_bytes_bf16;
   int32_t L, fp16, d_in, pad;
   float lo, scale;
   float T[3];  // object placement: local = world - T
+  float bs_c[3], bs_r2;  // bounding sphere of the proxy (local frame), padded
   LevelDev lv[INOLF_MAX_LEVELS];
 };
 
@@ -65,8 +72,9 @@ struct ServeSlot {  // mapped host memory, written by the host at submission
   uint32_t cancelled;
 };
 
-struct ServeTile {  // ring entry, mapped host memory
-  uint32_t slot, gen, tx, ty, tiles_total, pad;
+struct __align__(16) ServeTile {  // ring entry, mapped host memory (two 16-byte loads)
+  uint32_t slot, gen, tx, ty;
+  uint32_t tiles_total, pad0, pad1, pad2;
 };
 
 struct ServeDone {  // completion record, mapped host memory, written by the device
@@ -120,6 +128,14 @@ __device__ __forceinline__ uint32_t ld_acq_sys_u32(const uint32_t* p) {
 }
 __device__ __forceinline__ uint32_t ld_vol_u32(const uint32_t* p) { return *(const volatile uint32_t*)p; }
 __device__ __forceinline__ float ld_vol_f32(const float* p) { return *(const volatile float*)p; }
+__device__ __forceinline__ uint4 ld_vol_v4(const void* p) {
+  uint4 v;
+  asm volatile("ld.volatile.global.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p)
+               : "memory");
+  return v;
+}
 __device__ __forceinline__ void st_rel_sys_u32(uint32_t* p, uint32_t v) {
   asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -165,74 +181,130 @@ __device__ __forceinline__ float4 mlp_f32(const float4* W1T, const float4* W2, c
   return make_float4(sigmoidf_(acc.x), sigmoidf_(acc.y), sigmoidf_(acc.z), sigmoidf_(acc.w));
 }
 
-__global__ void __launch_bounds__(kServeThreads) k_serve(const __grid_constant__ ServeKParams kp) {
-  extern __shared__ float4 smem4[];  // FP32 weights of the object being shaded
+// Shared-memory plan of k_serve (dynamic part):
+//   [0, kServeWBytes)      FP32 weights of one object (FP32 requests) or its
+//                           BF16 operand blob (BF16 requests)
+//   A tiles                2 x 128 rows x 64 BF16 (tensor-core operand)
+//   rgba of every hit      256 pixels x K float4
+//   hit list by object     256 x K u16 (pixel * K + rank)
+//   2 mbarriers + TMEM address slot
+static constexpr uint32_t kServeWBytes = (48 * 64 + 64 * 64 + 64 * 4) * 4;  // 30 720
+static constexpr uint32_t kServeABytes = 2u * 128u * 64u * 2u;              // 32 768
+static constexpr size_t kServeSmem =
+    kServeWBytes + kServeABytes + kServeThreads * kServeMaxK * 16 + kServeThreads * kServeMaxK * 2 + 64;
+
+__global__ void __launch_bounds__(kServeThreads, 2) k_serve(const __grid_constant__ ServeKParams kp) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  float4* sWf = reinterpret_cast<float4*>(smem);
+  uint8_t* sA = smem + kServeWBytes;
+  float4* s_rgba = reinterpret_cast<float4*>(sA + kServeABytes);
+  uint16_t* s_list = reinterpret_cast<uint16_t*>(s_rgba + kServeThreads * kServeMaxK);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(s_list + kServeThreads * kServeMaxK);  // [0] weights, [1] MMA
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2);
   __shared__ int s_cmd;
   __shared__ unsigned long long s_idx;
   __shared__ uint32_t s_slot, s_gen, s_tx, s_ty, s_tiles_total;
-  __shared__ int s_W, s_H, s_status, s_skip;
+  __shared__ int s_W, s_H, s_status, s_skip, s_prec, s_have;
   __shared__ float* s_out;
   __shared__ float s_cam[13];
-  __shared__ uint32_t s_obj_hits[kServeMaxObjects];
+  __shared__ uint32_t s_cnt[kServeMaxObjects], s_off[kServeMaxObjects + 1];
+  __shared__ float s_ht[kServeThreads * kServeMaxK];
   const int tid = threadIdx.x;
   const unsigned long long t_start = gtimer();
+  if (tid == 0) {
+    s_have = 0;
+    s_slot = 0xFFFFFFFFu;
+    tc::mbar_init(&bars[0], 1);
+    tc::mbar_init(&bars[1], 1);
+    tc::fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid < 32) tc::tmem_alloc(tslot, 128);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = *tslot;
+  uint32_t w_phase = 0, mma_phase = 0;
+  bool broken = false;
 
-  while (true) {
-    // ---- claim one published tile (thread 0), bounded idle wait ----
+  unsigned long long batch_next = 0, batch_end = 0;  // tiles claimed but not yet processed (thread 0)
+  while (!broken) {
+    // ---- claim a batch of up to kServeClaim published tiles (thread 0), bounded idle wait ----
     if (tid == 0) {
       int cmd = 1;
-      while (true) {
+      if (batch_next < batch_end) {
+        s_idx = batch_next++;
+        cmd = 0;
+      }
+      while (cmd) {
         if (ld_vol_u32(&kp.ctl->stop)) break;
         const unsigned long long pub = ld_acq_sys_u64(&kp.ctl->published);
-        const unsigned long long h = atomicAdd(&kp.st->head, 0ull);
-        if (h < pub) {
-          if (atomicCAS(&kp.st->head, h, h + 1) == h) {
+        unsigned long long h = *(volatile unsigned long long*)&kp.st->head;
+        bool claimed = false;
+        while (h < pub) {  // one CAS claims min(kServeClaim, pub - h) consecutive tiles
+          const unsigned long long n = min((unsigned long long)kServeClaim, pub - h);
+          const unsigned long long prev = atomicCAS(&kp.st->head, h, h + n);
+          if (prev == h) {
             s_idx = h;
-            cmd = 0;
-            atomicMax(&kp.st->last_activity, gtimer());
+            batch_next = h + 1;
+            batch_end = h + n;
+            claimed = true;
             break;
           }
-          continue;
+          h = prev;
+        }
+        if (claimed) {
+          cmd = 0;
+          atomicMax(&kp.st->last_activity, gtimer());
+          break;
         }
         const unsigned long long now = gtimer();
-        const unsigned long long last = max((unsigned long long)atomicAdd(&kp.st->last_activity, 0ull), t_start);
+        const unsigned long long last =
+            max(*(volatile unsigned long long*)&kp.st->last_activity, t_start);
         if (now > last + kp.idle_limit_ns) break;  // idle: exit, the host relaunches on new work
         __nanosleep(1000);
       }
       s_cmd = cmd;
       if (cmd == 0) {
         const ServeTile* e = kp.ring + (s_idx % kp.ring_cap);
-        s_slot = ld_vol_u32(&e->slot);
-        s_gen = ld_vol_u32(&e->gen);
-        s_tx = ld_vol_u32(&e->tx);
-        s_ty = ld_vol_u32(&e->ty);
-        s_tiles_total = ld_vol_u32(&e->tiles_total);
+        const uint4 e0 = ld_vol_v4(e), e1 = ld_vol_v4(reinterpret_cast<const uint4*>(e) + 1);
+        const bool same = e0.x == s_slot && e0.y == s_gen && s_have;  // descriptor cached from the last tile
+        s_slot = e0.x;
+        s_gen = e0.y;
+        s_tx = e0.z;
+        s_ty = e0.w;
+        s_tiles_total = e1.x;
         const ServeSlot* sl = kp.slots + s_slot;
-        // bounded wait for the request descriptor of this generation
         int status = 0;
-        const unsigned long long t0 = gtimer();
-        while (ld_acq_sys_u32(&sl->gen) != s_gen) {
-          if (gtimer() - t0 > kp.wait_limit_ns) {
-            status = INOLF_E_TIMEOUT;
-            break;
+        if (!same) {
+          // bounded wait for the request descriptor of this generation
+          const unsigned long long t0 = gtimer();
+          while (ld_acq_sys_u32(&sl->gen) != s_gen) {
+            if (gtimer() - t0 > kp.wait_limit_ns) {
+              status = INOLF_E_TIMEOUT;
+              break;
+            }
+            __nanosleep(500);
           }
-          __nanosleep(500);
+          if (!status) {
+            s_W = (int)ld_vol_u32((const uint32_t*)&sl->W);
+            s_H = (int)ld_vol_u32((const uint32_t*)&sl->H);
+            s_prec = (int)ld_vol_u32((const uint32_t*)&sl->prec);
+            s_out = *(float* const volatile*)&sl->out;
+            for (int k = 0; k < 13; ++k) s_cam[k] = ld_vol_f32(&sl->cam[k]);
+          }
+          s_have = status == 0;
         }
         s_status = status;
         s_skip = status != 0;
-        if (!status) {
-          if (ld_vol_u32(&sl->cancelled)) {
-            s_status = INOLF_E_CANCELLED;
-            s_skip = 1;
-          }
-          s_W = (int)ld_vol_u32((const uint32_t*)&sl->W);
-          s_H = (int)ld_vol_u32((const uint32_t*)&sl->H);
-          s_out = *(float* const volatile*)&sl->out;
-          for (int k = 0; k < 13; ++k) s_cam[k] = ld_vol_f32(&sl->cam[k]);
+        // cancellation is checked every 16 tiles of a request
+        if (!status && ((s_idx & 15ull) == 0 || !same) && ld_vol_u32(&sl->cancelled)) {
+          s_status = INOLF_E_CANCELLED;
+          s_skip = 1;
         }
       }
     }
-    if (tid < kServeMaxObjects) s_obj_hits[tid] = 0;
+    if (tid < kServeMaxObjects) s_cnt[tid] = 0;
     __syncthreads();
     if (s_cmd) break;
 
@@ -250,6 +322,12 @@ __global__ void __launch_bounds__(kServeThreads) k_serve(const __grid_constant__
         float ol[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) ol[a] = __fsub_rn(o[a], ob.T[a]);
+        {  // skip objects whose padded bounding sphere the ray misses
+          const float cx = ol[0] - ob.bs_c[0], cy = ol[1] - ob.bs_c[1], cz = ol[2] - ob.bs_c[2];
+          const float b = cx * d[0] + cy * d[1] + cz * d[2];
+          const float c2 = cx * cx + cy * cy + cz * cz - ob.bs_r2;
+          if (c2 > 0.f && (b > 0.f || b * b < c2)) continue;
+        }
         int32_t id;
         float t;
         closest_hit_bvh(ob.nodes, ob.tris, &kp.st->err, ol, d, id, t);
@@ -266,58 +344,132 @@ __global__ void __launch_bounds__(kServeThreads) k_serve(const __grid_constant__
           if (nh < kp.K) ++nh;
         }
       }
-      for (int q = 0; q < nh; ++q) atomicOr(&s_obj_hits[hk[q]], 1u);
+    }
+    // group the tile's hits by object: rank within the object's list
+    uint32_t rank[kServeMaxK];
+    for (int q = 0; q < nh; ++q) {
+      rank[q] = atomicAdd(&s_cnt[hk[q]], 1u);
+      s_ht[tid * kServeMaxK + q] = ht[q];
+    }
+    __syncthreads();
+    if (tid == 0) {
+      uint32_t acc = 0;
+      for (int k = 0; k < kServeMaxObjects; ++k) { s_off[k] = acc; acc += s_cnt[k]; }
+      s_off[kServeMaxObjects] = acc;
+    }
+    __syncthreads();
+    for (int q = 0; q < nh; ++q) s_list[s_off[hk[q]] + rank[q]] = (uint16_t)(tid * kServeMaxK + q);
+    __syncthreads();
+
+    // ---- shade the hits object by object ----
+    for (int k = 0; k < kp.n_objs && !broken; ++k) {
+      const uint32_t cnt = s_cnt[k];
+      if (!cnt) continue;  // uniform: no pixel of the tile hits object k
+      const ServeObj& ob = kp.objs[k];
+      const int din = ob.d_in;
+      if (s_prec == INOLF_FP32) {
+        const int nw4 = (din * 64 + 64 * 64 + 64 * 4) / 4;
+        for (int q = tid; q < nw4; q += kServeThreads) sWf[q] = reinterpret_cast<const float4*>(ob.w_f32)[q];
+        __syncthreads();
+        for (int q = 0; q < nh; ++q) {
+          if (hk[q] != k) continue;
+          float ol[3], x3[3];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) ol[a] = __fsub_rn(o[a], ob.T[a]);
+          hit_unit_coords_ls(ob.lo, ob.scale, ol, d, ht[q], x3);
+          float x[kServeMaxDin];
+          for (int l = 0; l < ob.L; ++l) {
+            uint32_t slots[8];
+            float e0, e1;
+            encode_level(ob.lv[l], ob.fp16, x3, slots, e0, e1);
+            x[2 * l] = e0;
+            x[2 * l + 1] = e1;
+          }
+          sh16c(kp.shc, d, x + 2 * ob.L);
+          s_rgba[tid * kServeMaxK + q] = mlp_f32(sWf, sWf + din * 16, sWf + din * 16 + 64 * 16, x, din);
+        }
+        __syncthreads();
+      } else {
+        // BF16 tensor-core MLP: stage the object's operand blob by one bulk copy
+        const uint32_t K1 = (uint32_t)ob.tc_k1_bf16, chunks1 = K1 / 8u;
+        if (tid == 0) {
+          tc::mbar_arrive_expect_tx(&bars[0], ob.tc_bytes_bf16);
+          tc::bulk_g2s(smem, ob.w_bf16, ob.tc_bytes_bf16, &bars[0]);
+        }
+        const bool okw = tc::mbar_wait(&bars[0], w_phase, kWaitLimitNs);
+        w_phase ^= 1u;
+        if (__syncthreads_or(!okw)) { broken = true; break; }
+        const uint8_t* sB1 = smem;
+        const uint8_t* sB2 = smem + 64u * K1 * 2u;
+        const float* sW3 = reinterpret_cast<const float*>(sB2 + 64u * 64u * 2u);
+        const uint32_t t = (uint32_t)tid >> 7, row = (uint32_t)tid & 127u;
+        uint8_t* A = sA + t * (128u * 64u * 2u);
+        for (uint32_t base = 0; base < cnt; base += kServeThreads) {
+          const bool mine = base + (uint32_t)tid < cnt;
+          uint32_t entry = 0;
+          if (mine) {
+            entry = s_list[s_off[k] + base + tid];
+            const int p = (int)(entry / kServeMaxK);
+            const float th = s_ht[entry];
+            const int pi = (int)s_tx * kServeTile + (p & 15), pj = (int)s_ty * kServeTile + (p >> 4);
+            float po[3], pd[3], ol[3], x3[3];
+            make_ray(s_cam, s_W, s_H, pi, pj, po, pd);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) ol[a] = __fsub_rn(po[a], ob.T[a]);
+            hit_unit_coords_ls(ob.lo, ob.scale, ol, pd, th, x3);
+            for (int l = 0; l < ob.L; ++l) {
+              uint32_t slots[8];
+              float e0, e1;
+              encode_level(ob.lv[l], ob.fp16, x3, slots, e0, e1);
+              store_pair<false>(A, row, 2u * l, chunks1, e0, e1, 1.f);
+            }
+            float sh[16];
+            sh16c(kp.shc, pd, sh);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) store_pair<false>(A, row, 2u * ob.L + 2u * u, chunks1, sh[2 * u], sh[2 * u + 1], 1.f);
+            for (uint32_t kk = (uint32_t)din; kk < K1; kk += 2) store_pair<false>(A, row, kk, chunks1, 0.f, 0.f, 1.f);
+          } else {
+            for (uint32_t c = 0; c < chunks1; ++c)
+              *reinterpret_cast<uint4*>(A + tc::core_off(row, c, chunks1)) = make_uint4(0, 0, 0, 0);
+          }
+          float4 rgba;
+          const TcScales sc = TcScales::make(false, nullptr, nullptr);
+          if (!tc_mlp_run<false>(sA, sB1, sB2, sW3, K1, tmem, &bars[1], mma_phase, sc, rgba)) {
+            broken = true;
+            break;
+          }
+          if (mine) s_rgba[entry] = rgba;
+        }
+      }
     }
     __syncthreads();
 
-    // ---- shade the hits object by object (weights staged in shared memory) ----
-    float4 rgba[kServeMaxK];
-    for (int k = 0; k < kp.n_objs; ++k) {
-      if (!s_obj_hits[k]) continue;  // uniform: no pixel of the tile hits object k
-      const ServeObj& ob = kp.objs[k];
-      const int din = ob.d_in;
-      const int nw4 = (din * 64 + 64 * 64 + 64 * 4) / 4;
-      for (int q = tid; q < nw4; q += kServeThreads) smem4[q] = reinterpret_cast<const float4*>(ob.w_f32)[q];
-      __syncthreads();
-      for (int q = 0; q < nh; ++q) {
-        if (hk[q] != k) continue;
-        float ol[3], x3[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) ol[a] = __fsub_rn(o[a], ob.T[a]);
-        hit_unit_coords_ls(ob.lo, ob.scale, ol, d, ht[q], x3);
-        float x[kServeMaxDin];
-        for (int l = 0; l < ob.L; ++l) {
-          uint32_t slots[8];
-          float e0, e1;
-          encode_level(ob.lv[l], ob.fp16, x3, slots, e0, e1);
-          x[2 * l] = e0;
-          x[2 * l + 1] = e1;
-        }
-        sh16c(kp.shc, d, x + 2 * ob.L);
-        rgba[q] = mlp_f32(smem4, smem4 + din * 16, smem4 + din * 16 + 64 * 16, x, din);
-      }
-      __syncthreads();
-    }
-
     // ---- composite front to back, straight alpha out ----
-    if (valid) {
+    if (valid && !broken) {
       float C0 = 0.f, C1 = 0.f, C2 = 0.f, A = 0.f;
       for (int q = 0; q < nh; ++q) {
-        const float w = (1.0f - A) * rgba[q].w;
-        C0 += w * rgba[q].x;
-        C1 += w * rgba[q].y;
-        C2 += w * rgba[q].z;
+        const float4 c = s_rgba[tid * kServeMaxK + q];
+        const float w = (1.0f - A) * c.w;
+        C0 += w * c.x;
+        C1 += w * c.y;
+        C2 += w * c.z;
         A += w;
       }
       const float4 px = A > 0.f ? make_float4(C0 / A, C1 / A, C2 / A, A) : make_float4(0.f, 0.f, 0.f, 0.f);
       reinterpret_cast<float4*>(s_out)[(size_t)j * s_W + i] = px;
     }
-    __threadfence_system();
     __syncthreads();
     // ---- tile done; the last tile of the request publishes its completion ----
+    // (bar.sync orders the CTA's frame writes before thread 0's device-scope
+    // fence and counter update; the CTA that completes the request observes
+    // every other tile's update and issues the one system-scope fence before
+    // the completion record, which makes the whole frame visible to the host)
     if (tid == 0) {
+      __threadfence();
       const uint32_t slot = s_slot;
-      if (s_status) atomicCAS(&kp.st->status[slot], 0, s_status);
+      const int st = broken ? INOLF_E_TIMEOUT : s_status;
+      if (broken) atomicOr(&kp.st->err, 4u);
+      if (st) atomicCAS(&kp.st->status[slot], 0, st);
       const uint32_t n = atomicAdd(&kp.st->tiles_done[slot], 1u) + 1u;
       if (n == s_tiles_total) {
         const int status = atomicExch(&kp.st->status[slot], 0);
@@ -328,6 +480,14 @@ __global__ void __launch_bounds__(kServeThreads) k_serve(const __grid_constant__
       }
     }
     __syncthreads();
+  }
+  if (broken) {  // let tensor-core work still in flight finish before freeing TMEM
+    tc::mbar_wait(&bars[1], mma_phase ^ 1u, kWaitLimitNs);
+  }
+  __syncthreads();
+  if (tid < 32) {
+    tc::fence_after();
+    tc::tmem_dealloc(tmem, 128);
   }
 }
 
@@ -433,7 +593,7 @@ static void serve_free(inolf_server* s) {
   delete s;
 }
 
-static size_t serve_smem_bytes() { return (size_t)(48 * 64 + 64 * 64 + 64 * 4) * sizeof(float); }
+static size_t serve_smem_bytes() { return kServeSmem; }
 
 // Launches the persistent kernel if it is not running (must hold s->mu).
 static inolf_status ensure_running(inolf_server* s) {
@@ -528,7 +688,7 @@ extern "C" inolf_status inolf_serve_create(const inolf_serve_params* prm, inolf_
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
   cudaFuncSetAttribute(k_serve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)serve_smem_bytes());
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_serve, kServeThreads, serve_smem_bytes());
-  occ = std::max(1, occ);
+  occ = std::max(1, std::min(occ, 4));  // each CTA holds 128 of the SM's 512 TMEM columns
   if (p.ctas_per_sm > 0) occ = std::min(occ, p.ctas_per_sm);
   s->grid = sms * occ;
   cudaGetLastError();
@@ -548,12 +708,17 @@ extern "C" inolf_status inolf_serve_add_object(inolf_server* s, const inolf_obje
   so.nodes = (const float4*)o.nodes;
   so.tris = (const float4*)o.tris;
   so.w_f32 = o.w_f32;
+  so.w_bf16 = o.w_bf16;
+  so.tc_k1_bf16 = o.tc_k1_bf16;
+  so.tc_bytes_bf16 = o.tc_bytes_bf16;
   so.L = o.L;
   so.fp16 = o.fp16;
   so.d_in = o.d_in;
   so.lo = o.lo;
   so.scale = o.scale;
   for (int k = 0; k < 3; ++k) so.T[k] = translation[k];
+  for (int k = 0; k < 3; ++k) so.bs_c[k] = o.bsphere[k];
+  so.bs_r2 = o.bsphere[3] * o.bsphere[3];
   for (int l = 0; l < o.L; ++l) so.lv[l] = o.lv[l];
   s->objs.push_back(so);
   s->objs_dirty = true;
@@ -565,7 +730,8 @@ extern "C" inolf_status inolf_serve_submit(inolf_server* s, const inolf_request*
   if (!s || !r || !ticket) return fail(INOLF_E_INVALID, "inolf_serve_submit: NULL argument");
   if (r->width < 1 || r->height < 1 || r->width > s->prm.max_width || r->height > s->prm.max_height)
     return fail(INOLF_E_INVALID, "inolf_serve_submit: resolution outside (0, max]");
-  if (r->precision != INOLF_FP32) return fail(INOLF_E_UNSUPPORTED, "inolf_serve_submit: only FP32 shading is served");
+  if (r->precision != INOLF_FP32 && r->precision != INOLF_BF16)
+    return fail(INOLF_E_UNSUPPORTED, "inolf_serve_submit: FP32 and BF16 shading are served");
   std::lock_guard<std::mutex> lk(s->mu);
   if (s->objs.empty()) return fail(INOLF_E_INVALID, "inolf_serve_submit: no objects");
   int slot = -1;

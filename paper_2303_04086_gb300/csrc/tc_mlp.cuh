@@ -1,0 +1,165 @@
+// Layers 1-3 of the MLP F_s on the tensor cores for 2 x 128 rows whose A1
+// operand rows are already in shared memory (shared by the render and serve
+// kernels).  256 threads; thread tid owns row tid & 127 of tile tid >> 7.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include "kernels_common.cuh"
+#include "tc_ptx.cuh"
+
+namespace inolf {
+
+static constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s: the MMAs of a tile take microseconds
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+__device__ __forceinline__ uint16_t pack_fp8(float a, float b) {
+  return (uint16_t)__nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+}
+__device__ __forceinline__ float round_bf16(float a) { return __bfloat162float(__float2bfloat16_rn(a)); }
+__device__ __forceinline__ float round_fp8(float a) {
+  __half_raw h = __nv_cvt_fp8_to_halfraw(__nv_cvt_float_to_fp8(a, __NV_SATFINITE, __NV_E4M3), __NV_E4M3);
+  return __half2float(__half(h));
+}
+
+// stores the pair (a, b) of input column k (even) of row `row`
+template <bool kFP8>
+__device__ __forceinline__ void store_pair(uint8_t* A, uint32_t row, uint32_t k, uint32_t chunks, float a, float b,
+                                           float inv_scale) {
+  if (kFP8) {
+    const uint32_t off = tc::core_off(row, k >> 4, chunks) + (k & 15u);
+    *reinterpret_cast<uint16_t*>(A + off) = pack_fp8(a * inv_scale, b * inv_scale);
+  } else {
+    const uint32_t off = tc::core_off(row, k >> 3, chunks) + (k & 7u) * 2u;
+    *reinterpret_cast<uint32_t*>(A + off) = pack_bf16(a, b);
+  }
+}
+
+
+// Precision-dependent scales (FP8: per-tensor, amax / 448; BF16: unit).
+struct TcScales {
+  float inv_sx, mul1, inv_sh1, mul2, sh2, inv_sh2;
+  __device__ static TcScales make(bool fp8, const float act[3], const float w[3]) {
+    TcScales s;
+    s.inv_sx = fp8 ? 1.0f / act[0] : 1.0f;
+    s.mul1 = fp8 ? act[0] * w[0] : 1.0f;
+    s.inv_sh1 = fp8 ? 1.0f / act[1] : 1.0f;
+    s.mul2 = fp8 ? act[1] * w[1] : 1.0f;
+    s.sh2 = fp8 ? act[2] : 1.0f;
+    s.inv_sh2 = fp8 ? 1.0f / act[2] : 1.0f;
+    return s;
+  }
+};
+
+// Steps after the A1 rows are written: D1 = A1 W1^T (tcgen05, TMEM), ReLU and
+// quantisation into A2 (in place of A1), D2 = A2 W2^T, ReLU, quantisation,
+// W3 on the CUDA cores and sigmoid.  Every thread of the CTA must call it;
+// `out` receives the thread's row.  Returns false (uniformly) when an MMA
+// completion wait ran out.
+template <bool kFP8>
+__device__ __forceinline__ bool tc_mlp_run(uint8_t* sA, const uint8_t* sB1, const uint8_t* sB2, const float* sW3,
+                                           uint32_t K1, uint32_t tmem, uint64_t* bar, uint32_t& phase,
+                                           const TcScales& sc, float4& out) {
+  constexpr uint32_t ES = kFP8 ? 1u : 2u;
+  constexpr uint32_t KSTEP_CHUNKS = 2;  // one MMA consumes 32 bytes of K per row
+  constexpr uint32_t tile_bytes = 128u * 64u * ES;
+  const uint32_t chunks1 = K1 * ES / 16u, chunks2 = 64u * ES / 16u;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const uint32_t t = (uint32_t)tid >> 7, row = (uint32_t)tid & 127u;
+  uint8_t* A = sA + t * tile_bytes;
+  const uint32_t lane_base = ((uint32_t)(warp & 3) * 32u) << 16;
+  const uint32_t id = tc::idesc(128, 64, kFP8 ? 0u : 1u);
+  tc::fence_async_smem();
+  __syncthreads();
+  // ---- D1 = A1 W1^T ----
+  if (tid == 0) {
+    tc::fence_after();
+    for (uint32_t tt = 0; tt < 2; ++tt) {
+      const uint32_t a0 = tc::smem_u32(sA + tt * tile_bytes), b0 = tc::smem_u32(sB1);
+      for (uint32_t s = 0; s < chunks1 / KSTEP_CHUNKS; ++s) {
+        const uint64_t ad = tc::desc_kmajor(a0 + s * 256u, 128u, chunks1 * 128u);
+        const uint64_t bd = tc::desc_kmajor(b0 + s * 256u, 128u, chunks1 * 128u);
+        if (kFP8) tc::mma_fp8(tmem + tt * 64u, ad, bd, id, s > 0);
+        else tc::mma_bf16(tmem + tt * 64u, ad, bd, id, s > 0);
+      }
+    }
+    tc::mma_commit(bar);
+  }
+  bool ok = tc::mbar_wait(bar, phase, kWaitLimitNs);
+  phase ^= 1u;
+  if (__syncthreads_or(!ok)) return false;
+  tc::fence_after();
+  // ---- ReLU, quantise -> A2 row ----
+#pragma unroll 1
+  for (uint32_t c = 0; c < 4; ++c) {
+    float v[16];
+    tc::tmem_ld16(tmem + lane_base + t * 64u + c * 16u, v);
+    if (kFP8) {
+      uint32_t w[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float a0 = fmaxf(v[4 * q + 0] * sc.mul1, 0.f) * sc.inv_sh1;
+        const float a1 = fmaxf(v[4 * q + 1] * sc.mul1, 0.f) * sc.inv_sh1;
+        const float a2 = fmaxf(v[4 * q + 2] * sc.mul1, 0.f) * sc.inv_sh1;
+        const float a3 = fmaxf(v[4 * q + 3] * sc.mul1, 0.f) * sc.inv_sh1;
+        w[q] = (uint32_t)pack_fp8(a0, a1) | ((uint32_t)pack_fp8(a2, a3) << 16);
+      }
+      *reinterpret_cast<uint4*>(A + tc::core_off(row, c, chunks2)) = make_uint4(w[0], w[1], w[2], w[3]);
+    } else {
+      uint32_t w[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) w[q] = pack_bf16(fmaxf(v[2 * q], 0.f), fmaxf(v[2 * q + 1], 0.f));
+      *reinterpret_cast<uint4*>(A + tc::core_off(row, 2 * c, chunks2)) = make_uint4(w[0], w[1], w[2], w[3]);
+      *reinterpret_cast<uint4*>(A + tc::core_off(row, 2 * c + 1, chunks2)) = make_uint4(w[4], w[5], w[6], w[7]);
+    }
+  }
+  tc::fence_before();
+  tc::fence_async_smem();
+  __syncthreads();
+  // ---- D2 = A2 W2^T ----
+  if (tid == 0) {
+    tc::fence_after();
+    for (uint32_t tt = 0; tt < 2; ++tt) {
+      const uint32_t a0 = tc::smem_u32(sA + tt * tile_bytes), b0 = tc::smem_u32(sB2);
+      for (uint32_t s = 0; s < chunks2 / KSTEP_CHUNKS; ++s) {
+        const uint64_t ad = tc::desc_kmajor(a0 + s * 256u, 128u, chunks2 * 128u);
+        const uint64_t bd = tc::desc_kmajor(b0 + s * 256u, 128u, chunks2 * 128u);
+        if (kFP8) tc::mma_fp8(tmem + tt * 64u, ad, bd, id, s > 0);
+        else tc::mma_bf16(tmem + tt * 64u, ad, bd, id, s > 0);
+      }
+    }
+    tc::mma_commit(bar);
+  }
+  ok = tc::mbar_wait(bar, phase, kWaitLimitNs);
+  phase ^= 1u;
+  if (__syncthreads_or(!ok)) return false;
+  tc::fence_after();
+  // ---- ReLU, quantise, W3, sigmoid ----
+  float out0 = 0.f, out1 = 0.f, out2 = 0.f, out3 = 0.f;
+#pragma unroll 1
+  for (uint32_t c = 0; c < 4; ++c) {
+    float v[16];
+    tc::tmem_ld16(tmem + lane_base + t * 64u + c * 16u, v);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      float a = fmaxf(v[j] * sc.mul2, 0.f);
+      a = kFP8 ? round_fp8(a * sc.inv_sh2) * sc.sh2 : round_bf16(a);
+      const uint32_t col = c * 16u + (uint32_t)j;
+      out0 += sW3[0 * 64 + col] * a;
+      out1 += sW3[1 * 64 + col] * a;
+      out2 += sW3[2 * 64 + col] * a;
+      out3 += sW3[3 * 64 + col] * a;
+    }
+  }
+  out = make_float4(sigmoidf_(out0), sigmoidf_(out1), sigmoidf_(out2), sigmoidf_(out3));
+  tc::fence_before();
+  __syncthreads();
+  return true;
+}
+
+}  // namespace inolf

@@ -191,3 +191,49 @@ def test_cancel_and_idle_relaunch(env):
     assert np.abs(srv.frame(res).cpu().numpy() - ref).max() <= TOL
     srv.release(t)
     srv.close()
+
+
+def test_bf16_serving_matches_render_and_oracle(env):
+    torch, inolf, scenes, objs = env
+    # one object: the served BF16 frame equals the BF16 render of that object
+    srv = inolf.Server(hbm_budget=64 << 20, max_slots=4, max_width=512, max_height=512)
+    srv.add_object(objs[0])
+    cam = synth.camera((0.3, 0.2, 3.0))
+    t = srv.submit(cam, 200, 150, "bf16")
+    st, res = _done(srv, t)
+    assert st == inolf.OK
+    got = srv.frame(res).cpu().numpy()
+    ref = inolf.render(objs[0], cam[None], 200, 150, "bf16").cpu().numpy()[0]
+    assert np.abs(got - ref).max() <= TOL
+    srv.release(t)
+    srv.close()
+    # several objects: the BF16 composite is within the BF16 bar of the FP64 oracle
+    srv = _multi_server(inolf, objs, hbm_budget=64 << 20, max_slots=8, max_width=256, max_height=256)
+    cam = synth.camera((0.5, 1.0, 8.0), target=(0.2, 0.3, -0.8))
+    W = H = 128
+    mixed = [srv.submit(cam, W, H, "bf16")] + [srv.submit(synth.camera((7.0, 2.0, -4.0)), 96, 64, "fp32")
+                                               for _ in range(3)]
+    frames = []
+    for tk in mixed:
+        st, res = _done(srv, tk)
+        assert st == inolf.OK
+        frames.append(srv.frame(res).cpu().numpy())
+        srv.release(tk)
+    srv.close()
+    got = frames[0].reshape(-1, 4)
+    o, d = oracle.raygen(cam, W, H)
+    per = [oracle.Oracle(sc).render_rays((o - np.float32(pl)).astype(np.float32), d)
+           for sc, pl in zip(scenes, PLACES)]
+    ref = np.zeros((W * H, 4))
+    for px in range(W * H):
+        hits = sorted((per[k]["t"][px], k) for k in range(len(per)) if per[k]["tri"][px] >= 0)[:4]
+        C, A = np.zeros(3), 0.0
+        for _, k in hits:
+            c = per[k]["rgba"][px]
+            w = (1 - A) * c[3]
+            C += w * c[:3]
+            A += w
+        if A > 0:
+            ref[px, :3] = C / A
+            ref[px, 3] = A
+    assert np.abs(got - ref).max() <= 1e-2
