@@ -393,16 +393,18 @@ __device__ __forceinline__ void finish_level(const LevelDev& lv, int fp16, const
 #pragma unroll
     for (int cc = 0; cc < 8; ++cc) v[cc] = __ldg(tb + slots[cc]);
   }
+  // trilinear interpolation as nested lerps along x, then y, then z
   const float* f = s.f;
-  const float gx = 1.0f - f[0], gy = 1.0f - f[1], gz = 1.0f - f[2];
-  e0 = 0.0f;
-  e1 = 0.0f;
+  float ax[4], bx[4];
 #pragma unroll
-  for (int cc = 0; cc < 8; ++cc) {
-    const float w = ((cc & 1) ? f[0] : gx) * ((cc & 2) ? f[1] : gy) * ((cc & 4) ? f[2] : gz);
-    e0 += w * v[cc].x;
-    e1 += w * v[cc].y;
+  for (int k = 0; k < 4; ++k) {
+    ax[k] = fmaf(f[0], v[2 * k + 1].x - v[2 * k].x, v[2 * k].x);
+    bx[k] = fmaf(f[0], v[2 * k + 1].y - v[2 * k].y, v[2 * k].y);
   }
+  const float ay0 = fmaf(f[1], ax[1] - ax[0], ax[0]), ay1 = fmaf(f[1], ax[3] - ax[2], ax[2]);
+  const float by0 = fmaf(f[1], bx[1] - bx[0], bx[0]), by1 = fmaf(f[1], bx[3] - bx[2], bx[2]);
+  e0 = fmaf(f[2], ay1 - ay0, ay0);
+  e1 = fmaf(f[2], by1 - by0, by0);
 }
 
 // Eq. 1 slots of the 8 corners and the interpolated features of one level.

@@ -5,7 +5,7 @@
 //            traversal of the proxy mesh (FP32 Moller-Trumbore, closest =
 //            lexicographic (t, triangle id) minimum), then warp-ballot
 //            compaction of the hitting rays into a dense hit list
-//            (one global atomic per warp).  Misses write RGBA = 0.
+//            (one global atomic per CTA).  Misses write RGBA = 0.
 //   k_shade  persistent over the hit list, one thread per hit ray: the
 //            Sec. 4.1 grid vertex of the hit point on every level, Eq. 1
 //            perfect-hash slots of the 8 voxel corners, feature gather,
@@ -62,12 +62,21 @@ __global__ void __launch_bounds__(256) k_trace(const __grid_constant__ Params p,
   if (valid) closest_hit(p, o, d, tri, t);
   const bool hit = valid && tri >= 0;
 
-  // compaction: warp ballot + one global atomic per warp (no CTA barrier, so
-  // a warp whose rays finish early does not wait for the slowest warp)
+  // compaction: warp ballot + per-CTA prefix + one global atomic per CTA, so
+  // the hits of a 16 x 16 pixel tile stay contiguous in the hit list and a
+  // shade tile covers neighbouring pixels (cache locality of the gather)
+  __shared__ uint32_t s_warp[8];
+  __shared__ uint32_t s_base;
   const uint32_t mask = __ballot_sync(0xffffffffu, hit);
-  uint32_t wbase = 0;
-  if (lane == 0 && mask) wbase = atomicAdd(p.counter, (uint32_t)__popc(mask));
-  wbase = __shfl_sync(0xffffffffu, wbase, 0);
+  if (lane == 0) s_warp[warp] = __popc(mask);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t acc = 0;
+    for (int w = 0; w < 8; ++w) { uint32_t c = s_warp[w]; s_warp[w] = acc; acc += c; }
+    s_base = acc ? atomicAdd(p.counter, acc) : 0u;
+  }
+  __syncthreads();
+  const uint32_t wbase = s_base + s_warp[warp];
   if (valid) {
     const int64_t g = p.ray_base + ray;
     if (hit) {
