@@ -132,14 +132,21 @@ def _barrier(world):
         dist.barrier()
 
 
-def _max_over_ranks(x, world):
+def _max_over_ranks(x, world, device="cuda"):
+    """Slowest rank's time (timing plumbing only: the replicas exchange no data)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_throughput(units_per_rank, seconds_max, world):
+    """Whole-job throughput of N independent replicas (weak scaling): all
+    ranks' units over the slowest rank's time."""
+    return units_per_rank * world / seconds_max
 
 
 def make_workload(small: bool, views: int):
@@ -419,8 +426,7 @@ def run_native(a):
         ms, stats = timed("fp32", a.steps, a.warmup, with_stats=True)
     ms = _max_over_ranks(ms, world)
     clocks = clk.summary()
-    rays_all = n_rays * a.steps * world
-    value = rays_all / (ms / 1e3) / 1e6
+    value = replica_throughput(n_rays * a.steps, ms / 1e3, world) / 1e6
 
     # precision variants: BF16 / FP8-e4m3 MLP on the tensor cores (FP8
     # activation scales calibrated once from the FP32 path on view 0)
