@@ -293,6 +293,72 @@ def run_serving(seconds=10.0, warmup=1.0, rate_hz=50.0, seed=0, prec="bf16"):
                     "budget) full at arrival"}
 
 
+def run_zoom_sweep(obj, W, H, prec="bf16", distances=(6.0, 4.0, 3.0, 2.5, 2.0, 1.6, 1.35)):
+    """Speed vs camera distance at 4K (the linear-in-covered-pixels claim of
+    one query per ray, Sec. 8.2): one view per distance; time vs hit rays is
+    fitted by a line."""
+    import torch
+    from paper_2303_04086_gb300 import inolf, synth
+    rgba = torch.empty((1, H, W, 4), device="cuda")
+    tri = torch.empty((1, H, W), dtype=torch.int32, device="cuda")
+    ws = torch.empty((inolf.render_workspace_bytes(W * H) + 15) // 16 * 4, dtype=torch.int32, device="cuda")
+    rows = []
+    for r in distances:
+        cam = synth.camera((0.0, 0.0, r))[None]
+        inolf.render(obj, cam, W, H, prec, rgba_out=rgba, tri_out=tri, workspace=ws)
+        torch.cuda.synchronize()
+        hits = int((tri >= 0).sum().item())
+        evs = []
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            inolf.render(obj, cam, W, H, prec, rgba_out=rgba, workspace=ws)
+            e1.record()
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        ms = min(a.elapsed_time(b) for a, b in evs)
+        rows.append({"distance": r, "hit_fraction": hits / (W * H), "ms": ms, "mrays_per_s": W * H / ms / 1e3})
+    x = np.array([q["hit_fraction"] for q in rows]) * W * H
+    y = np.array([q["ms"] for q in rows])
+    A = np.stack([np.ones_like(x), x], 1)
+    coef, *_ = np.linalg.lstsq(A, y, rcond=None)
+    r2 = 1 - ((A @ coef - y) ** 2).sum() / max(((y - y.mean()) ** 2).sum(), 1e-30)
+    return {"precision": prec, "points": rows, "fit_ms": {"intercept": float(coef[0]),
+            "per_mhit": float(coef[1] * 1e6), "r2": float(r2)}}
+
+
+def run_looking_glass(views=45, W=420, H=560, arc_deg=40.0, seed=0):
+    """A 45-view light-field quilt (Sec. 7, Looking Glass display): 45
+    consecutive viewpoints on a horizontal arc, submitted together to the
+    serving loop over the 12-object scene."""
+    from paper_2303_04086_gb300 import inolf, synth
+    scenes, places, _ = serving_workload(seed)
+    centre = np.mean(places, 0)
+    srv = inolf.Server(hbm_budget=1 << 30, max_slots=64, max_width=W, max_height=H)
+    objs = [inolf.object_create(sc) for sc in scenes]
+    for o, p in zip(objs, places):
+        srv.add_object(o, p)
+    cams = []
+    for k in range(views):
+        a = np.radians(-arc_deg / 2 + arc_deg * k / (views - 1))
+        eye = centre + 12.0 * np.array([np.sin(a), 0.15, np.cos(a)])
+        cams.append(synth.camera(tuple(eye), target=tuple(centre)))
+    times = []
+    for rep in range(4):
+        t0 = time.perf_counter()
+        ts = [srv.submit(c, W, H, "bf16") for c in cams]
+        for t in ts:
+            st, _ = srv.wait(t)
+            assert st == inolf.OK
+        times.append(time.perf_counter() - t0)
+        for t in ts:
+            srv.release(t)
+    srv.close()
+    best = min(times[1:])
+    return {"views": views, "view_res": [W, H], "quilt_ms": best * 1e3, "quilts_per_s": 1.0 / best,
+            "mrays_per_s": views * W * H / best / 1e6, "precision": "bf16"}
+
+
 def run_training(steps=40, batch=1 << 18, n_views=100, res=800, prec="bf16"):
     """Differentiation workload: a teacher object (seed 1) renders 100 target
     views at 800x800; a student (seed 2) trains toward them with batches of
@@ -526,11 +592,14 @@ def run_native(a):
            "precisions": precisions, "hit_mrays_per_s": n_hit * a.steps * world / (ms / 1e3) / 1e6}
     if fp32_acc is not None:
         out["accuracy_vs_oracle"] = fp32_acc
+    if rank == 0 and not a.small:
+        out["zoom_sweep"] = run_zoom_sweep(obj, W, H)
     if rank == 0 and not a.no_serving and not a.small:
         del rgba, ws
         torch.cuda.empty_cache()
         out["serving"] = run_serving(seconds=a.serving_seconds)
         out["training"] = run_training()
+        out["looking_glass"] = run_looking_glass()
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
