@@ -375,13 +375,16 @@ __device__ __forceinline__ void finish_level(const LevelDev& lv, int fp16, const
   const int32_t m = lv.m;
 #pragma unroll
   for (int cc = 0; cc < 8; ++cc) {
-    int32_t sx = ((cc & 1) ? s.h0n[0] : s.h0[0]) + (int32_t)(s.ph[cc] & 1023u);
-    int32_t sy = ((cc & 2) ? s.h0n[1] : s.h0[1]) + (int32_t)((s.ph[cc] >> 10) & 1023u);
-    int32_t sz = ((cc & 4) ? s.h0n[2] : s.h0[2]) + (int32_t)((s.ph[cc] >> 20) & 1023u);
-    sx -= sx >= m ? m : 0;
-    sy -= sy >= m ? m : 0;
-    sz -= sz >= m ? m : 0;
-    slots[cc] = (uint32_t)(sx + m * (sy + m * sz));
+    // (h0 + phi) mod m per axis as min(s, s - m) in unsigned arithmetic
+    // (s < 2m: s - m wraps above s exactly when s < m)
+    const uint32_t um = (uint32_t)m;
+    uint32_t sx = (uint32_t)((cc & 1) ? s.h0n[0] : s.h0[0]) + (s.ph[cc] & 1023u);
+    uint32_t sy = (uint32_t)((cc & 2) ? s.h0n[1] : s.h0[1]) + ((s.ph[cc] >> 10) & 1023u);
+    uint32_t sz = (uint32_t)((cc & 4) ? s.h0n[2] : s.h0[2]) + (s.ph[cc] >> 20);
+    sx = min(sx, sx - um);
+    sy = min(sy, sy - um);
+    sz = min(sz, sz - um);
+    slots[cc] = sx + um * (sy + um * sz);
   }
   float2 v[8];
   if (fp16) {
