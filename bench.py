@@ -227,13 +227,17 @@ def serving_workload(seed: int = 0):
     return scenes, [tuple(map(float, p)) for p in places], viewers
 
 
-def run_serving(seconds=10.0, warmup=1.0, rate_hz=50.0, seed=0, prec="bf16"):
+def run_serving(seconds=10.0, warmup=1.0, rate_hz=50.0, seed=0, prec="bf16", policy=1,
+                max_rays_in_flight=64_000_000):
     """Poisson frame requests of 32 viewers against the persistent request
     loop; returns p50/p99 submit->complete latency, throughput, refusals."""
     import heapq
     from paper_2303_04086_gb300 import inolf, synth
     scenes, places, viewers = serving_workload(seed)
-    srv = inolf.Server(hbm_budget=8 << 30, max_slots=64, max_width=3840, max_height=2160, max_hits=4)
+    srv = inolf.Server(hbm_budget=8 << 30, max_slots=64, max_width=3840, max_height=2160, max_hits=4,
+                       policy=policy, max_rays_in_flight=max_rays_in_flight if policy == 1 else 0)
+    for v in range(len(viewers)):
+        srv.set_viewer(v, rate_hz)
     objs = [inolf.object_create(sc) for sc in scenes]
     for o, p in zip(objs, places):
         srv.add_object(o, p)
@@ -282,6 +286,7 @@ def run_serving(seconds=10.0, warmup=1.0, rate_hz=50.0, seed=0, prec="bf16"):
             break
         time.sleep(0.0002)
     wall = time.perf_counter() - t0 - warmup
+    counters = srv.counters()
     srv.close()
     lat_ms = np.array(lat) * 1e3
     return {"viewers": len(viewers), "objects": len(objs), "rate_hz_per_viewer": rate_hz, "seconds": seconds,
@@ -289,6 +294,8 @@ def run_serving(seconds=10.0, warmup=1.0, rate_hz=50.0, seed=0, prec="bf16"):
             "p50_ms": float(np.percentile(lat_ms, 50)) if len(lat_ms) else None,
             "p99_ms": float(np.percentile(lat_ms, 99)) if len(lat_ms) else None,
             "refused": refused, "submitted": submitted, "precision": prec,
+            "policy": "algorithm1" if policy == 1 else "arrival-order",
+            "max_rays_in_flight": max_rays_in_flight if policy == 1 else None, "counters": counters,
             "note": "latency = arrival time -> completion seen by the poller; refused = admission (slots/HBM "
                     "budget) full at arrival"}
 
@@ -597,7 +604,8 @@ def run_native(a):
     if rank == 0 and not a.no_serving and not a.small:
         del rgba, ws
         torch.cuda.empty_cache()
-        out["serving"] = run_serving(seconds=a.serving_seconds)
+        out["serving"] = run_serving(seconds=a.serving_seconds, policy=1)
+        out["serving_fifo"] = run_serving(seconds=a.serving_seconds, policy=0)
         out["training"] = run_training()
         out["looking_glass"] = run_looking_glass()
     if rank == 0:

@@ -245,6 +245,8 @@ typedef struct {
   int64_t wait_limit_ns;   /* bound of the device wait for a request descriptor, default 1 s */
   int64_t idle_limit_ns;   /* the persistent kernel exits after this long without work, default 20 ms */
   int32_t ctas_per_sm;     /* persistent CTAs per SM, 0 = as many as fit */
+  int32_t policy;          /* 0: dispatch in arrival order; 1: Algorithm 1 (inolf_sched_*) */
+  int64_t max_rays_in_flight; /* policy 1: ray budget of the device (0 = none) */
 } inolf_serve_params;
 
 #define INOLF_REQ_TEST_DROP_DESCRIPTOR 1u /* fault injection: the request descriptor is never published */
@@ -274,6 +276,10 @@ inolf_status inolf_serve_create(const inolf_serve_params* params, inolf_server**
  * flight.  The object must outlive the server. */
 inolf_status inolf_serve_add_object(inolf_server* srv, const inolf_object* obj, const float translation[3]);
 
+/* Target frame rate of a viewer for policy 1 (default 50 Hz: one camera
+ * update every 20 ms, as the paper's clients send). */
+inolf_status inolf_serve_set_viewer(inolf_server* srv, uint32_t viewer_id, double target_fps);
+
 /* Admits a request (INOLF_E_BUDGET when every slot is busy or the frame
  * does not fit the HBM budget: nothing is queued, retry later) and publishes
  * its 16x16 tiles to the running kernel (launching it if idle).  Each pixel
@@ -297,6 +303,41 @@ inolf_status inolf_serve_release(inolf_server* srv, uint64_t ticket);
 /* Stops the persistent kernel (it finishes the tiles it holds) and frees
  * everything. */
 inolf_status inolf_serve_destroy(inolf_server* srv);
+
+/* Counters of the request loop: admitted, refused at admission (slots/HBM
+ * budget), denied by the starvation state (policy 1), completed. */
+inolf_status inolf_serve_counters(inolf_server* srv, int64_t* admitted, int64_t* refused, int64_t* denied,
+                                  int64_t* completed);
+
+/* ------------------------------------------------------------------------ */
+/* Multi-user scheduling policy (Sec. 6.2, Algorithm 1, Eq. 13), host-only.  */
+/* Every call takes the current time in ns from the caller (deterministic).  */
+/* ------------------------------------------------------------------------ */
+typedef struct inolf_sched inolf_sched;
+
+/* max_rays_in_flight: the device's ray budget (0 = unlimited). */
+inolf_status inolf_sched_create(int64_t max_rays_in_flight, inolf_sched** out);
+void inolf_sched_destroy(inolf_sched* s);
+/* Registers a viewer (a client) with its target frame rate FPS_i. */
+inolf_status inolf_sched_set_viewer(inolf_sched* s, uint32_t viewer, double target_fps, int64_t now_ns);
+/* Queues frame `id` of `viewer` with `rays` rays.  INOLF_E_BUDGET when the
+ * scheduler is in the starvation state and the viewer is a new client. */
+inolf_status inolf_sched_admit(inolf_sched* s, uint32_t viewer, uint64_t id, int64_t rays, int64_t now_ns);
+/* Next frame to dispatch: starved frames first (a frame is starved when its
+ * viewer's target time last_frame + w, w = 1/FPS - t, t the moving average
+ * of completion times, has passed), else by the viewers' (frames in flight,
+ * target time) while the rays in flight fit the budget.  INOLF_PENDING when
+ * nothing may be dispatched now. */
+inolf_status inolf_sched_next(inolf_sched* s, int64_t now_ns, uint64_t* id);
+/* Frame `id` finished: updates its viewer's moving average and last frame. */
+inolf_status inolf_sched_complete(inolf_sched* s, uint64_t id, int64_t now_ns);
+/* Drops a frame that is still pending. */
+inolf_status inolf_sched_cancel(inolf_sched* s, uint64_t id);
+/* State: starvation flag, rays in flight, frames pending, admissions denied. */
+inolf_status inolf_sched_state(inolf_sched* s, int64_t now_ns, int32_t* starving, int64_t* rays_in_flight,
+                               int64_t* pending, int64_t* denied);
+/* Current wait time w_i (Eq. 13) and target time of a viewer. */
+inolf_status inolf_sched_wait_ns(inolf_sched* s, uint32_t viewer, int64_t* w_ns, int64_t* target_ns);
 
 /* ------------------------------------------------------------------------ */
 /* Allocation-free rendering (the paper has no counterpart: this exists for   */

@@ -29,9 +29,11 @@
 #include <chrono>
 #include <cstring>
 #include <map>
+#include <atomic>
 #include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "inolf_internal.h"
@@ -504,6 +506,7 @@ using Clock = std::chrono::steady_clock;
 
 struct SlotMeta {
   bool busy = false;
+  bool published = false;
   bool done_seen = false;
   uint64_t ticket = 0;
   uint32_t gen = 0;
@@ -547,7 +550,16 @@ struct inolf_server {
   std::vector<uint32_t> slot_gen;  // last generation issued per slot
   std::map<uint64_t, int> by_ticket;
   uint64_t next_ticket = 1;
+  // scheduling (policy 1: Algorithm 1) and the host dispatcher thread
+  inolf_sched* sched = nullptr;
+  std::thread loop;
+  std::atomic<bool> quit{false};
+  int64_t n_admitted = 0, n_refused = 0, n_denied = 0, n_completed = 0;
 };
+
+static int64_t now_ns() {
+  return std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now().time_since_epoch()).count();
+}
 
 static bool arena_alloc(inolf_server* s, size_t bytes, size_t* off) {
   for (auto it = s->free_blocks.begin(); it != s->free_blocks.end(); ++it) {
@@ -580,6 +592,9 @@ static void arena_free(inolf_server* s, size_t off, size_t bytes) {
 }
 
 static void serve_free(inolf_server* s) {
+  s->quit = true;
+  if (s->loop.joinable()) s->loop.join();
+  if (s->sched) inolf_sched_destroy(s->sched);
   if (s->stream) cudaStreamSynchronize(s->stream);
   if (s->kernel_done) cudaEventDestroy(s->kernel_done);
   if (s->stream) cudaStreamDestroy(s->stream);
@@ -633,6 +648,71 @@ static inolf_status ensure_running(inolf_server* s) {
   return INOLF_OK;
 }
 
+// Publishes the tiles of an admitted request to the device ring (must hold s->mu).
+static inolf_status publish_locked(inolf_server* s, int slot) {
+  SlotMeta& m = s->slots[slot];
+  const uint32_t tx = (uint32_t)((m.W + kServeTile - 1) / kServeTile);
+  const uint32_t ty = (uint32_t)((m.H + kServeTile - 1) / kServeTile);
+  for (uint32_t y = 0; y < ty; ++y)
+    for (uint32_t x = 0; x < tx; ++x) {
+      ServeTile& e = s->h_ring[(s->published + (unsigned long long)y * tx + x) % s->ring_cap];
+      e.slot = (uint32_t)slot;
+      e.gen = m.gen;
+      e.tx = x;
+      e.ty = y;
+      e.tiles_total = tx * ty;
+    }
+  s->published += (unsigned long long)tx * ty;
+  __atomic_store_n(&s->h_ctl->published, s->published, __ATOMIC_RELEASE);
+  m.published = true;
+  return ensure_running(s);
+}
+
+// Records the requests the device has completed (must hold s->mu).
+static void completions_locked(inolf_server* s) {
+  const int64_t t = now_ns();
+  for (int k = 0; k < (int)s->slots.size(); ++k) {
+    SlotMeta& m = s->slots[k];
+    if (!m.busy || !m.published || m.done_seen) continue;
+    if (__atomic_load_n(&s->h_done[k].gen, __ATOMIC_ACQUIRE) != m.gen) continue;
+    m.done_seen = true;
+    m.status = __atomic_load_n(&s->h_done[k].status, __ATOMIC_ACQUIRE);
+    m.latency_ns = std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now() - m.submitted).count();
+    ++s->n_completed;
+    if (s->sched) inolf_sched_complete(s->sched, m.ticket, t);
+  }
+}
+
+// Dispatches admitted requests in the policy's order (must hold s->mu).
+static inolf_status dispatch_locked(inolf_server* s) {
+  if (!s->sched) return INOLF_OK;
+  uint64_t id = 0;
+  while (inolf_sched_next(s->sched, now_ns(), &id) == INOLF_OK) {
+    auto it = s->by_ticket.find(id);
+    if (it == s->by_ticket.end()) continue;
+    const inolf_status st = publish_locked(s, it->second);
+    if (st != INOLF_OK) return st;
+  }
+  return INOLF_OK;
+}
+
+// The host side of the request loop: observes completions, dispatches
+// queued requests and relaunches the persistent kernel when it went idle
+// with work outstanding.
+static void dispatcher(inolf_server* s) {
+  while (!s->quit) {
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      completions_locked(s);
+      dispatch_locked(s);
+      bool outstanding = false;
+      for (auto& m : s->slots) outstanding |= m.busy && m.published && !m.done_seen;
+      if (outstanding) ensure_running(s);
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
 extern "C" inolf_status inolf_serve_create(const inolf_serve_params* prm, inolf_server** out) {
   clear_error();
   if (!out) return fail(INOLF_E_INVALID, "inolf_serve_create: out is NULL");
@@ -646,10 +726,13 @@ extern "C" inolf_status inolf_serve_create(const inolf_serve_params* prm, inolf_
   p.wait_limit_ns = 1000000000;
   p.idle_limit_ns = 20000000;
   p.ctas_per_sm = 0;
+  p.policy = 0;
+  p.max_rays_in_flight = 0;
   if (prm) p = *prm;
   if (p.hbm_budget < 4096 || p.max_slots < 1 || p.max_slots > kServeMaxSlots || p.max_width < 1 ||
       p.max_height < 1 || p.max_width > 16384 || p.max_height > 16384 || p.max_hits < 1 ||
-      p.max_hits > kServeMaxK || p.wait_limit_ns <= 0 || p.idle_limit_ns <= 0 || p.ctas_per_sm < 0)
+      p.max_hits > kServeMaxK || p.wait_limit_ns <= 0 || p.idle_limit_ns <= 0 || p.ctas_per_sm < 0 ||
+      p.policy < 0 || p.policy > 1 || p.max_rays_in_flight < 0)
     return fail(INOLF_E_INVALID, "inolf_serve_create: bad parameters");
   inolf_server* s = new (std::nothrow) inolf_server();
   if (!s) return fail(INOLF_E_OOM, "inolf_serve_create: oom");
@@ -692,7 +775,29 @@ extern "C" inolf_status inolf_serve_create(const inolf_serve_params* prm, inolf_
   if (p.ctas_per_sm > 0) occ = std::min(occ, p.ctas_per_sm);
   s->grid = sms * occ;
   cudaGetLastError();
+  if (p.policy == 1 && inolf_sched_create(p.max_rays_in_flight, &s->sched) != INOLF_OK) return bad("scheduler");
+  s->loop = std::thread(dispatcher, s);
   *out = s;
+  return INOLF_OK;
+}
+
+extern "C" inolf_status inolf_serve_set_viewer(inolf_server* s, uint32_t viewer_id, double target_fps) {
+  clear_error();
+  if (!s || !(target_fps > 0)) return fail(INOLF_E_INVALID, "inolf_serve_set_viewer: bad argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (!s->sched) return INOLF_OK;  // policy 0 ignores target rates
+  return inolf_sched_set_viewer(s->sched, viewer_id, target_fps, now_ns());
+}
+
+extern "C" inolf_status inolf_serve_counters(inolf_server* s, int64_t* admitted, int64_t* refused, int64_t* denied,
+                                             int64_t* completed) {
+  clear_error();
+  if (!s) return fail(INOLF_E_INVALID, "inolf_serve_counters: NULL server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (admitted) *admitted = s->n_admitted;
+  if (refused) *refused = s->n_refused;
+  if (denied) *denied = s->n_denied;
+  if (completed) *completed = s->n_completed;
   return INOLF_OK;
 }
 
@@ -737,14 +842,30 @@ extern "C" inolf_status inolf_serve_submit(inolf_server* s, const inolf_request*
   int slot = -1;
   for (int k = 0; k < (int)s->slots.size(); ++k)
     if (!s->slots[k].busy) { slot = k; break; }
-  if (slot < 0) return fail(INOLF_E_BUDGET, "inolf_serve_submit: all request slots are in use");
+  if (slot < 0) {
+    ++s->n_refused;
+    return fail(INOLF_E_BUDGET, "inolf_serve_submit: all request slots are in use");
+  }
   const size_t bytes = ((size_t)r->width * r->height * 16 + 255) & ~(size_t)255;
   size_t off = 0;
-  if (!arena_alloc(s, bytes, &off)) return fail(INOLF_E_BUDGET, "inolf_serve_submit: HBM budget exhausted");
+  if (!arena_alloc(s, bytes, &off)) {
+    ++s->n_refused;
+    return fail(INOLF_E_BUDGET, "inolf_serve_submit: HBM budget exhausted");
+  }
+  const uint64_t tk = s->next_ticket++;
+  if (s->sched) {
+    const inolf_status a = inolf_sched_admit(s->sched, r->viewer_id, tk, (int64_t)r->width * r->height, now_ns());
+    if (a != INOLF_OK) {
+      arena_free(s, off, bytes);
+      ++s->n_denied;
+      return a;  // INOLF_E_BUDGET in the starvation state
+    }
+  }
+  ++s->n_admitted;
   SlotMeta& m = s->slots[slot];
   m = SlotMeta();
   m.busy = true;
-  m.ticket = s->next_ticket++;
+  m.ticket = tk;
   m.gen = ++s->slot_gen[slot];
   if (m.gen == 0) m.gen = s->slot_gen[slot] = 1;
   m.off = off;
@@ -767,19 +888,9 @@ extern "C" inolf_status inolf_serve_submit(inolf_server* s, const inolf_request*
   // the generation is written last: the device reads the descriptor once it
   // sees this generation (the test-only flag leaves it out)
   if (!(r->flags & INOLF_REQ_TEST_DROP_DESCRIPTOR)) __atomic_store_n(&hs.gen, m.gen, __ATOMIC_RELEASE);
-  for (uint32_t y = 0; y < ty; ++y)
-    for (uint32_t x = 0; x < tx; ++x) {
-      ServeTile& e = s->h_ring[(s->published + (unsigned long long)y * tx + x) % s->ring_cap];
-      e.slot = (uint32_t)slot;
-      e.gen = m.gen;
-      e.tx = x;
-      e.ty = y;
-      e.tiles_total = tx * ty;
-    }
-  s->published += (unsigned long long)tx * ty;
-  __atomic_store_n(&s->h_ctl->published, s->published, __ATOMIC_RELEASE);
   *ticket = m.ticket;
-  return ensure_running(s);
+  if (!s->sched) return publish_locked(s, slot);  // policy 0: arrival order
+  return dispatch_locked(s);
 }
 
 extern "C" inolf_status inolf_serve_poll(inolf_server* s, uint64_t ticket, inolf_result* res) {
@@ -790,14 +901,12 @@ extern "C" inolf_status inolf_serve_poll(inolf_server* s, uint64_t ticket, inolf
   if (it == s->by_ticket.end()) return fail(INOLF_E_UNKNOWN_TICKET, "inolf_serve_poll: unknown ticket");
   SlotMeta& m = s->slots[it->second];
   if (!m.done_seen) {
-    const uint32_t g = __atomic_load_n(&s->h_done[it->second].gen, __ATOMIC_ACQUIRE);
-    if (g != m.gen) {
-      const inolf_status e = ensure_running(s);  // relaunch if the kernel went idle
+    completions_locked(s);
+    if (!m.done_seen) {
+      inolf_status e = dispatch_locked(s);
+      if (e == INOLF_OK && m.published) e = ensure_running(s);  // relaunch if the kernel went idle
       return e != INOLF_OK ? e : INOLF_PENDING;
     }
-    m.done_seen = true;
-    m.status = __atomic_load_n(&s->h_done[it->second].status, __ATOMIC_ACQUIRE);
-    m.latency_ns = std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now() - m.submitted).count();
   }
   if (res) {
     res->frame = reinterpret_cast<const float*>(s->arena + m.off);
@@ -817,6 +926,13 @@ extern "C" inolf_status inolf_serve_cancel(inolf_server* s, uint64_t ticket) {
   std::lock_guard<std::mutex> lk(s->mu);
   auto it = s->by_ticket.find(ticket);
   if (it == s->by_ticket.end()) return fail(INOLF_E_UNKNOWN_TICKET, "inolf_serve_cancel: unknown ticket");
+  SlotMeta& m = s->slots[it->second];
+  if (!m.published && s->sched && inolf_sched_cancel(s->sched, ticket) == INOLF_OK) {
+    m.done_seen = true;  // never reached the device
+    m.status = INOLF_E_CANCELLED;
+    m.latency_ns = std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now() - m.submitted).count();
+    return INOLF_OK;
+  }
   __atomic_store_n(&s->h_slots[it->second].cancelled, 1u, __ATOMIC_RELEASE);
   return INOLF_OK;
 }
@@ -838,6 +954,8 @@ extern "C" inolf_status inolf_serve_release(inolf_server* s, uint64_t ticket) {
 extern "C" inolf_status inolf_serve_destroy(inolf_server* s) {
   clear_error();
   if (!s) return INOLF_OK;
+  s->quit = true;
+  if (s->loop.joinable()) s->loop.join();
   {
     std::lock_guard<std::mutex> lk(s->mu);
     __atomic_store_n(&s->h_ctl->stop, 1u, __ATOMIC_RELEASE);

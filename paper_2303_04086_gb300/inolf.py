@@ -441,7 +441,8 @@ class Field:
 class ServeParams(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_size_t), ("max_slots", ctypes.c_int32), ("max_width", ctypes.c_int32),
                 ("max_height", ctypes.c_int32), ("max_hits", ctypes.c_int32), ("wait_limit_ns", ctypes.c_int64),
-                ("idle_limit_ns", ctypes.c_int64), ("ctas_per_sm", ctypes.c_int32)]
+                ("idle_limit_ns", ctypes.c_int64), ("ctas_per_sm", ctypes.c_int32), ("policy", ctypes.c_int32),
+                ("max_rays_in_flight", ctypes.c_int64)]
 
 
 class Request(ctypes.Structure):
@@ -477,7 +478,8 @@ class Server:
     """inolf_server: persistent-kernel request loop over resident objects."""
 
     def __init__(self, hbm_budget=4 << 30, max_slots=48, max_width=3840, max_height=2160, max_hits=4,
-                 wait_limit_ns=1_000_000_000, idle_limit_ns=20_000_000, ctas_per_sm=0):
+                 wait_limit_ns=1_000_000_000, idle_limit_ns=20_000_000, ctas_per_sm=0, policy=0,
+                 max_rays_in_flight=0):
         L = lib()
         vp = ctypes.c_void_p
         L.inolf_serve_create.argtypes = [ctypes.POINTER(ServeParams), ctypes.POINTER(vp)]
@@ -487,8 +489,10 @@ class Server:
         L.inolf_serve_cancel.argtypes = [vp, ctypes.c_uint64]
         L.inolf_serve_release.argtypes = [vp, ctypes.c_uint64]
         L.inolf_serve_destroy.argtypes = [vp]
+        L.inolf_serve_set_viewer.argtypes = [vp, ctypes.c_uint32, ctypes.c_double]
+        L.inolf_serve_counters.argtypes = [vp] + [ctypes.POINTER(ctypes.c_int64)] * 4
         prm = ServeParams(hbm_budget, max_slots, max_width, max_height, max_hits, wait_limit_ns, idle_limit_ns,
-                          ctas_per_sm)
+                          ctas_per_sm, policy, max_rays_in_flight)
         h = vp()
         _check(L.inolf_serve_create(ctypes.byref(prm), ctypes.byref(h)))
         self._h = h.value
@@ -539,6 +543,14 @@ class Server:
     def cancel(self, ticket: int):
         _check(lib().inolf_serve_cancel(self._h, ticket))
 
+    def set_viewer(self, viewer_id: int, target_fps: float):
+        _check(lib().inolf_serve_set_viewer(self._h, viewer_id, target_fps))
+
+    def counters(self) -> dict:
+        v = [ctypes.c_int64() for _ in range(4)]
+        _check(lib().inolf_serve_counters(self._h, *[ctypes.byref(x) for x in v]))
+        return dict(zip(("admitted", "refused", "denied", "completed"), (x.value for x in v)))
+
     def release(self, ticket: int):
         _check(lib().inolf_serve_release(self._h, ticket))
 
@@ -549,3 +561,62 @@ class Server:
 
     def __del__(self):
         self.close()
+
+
+# ---------------------------------------------------------------------------
+# scheduling policy (Algorithm 1), host-only
+# ---------------------------------------------------------------------------
+class Scheduler:
+    """inolf_sched: the multi-user dispatch policy; times are given in ns."""
+
+    def __init__(self, max_rays_in_flight: int = 0):
+        L = lib()
+        vp, i64, u32, u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64
+        L.inolf_sched_create.argtypes = [i64, ctypes.POINTER(vp)]
+        L.inolf_sched_destroy.argtypes = [vp]
+        L.inolf_sched_destroy.restype = None
+        L.inolf_sched_set_viewer.argtypes = [vp, u32, ctypes.c_double, i64]
+        L.inolf_sched_admit.argtypes = [vp, u32, u64, i64, i64]
+        L.inolf_sched_next.argtypes = [vp, i64, ctypes.POINTER(u64)]
+        L.inolf_sched_complete.argtypes = [vp, u64, i64]
+        L.inolf_sched_cancel.argtypes = [vp, u64]
+        L.inolf_sched_state.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_int32)] + [ctypes.POINTER(i64)] * 3
+        L.inolf_sched_wait_ns.argtypes = [vp, u32, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        h = vp()
+        _check(L.inolf_sched_create(max_rays_in_flight, ctypes.byref(h)))
+        self._h = h.value
+
+    def set_viewer(self, viewer, fps, now):
+        _check(lib().inolf_sched_set_viewer(self._h, viewer, fps, now))
+
+    def admit(self, viewer, fid, rays, now) -> int:
+        """Status: OK, or E_BUDGET when a new client is denied (starvation)."""
+        return lib().inolf_sched_admit(self._h, viewer, fid, rays, now)
+
+    def next(self, now):
+        i = ctypes.c_uint64()
+        st = lib().inolf_sched_next(self._h, now, ctypes.byref(i))
+        return i.value if st == OK else None
+
+    def complete(self, fid, now):
+        _check(lib().inolf_sched_complete(self._h, fid, now))
+
+    def cancel(self, fid) -> int:
+        return lib().inolf_sched_cancel(self._h, fid)
+
+    def state(self, now) -> dict:
+        st = ctypes.c_int32()
+        v = [ctypes.c_int64() for _ in range(3)]
+        _check(lib().inolf_sched_state(self._h, now, ctypes.byref(st), *[ctypes.byref(x) for x in v]))
+        return {"starving": bool(st.value), "rays_in_flight": v[0].value, "pending": v[1].value,
+                "denied": v[2].value}
+
+    def wait_ns(self, viewer):
+        w, t = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().inolf_sched_wait_ns(self._h, viewer, ctypes.byref(w), ctypes.byref(t)))
+        return w.value, t.value
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.inolf_sched_destroy(self._h)
+            self._h = None

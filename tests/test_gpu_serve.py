@@ -237,3 +237,28 @@ def test_bf16_serving_matches_render_and_oracle(env):
             ref[px, :3] = C / A
             ref[px, 3] = A
     assert np.abs(got - ref).max() <= 1e-2
+
+
+def test_algorithm1_policy_serves_all_viewers(env):
+    torch, inolf, scenes, objs = env
+    srv = _multi_server(inolf, objs, hbm_budget=256 << 20, max_slots=16, max_width=512, max_height=512,
+                        policy=1, max_rays_in_flight=300_000)
+    for v in range(4):
+        srv.set_viewer(v, 60.0 + 20 * v)
+    cam = synth.camera((1.0, 2.0, 9.0), target=(0.0, 0.0, -0.5))
+    ref_t = srv.submit(cam, 320, 200, viewer_id=0)
+    st, res = _done(srv, ref_t)
+    assert st == inolf.OK
+    ref = srv.frame(res).cpu().numpy()
+    srv.release(ref_t)
+    tickets = []
+    for k in range(12):
+        tickets.append((srv.submit(cam, 320, 200, viewer_id=k % 4), k))
+    for t, k in tickets:
+        st, res = _done(srv, t)
+        assert st == inolf.OK
+        assert np.abs(srv.frame(res).cpu().numpy() - ref).max() <= TOL  # same frame whatever the order
+        srv.release(t)
+    c = srv.counters()
+    assert c["admitted"] == 13 and c["completed"] == 13 and c["denied"] == 0
+    srv.close()
