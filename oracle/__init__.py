@@ -11,11 +11,19 @@ of the 8 corner features with FP64 trilinear interpolation, FP64 real SH of
 degree <= 3 of the view direction, and the FP64 MLP F_s (ReLU, ReLU,
 sigmoid).  The analytic FP64 backward follows the L2 objective of Eq. 8.
 
+The decoupled variant of Sec. 4.2 (Eqs. 4-7) is :class:`Cubes` (density
+march: hit = first sample of largest weight w_i, alpha_c = accumulated weight)
+plus :meth:`Oracle.render_variant_rays` (F_s with alpha_c input, c = c_d + t c_s
+from the diffuse cubes).
+
 Pins (see tests/test_oracle_*.py): brute-force hits on tiny meshes, analytic
 sphere intersection, a hand-checked triangle, affine-field reproduction of the
 interpolation, SH closed form / orthonormality / addition theorem, a
 hand-evaluated 2-ray MLP, central finite differences of the gradient, and
-Eq. 1 checked for injectivity on hashes built by the library.
+Eq. 1 checked for injectivity on hashes built by the library; for the march:
+homogeneous-medium transmittance in closed form, the entry-sample argmax, the
+telescoping sum of the weights, affine density fields, zero density, the
+analytic sphere-shell radius of hit points, and the Eq. 7 special cases.
 """
 from __future__ import annotations
 
@@ -76,6 +84,16 @@ def lib():
     L.orc_backward.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp, vp]
     L.orc_preacts.argtypes = [vp, vp, vp, i64, vp, vp]
     L.orc_psh_slots.argtypes = [vp, i32, i32, vp, i64, vp]
+    L.orc_cubes_create.argtypes = [i32, i32, i64, vp, vp, vp, f32, f32, f32, f32, f32, f32]
+    L.orc_cubes_create.restype = vp
+    L.orc_cubes_free.argtypes = [vp]
+    L.orc_density.argtypes = [vp, vp, vp, vp, i64, vp]
+    L.orc_march.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.orc_shade_variant_at.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp]
+    L.orc_render_variant_rays.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp, vp]
+    L.orc_render_variant_rays.restype = i64
+    L.orc_render_variant_pixels.argtypes = [vp, vp, vp, i32, i32, vp, i64, vp, vp, vp, vp]
+    L.orc_render_variant_pixels.restype = i64
     L.orc_max_threads.restype = i32
     L.orc_set_threads.argtypes = [i32]
     _lib = L
@@ -197,6 +215,7 @@ class Oracle:
             np.float32(s.domain_lo), np.float32(1.0 / s.domain_side))
         if not self.h:
             raise ValueError("oracle scene rejected its inputs")
+        self.cubes = None if getattr(s, "cubes", None) is None else Cubes(s.cubes, lo=s.domain_lo)
 
     def __del__(self):
         if getattr(self, "h", None):
@@ -255,3 +274,88 @@ class Oracle:
         z1 = np.empty((len(o), self.hidden)); z2 = np.empty((len(o), self.hidden))
         lib().orc_preacts(self.h, _p(o), _p(d), len(o), _p(z1), _p(z2))
         return z1, z2
+
+
+class Cubes:
+    """The oracle's view of a ``synth.Cubes`` record: the density / diffuse
+    value of a fine vertex is the one any listed cube gives it (0 if none)."""
+
+    def __init__(self, cubes, lo: float = -1.5):
+        self.c = cubes
+        self._cells = np.ascontiguousarray(cubes.cells, np.int32)
+        self._dens = _f32(cubes.density)
+        self._diff = None if cubes.diffuse is None else _f32(cubes.diffuse)
+        side = np.float32(cubes.side)
+        self.h = lib().orc_cubes_create(int(cubes.b), int(cubes.r), len(self._cells), _p(self._cells),
+                                        _p(self._dens), _p(self._diff), np.float32(lo),
+                                        np.float32(1.0 / float(cubes.side)), side, np.float32(cubes.step),
+                                        np.float32(cubes.t_min), np.float32(cubes.alpha_miss))
+        if not self.h:
+            raise ValueError("oracle cubes rejected their inputs")
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().orc_cubes_free(self.h)
+            self.h = None
+
+    def density(self, o, d, t) -> np.ndarray:
+        """FP32 density at o + t d."""
+        o = _f32(o); d = _f32(d); t = _f32(t)
+        out = np.empty(len(o), np.float32)
+        lib().orc_density(self.h, _p(o), _p(d), _p(t), len(o), _p(out))
+        return out
+
+    def march(self, o, d) -> dict:
+        """Hit sample k (-1 = miss), its t, alpha_c, the two largest weights
+        with their samples, the samples taken and the last T before the stop."""
+        o = _f32(o); d = _f32(d)
+        n = len(o)
+        out = {"k": np.empty(n, np.int32), "t": np.empty(n, np.float32), "alpha": np.empty(n, np.float32),
+               "wmax": np.empty(n, np.float32), "k2": np.empty(n, np.int32), "w2": np.empty(n, np.float32),
+               "n": np.empty(n, np.int32), "T_prev": np.empty(n, np.float32)}
+        lib().orc_march(self.h, _p(o), _p(d), n, *[_p(out[k]) for k in ("k", "t", "alpha", "wmax", "k2", "w2",
+                                                                          "n", "T_prev")])
+        return out
+
+
+def _variant_handles(orc):
+    if orc.cubes is None:
+        raise ValueError("the scene has no density cubes")
+    return orc.h, orc.cubes.h
+
+
+def _attach_variant():
+    def render_variant_rays(self, o, d):
+        hs, hc = _variant_handles(self)
+        o = _f32(o); d = _f32(d)
+        n = len(o)
+        rgba = np.empty((n, 4), np.float64)
+        k = np.empty(n, np.int32); t = np.empty(n, np.float32); a = np.empty(n, np.float32)
+        missing = lib().orc_render_variant_rays(hs, hc, _p(o), _p(d), n, _p(rgba), _p(k), _p(t), _p(a))
+        return {"rgba": rgba, "k": k, "t": t, "alpha": a, "missing": int(missing)}
+
+    def render_variant_pixels(self, cam, W: int, H: int, pix: Optional[np.ndarray] = None):
+        hs, hc = _variant_handles(self)
+        cam = _f32(cam)
+        n = W * H if pix is None else len(pix)
+        pix = None if pix is None else np.ascontiguousarray(pix, np.int64)
+        rgba = np.empty((n, 4), np.float64)
+        k = np.empty(n, np.int32); t = np.empty(n, np.float32); a = np.empty(n, np.float32)
+        missing = lib().orc_render_variant_pixels(hs, hc, _p(cam), W, H, _p(pix), n, _p(rgba), _p(k), _p(t),
+                                                  _p(a))
+        return {"rgba": rgba, "k": k, "t": t, "alpha": a, "missing": int(missing)}
+
+    def shade_variant_at(self, o, d, t, alpha_c):
+        """Variant shading (Eqs. 5, 7) at given hits (t, alpha_c)."""
+        hs, hc = _variant_handles(self)
+        o = _f32(o); d = _f32(d); t = _f32(t); alpha_c = _f32(alpha_c)
+        rgba = np.empty((len(o), 4), np.float64)
+        lib().orc_shade_variant_at(hs, hc, _p(o), _p(d), _p(t), _p(alpha_c), len(o), _p(rgba))
+        return rgba
+
+    Oracle.render_variant_rays = render_variant_rays
+    Oracle.render_variant_pixels = render_variant_pixels
+    Oracle.shade_variant_at = shade_variant_at
+
+
+_attach_variant()

@@ -24,7 +24,13 @@
  *   6. the MLP F_s of Eq. 3: 64 ReLU, 64 ReLU, 4 sigmoid, no bias, FP64;
  *   7. misses render (0, 0, 0, 0);
  *   8. the analytic FP64 gradient of the per-ray outputs with respect to the
- *      weights and the corner features, for the L2 objective of Eq. 8.
+ *      weights and the corner features, for the L2 objective of Eq. 8;
+ *   9. the paper's decoupled variant (Sec. 4.2, Eqs. 4-7): the hit point is
+ *      the march sample of largest blending weight w_i = T_i (1 - exp(-sigma_i
+ *      delta)) (Eq. 4) through a density field given as texture cubes, the
+ *      coarse opacity alpha_c = sum_i w_i is an extra input of F_s (Eq. 5),
+ *      and the colour is c = c_d + t c_s (Eq. 7) with (c_d, t) read from
+ *      diffuse texture cubes at the hit point.
  *
  * Every FP32 step is written as separate IEEE operations; this file must be
  * compiled with -ffp-contract=off (no fused multiply-add), so that the same
@@ -397,6 +403,7 @@ typedef struct {
   orc_bvh* bvh;
   orc_domain dom;
   int32_t L, nfeat, d_in, hidden, d_out;
+  int32_t alpha_in; /* 1: the last MLP input is alpha_c (Eq. 5) */
   int32_t N[ORC_MAX_LEVELS];
   int64_t nkeys[ORC_MAX_LEVELS];
   uint64_t* keys[ORC_MAX_LEVELS];
@@ -424,12 +431,13 @@ void* orc_scene_create(const float* V, const int32_t* F, int32_t nF, int32_t L, 
                        const uint64_t* const* keys, const int64_t* nkeys, const float* const* feats, int32_t nfeat,
                        const float* w1, const float* w2, const float* w3, int32_t d_in, int32_t hidden,
                        int32_t d_out, float lo, float scale) {
-  if (L < 1 || L > ORC_MAX_LEVELS || d_in != L * nfeat + 16) return 0;
+  if (L < 1 || L > ORC_MAX_LEVELS || (d_in != L * nfeat + 16 && d_in != L * nfeat + 17)) return 0;
   orc_scene* s = (orc_scene*)calloc(1, sizeof(orc_scene));
   s->bvh = (orc_bvh*)orc_bvh_build(V, F, nF);
   s->dom.lo = lo;
   s->dom.scale = scale;
   s->L = L; s->nfeat = nfeat; s->d_in = d_in; s->hidden = hidden; s->d_out = d_out;
+  s->alpha_in = d_in == L * nfeat + 17;
   for (int32_t l = 0; l < L; ++l) {
     s->N[l] = N[l];
     s->nkeys[l] = nkeys[l];
@@ -770,6 +778,319 @@ void orc_psh_slots(const uint32_t* phi, int32_t m, int32_t r, const int32_t* coo
     for (int q = 0; q < 3; ++q) s[q] = (h0[q] + ph[q]) % m;
     slots[i] = s[0] + (int64_t)m * (s[1] + (int64_t)m * s[2]);
   }
+}
+
+/* ------------------------------------------------------------------------ */
+/* 9. The decoupled variant (Sec. 4.2 "Hit Point Estimation and Opacity      */
+/*    Refinement", "Diffuse and Specular Component", "Density Texture        */
+/*    Cubes", "Diffuse Texture Cubes").                                      */
+/*                                                                            */
+/* Density: a field on the fine vertex lattice K = b r of the scene cube,    */
+/* given as cubes: cube i covers base cell cells[i] and lists the values of  */
+/* its (r+1)^3 vertices cells[i] r + (0..r)^3 (x fastest).  The value at a   */
+/* vertex is the one listed by any cube that contains it, 0 when no cube     */
+/* does.  The density at a point is the trilinear interpolation of its fine  */
+/* cell's 8 vertices written as successive linear interpolations along x,   */
+/* then y, then z, lerp(a, b, f) = a + f (b - a), in FP32 (the filtering a  */
+/* texture unit performs; FP32 because it decides the argmax below).        */
+/*                                                                            */
+/* March: samples t_k = t0 + k delta (FP32), k = 0, 1, ... while t_k <= t1,  */
+/* where [t0, t1] is the ray's span inside the scene cube (t0 >= 0).  With   */
+/* T_0 = 1 and e_k = exp(-sigma_k delta):  w_k = T_k (1 - e_k),              */
+/* T_{k+1} = T_k e_k (Eq. 4 evaluated sample by sample, FP32).  The march    */
+/* stops after the sample that brings T below t_min.  The hit sample is the  */
+/* first k of largest w_k; alpha_c = 1 - T at the stop (= sum_k w_k, the     */
+/* accumulated weights of Eq. 5); the ray misses when alpha_c <= alpha_miss. */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  int32_t b, r;
+  int64_t K, n;
+  uint64_t* ckeys;  /* sorted base-cell keys of the listed cubes */
+  int64_t* cidx;    /* cube index of ckeys[i] */
+  const float* dens;
+  const float* diff;
+  float lo, scale, side, step, t_min, alpha_miss;
+} orc_cubes;
+
+static int cmp_u64pair(const void* a, const void* b) {
+  const uint64_t x = ((const uint64_t*)a)[0], y = ((const uint64_t*)b)[0];
+  return (x > y) - (x < y);
+}
+
+/* The density / diffuse arrays are referenced, not copied: the caller keeps
+ * them alive while the handle exists. */
+void* orc_cubes_create(int32_t b, int32_t r, int64_t n, const int32_t* cells, const float* dens, const float* diff,
+                       float lo, float scale, float side, float step, float t_min, float alpha_miss) {
+  if (b < 1 || r < 1 || n < 0 || !(step > 0.0f)) return 0;
+  orc_cubes* c = (orc_cubes*)calloc(1, sizeof(orc_cubes));
+  c->b = b; c->r = r; c->K = (int64_t)b * r; c->n = n;
+  c->dens = dens; c->diff = diff;
+  c->lo = lo; c->scale = scale; c->side = side; c->step = step; c->t_min = t_min; c->alpha_miss = alpha_miss;
+  uint64_t* pairs = (uint64_t*)malloc(sizeof(uint64_t) * 2 * (size_t)(n > 0 ? n : 1));
+  for (int64_t i = 0; i < n; ++i) {
+    pairs[2 * i] = pack_key(cells[3 * i], cells[3 * i + 1], cells[3 * i + 2]);
+    pairs[2 * i + 1] = (uint64_t)i;
+  }
+  qsort(pairs, (size_t)n, 2 * sizeof(uint64_t), cmp_u64pair);
+  c->ckeys = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(n > 0 ? n : 1));
+  c->cidx = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  for (int64_t i = 0; i < n; ++i) { c->ckeys[i] = pairs[2 * i]; c->cidx[i] = (int64_t)pairs[2 * i + 1]; }
+  free(pairs);
+  return c;
+}
+
+void orc_cubes_free(void* h) {
+  orc_cubes* c = (orc_cubes*)h;
+  if (!c) return;
+  free(c->ckeys);
+  free(c->cidx);
+  free(c);
+}
+
+/* Cube index and in-cube vertex offset of fine vertex v, or -1 when no cube
+ * lists it.  Candidate cubes along an axis: v / r, and v / r - 1 when v is on
+ * a cube face. */
+static int64_t vertex_entry(const orc_cubes* c, const int64_t v[3], int64_t* at) {
+  int64_t cand[3][2];
+  int nc[3];
+  for (int q = 0; q < 3; ++q) {
+    nc[q] = 0;
+    int64_t a = v[q] / c->r;
+    if (a < c->b) cand[q][nc[q]++] = a;
+    if (v[q] % c->r == 0 && a - 1 >= 0) cand[q][nc[q]++] = a - 1;
+  }
+  for (int iz = 0; iz < nc[2]; ++iz)
+    for (int iy = 0; iy < nc[1]; ++iy)
+      for (int ix = 0; ix < nc[0]; ++ix) {
+        int64_t k = find_key(c->ckeys, c->n, pack_key(cand[0][ix], cand[1][iy], cand[2][iz]));
+        if (k < 0) continue;
+        int64_t lx = v[0] - cand[0][ix] * c->r, ly = v[1] - cand[1][iy] * c->r, lz = v[2] - cand[2][iz] * c->r;
+        *at = lx + (int64_t)(c->r + 1) * (ly + (int64_t)(c->r + 1) * lz);
+        return c->cidx[k];
+      }
+  return -1;
+}
+
+static float vertex_density(const orc_cubes* c, const int64_t v[3]) {
+  int64_t at;
+  int64_t i = vertex_entry(c, v, &at);
+  return i < 0 ? 0.0f : c->dens[i * (int64_t)(c->r + 1) * (c->r + 1) * (c->r + 1) + at];
+}
+
+static float lerp32(float a, float b, float f) {
+  float diff = b - a;
+  float step = f * diff;
+  return a + step;
+}
+
+/* fine cell and fractions of the point o + t d (the FP32 steps of cell_of at N = K) */
+static void fine_cell(const orc_cubes* c, const float o[3], const float d[3], float t, int64_t cell[3],
+                      float f[3]) {
+  orc_domain dom = {c->lo, c->scale};
+  int32_t ci[3];
+  cell_of(dom, (int32_t)c->K, o, d, t, ci, f);
+  for (int q = 0; q < 3; ++q) cell[q] = ci[q];
+}
+
+static float density_at(const orc_cubes* c, const float o[3], const float d[3], float t) {
+  int64_t cell[3];
+  float f[3];
+  fine_cell(c, o, d, t, cell, f);
+  float s[8];
+  for (int k = 0; k < 8; ++k) {
+    int64_t v[3] = {cell[0] + (k & 1), cell[1] + ((k >> 1) & 1), cell[2] + ((k >> 2) & 1)};
+    s[k] = vertex_density(c, v);
+  }
+  float a00 = lerp32(s[0], s[1], f[0]);  /* y0 z0 */
+  float a10 = lerp32(s[2], s[3], f[0]);  /* y1 z0 */
+  float a01 = lerp32(s[4], s[5], f[0]);  /* y0 z1 */
+  float a11 = lerp32(s[6], s[7], f[0]);  /* y1 z1 */
+  float b0 = lerp32(a00, a10, f[1]);
+  float b1 = lerp32(a01, a11, f[1]);
+  return lerp32(b0, b1, f[2]);
+}
+
+void orc_density(const void* h, const float* o, const float* d, const float* t, int64_t n, float* sigma) {
+  const orc_cubes* c = (const orc_cubes*)h;
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) sigma[i] = density_at(c, o + 3 * i, d + 3 * i, t[i]);
+}
+
+/* Span [t0, t1] of the ray inside the scene cube [lo, lo + side]^3 (slab
+ * test in FP32: per axis (plane - o) / d, axes with d = 0 only test o).
+ * Returns 0 when the ray does not enter it. */
+static int cube_span(const orc_cubes* c, const float o[3], const float d[3], float* t0, float* t1) {
+  const float lo = c->lo, hi = c->lo + c->side;
+  float a = 0.0f, z = INFINITY;
+  for (int q = 0; q < 3; ++q) {
+    if (d[q] == 0.0f) {
+      if (o[q] < lo || o[q] > hi) return 0;
+      continue;
+    }
+    float ta = (lo - o[q]) / d[q];
+    float tb = (hi - o[q]) / d[q];
+    float tn = ta < tb ? ta : tb, tf = ta < tb ? tb : ta;
+    if (tn > a) a = tn;
+    if (tf < z) z = tf;
+  }
+  if (a > z) return 0;
+  *t0 = a;
+  *t1 = z;
+  return 1;
+}
+
+typedef struct {
+  int32_t k;      /* hit sample, -1 = miss */
+  float t;        /* its t (0 on miss) */
+  float alpha;    /* alpha_c = 1 - T at the stop */
+  float wmax;     /* largest weight */
+  int32_t k2;     /* sample of the second largest weight (-1 if none) */
+  float w2;
+  int32_t n;      /* samples taken */
+  float T_prev;   /* transmittance before the last sample (stop-decision margin) */
+} orc_march_res;
+
+static void march_ray(const orc_cubes* c, const float o[3], const float d[3], orc_march_res* m) {
+  m->k = -1; m->t = 0.0f; m->alpha = 0.0f; m->wmax = 0.0f; m->k2 = -1; m->w2 = 0.0f; m->n = 0; m->T_prev = 1.0f;
+  float t0, t1;
+  if (!cube_span(c, o, d, &t0, &t1)) return;
+  float T = 1.0f;
+  int32_t kbest = -1;
+  float tbest = 0.0f;
+  for (int32_t k = 0;; ++k) {
+    float t = t0 + (float)k * c->step;
+    if (t > t1) break;
+    m->n = k + 1;
+    float sigma = density_at(c, o, d, t);
+    float e = expf(-(sigma * c->step));
+    float w = T * (1.0f - e);
+    m->T_prev = T;
+    T = T * e;
+    if (w > m->wmax) {
+      m->w2 = m->wmax; m->k2 = kbest;
+      m->wmax = w; kbest = k; tbest = t;
+    } else if (w > m->w2) {
+      m->w2 = w; m->k2 = k;
+    }
+    if (T < c->t_min) break;
+  }
+  m->alpha = 1.0f - T;
+  if (m->alpha > c->alpha_miss && kbest >= 0) {
+    m->k = kbest;
+    m->t = tbest;
+  }
+}
+
+/* Stage output of the march for n explicit rays (any output may be NULL). */
+void orc_march(const void* h, const float* o, const float* d, int64_t n, int32_t* k, float* t, float* alpha,
+               float* wmax, int32_t* k2, float* w2, int32_t* nsamp, float* T_prev) {
+  const orc_cubes* c = (const orc_cubes*)h;
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t i = 0; i < n; ++i) {
+    orc_march_res m;
+    march_ray(c, o + 3 * i, d + 3 * i, &m);
+    if (k) k[i] = m.k;
+    if (t) t[i] = m.t;
+    if (alpha) alpha[i] = m.alpha;
+    if (wmax) wmax[i] = m.wmax;
+    if (k2) k2[i] = m.k2;
+    if (w2) w2[i] = m.w2;
+    if (nsamp) nsamp[i] = m.n;
+    if (T_prev) T_prev[i] = m.T_prev;
+  }
+}
+
+/* Diffuse (c_d r, g, b, tint) at the point o + t d: FP64 trilinear of the 4
+ * channels of its fine cell's vertices, weights prod_axis (bit ? f : 1 - f).
+ * Returns the number of corners no cube lists (their channels count as 0). */
+static int diffuse_at(const orc_cubes* c, const float o[3], const float d[3], float t, double out[4]) {
+  int64_t cell[3];
+  float f[3];
+  fine_cell(c, o, d, t, cell, f);
+  int missing = 0;
+  for (int ch = 0; ch < 4; ++ch) out[ch] = 0.0;
+  const int64_t nv = (int64_t)(c->r + 1) * (c->r + 1) * (c->r + 1);
+  for (int k = 0; k < 8; ++k) {
+    int64_t v[3] = {cell[0] + (k & 1), cell[1] + ((k >> 1) & 1), cell[2] + ((k >> 2) & 1)};
+    double w = 1.0;
+    for (int q = 0; q < 3; ++q) w *= ((k >> q) & 1) ? (double)f[q] : 1.0 - (double)f[q];
+    int64_t at;
+    int64_t i = vertex_entry(c, v, &at);
+    if (i < 0 || !c->diff) { ++missing; continue; }
+    const float* p = c->diff + (size_t)(i * nv + at) * 4;
+    for (int ch = 0; ch < 4; ++ch) out[ch] += w * (double)p[ch];
+  }
+  return missing;
+}
+
+/* Shading of the variant at a given hit: x = [E(P), SH(d), alpha_c] (Eq. 5),
+ * (c_s, alpha) = F_s(x), (c_d, tint) from the diffuse cubes, c = c_d + tint
+ * c_s (Eq. 7); rgba = (c, alpha).  Returns missing corner lookups. */
+static int64_t shade_variant(const orc_scene* s, const orc_cubes* c, const float o[3], const float d[3], float t,
+                             float alpha_c, double* rgba) {
+  double x[ORC_MAXD], z1[ORC_MAXD], a1[ORC_MAXD], z2[ORC_MAXD], a2[ORC_MAXD], out[8];
+  int64_t miss = encode_ray(s, o, d, t, x, 0, 0);
+  double dir[3] = {d[0], d[1], d[2]};
+  orc_sh16(dir, x + s->L * s->nfeat);
+  x[s->L * s->nfeat + 16] = (double)alpha_c;
+  mlp_forward(s, x, z1, a1, z2, a2, out);
+  double df[4];
+  miss += diffuse_at(c, o, d, t, df);
+  for (int ch = 0; ch < 3; ++ch) rgba[ch] = df[ch] + df[3] * out[ch];
+  rgba[3] = out[3];
+  return miss;
+}
+
+void orc_shade_variant_at(const void* hs, const void* hc, const float* o, const float* d, const float* t,
+                          const float* alpha_c, int64_t n, double* rgba) {
+  const orc_scene* s = (const orc_scene*)hs;
+  const orc_cubes* c = (const orc_cubes*)hc;
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t i = 0; i < n; ++i) shade_variant(s, c, o + 3 * i, d + 3 * i, t[i], alpha_c[i], rgba + 4 * i);
+}
+
+/* The variant end to end for explicit rays or for pixels of one view
+ * (cam != NULL: pix = j * W + i, NULL = all).  k / t / alpha may be NULL.
+ * Misses render (0, 0, 0, 0).  Returns missing corner lookups. */
+static int64_t render_variant_one(const orc_scene* s, const orc_cubes* c, const float o[3], const float d[3],
+                                  double* rgba, int32_t* k, float* t, float* alpha) {
+  orc_march_res m;
+  march_ray(c, o, d, &m);
+  if (k) *k = m.k;
+  if (t) *t = m.t;
+  if (alpha) *alpha = m.alpha;
+  if (m.k < 0) {
+    for (int ch = 0; ch < 4; ++ch) rgba[ch] = 0.0;
+    return 0;
+  }
+  return shade_variant(s, c, o, d, m.t, m.alpha, rgba);
+}
+
+int64_t orc_render_variant_rays(const void* hs, const void* hc, const float* o, const float* d, int64_t n,
+                                double* rgba, int32_t* k, float* t, float* alpha) {
+  const orc_scene* s = (const orc_scene*)hs;
+  const orc_cubes* c = (const orc_cubes*)hc;
+  int64_t missing = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : missing)
+  for (int64_t i = 0; i < n; ++i)
+    missing += render_variant_one(s, c, o + 3 * i, d + 3 * i, rgba + 4 * i, k ? k + i : 0, t ? t + i : 0,
+                                  alpha ? alpha + i : 0);
+  return missing;
+}
+
+int64_t orc_render_variant_pixels(const void* hs, const void* hc, const float* cam, int32_t W, int32_t H,
+                                  const int64_t* pix, int64_t n, double* rgba, int32_t* k, float* t, float* alpha) {
+  const orc_scene* s = (const orc_scene*)hs;
+  const orc_cubes* c = (const orc_cubes*)hc;
+  int64_t missing = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : missing)
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t p = pix ? pix[i] : i;
+    float o[3], d[3];
+    orc_ray(cam, W, H, (int32_t)(p % W), (int32_t)(p / W), o, d);
+    missing += render_variant_one(s, c, o, d, rgba + 4 * i, k ? k + i : 0, t ? t + i : 0, alpha ? alpha + i : 0);
+  }
+  return missing;
 }
 
 int32_t orc_max_threads(void) {

@@ -13,6 +13,11 @@ synthetic geometry in place of the paper's captured objects):
                       N = 16/32/64/128, band 0.05, F=2 features, MLP 24-64-64-4;
 * ``full_scene``      displaced geodesic sphere (200 000 triangles), L=16 levels
                       N_l = round(16 * 128^(l/15)), band 2 cells, MLP 48-64-64-4;
+* ``tiny_density_scene`` / ``full_density_scene``  the same two objects for the
+                      paper's decoupled variant: density and diffuse texture
+                      cubes of a shell around the surface (Sec. 4.2) instead of
+                      the mesh, PSH levels built from the voxels around every
+                      possible hit point, MLP input + alpha_c (d_in + 1);
 * cameras on a ring / Fibonacci sphere looking at the origin, 45 deg FOV.
 """
 from __future__ import annotations
@@ -71,9 +76,17 @@ def _load():
     lib.syn_camera.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]
     lib.syn_unpack_keys.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
     lib.syn_free.argtypes = [ctypes.c_void_p]
+    lib.syn_density_cubes.argtypes = [ctypes.c_uint64, ctypes.c_double, ctypes.c_double, ctypes.c_int32,
+                                      ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_int32, P(c_ip), P(c_fp), P(c_fp),
+                                      P(ctypes.c_int64)]
+    lib.syn_live_level_vertices.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                            ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p]
     lib.syn_splitmix64.argtypes = [ctypes.c_uint64]
     lib.syn_splitmix64.restype = ctypes.c_uint64
-    for name in ("syn_icosphere", "syn_geodesic", "syn_band_vertices"):
+    for name in ("syn_icosphere", "syn_geodesic", "syn_band_vertices", "syn_density_cubes",
+                 "syn_live_level_vertices"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -190,6 +203,81 @@ def fibonacci_cameras(n: int, radius: float, fovy_deg: float = 45.0) -> np.ndarr
 
 
 @dataclass
+class Cubes:
+    """Density (and diffuse) texture cubes of one object (Sec. 4.2).
+
+    Base grid of b^3 cells over the scene cube; cube i covers base cell
+    cells[i] and holds the (r+1)^3 fine vertices cells[i] * r + (0..r)^3
+    (x fastest) of the fine grid K = b r.  density[i] are their sigma values,
+    diffuse[i] their (c_d r, g, b, tint).  The march takes samples every
+    `step` from the ray's entry into the scene cube, stops once the
+    transmittance falls below `t_min`, and a ray whose coarse opacity stays at
+    or below `alpha_miss` is a miss."""
+    b: int
+    r: int
+    cells: np.ndarray
+    density: np.ndarray
+    diffuse: Optional[np.ndarray]
+    step: float
+    t_min: float = 1e-4
+    alpha_miss: float = 1e-4
+    side: float = DOMAIN_SIDE
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return len(self.cells)
+
+
+def density_cubes(seed: int, radius: float, amp: float, b: int, r: int, w: float, sigma_max: float,
+                  diffuse: bool = True, lo: float = DOMAIN_LO, side: float = DOMAIN_SIDE):
+    """(cells [n][3] int32, density [n][(r+1)^3] f32, diffuse [n][(r+1)^3][4] f32 or None)
+    of a shell sigma = sigma_max max(0, 1 - |s| / w) around r = radius (1 + amp n(q))."""
+    lib = _load()
+    cp = ctypes.POINTER(ctypes.c_int32)()
+    dp = ctypes.POINTER(ctypes.c_float)()
+    fp = ctypes.POINTER(ctypes.c_float)()
+    n = ctypes.c_int64()
+    rc = lib.syn_density_cubes(seed, radius, amp, b, r, lo, side, w, sigma_max, int(diffuse), ctypes.byref(cp),
+                               ctypes.byref(dp), ctypes.byref(fp), ctypes.byref(n))
+    if rc != 0:
+        raise RuntimeError(f"syn_density_cubes failed ({rc})")
+    nv = (r + 1) ** 3
+    cells = np.ctypeslib.as_array(cp, shape=(max(n.value, 1) * 3,))[: n.value * 3].reshape(n.value, 3).copy()
+    dens = np.ctypeslib.as_array(dp, shape=(max(n.value * nv, 1),))[: n.value * nv].reshape(n.value, nv).copy()
+    lib.syn_free(ctypes.cast(cp, ctypes.c_void_p))
+    lib.syn_free(ctypes.cast(dp, ctypes.c_void_p))
+    diff = None
+    if diffuse:
+        diff = np.ctypeslib.as_array(fp, shape=(max(n.value * nv * 4, 1),))[: n.value * nv * 4]
+        diff = diff.reshape(n.value, nv, 4).copy()
+        lib.syn_free(ctypes.cast(fp, ctypes.c_void_p))
+    return cells, dens, diff
+
+
+def live_level_vertices(cells: np.ndarray, density: np.ndarray, b: int, r: int, resolutions) -> List[np.ndarray]:
+    """Sorted packed corner keys, per level, of the level cells any point of a
+    live fine cell (one with a vertex of non-zero density) can fall in."""
+    lib = _load()
+    cells = np.ascontiguousarray(cells, np.int32)
+    density = np.ascontiguousarray(density, np.float32)
+    res = np.ascontiguousarray(resolutions, np.int32)
+    L = len(res)
+    kp = (ctypes.POINTER(ctypes.c_uint64) * L)()
+    nn = (ctypes.c_int64 * L)()
+    rc = lib.syn_live_level_vertices(_ptr(cells), _ptr(density), len(cells), b, r, L,
+                                     _ptr(res), ctypes.cast(kp, ctypes.c_void_p), ctypes.cast(nn, ctypes.c_void_p))
+    if rc != 0:
+        raise RuntimeError(f"syn_live_level_vertices failed ({rc})")
+    out = []
+    for l in range(L):
+        k = np.ctypeslib.as_array(kp[l], shape=(max(nn[l], 1),))[: nn[l]].copy()
+        lib.syn_free(ctypes.cast(kp[l], ctypes.c_void_p))
+        out.append(k)
+    return out
+
+
+@dataclass
 class Scene:
     """One i-NOLF object's inputs.  keys[l] are sorted packed vertex keys of
     level l and features[l][i] belongs to keys[l][i]."""
@@ -205,6 +293,7 @@ class Scene:
     domain_lo: float = DOMAIN_LO
     domain_side: float = DOMAIN_SIDE
     meta: dict = field(default_factory=dict)
+    cubes: Optional[Cubes] = None  # set: the decoupled variant (hit by density march, alpha_c input, diffuse)
 
     @property
     def n_levels(self) -> int:
@@ -212,7 +301,7 @@ class Scene:
 
     @property
     def d_in(self) -> int:
-        return self.n_levels * N_FEATURES + N_SH
+        return self.n_levels * N_FEATURES + N_SH + (1 if self.cubes is not None else 0)
 
 
 def full_resolutions(n_levels: int = 16, base: int = 16, top: int = 2048) -> List[int]:
@@ -248,3 +337,39 @@ def full_scene(seed: int = 0, freq: int = 100, n_levels: int = 16, top: int = 20
     bands = [band_cells * DOMAIN_SIDE / N for N in res]
     return _build_scene(V, F, res, bands, seed, fp16,
                         {"name": "geodesic%d-L%d" % (freq, n_levels), "seed": seed})
+
+
+def _density_scene(seed, radius, amp, b, r, resolutions, w_cells, opacity, fp16, meta) -> Scene:
+    side = DOMAIN_SIDE
+    K = b * r
+    w = w_cells * side / K
+    sigma_max = opacity / w
+    cells, dens, diff = density_cubes(seed, radius, amp, b, r, w, sigma_max, True)
+    step = float(np.float32(side / K))
+    cubes = Cubes(b, r, cells, dens, diff, step, meta={"w": w, "sigma_max": sigma_max, "radius": radius,
+                                                       "amp": amp})
+    keys = live_level_vertices(cells, dens, b, r, resolutions)
+    feats = [features(seed, l, k, fp16=fp16) for l, k in enumerate(keys)]
+    d_in = len(resolutions) * N_FEATURES + N_SH + 1
+    w1, w2, w3 = xavier(seed, d_in)
+    empty_v = np.zeros((0, 3), np.float32)
+    empty_f = np.zeros((0, 3), np.int32)
+    return Scene(empty_v, empty_f, list(resolutions), keys, feats, w1, w2, w3, fp16, meta=meta, cubes=cubes)
+
+
+def tiny_density_scene(seed: int = 0, fp16: bool = False, resolutions=(16, 32, 64, 128), b: int = 16, r: int = 8,
+                       w_cells: float = 2.0, opacity: float = 12.0) -> Scene:
+    """Unit sphere as a density shell (half-width w_cells fine cells, optical
+    depth `opacity` across it) in b^3 base cells of r^3 fine cells (K = 128),
+    L=4 levels at N = 16/32/64/128, MLP 25-64-64-4."""
+    return _density_scene(seed, 1.0, 0.0, b, r, resolutions, w_cells, opacity, fp16,
+                          {"name": "sphere-shell-b%d-r%d-L%d" % (b, r, len(resolutions)), "seed": seed})
+
+
+def full_density_scene(seed: int = 0, n_levels: int = 16, top: int = 2048, b: int = 128, r: int = 16,
+                       amp: float = 0.1, w_cells: float = 2.0, opacity: float = 12.0, fp16: bool = False) -> Scene:
+    """The displaced sphere of ``full_scene`` as a density shell in 128^3 base
+    cells of 16^3 fine cells (K = 2048), L levels 16..top, MLP 49-64-64-4."""
+    res = full_resolutions(n_levels, 16, top)
+    return _density_scene(seed, 1.0, amp, b, r, res, w_cells, opacity, fp16,
+                          {"name": "displaced-shell-b%d-r%d-L%d" % (b, r, n_levels), "seed": seed})

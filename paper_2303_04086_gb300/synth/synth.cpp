@@ -163,6 +163,64 @@ inline bool bit_get(const uint64_t* bits, uint64_t i) {
   return (__atomic_load_n(&bits[i >> 6], __ATOMIC_RELAXED) >> (i & 63)) & 1ull;
 }
 
+// All 8 corners of the cells set in `occ` (N^3 cells, bit x + N (y + N z)),
+// packed and sorted ascending.  Returns 0, or -2 when memory runs out.
+int cells_to_keys(const uint64_t* occ, int32_t N, uint64_t** keys_out, int64_t* n_out) {
+  const uint64_t n1 = (uint64_t)N, ncell = n1 * n1 * n1;
+  const uint64_t nv1 = n1 + 1, nvert = nv1 * nv1 * nv1;
+  uint64_t* vbits = (uint64_t*)std::calloc((nvert + 63) / 64, 8);
+  if (!vbits) return -2;
+  const int64_t nwords = (int64_t)((ncell + 63) / 64);
+#pragma omp parallel for schedule(dynamic, 1024)
+  for (int64_t w = 0; w < nwords; ++w) {
+    uint64_t word = occ[w];
+    while (word) {
+      int b = __builtin_ctzll(word);
+      word &= word - 1;
+      uint64_t lin = (uint64_t)w * 64 + (uint64_t)b;
+      uint64_t x = lin % n1, y = (lin / n1) % n1, z = lin / (n1 * n1);
+      for (int d = 0; d < 8; ++d) {
+        uint64_t vx = x + (d & 1), vy = y + ((d >> 1) & 1), vz = z + ((d >> 2) & 1);
+        bit_set(vbits, vx + nv1 * (vy + nv1 * vz));
+      }
+    }
+  }
+  const int64_t vwords = (int64_t)((nvert + 63) / 64);
+  int64_t count = 0;
+#pragma omp parallel for reduction(+ : count) schedule(static)
+  for (int64_t w = 0; w < vwords; ++w) count += __builtin_popcountll(vbits[w]);
+  uint64_t* keys = (uint64_t*)std::malloc(sizeof(uint64_t) * (count ? count : 1));
+  if (!keys) { std::free(vbits); return -2; }
+  // Ordered extraction: linear index x + (N+1)(y + (N+1) z) increases with
+  // (z, y, x), which is also the order of the packed keys.
+  int64_t pos = 0;
+  for (int64_t w = 0; w < vwords; ++w) {
+    uint64_t word = vbits[w];
+    while (word) {
+      int b = __builtin_ctzll(word);
+      word &= word - 1;
+      uint64_t lin = (uint64_t)w * 64 + (uint64_t)b;
+      uint64_t x = lin % nv1, y = (lin / nv1) % nv1, z = lin / (nv1 * nv1);
+      keys[pos++] = x | (y << 21) | (z << 42);
+    }
+  }
+  std::free(vbits);
+  *keys_out = keys;
+  *n_out = count;
+  return 0;
+}
+
+// Radial signed distance of point p to the surface r = radius (1 + amp n(q)),
+// q = p / |p|, n = fractal_noise (the displaced sphere of syn_geodesic when
+// radius = 1; a plain sphere when amp = 0).
+double shell_distance(uint64_t seed, double radius, double amp, V3 p) {
+  const double len = std::sqrt(dot(p, p));
+  if (len < 1e-12) return -radius;
+  const V3 q = (1.0 / len) * p;
+  const double R = radius * (1.0 + (amp != 0.0 ? amp * fractal_noise(seed, q) : 0.0));
+  return len - R;
+}
+
 }  // namespace
 
 extern "C" {
@@ -327,48 +385,9 @@ int syn_band_vertices(const float* V, int32_t nV, const int32_t* F, int32_t nF, 
           if (point_triangle_dist2(p, a, b, c) <= R * R) bit_set(occ, lin);
         }
   }
-  const uint64_t nv1 = n1 + 1, nvert = nv1 * nv1 * nv1;
-  uint64_t* vbits = (uint64_t*)std::calloc((nvert + 63) / 64, 8);
-  if (!vbits) { std::free(occ); return -2; }
-  const int64_t nwords = (int64_t)((ncell + 63) / 64);
-#pragma omp parallel for schedule(dynamic, 1024)
-  for (int64_t w = 0; w < nwords; ++w) {
-    uint64_t word = occ[w];
-    while (word) {
-      int b = __builtin_ctzll(word);
-      word &= word - 1;
-      uint64_t lin = (uint64_t)w * 64 + (uint64_t)b;
-      uint64_t x = lin % n1, y = (lin / n1) % n1, z = lin / (n1 * n1);
-      for (int d = 0; d < 8; ++d) {
-        uint64_t vx = x + (d & 1), vy = y + ((d >> 1) & 1), vz = z + ((d >> 2) & 1);
-        bit_set(vbits, vx + nv1 * (vy + nv1 * vz));
-      }
-    }
-  }
+  const int rc = cells_to_keys(occ, N, keys_out, n_out);
   std::free(occ);
-  const int64_t vwords = (int64_t)((nvert + 63) / 64);
-  int64_t count = 0;
-#pragma omp parallel for reduction(+ : count) schedule(static)
-  for (int64_t w = 0; w < vwords; ++w) count += __builtin_popcountll(vbits[w]);
-  uint64_t* keys = (uint64_t*)std::malloc(sizeof(uint64_t) * (count ? count : 1));
-  if (!keys) { std::free(vbits); return -2; }
-  // Ordered extraction: linear index x + (N+1)(y + (N+1) z) increases with
-  // (z, y, x), which is also the order of the packed keys.
-  int64_t pos = 0;
-  for (int64_t w = 0; w < vwords; ++w) {
-    uint64_t word = vbits[w];
-    while (word) {
-      int b = __builtin_ctzll(word);
-      word &= word - 1;
-      uint64_t lin = (uint64_t)w * 64 + (uint64_t)b;
-      uint64_t x = lin % nv1, y = (lin / nv1) % nv1, z = lin / (nv1 * nv1);
-      keys[pos++] = x | (y << 21) | (z << 42);
-    }
-  }
-  std::free(vbits);
-  *keys_out = keys;
-  *n_out = count;
-  return 0;
+  return rc;
 }
 
 void syn_unpack_keys(const uint64_t* keys, int64_t n, int32_t* coords) {
@@ -432,6 +451,191 @@ void syn_camera(const double eye[3], const double target[3], const double up[3],
     out[3 * i + 2] = (float)rows[i].z;
   }
   out[12] = (float)std::tan(0.5 * fovy_deg * M_PI / 180.0);
+}
+
+// Density and diffuse texture cubes of a shell around the surface
+// r = radius (1 + amp n(q)) (the inputs of Sec. 4.2 "Density Texture Cubes"
+// and "Diffuse Texture Cubes", standing in for a trained density field and a
+// cached diffuse network).  The domain cube [lo, lo + side]^3 has a base grid
+// of b^3 cells; cube c (base cell, 0..b-1 per axis) holds the (r+1)^3 fine
+// vertices v = c r + (0..r)^3 (x fastest) of the fine grid K = b r, vertex v
+// at position lo + v side / K.  Per fine vertex, in FP64 rounded to FP32:
+//   density  sigma(v) = sigma_max max(0, 1 - |s(v)| / w), s = shell_distance;
+//   diffuse  (c_d r, g, b, tint) = 0.05 + 0.9 u01(SplitMix64 draw keyed by
+//            (seed, vertex key, channel)) when `diffuse` != 0.
+// A cube is listed when at least one of its vertices has sigma > 0; listed
+// cubes are sorted by x + b (y + b z).  Vertices are skipped (left 0) only
+// when a Lipschitz bound on s proves |s| >= w, so every vertex's value is the
+// formula's, whichever cube holds it.  Returns 0, -1 (bad argument), -2 (oom).
+int syn_density_cubes(uint64_t seed, double radius, double amp, int32_t b, int32_t r, double lo, double side,
+                      double w, double sigma_max, int32_t diffuse, int32_t** cells_out, float** density_out,
+                      float** diffuse_out, int64_t* n_out) {
+  if (b < 1 || r < 1 || b > 1024 || r > 64 || !(w > 0) || !(side > 0) || !cells_out || !density_out ||
+      !n_out || (diffuse && !diffuse_out))
+    return -1;
+  const int64_t K = (int64_t)b * r;
+  const double hb = side / b, hf = side / (double)K;
+  // |grad s| <= sqrt(1 + (|grad n| amp radius / |p|)^2) for |p| >= radius / 2,
+  // |grad n| <= 3 sqrt(3) (2 + 0.5 * 4 + 0.25 * 8) / 1.75 < 18 (smoothstep slope
+  // 1.5 times the lattice value range 2, per octave times its frequency)
+  const double lip = std::sqrt(1.0 + std::pow(18.0 * amp * 2.0, 2.0)) + 1e-3;
+  const int64_t nb = (int64_t)b * b * b;
+  std::vector<uint8_t> cand((size_t)nb, 0);
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int64_t lin = 0; lin < nb; ++lin) {
+    const int64_t x = lin % b, y = (lin / b) % b, z = lin / ((int64_t)b * b);
+    const V3 c = {lo + (x + 0.5) * hb, lo + (y + 0.5) * hb, lo + (z + 0.5) * hb};
+    const double s = shell_distance(seed, radius, amp, c);
+    cand[(size_t)lin] = std::fabs(s) < w + lip * 0.5 * std::sqrt(3.0) * hb + 1e-9;
+  }
+  std::vector<int64_t> cl;
+  for (int64_t lin = 0; lin < nb; ++lin)
+    if (cand[(size_t)lin]) cl.push_back(lin);
+  const int64_t nc = (int64_t)cl.size();
+  const int64_t nv = (int64_t)(r + 1) * (r + 1) * (r + 1);
+  std::vector<float> dens((size_t)(nc * nv), 0.0f);
+  std::vector<uint8_t> keep((size_t)nc, 0);
+  // sub-blocks of up to 4^3 fine cells, each tested at its centre first
+  const int sb = std::min(4, r);
+  const int nsb = (r + sb - 1) / sb;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t q = 0; q < nc; ++q) {
+    const int64_t lin = cl[(size_t)q];
+    const int64_t cx = lin % b, cy = (lin / b) % b, cz = lin / ((int64_t)b * b);
+    float* blk = dens.data() + (size_t)(q * nv);
+    bool any = false;
+    for (int bz = 0; bz < nsb; ++bz)
+      for (int by = 0; by < nsb; ++by)
+        for (int bx = 0; bx < nsb; ++bx) {
+          const int x0 = bx * sb, y0 = by * sb, z0 = bz * sb;
+          const int x1 = std::min(r, x0 + sb), y1 = std::min(r, y0 + sb), z1 = std::min(r, z0 + sb);
+          const V3 m = {lo + (cx * r + 0.5 * (x0 + x1)) * hf, lo + (cy * r + 0.5 * (y0 + y1)) * hf,
+                        lo + (cz * r + 0.5 * (z0 + z1)) * hf};
+          const double half_diag = 0.5 * hf * std::sqrt((double)((x1 - x0) * (x1 - x0) + (y1 - y0) * (y1 - y0) +
+                                                                 (z1 - z0) * (z1 - z0)));
+          if (std::fabs(shell_distance(seed, radius, amp, m)) >= w + lip * half_diag + 1e-9) continue;
+          for (int k = z0; k <= z1; ++k)
+            for (int j = y0; j <= y1; ++j)
+              for (int i = x0; i <= x1; ++i) {
+                const V3 p = {lo + (double)(cx * r + i) * hf, lo + (double)(cy * r + j) * hf,
+                              lo + (double)(cz * r + k) * hf};
+                const double s = shell_distance(seed, radius, amp, p);
+                const double v = sigma_max * std::max(0.0, 1.0 - std::fabs(s) / w);
+                const float fv = (float)v;
+                blk[(size_t)i + (size_t)(r + 1) * ((size_t)j + (size_t)(r + 1) * (size_t)k)] = fv;
+                if (fv > 0.0f) any = true;
+              }
+        }
+    keep[(size_t)q] = any;
+  }
+  int64_t n = 0;
+  for (int64_t q = 0; q < nc; ++q) n += keep[(size_t)q];
+  int32_t* cells = (int32_t*)std::malloc(sizeof(int32_t) * 3 * (size_t)std::max<int64_t>(n, 1));
+  float* dout = (float*)std::malloc(sizeof(float) * (size_t)std::max<int64_t>(n * nv, 1));
+  float* fout = diffuse ? (float*)std::malloc(sizeof(float) * 4 * (size_t)std::max<int64_t>(n * nv, 1)) : nullptr;
+  if (!cells || !dout || (diffuse && !fout)) {
+    std::free(cells); std::free(dout); std::free(fout);
+    return -2;
+  }
+  std::vector<int64_t> dst((size_t)nc, -1);
+  for (int64_t q = 0, o = 0; q < nc; ++q)
+    if (keep[(size_t)q]) dst[(size_t)q] = o++;
+  const uint64_t dseed = splitmix64(seed ^ 0x64696666ull);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t q = 0; q < nc; ++q) {
+    const int64_t o = dst[(size_t)q];
+    if (o < 0) continue;
+    const int64_t lin = cl[(size_t)q];
+    const int64_t cx = lin % b, cy = (lin / b) % b, cz = lin / ((int64_t)b * b);
+    cells[3 * o + 0] = (int32_t)cx;
+    cells[3 * o + 1] = (int32_t)cy;
+    cells[3 * o + 2] = (int32_t)cz;
+    std::memcpy(dout + (size_t)(o * nv), dens.data() + (size_t)(q * nv), sizeof(float) * (size_t)nv);
+    if (fout) {
+      float* f = fout + (size_t)(o * nv) * 4;
+      for (int k = 0; k <= r; ++k)
+        for (int j = 0; j <= r; ++j)
+          for (int i = 0; i <= r; ++i) {
+            const uint64_t key = (uint64_t)(cx * r + i) | ((uint64_t)(cy * r + j) << 21) | ((uint64_t)(cz * r + k) << 42);
+            const size_t at = (size_t)i + (size_t)(r + 1) * ((size_t)j + (size_t)(r + 1) * (size_t)k);
+            for (int ch = 0; ch < 4; ++ch)
+              f[at * 4 + ch] = (float)(0.05 + 0.9 * u01(splitmix64(dseed ^ (key * 4 + (uint64_t)ch))));
+          }
+    }
+  }
+  *cells_out = cells;
+  *density_out = dout;
+  if (diffuse_out) *diffuse_out = fout;
+  *n_out = n;
+  return 0;
+}
+
+// Occupied vertex sets of the encoder levels for a density-cube object: the
+// voxels surrounding every possible hit point (Sec. 4.2, "Implementation with
+// PSH encoding").  A hit point is a march sample with sigma > 0, so it lies in
+// a live fine cell (a fine cell with a vertex of non-zero density, found from
+// the cube blocks of syn_density_cubes).  With K = b r a power of two, K x is
+// exact in FP32, so a point of fine cell c satisfies c / K <= x < (c+1) / K
+// and the FP32 product N x lands in level cells (N c) div K .. (N (c+1)) div K
+// (monotone rounding), clamped to N - 1.  Every such level cell is occupied;
+// keys_out[l] receives the sorted packed keys of all 8 corners of level l's
+// occupied cells.  Returns 0, -1 or -2.
+int syn_live_level_vertices(const int32_t* cells, const float* density, int64_t n_cubes, int32_t b, int32_t r,
+                            int32_t n_levels, const int32_t* N, uint64_t** keys_out, int64_t* n_out) {
+  if (!cells || !density || n_cubes < 0 || b < 1 || r < 1 || n_levels < 1 || !N || !keys_out || !n_out) return -1;
+  const int64_t K = (int64_t)b * r;
+  const int64_t nv = (int64_t)(r + 1) * (r + 1) * (r + 1);
+  // live fine cells as (cube, local cell) bitmask rows of r^3 bits
+  const int64_t cpc = (int64_t)r * r * r, words = (cpc + 63) / 64;
+  std::vector<uint64_t> live((size_t)(n_cubes * words), 0);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t q = 0; q < n_cubes; ++q) {
+    const float* blk = density + (size_t)(q * nv);
+    auto at = [&](int i, int j, int k) { return blk[i + (r + 1) * (j + (r + 1) * k)]; };
+    for (int k = 0; k < r; ++k)
+      for (int j = 0; j < r; ++j)
+        for (int i = 0; i < r; ++i) {
+          bool any = false;
+          for (int d = 0; d < 8 && !any; ++d) any = at(i + (d & 1), j + ((d >> 1) & 1), k + ((d >> 2) & 1)) > 0.0f;
+          if (any) {
+            const int64_t c = i + (int64_t)r * (j + (int64_t)r * k);
+            live[(size_t)(q * words + (c >> 6))] |= 1ull << (c & 63);
+          }
+        }
+  }
+  for (int32_t l = 0; l < n_levels; ++l) {
+    const int64_t n1 = N[l];
+    if (n1 < 1 || n1 > (1 << 20) - 2) return -1;
+    const uint64_t ncell = (uint64_t)n1 * n1 * n1;
+    uint64_t* occ = (uint64_t*)std::calloc((ncell + 63) / 64, 8);
+    if (!occ) return -2;
+    std::vector<int64_t> lo_of((size_t)K), hi_of((size_t)K);
+    for (int64_t c = 0; c < K; ++c) {
+      lo_of[(size_t)c] = std::min(n1 - 1, (n1 * c) / K);
+      hi_of[(size_t)c] = std::min(n1 - 1, (n1 * (c + 1)) / K);
+    }
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t q = 0; q < n_cubes; ++q) {
+      const int64_t bx = cells[3 * q], by = cells[3 * q + 1], bz = cells[3 * q + 2];
+      for (int64_t c = 0; c < cpc; ++c) {
+        if (!((live[(size_t)(q * words + (c >> 6))] >> (c & 63)) & 1ull)) continue;
+        const int64_t fx = bx * r + c % r, fy = by * r + (c / r) % r, fz = bz * r + c / ((int64_t)r * r);
+        for (int64_t z = lo_of[(size_t)fz]; z <= hi_of[(size_t)fz]; ++z)
+          for (int64_t y = lo_of[(size_t)fy]; y <= hi_of[(size_t)fy]; ++y)
+            for (int64_t x = lo_of[(size_t)fx]; x <= hi_of[(size_t)fx]; ++x) {
+              const uint64_t lin = (uint64_t)x + (uint64_t)n1 * ((uint64_t)y + (uint64_t)n1 * (uint64_t)z);
+              if (!bit_get(occ, lin)) bit_set(occ, lin);
+            }
+      }
+    }
+    const int rc = cells_to_keys(occ, (int32_t)n1, &keys_out[l], &n_out[l]);
+    std::free(occ);
+    if (rc != 0) {
+      for (int32_t m = 0; m < l; ++m) { std::free(keys_out[m]); keys_out[m] = nullptr; }
+      return rc;
+    }
+  }
+  return 0;
 }
 
 }  // extern "C"
