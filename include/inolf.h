@@ -110,6 +110,26 @@ inolf_status inolf_build_hash(const int32_t* coords, int64_t n, int32_t grid_ext
 void inolf_hash_free(inolf_hash* h);
 
 /* ------------------------------------------------------------------------ */
+/* Density and diffuse texture cubes (Sec. 4.2, "Density Texture Cubes",     */
+/* "Diffuse Texture Cubes"): the paper's own hit-point estimation and the   */
+/* decoupled diffuse/specular variant of the renderer.                       */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  int32_t b;              /* base grid: b^3 cells over the scene cube; power of two */
+  int32_t r;              /* cube resolution: r^3 fine cells, (r+1)^3 vertex samples; power of
+                             two; the fine grid K = b r is at most 4096 */
+  int64_t n_cubes;        /* listed cubes (cells with any non-zero density) */
+  const int32_t* cells;   /* host [n_cubes][3]: base cell of cube i, distinct, each in [0, b) */
+  const float* density;   /* host [n_cubes][(r+1)^3]: sigma >= 0 at fine vertices cells[i] r +
+                             (0..r)^3, x fastest; vertices shared by two cubes must agree */
+  const float* diffuse;   /* host [n_cubes][(r+1)^3][4]: (c_d r, g, b, tint) at the same vertices */
+  float side;             /* edge of the scene cube [domain_lo, domain_lo + side]^3 */
+  float step;             /* march step delta (object units); side sqrt(3) / step < 2^20 */
+  float t_min;            /* the march stops once the transmittance falls below t_min (0..1) */
+  float alpha_miss;       /* a ray whose coarse opacity alpha_c <= alpha_miss misses (0..1) */
+} inolf_cubes_desc;
+
+/* ------------------------------------------------------------------------ */
 /* Object: proxy mesh + per-level hashes and feature tables + MLP weights.   */
 /* ------------------------------------------------------------------------ */
 typedef struct {
@@ -135,6 +155,13 @@ typedef struct {
   /* object frame */
   float domain_lo;                  /* lo (same on all axes), e.g. -1.5 */
   float domain_scale;               /* scale = 1 / side, e.g. (float)(1/3) */
+  /* NULL: hit points come from the proxy mesh (one query per ray, Eqs. 2-3).
+     Set: the decoupled variant of Sec. 4.2 -- the mesh may be empty
+     (n_vertices = n_triangles = 0), hit points come from the density march
+     (Eq. 4), the MLP takes alpha_c as one more input (Eq. 5: d_in = n_levels *
+     F + 17, w1 is [64][d_in]) and the colour is c = c_d + tint c_s (Eq. 7)
+     with (c_d, tint) from the diffuse cubes; the alpha channel is F_s's. */
+  const inolf_cubes_desc* cubes;
 } inolf_object_desc;
 
 typedef struct inolf_object inolf_object;
@@ -164,14 +191,17 @@ inolf_status inolf_object_table_rows(const inolf_object* obj, int32_t level, int
 /* Forward rendering (Sec. 4.2, one query per ray).                          */
 /* ------------------------------------------------------------------------ */
 
-/* Workspace bytes inolf_render / inolf_render_rays need for n_rays rays. */
+/* Workspace bytes inolf_render / inolf_render_rays / inolf_march_rays need
+ * for n_rays rays (a header plus 12 bytes per ray: the hit list and, for
+ * density-cube objects, each hit's alpha_c). */
 size_t inolf_render_workspace_bytes(int64_t n_rays);
 
 /* Renders n_views pinhole views of W x H pixels.
  *   cams       host, n_views x 13 floats (camera records)
  *   rgba_out   device, [n_views][H][W][4] FP32, straight alpha; rays that miss
  *              the proxy get (0, 0, 0, 0)
- *   tri_out    device [n_views][H][W] int32 closest triangle (-1 = miss), or NULL
+ *   tri_out    device [n_views][H][W] int32 closest triangle (-1 = miss), or NULL;
+ *              for objects with density cubes: the hit sample k of the march
  *   t_out      device [n_views][H][W] FP32 hit distance (0 on miss), or NULL
  *   workspace  device, >= inolf_render_workspace_bytes(n_views * W * H) bytes,
  *              16-byte aligned, owned by the caller; contents undefined after
@@ -186,6 +216,21 @@ inolf_status inolf_render_rays(const inolf_object* obj, const float* o, const fl
                                inolf_precision prec, float* rgba_out, int32_t* tri_out, float* t_out,
                                void* workspace, size_t workspace_bytes, void* stream);
 
+/* Hit-point estimation alone, for objects with density cubes (Sec. 4.2,
+ * "Hit Point Estimation and Opacity Refinement", Eq. 4).  For n explicit rays
+ * (o, d device [n][3] FP32, object frame, d unit length): samples t_k = t0 +
+ * k step (FP32) from the ray's entry t0 >= 0 into the scene cube while t_k <=
+ * its exit, density sigma_k = trilinear interpolation (successive FP32 lerps
+ * along x, y, z) of the fine cell's 8 vertex samples (0 outside listed cubes),
+ * w_k = T_k (1 - e_k), T_{k+1} = T_k e_k with e_k = exp(-sigma_k step); the
+ * march stops after the sample that brings T below t_min.  The hit is the
+ * first sample of largest w_k, alpha_c = 1 - T; alpha_c <= alpha_miss is a
+ * miss.  Outputs (device, [n], each may be NULL): k_out hit sample (-1 =
+ * miss), t_out its t (0 on miss), alpha_out alpha_c.  Errors: INOLF_E_INVALID
+ * (also for objects without cubes), INOLF_E_CUDA. */
+inolf_status inolf_march_rays(const inolf_object* obj, const float* o, const float* d, int64_t n, int32_t* k_out,
+                              float* t_out, float* alpha_out, void* workspace, size_t workspace_bytes, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Training (Sec. 4.2 "Training", Eq. 8).                                     */
 /* ------------------------------------------------------------------------ */
@@ -198,7 +243,9 @@ inolf_status inolf_render_rays(const inolf_object* obj, const float* o, const fl
  * [4][64] (device FP32, row-major).  Activations are recomputed from the
  * object's current parameters; rays that miss contribute nothing.  Feature
  * gradients are scattered with atomics, weight gradients are reduced per
- * CTA first.  workspace as for inolf_render_rays. */
+ * CTA first.  workspace as for inolf_render_rays.  Objects with density
+ * cubes: INOLF_E_UNSUPPORTED (their training path, the hash-grid diffuse
+ * branch of Eq. 6, is not part of this library). */
 inolf_status inolf_backward(const inolf_object* obj, const float* o, const float* d, int64_t n,
                             const float* d_rgba, float* const* grad_tables, float* grad_w1, float* grad_w2,
                             float* grad_w3, void* workspace, size_t workspace_bytes, void* stream);
@@ -273,7 +320,8 @@ inolf_status inolf_serve_create(const inolf_serve_params* params, inolf_server**
 
 /* Makes an object resident in the scene at a translation (object frame =
  * world - translation).  Up to 16 objects; only while no request is in
- * flight.  The object must outlive the server. */
+ * flight.  The object must outlive the server.  Objects with density cubes:
+ * INOLF_E_UNSUPPORTED (the serving loop composites mesh-proxy objects). */
 inolf_status inolf_serve_add_object(inolf_server* srv, const inolf_object* obj, const float translation[3]);
 
 /* Target frame rate of a viewer for policy 1 (default 50 Hz: one camera

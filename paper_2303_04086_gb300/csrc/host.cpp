@@ -425,8 +425,122 @@ inolf_status upload_weights(Object& o, const float* w1, const float* w2, const f
 static void destroy_object(Object& o) {
   auto f = [](void* p) { if (p) cudaFree(p); };
   f(o.nodes); f(o.tris); f(o.w_f32); f(o.w_bf16); f(o.w_fp8);
+  f((void*)o.cub.grid); f((void*)o.cub.dens); f((void*)o.cub.diff);
   for (int l = 0; l < o.L; ++l) { f((void*)o.lv[l].phi); f((void*)o.lv[l].table); }
   o = Object();
+}
+
+// Chebyshev (L-infinity) distance, in cells, from every cell of a b^3 grid to
+// the nearest listed cell, capped at `cap`: the 1-D distance along x, then
+// along y and z the minimum over the line of max(|offset|, previous pass),
+// which composes to min over listed cells of max(|dx|, |dy|, |dz|).
+static std::vector<int32_t> chebyshev_distance(const std::vector<uint8_t>& listed, int32_t b, int32_t cap) {
+  const int64_t n = (int64_t)b * b * b;
+  std::vector<int32_t> a(n), c(n);
+  auto at = [b](int64_t x, int64_t y, int64_t z) { return x + (int64_t)b * (y + (int64_t)b * z); };
+  for (int64_t z = 0; z < b; ++z)
+    for (int64_t y = 0; y < b; ++y) {
+      int32_t run = cap;
+      for (int64_t x = 0; x < b; ++x) {
+        run = listed[at(x, y, z)] ? 0 : std::min(cap, run + 1);
+        a[at(x, y, z)] = run;
+      }
+      run = cap;
+      for (int64_t x = b - 1; x >= 0; --x) {
+        run = listed[at(x, y, z)] ? 0 : std::min(cap, run + 1);
+        a[at(x, y, z)] = std::min(a[at(x, y, z)], run);
+      }
+    }
+  auto line_pass = [&](const std::vector<int32_t>& in, std::vector<int32_t>& out, int axis) {
+    for (int64_t i = 0; i < b; ++i)
+      for (int64_t j = 0; j < b; ++j)
+        for (int64_t k = 0; k < b; ++k) {
+          auto idx = [&](int64_t m) { return axis == 1 ? at(i, m, j) : at(i, j, m); };
+          int32_t best = in[idx(k)];
+          for (int64_t off = 1; off < best && off < b; ++off) {
+            if (k - off >= 0) best = std::min(best, std::max((int32_t)off, in[idx(k - off)]));
+            if (k + off < b) best = std::min(best, std::max((int32_t)off, in[idx(k + off)]));
+          }
+          out[idx(k)] = best;
+        }
+  };
+  line_pass(a, c, 1);
+  line_pass(c, a, 2);
+  return a;
+}
+
+// Uploads the density / diffuse cubes and builds the base grid of cube
+// indices and empty-space distances.
+static inolf_status create_cubes(Object& o, const inolf_cubes_desc& C, cudaStream_t st) {
+  const int32_t b = C.b, r = C.r;
+  const int64_t nb = (int64_t)b * b * b, nv = (int64_t)(r + 1) * (r + 1) * (r + 1);
+  std::vector<int32_t> grid(nb, -1);
+  std::vector<uint8_t> listed(nb, 0);
+  for (int64_t i = 0; i < C.n_cubes; ++i) {
+    const int32_t x = C.cells[3 * i], y = C.cells[3 * i + 1], z = C.cells[3 * i + 2];
+    const int64_t lin = x + (int64_t)b * (y + (int64_t)b * z);
+    if (listed[lin]) return fail(INOLF_E_INVALID, "inolf_object_create: cube listed twice");
+    listed[lin] = 1;
+    grid[lin] = (int32_t)i;
+  }
+  const int32_t cap = std::min<int32_t>(b, 255);
+  const std::vector<int32_t> dist = chebyshev_distance(listed, b, cap);
+  for (int64_t i = 0; i < nb; ++i)
+    if (!listed[i]) grid[i] = -std::max<int32_t>(1, dist[i]);
+  void* dg = nullptr;
+  void* dd = nullptr;
+  void* df = nullptr;
+  if (cudaMalloc(&dg, sizeof(int32_t) * nb) != cudaSuccess) return fail(INOLF_E_OOM, "cudaMalloc cube grid");
+  o.cub.grid = (const int32_t*)dg;
+  const size_t dbytes = sizeof(float) * (size_t)std::max<int64_t>(C.n_cubes * nv, 1);
+  const size_t fbytes = sizeof(float4) * (size_t)std::max<int64_t>(C.n_cubes * nv, 1);
+  if (cudaMalloc(&dd, dbytes) != cudaSuccess) return fail(INOLF_E_OOM, "cudaMalloc density cubes");
+  o.cub.dens = (const float*)dd;
+  if (cudaMalloc(&df, fbytes) != cudaSuccess) return fail(INOLF_E_OOM, "cudaMalloc diffuse cubes");
+  o.cub.diff = (const float4*)df;
+  o.bytes += sizeof(int32_t) * nb + dbytes + fbytes;
+  if (cudaMemcpyAsync(dg, grid.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      (C.n_cubes > 0 &&
+       (cudaMemcpyAsync(dd, C.density, sizeof(float) * C.n_cubes * nv, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(df, C.diffuse, sizeof(float4) * C.n_cubes * nv, cudaMemcpyHostToDevice, st) !=
+            cudaSuccess)) ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return fail(INOLF_E_CUDA, "inolf_object_create: cube upload failed");
+  CubesDev& c = o.cub;
+  c.b = b;
+  c.r = r;
+  c.rshift = 0;
+  while ((1 << c.rshift) < r) ++c.rshift;
+  c.K = b * r;
+  c.K_f = (float)c.K;
+  c.hi = o.lo + C.side;
+  c.step = C.step;
+  c.t_min = C.t_min;
+  c.alpha_miss = C.alpha_miss;
+  return INOLF_OK;
+}
+
+static bool pow2(int32_t v) { return v >= 1 && (v & (v - 1)) == 0; }
+
+// Argument checks of a cube description (before anything is allocated).
+static inolf_status check_cubes(const inolf_cubes_desc& C) {
+  if (!pow2(C.b) || !pow2(C.r) || (int64_t)C.b * C.r > 4096)
+    return fail(INOLF_E_INVALID, "inolf_object_create: cubes need b, r powers of two with b r <= 4096");
+  if (C.n_cubes < 0 || C.n_cubes > (int64_t)C.b * C.b * C.b ||
+      (C.n_cubes > 0 && (!C.cells || !C.density || !C.diffuse)))
+    return fail(INOLF_E_INVALID, "inolf_object_create: bad cube list");
+  if (!(C.side > 0) || !std::isfinite(C.side) || !(C.step > 0) || !std::isfinite(C.step) ||
+      !((double)C.side * std::sqrt(3.0) / C.step < (double)(1 << 20) - 2))
+    return fail(INOLF_E_INVALID, "inolf_object_create: bad march side / step");
+  if (!(C.t_min > 0 && C.t_min <= 1) || !(C.alpha_miss >= 0 && C.alpha_miss < 1))
+    return fail(INOLF_E_INVALID, "inolf_object_create: bad t_min / alpha_miss");
+  for (int64_t i = 0; i < 3 * C.n_cubes; ++i)
+    if (C.cells[i] < 0 || C.cells[i] >= C.b) return fail(INOLF_E_INVALID, "inolf_object_create: cube cell out of range");
+  const int64_t nv = (int64_t)(C.r + 1) * (C.r + 1) * (C.r + 1);
+  for (int64_t i = 0; i < C.n_cubes * nv; ++i)
+    if (!(C.density[i] >= 0) || !std::isfinite(C.density[i]))
+      return fail(INOLF_E_INVALID, "inolf_object_create: densities must be finite and >= 0");
+  return INOLF_OK;
 }
 
 extern "C" inolf_status inolf_object_create(const inolf_object_desc* desc, void* stream, inolf_object** out) {
@@ -434,8 +548,16 @@ extern "C" inolf_status inolf_object_create(const inolf_object_desc* desc, void*
   if (!desc || !out) return fail(INOLF_E_INVALID, "inolf_object_create: NULL argument");
   *out = nullptr;
   const inolf_object_desc& D = *desc;
-  if (D.n_vertices <= 0 || D.n_triangles <= 0 || !D.vertices || !D.triangles)
+  const bool variant = D.cubes != nullptr;
+  if (variant) {
+    inolf_status cs = check_cubes(*D.cubes);
+    if (cs != INOLF_OK) return cs;
+  }
+  const bool have_mesh = D.n_vertices > 0 && D.n_triangles > 0;
+  if (!variant && (!have_mesh || !D.vertices || !D.triangles))
     return fail(INOLF_E_INVALID, "inolf_object_create: empty or missing proxy mesh");
+  if (variant && (D.n_vertices != 0 || D.n_triangles != 0))
+    return fail(INOLF_E_INVALID, "inolf_object_create: objects with density cubes take no proxy mesh");
   if (D.n_levels < 1 || D.n_levels > INOLF_MAX_LEVELS || D.n_features != 2 || !D.resolution || !D.hashes ||
       !D.features)
     return fail(INOLF_E_INVALID, "inolf_object_create: bad level description (1..16 levels, F = 2)");
@@ -457,15 +579,21 @@ extern "C" inolf_status inolf_object_create(const inolf_object_desc* desc, void*
   if (cudaGetDevice(&o.device) != cudaSuccess) { delete obj; return fail(INOLF_E_CUDA, "cudaGetDevice failed"); }
   o.L = D.n_levels;
   o.F = D.n_features;
-  o.d_in = D.n_levels * D.n_features + INOLF_N_SH;
+  o.d_in = D.n_levels * D.n_features + INOLF_N_SH + (variant ? 1 : 0);
+  o.variant = variant ? 1 : 0;
   o.fp16 = D.features_fp16 ? 1 : 0;
   o.lo = D.domain_lo;
   o.scale = D.domain_scale;
   for (int k = 0; k < 3; ++k) o.fp8_act_scale[k] = D.fp8_act_scale[k];
 
+  if (variant) {
+    inolf_status cs = create_cubes(o, *D.cubes, st);
+    if (cs != INOLF_OK) { destroy_object(o); delete obj; return cs; }
+  }
+
   // --- bounding sphere of the proxy (box centre, farthest vertex), padded
   //     so that FP32 rounding of the ray-sphere test never culls a hit ---
-  {
+  if (!variant) {
     double lo3[3] = {1e300, 1e300, 1e300}, hi3[3] = {-1e300, -1e300, -1e300};
     for (int32_t v = 0; v < D.n_vertices; ++v)
       for (int k = 0; k < 3; ++k) {
@@ -485,6 +613,7 @@ extern "C" inolf_status inolf_object_create(const inolf_object_desc* desc, void*
   }
 
   // --- BVH ---
+  if (!variant) {
   Builder b;
   b.V = D.vertices;
   b.F = D.triangles;
@@ -542,6 +671,7 @@ extern "C" inolf_status inolf_object_create(const inolf_object_desc* desc, void*
   CUDA_TRY(cudaMemcpyAsync(o.tris, tri.data(), tri.size() * sizeof(float), cudaMemcpyHostToDevice, st));
   o.bytes += b.nodes.size() * sizeof(float) + tri.size() * sizeof(float);
   CUDA_TRY(cudaStreamSynchronize(st));
+  }  // !variant
 
   // --- levels: Phi and feature tables in slot order ---
   for (int l = 0; l < o.L; ++l) {

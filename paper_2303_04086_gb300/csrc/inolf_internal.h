@@ -5,6 +5,8 @@
 #include <cstddef>
 #include <string>
 
+#include <vector_types.h>
+
 #include "../../include/inolf.h"
 
 namespace inolf {
@@ -23,6 +25,21 @@ struct LevelDev {
   float inv_r;            // 1/r rounded to FP32
   const uint32_t* phi;    // r^3 packed offsets
   const void* table;      // m^3 rows of F=2 features: float2 (FP32) or __half2 (FP16)
+};
+
+// Density and diffuse texture cubes as the kernels see them (Sec. 4.2).
+// grid[x + b (y + b z)] of a base cell is its cube's index, or -D for an
+// unlisted cell whose nearest listed cube is D >= 1 base cells away in the
+// Chebyshev metric (every cell within D - 1 of it is unlisted too).
+struct CubesDev {
+  const int32_t* grid;   // b^3
+  const float* dens;     // n x (r+1)^3 sigma, x fastest
+  const float4* diff;    // n x (r+1)^3 (c_d r, g, b, tint)
+  int32_t b, r, rshift;  // r = 1 << rshift
+  int32_t K;             // fine cells per axis, b r
+  float K_f;             // (float)K
+  float hi;              // lo + side (FP32): upper corner of the scene cube
+  float step, t_min, alpha_miss;
 };
 
 // Device-resident object (all pointers are device memory unless noted).
@@ -49,8 +66,14 @@ struct Object {
   uint32_t tc_bytes_bf16 = 0, tc_bytes_fp8 = 0;
   float fp8_w_scale[3] = {0, 0, 0};
   float fp8_act_scale[3] = {0, 0, 0};
+  // decoupled variant (density march, alpha_c input, diffuse cubes)
+  int variant = 0;
+  CubesDev cub = {};
   size_t bytes = 0;
 };
+
+// Hit-list bytes per ray: (ray, t) records, plus alpha_c for the variant.
+inline size_t hit_bytes_per_ray(const Object& o) { return o.variant ? 12 : 8; }
 
 // Brackets one kernel launch with CUDA events when statistics are enabled
 // (stats.cpp).
@@ -79,7 +102,8 @@ struct RayBatch {
 
 inolf_status launch_render(const Object& obj, const RayBatch& rays, inolf_precision prec, float* rgba,
                            int32_t* tri_out, float* t_out, uint32_t* slots_out, float* feat_out,
-                           void* workspace, size_t workspace_bytes, void* stream, bool amax = false);
+                           void* workspace, size_t workspace_bytes, void* stream, bool amax = false,
+                           float* alpha_out = nullptr, bool hits_only = false);
 
 size_t workspace_bytes(int64_t n_rays);
 

@@ -50,9 +50,14 @@ struct Params {
   float* t_out;
   uint32_t* slots_out;
   float* feat_out;
+  // decoupled variant (Sec. 4.2): density march, alpha_c input, diffuse cubes
+  int32_t variant;
+  CubesDev cub;
+  float* alpha_out;    // march stage output (inolf_march_rays), or NULL
   // workspace
   uint32_t* counter;   // [0] hit count, [1] error flags, [4..6] activation amax bits
   uint2* hits;         // (ray index in launch, t bits)
+  float* hit_alpha;    // variant: alpha_c of each hit-list entry
 };
 
 // Backward-pass arguments (passed by value: every pointer is device memory).
@@ -434,6 +439,160 @@ __device__ __forceinline__ void encode_all_levels(const Params& p, const float x
     emit(l, e0, e1, slots);
     cur = nxt;
   }
+}
+
+// ---------------------------------------------------------------------------
+// Density texture cubes (Sec. 4.2): the hit-point march of Eq. 4 and the
+// diffuse lookup of Eq. 7.
+// ---------------------------------------------------------------------------
+static constexpr int32_t kMaxMarchSteps = 1 << 20;  // > side sqrt(3) / step + 1, checked at creation
+static constexpr float kSkipMargin = 0.05f;          // fine cells kept between a skipped sample and a block face
+
+// Span [t0, t1] of the ray inside the scene cube [lo, hi]^3: per axis the
+// plane distances (plane - o) / d in FP32, axes with d = 0 only test o.
+__device__ __forceinline__ bool cube_span(float lo, float hi, const float o[3], const float d[3], float& t0,
+                                          float& t1) {
+  float a = 0.0f, z = INFINITY;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    if (d[q] == 0.0f) {
+      if (o[q] < lo || o[q] > hi) return false;
+      continue;
+    }
+    const float ta = __fdiv_rn(__fsub_rn(lo, o[q]), d[q]);
+    const float tb = __fdiv_rn(__fsub_rn(hi, o[q]), d[q]);
+    a = fmaxf(a, fminf(ta, tb));
+    z = fminf(z, fmaxf(ta, tb));
+  }
+  if (a > z) return false;
+  t0 = a;
+  t1 = z;
+  return true;
+}
+
+// a + f (b - a) with each operation rounded on its own
+__device__ __forceinline__ float lerp_rn(float a, float b, float f) { return __fadd_rn(a, __fmul_rn(f, __fsub_rn(b, a))); }
+
+// Fine cell (clamped to the grid), in-cell fractions and unclamped fine
+// coordinates of the point with scene-unit coordinates x.
+__device__ __forceinline__ void fine_cell(const CubesDev& c, const float x[3], int32_t ci[3], float f[3],
+                                          float u[3]) {
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    u[q] = __fmul_rn(c.K_f, x[q]);
+    int32_t v = (int32_t)floorf(u[q]);
+    v = v < 0 ? 0 : (v > c.K - 1 ? c.K - 1 : v);
+    ci[q] = v;
+    f[q] = __fsub_rn(u[q], __int2float_rn(v));
+  }
+}
+
+// The march of one ray (Eq. 4): samples t_k = t0 + k step, sigma_k from the
+// cubes, w_k = T_k (1 - e_k), T_{k+1} = T_k e_k, e_k = exp(-sigma_k step),
+// stop once T < t_min; hit = first sample of largest w_k, alpha_c = 1 - T.
+// Samples in unlisted base cells have sigma = 0 and change nothing; the
+// march skips the ones that provably stay inside the empty block of base
+// cells around the current one (with a margin of kSkipMargin fine cells, far
+// above the FP32 error of the sample coordinates), so the samples it
+// evaluates, and therefore the result, are those of the plain loop.
+__device__ __forceinline__ void march_ray(const CubesDev& c, float lo, float scale, const float o[3],
+                                          const float d[3], int32_t& k_hit, float& t_hit, float& alpha) {
+  k_hit = -1;
+  t_hit = 0.0f;
+  alpha = 0.0f;
+  float t0, t1;
+  if (!cube_span(lo, c.hi, o, d, t0, t1)) return;
+  float du[3];  // fine cells advanced per sample along each axis
+#pragma unroll
+  for (int q = 0; q < 3; ++q) du[q] = fabsf(c.K_f * scale * d[q] * c.step);
+  const int32_t R1 = c.r + 1;
+  float T = 1.0f, wmax = 0.0f, tbest = 0.0f;
+  int32_t kbest = -1;
+  int32_t k = 0;
+  for (int32_t guard = 0; guard < kMaxMarchSteps; ++guard) {  // k grows by >= 1 per iteration
+    const float t = __fadd_rn(t0, __fmul_rn(__int2float_rn(k), c.step));
+    if (t > t1) break;
+    float x[3], u[3], f[3];
+    int32_t ci[3];
+    hit_unit_coords_ls(lo, scale, o, d, t, x);
+    fine_cell(c, x, ci, f, u);
+    const int32_t bx = ci[0] >> c.rshift, by = ci[1] >> c.rshift, bz = ci[2] >> c.rshift;
+    const int32_t e = __ldg(c.grid + bx + c.b * (by + c.b * bz));
+    if (e < 0) {
+      // every base cell within D - 1 of this one is empty: skip the samples
+      // that stay inside that block
+      const int32_t D = -e;
+      const int32_t bq[3] = {bx, by, bz};
+      float s = 1048576.0f;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        if (du[q] > 0.0f) {
+          const float rem = d[q] > 0.0f ? __int2float_rn((bq[q] + D) * c.r) - u[q]
+                                        : u[q] - __int2float_rn((bq[q] - D + 1) * c.r);
+          s = fminf(s, (rem - kSkipMargin) / du[q]);
+        }
+      }
+      k += 1 + (s >= 1.0f ? (int32_t)s : 0);
+      continue;
+    }
+    const float* v0 = c.dens + (size_t)e * R1 * R1 * R1 + (ci[0] - (bx << c.rshift)) +
+                      R1 * ((ci[1] - (by << c.rshift)) + R1 * (ci[2] - (bz << c.rshift)));
+    const float s000 = __ldg(v0), s100 = __ldg(v0 + 1);
+    const float s010 = __ldg(v0 + R1), s110 = __ldg(v0 + R1 + 1);
+    const float s001 = __ldg(v0 + R1 * R1), s101 = __ldg(v0 + R1 * R1 + 1);
+    const float s011 = __ldg(v0 + R1 * R1 + R1), s111 = __ldg(v0 + R1 * R1 + R1 + 1);
+    const float a00 = lerp_rn(s000, s100, f[0]), a10 = lerp_rn(s010, s110, f[0]);
+    const float a01 = lerp_rn(s001, s101, f[0]), a11 = lerp_rn(s011, s111, f[0]);
+    const float sigma = lerp_rn(lerp_rn(a00, a10, f[1]), lerp_rn(a01, a11, f[1]), f[2]);
+    if (sigma != 0.0f) {  // sigma = 0: w = 0 and T unchanged
+      const float ek = expf(-__fmul_rn(sigma, c.step));
+      const float w = __fmul_rn(T, __fsub_rn(1.0f, ek));
+      T = __fmul_rn(T, ek);
+      if (w > wmax) {
+        wmax = w;
+        kbest = k;
+        tbest = t;
+      }
+      if (T < c.t_min) break;
+    }
+    ++k;
+  }
+  alpha = __fsub_rn(1.0f, T);
+  if (alpha > c.alpha_miss && kbest >= 0) {
+    k_hit = kbest;
+    t_hit = tbest;
+  }
+}
+
+// (c_d r, g, b, tint) at the point with scene-unit coordinates x: trilinear
+// interpolation of its fine cell's 8 diffuse samples (zero if the cell's
+// cube is not listed, which a hit point's never is).
+__device__ __forceinline__ float4 cube_diffuse(const CubesDev& c, const float x[3]) {
+  float u[3], f[3];
+  int32_t ci[3];
+  fine_cell(c, x, ci, f, u);
+  const int32_t bx = ci[0] >> c.rshift, by = ci[1] >> c.rshift, bz = ci[2] >> c.rshift;
+  const int32_t e = __ldg(c.grid + bx + c.b * (by + c.b * bz));
+  if (e < 0) return make_float4(0.f, 0.f, 0.f, 0.f);
+  const int32_t R1 = c.r + 1;
+  const float4* v0 = c.diff + (size_t)e * R1 * R1 * R1 + (ci[0] - (bx << c.rshift)) +
+                     R1 * ((ci[1] - (by << c.rshift)) + R1 * (ci[2] - (bz << c.rshift)));
+  float4 v[8];
+  v[0] = __ldg(v0);
+  v[1] = __ldg(v0 + 1);
+  v[2] = __ldg(v0 + R1);
+  v[3] = __ldg(v0 + R1 + 1);
+  v[4] = __ldg(v0 + R1 * R1);
+  v[5] = __ldg(v0 + R1 * R1 + 1);
+  v[6] = __ldg(v0 + R1 * R1 + R1);
+  v[7] = __ldg(v0 + R1 * R1 + R1 + 1);
+  auto lerp4 = [](float4 a, float4 b, float t) {
+    return make_float4(fmaf(t, b.x - a.x, a.x), fmaf(t, b.y - a.y, a.y), fmaf(t, b.z - a.z, a.z),
+                       fmaf(t, b.w - a.w, a.w));
+  };
+  const float4 y0 = lerp4(lerp4(v[0], v[1], f[0]), lerp4(v[2], v[3], f[0]), f[1]);
+  const float4 y1 = lerp4(lerp4(v[4], v[5], f[0]), lerp4(v[6], v[7], f[0]), f[1]);
+  return lerp4(y0, y1, f[2]);
 }
 
 }  // namespace inolf

@@ -111,7 +111,12 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_shade_tc(const __grid_constan
       sh16(p, d, sh);
 #pragma unroll
       for (int i = 0; i < 8; ++i) store_pair<kFP8>(A, row, 2u * p.L + 2u * i, chunks1, sh[2 * i], sh[2 * i + 1], inv_sx);
-      for (uint32_t k = (uint32_t)din; k < K1; k += 2) store_pair<kFP8>(A, row, k, chunks1, 0.f, 0.f, 1.f);
+      uint32_t k0 = 2u * p.L + 16u;
+      if (p.variant) {  // alpha_c, the last input of F_s (Eq. 5), then zero padding
+        store_pair<kFP8>(A, row, k0, chunks1, p.hit_alpha[h], 0.f, inv_sx);
+        k0 += 2u;
+      }
+      for (uint32_t k = k0; k < K1; k += 2) store_pair<kFP8>(A, row, k, chunks1, 0.f, 0.f, 1.f);
     } else {
       for (uint32_t c = 0; c < chunks1; ++c)
         *reinterpret_cast<uint4*>(A + tc::core_off(row, c, chunks1)) = make_uint4(0, 0, 0, 0);
@@ -121,7 +126,17 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_shade_tc(const __grid_constan
       bad = true;
       break;
     }
-    if (valid) p.rgba[p.ray_base + ray] = rgba;
+    if (valid) {
+      if (p.variant) {  // c = c_d + tint c_s (Eq. 7), diffuse read at the hit point
+        const uint2 rec = p.hits[h];
+        float o[3], d[3], x[3];
+        ray_of(p, ray, o, d);
+        hit_unit_coords(p, o, d, __uint_as_float(rec.y), x);
+        const float4 dc = cube_diffuse(p.cub, x);
+        rgba = make_float4(fmaf(dc.w, rgba.x, dc.x), fmaf(dc.w, rgba.y, dc.y), fmaf(dc.w, rgba.z, dc.z), rgba.w);
+      }
+      p.rgba[p.ray_base + ray] = rgba;
+    }
   }
   if (bad) {
     if (tid == 0) atomicOr(p.counter + 1, 4u);
@@ -210,6 +225,9 @@ inolf_status prepare_tc_weights(Object& obj, const float* w1, const float* w2, c
   return INOLF_OK;
 }
 
+// Largest weight blob: K1 = 64 (BF16: 64 x 64 x 2 + 64 x 64 x 2 + 4 x 64 x 4 bytes).
+static constexpr uint32_t kMaxTcWeightBytes = 17408;
+
 static size_t tc_smem_bytes(uint32_t wbytes, bool fp8) {
   const size_t tile = 128u * 64u * (fp8 ? 1u : 2u);
   return ((wbytes + 1023u) & ~1023u) + 2 * tile + 64;
@@ -247,11 +265,11 @@ inolf_status launch_shade_tc(const Params& p_in, inolf_precision prec, cudaStrea
       if (const char* e = std::getenv("INOLF_TC_CTAS_PER_SM")) n = std::min(n, std::atoi(e));
       return std::max(1, n);
     };
-    grid_bf16 = sms * ctas_per_sm((const void*)k_shade_tc<false>, tc_smem_bytes(16384, false));
-    grid_fp8 = sms * ctas_per_sm((const void*)k_shade_tc<true>, tc_smem_bytes(16384, true));
+    grid_bf16 = sms * ctas_per_sm((const void*)k_shade_tc<false>, tc_smem_bytes(kMaxTcWeightBytes, false));
+    grid_fp8 = sms * ctas_per_sm((const void*)k_shade_tc<true>, tc_smem_bytes(kMaxTcWeightBytes, true));
     cudaGetLastError();
   });
-  if (smem > (size_t)tc_smem_bytes(16384, fp8)) return fail(INOLF_E_INVALID, "tensor-core weights too large");
+  if (smem > (size_t)tc_smem_bytes(kMaxTcWeightBytes, fp8)) return fail(INOLF_E_INVALID, "tensor-core weights too large");
   const int grid = fp8 ? grid_fp8 : grid_bf16;
   {
     LaunchTimer lt(fp8 ? "k_shade_tc_fp8" : "k_shade_tc_bf16", st);

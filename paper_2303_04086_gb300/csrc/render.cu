@@ -32,15 +32,15 @@
 namespace inolf {
 
 // ---------------------------------------------------------------------------
-// k_trace
+// k_trace / k_march
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_trace(const __grid_constant__ Params p, int32_t tiles_x, int32_t tiles_y) {
+// Ray of this thread: mode 0 = 16 x 16 pixel tile per CTA, each warp an 8 x 4
+// block of pixels; mode 1 = explicit rays, 256 per CTA.
+__device__ __forceinline__ bool thread_ray(const Params& p, int32_t tiles_x, int32_t tiles_y, int64_t& ray, float o[3],
+                                           float d[3]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int64_t ray;       // index within this chunk
   bool valid;
-  float o[3], d[3];
   if (p.mode == 0) {
-    // 16 x 16 pixel tile per CTA, each warp an 8 x 4 block of pixels
     const int64_t tiles = (int64_t)tiles_x * tiles_y;
     const int view = (int)(blockIdx.x / tiles);
     const int64_t tr = blockIdx.x - (int64_t)view * tiles;
@@ -57,14 +57,15 @@ __global__ void __launch_bounds__(256) k_trace(const __grid_constant__ Params p,
       for (int k = 0; k < 3; ++k) { o[k] = p.ro[3 * ray + k]; d[k] = p.rd[3 * ray + k]; }
     }
   }
-  int32_t tri = -1;
-  float t = 0.0f;
-  if (valid) closest_hit(p, o, d, tri, t);
-  const bool hit = valid && tri >= 0;
+  return valid;
+}
 
-  // compaction: warp ballot + per-CTA prefix + one global atomic per CTA, so
-  // the hits of a 16 x 16 pixel tile stay contiguous in the hit list and a
-  // shade tile covers neighbouring pixels (cache locality of the gather)
+// Compaction: warp ballot + per-CTA prefix + one global atomic per CTA, so
+// the hits of a 16 x 16 pixel tile stay contiguous in the hit list and a
+// shade tile covers neighbouring pixels (cache locality of the gather).
+// Returns this thread's hit-list position (meaningful when hit).
+__device__ __forceinline__ uint32_t compact_hit(const Params& p, bool hit) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __shared__ uint32_t s_warp[8];
   __shared__ uint32_t s_base;
   const uint32_t mask = __ballot_sync(0xffffffffu, hit);
@@ -76,17 +77,54 @@ __global__ void __launch_bounds__(256) k_trace(const __grid_constant__ Params p,
     s_base = acc ? atomicAdd(p.counter, acc) : 0u;
   }
   __syncthreads();
-  const uint32_t wbase = s_base + s_warp[warp];
+  return s_base + s_warp[warp] + __popc(mask & ((1u << lane) - 1u));
+}
+
+__global__ void __launch_bounds__(256) k_trace(const __grid_constant__ Params p, int32_t tiles_x, int32_t tiles_y) {
+  int64_t ray;
+  float o[3], d[3];
+  const bool valid = thread_ray(p, tiles_x, tiles_y, ray, o, d);
+  int32_t tri = -1;
+  float t = 0.0f;
+  if (valid) closest_hit(p, o, d, tri, t);
+  const bool hit = valid && tri >= 0;
+  const uint32_t pos = compact_hit(p, hit);
   if (valid) {
     const int64_t g = p.ray_base + ray;
     if (hit) {
-      const uint32_t pos = wbase + __popc(mask & ((1u << lane) - 1u));
       p.hits[pos] = make_uint2((uint32_t)ray, __float_as_uint(t));
     } else if (p.rgba) {
       p.rgba[g] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     if (p.tri_out) p.tri_out[g] = tri;
     if (p.t_out) p.t_out[g] = hit ? t : 0.0f;
+  }
+}
+
+// The decoupled variant's hit estimation (Sec. 4.2, Eq. 4) in place of the
+// proxy trace: the density march of each ray, then the same compaction; the
+// hit record carries the hit sample's t and alpha_c goes alongside.
+// tri_out receives the hit sample k (-1 = miss), alpha_out alpha_c.
+__global__ void __launch_bounds__(256) k_march(const __grid_constant__ Params p, int32_t tiles_x, int32_t tiles_y) {
+  int64_t ray;
+  float o[3], d[3];
+  const bool valid = thread_ray(p, tiles_x, tiles_y, ray, o, d);
+  int32_t k = -1;
+  float t = 0.0f, alpha = 0.0f;
+  if (valid) march_ray(p.cub, p.lo, p.scale, o, d, k, t, alpha);
+  const bool hit = valid && k >= 0;
+  const uint32_t pos = compact_hit(p, hit);
+  if (valid) {
+    const int64_t g = p.ray_base + ray;
+    if (hit) {
+      p.hits[pos] = make_uint2((uint32_t)ray, __float_as_uint(t));
+      p.hit_alpha[pos] = alpha;
+    } else if (p.rgba) {
+      p.rgba[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (p.tri_out) p.tri_out[g] = k;
+    if (p.t_out) p.t_out[g] = hit ? t : 0.0f;
+    if (p.alpha_out) p.alpha_out[g] = alpha;
   }
 }
 
@@ -169,6 +207,19 @@ __global__ void __launch_bounds__(128) k_shade_f32(const __grid_constant__ Param
         h1[4 * q + 3] += a.w * s;
       }
     }
+    if (p.variant) {  // alpha_c, the last input of F_s (Eq. 5)
+      const float a_c = p.hit_alpha[h];
+      if (kMode == kAmax) amax_x = fmaxf(amax_x, a_c);
+      const float4* r = W1T + (2 * p.L + 16) * 16;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const float4 a = r[q];
+        h1[4 * q + 0] += a.x * a_c;
+        h1[4 * q + 1] += a.y * a_c;
+        h1[4 * q + 2] += a.z * a_c;
+        h1[4 * q + 3] += a.w * a_c;
+      }
+    }
 #pragma unroll
     for (int j = 0; j < 64; ++j) {
       h1[j] = fmaxf(h1[j], 0.0f);
@@ -195,8 +246,14 @@ __global__ void __launch_bounds__(128) k_shade_f32(const __grid_constant__ Param
       acc.z += w3.z * z;
       acc.w += w3.w * z;
     }
-    if (kMode == kShade)
-      p.rgba[p.ray_base + ray] = make_float4(sigmoidf_(acc.x), sigmoidf_(acc.y), sigmoidf_(acc.z), sigmoidf_(acc.w));
+    if (kMode == kShade) {
+      float4 out = make_float4(sigmoidf_(acc.x), sigmoidf_(acc.y), sigmoidf_(acc.z), sigmoidf_(acc.w));
+      if (p.variant) {  // c = c_d + tint c_s (Eq. 7)
+        const float4 dc = cube_diffuse(p.cub, x);
+        out = make_float4(fmaf(dc.w, out.x, dc.x), fmaf(dc.w, out.y, dc.y), fmaf(dc.w, out.z, dc.z), out.w);
+      }
+      p.rgba[p.ray_base + ray] = out;
+    }
   }
   if (kMode == kAmax) {
 #pragma unroll
@@ -254,6 +311,7 @@ __global__ void __launch_bounds__(kF32Threads, 3) k_shade_f32_tiled(const __grid
   float* W2T = W1T + din * 64;     // [64][64]  (W2 transposed: [in][out])
   float* W3 = W2T + 64 * 64;       // [4][64]
   float* act = W3 + 4 * 64;        // [64][kF32Tile] activations of the tile
+  float* dif = act + 64 * kF32Tile;  // variant: [4][kF32Tile] (c_d r, g, b, tint) of the tile's rays
   const int tid = threadIdx.x;
   // stage weights: W1T as packed on the host, W2 transposed here, W3 from W3T
   {
@@ -301,6 +359,13 @@ __global__ void __launch_bounds__(kF32Threads, 3) k_shade_f32_tiled(const __grid
         sh16(p, d, sh);
 #pragma unroll
         for (int k = 0; k < 16; ++k) act[(2 * p.L + k) * kF32Tile + ray_slot] = sh[k];
+        if (p.variant) act[(2 * p.L + 16) * kF32Tile + ray_slot] = p.hit_alpha[h];  // alpha_c (Eq. 5)
+      } else if (p.variant) {
+        const float4 dc = cube_diffuse(p.cub, x);
+        dif[0 * kF32Tile + ray_slot] = dc.x;
+        dif[1 * kF32Tile + ray_slot] = dc.y;
+        dif[2 * kF32Tile + ray_slot] = dc.z;
+        dif[3 * kF32Tile + ray_slot] = dc.w;
       }
     } else {
       for (int k = half; k < din; k += 2) act[k * kF32Tile + ray_slot] = 0.0f;
@@ -334,7 +399,13 @@ __global__ void __launch_bounds__(kF32Threads, 3) k_shade_f32_tiled(const __grid
       }
       if (valid) {
         float* out = reinterpret_cast<float*>(p.rgba + (p.ray_base + ray));
-        *reinterpret_cast<float2*>(out + 2 * half) = make_float2(sigmoidf_(z0), sigmoidf_(z1));
+        float2 v = make_float2(sigmoidf_(z0), sigmoidf_(z1));
+        if (p.variant) {  // c = c_d + tint c_s (Eq. 7); alpha stays F_s's
+          const float tint = dif[3 * kF32Tile + ray_slot];
+          v.x = fmaf(tint, v.x, dif[(2 * half) * kF32Tile + ray_slot]);
+          if (half == 0) v.y = fmaf(tint, v.y, dif[1 * kF32Tile + ray_slot]);
+        }
+        *reinterpret_cast<float2*>(out + 2 * half) = v;
       }
     }
     __syncthreads();  // before the next tile overwrites the activations
@@ -346,7 +417,7 @@ __global__ void __launch_bounds__(kF32Threads, 3) k_shade_f32_tiled(const __grid
 // ---------------------------------------------------------------------------
 static constexpr size_t kWsHeader = 256;
 
-size_t workspace_bytes(int64_t n_rays) { return kWsHeader + (size_t)std::max<int64_t>(n_rays, 1) * 8; }
+size_t workspace_bytes(int64_t n_rays) { return kWsHeader + (size_t)std::max<int64_t>(n_rays, 1) * 12; }
 static size_t workspace_bytes_min() { return workspace_bytes(1); }
 
 static int sm_count() {
@@ -382,6 +453,17 @@ static void fill_common(const Object& obj, Params& p) {
     p.fp8_act_scale[k] = obj.fp8_act_scale[k];
   }
   sh_constants(p.shc);
+  p.variant = obj.variant;
+  p.cub = obj.cub;
+}
+
+// Hit list (cap records) and, for the variant, the alpha_c array after it.
+static int64_t place_hit_list(const Object& obj, void* workspace, size_t ws_bytes, Params& p) {
+  const int64_t cap = (int64_t)((ws_bytes - kWsHeader) / hit_bytes_per_ray(obj));
+  p.counter = (uint32_t*)workspace;
+  p.hits = (uint2*)((char*)workspace + kWsHeader);
+  p.hit_alpha = obj.variant ? reinterpret_cast<float*>(p.hits + cap) : nullptr;
+  return cap;
 }
 
 static inolf_status check_launch(const char* what) {
@@ -394,7 +476,8 @@ inolf_status launch_shade_tc(const Params& p, inolf_precision prec, cudaStream_t
 
 inolf_status launch_render(const Object& obj, const RayBatch& rays, inolf_precision prec, float* rgba,
                            int32_t* tri_out, float* t_out, uint32_t* slots_out, float* feat_out,
-                           void* workspace, size_t ws_bytes, void* stream, bool amax) {
+                           void* workspace, size_t ws_bytes, void* stream, bool amax, float* alpha_out,
+                           bool hits_only) {
   cudaStream_t st = (cudaStream_t)stream;
   if (!workspace || ws_bytes < workspace_bytes(1) || ((uintptr_t)workspace & 15))
     return fail(INOLF_E_INVALID, "render: workspace missing, too small or not 16-byte aligned");
@@ -403,20 +486,17 @@ inolf_status launch_render(const Object& obj, const RayBatch& rays, inolf_precis
     return fail(INOLF_E_INVALID, "render: unknown precision");
   if (!encode && prec == INOLF_FP8 && !(obj.fp8_act_scale[0] > 0))
     return fail(INOLF_E_INVALID, "render: FP8 needs activation scales (inolf_object_set_fp8_scales)");
-  const int64_t cap = (int64_t)((ws_bytes - kWsHeader) / 8);
-  uint32_t* counter = (uint32_t*)workspace;
-  uint2* hits = (uint2*)((char*)workspace + kWsHeader);
-
   Params p{};
   fill_common(obj, p);
+  const int64_t cap = place_hit_list(obj, workspace, ws_bytes, p);
+  uint32_t* counter = p.counter;
   p.mode = rays.mode;
   p.rgba = (float4*)rgba;
   p.tri_out = tri_out;
   p.t_out = t_out;
   p.slots_out = slots_out;
   p.feat_out = feat_out;
-  p.counter = counter;
-  p.hits = hits;
+  p.alpha_out = alpha_out;
 
   const size_t smem_f32 = (size_t)(obj.d_in * 64 + 64 * 64 + 64 * 4) * sizeof(float);
   static std::once_flag attr_once;
@@ -426,11 +506,14 @@ inolf_status launch_render(const Object& obj, const RayBatch& rays, inolf_precis
     cudaFuncSetAttribute(k_shade_f32<kAmax>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
   });
   const int shade_grid = sm_count() * 8;
-  const size_t smem_f32_tiled = (size_t)(obj.d_in * 64 + 64 * 64 + 4 * 64 + 64 * kF32Tile) * sizeof(float);
+  const size_t smem_f32_tiled =
+      (size_t)(obj.d_in * 64 + 64 * 64 + 4 * 64 + 64 * kF32Tile + (obj.variant ? 4 * kF32Tile : 0)) * sizeof(float);
   static std::once_flag tiled_once;
   static int f32_ctas = 1;
   std::call_once(tiled_once, [&] {
-    const size_t mx = (size_t)(48 * 64 + 64 * 64 + 4 * 64 + 64 * kF32Tile) * sizeof(float);
+    // the largest configuration: 16 levels, alpha_c input and the diffuse tile
+    const size_t mx =
+        (size_t)((2 * INOLF_MAX_LEVELS + 17) * 64 + 64 * 64 + 4 * 64 + 64 * kF32Tile + 4 * kF32Tile) * sizeof(float);
     cudaFuncSetAttribute(k_shade_f32_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&f32_ctas, k_shade_f32_tiled, kF32Threads, mx);
     if (f32_ctas < 1) f32_ctas = 1;
@@ -441,12 +524,22 @@ inolf_status launch_render(const Object& obj, const RayBatch& rays, inolf_precis
   auto run_chunk = [&](int64_t n_chunk, int32_t tiles_x, int32_t tiles_y, int64_t trace_blocks) -> inolf_status {
     if (cudaMemsetAsync(counter, 0, 8, st) != cudaSuccess) return fail(INOLF_E_CUDA, "cudaMemsetAsync failed");
     (void)n_chunk;
-    {
-      LaunchTimer lt("k_trace", st);
-      k_trace<<<(unsigned)trace_blocks, 256, 0, st>>>(p, tiles_x, tiles_y);
+    if (obj.variant) {
+      {
+        LaunchTimer lt("k_march", st);
+        k_march<<<(unsigned)trace_blocks, 256, 0, st>>>(p, tiles_x, tiles_y);
+      }
+      inolf_status s = check_launch("k_march");
+      if (s != INOLF_OK) return s;
+    } else {
+      {
+        LaunchTimer lt("k_trace", st);
+        k_trace<<<(unsigned)trace_blocks, 256, 0, st>>>(p, tiles_x, tiles_y);
+      }
+      inolf_status s = check_launch("k_trace");
+      if (s != INOLF_OK) return s;
     }
-    inolf_status s = check_launch("k_trace");
-    if (s != INOLF_OK) return s;
+    if (hits_only) return INOLF_OK;
     if (encode) {
       LaunchTimer lt("k_encode", st);
       k_shade_f32<kEncode><<<shade_grid, 128, 0, st>>>(p);
@@ -506,6 +599,8 @@ inolf_status launch_backward_rays(const Object& obj, const float* o, const float
                                   float* const* grad_tables, float* gw1, float* gw2, float* gw3, void* workspace,
                                   size_t ws_bytes, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
+  if (obj.variant)
+    return fail(INOLF_E_UNSUPPORTED, "backward: objects with density cubes have no backward in this library");
   if (!workspace || ws_bytes < workspace_bytes(1) || ((uintptr_t)workspace & 15))
     return fail(INOLF_E_INVALID, "backward: workspace missing, too small or not 16-byte aligned");
   const int64_t cap = (int64_t)((ws_bytes - kWsHeader) / 8);
@@ -646,4 +741,20 @@ extern "C" inolf_status inolf_encode_rays(const inolf_object* obj, const float* 
   rb.n = n;
   return launch_render(obj->o, rb, INOLF_FP32, nullptr, nullptr, nullptr, slots_out, feat_out, workspace,
                        workspace_bytes, stream);
+}
+
+extern "C" inolf_status inolf_march_rays(const inolf_object* obj, const float* o, const float* d, int64_t n,
+                                         int32_t* k_out, float* t_out, float* alpha_out, void* workspace,
+                                         size_t workspace_bytes, void* stream) {
+  clear_error();
+  if (!obj || n < 0 || (n > 0 && (!o || !d))) return fail(INOLF_E_INVALID, "inolf_march_rays: bad argument");
+  if (!obj->o.variant) return fail(INOLF_E_INVALID, "inolf_march_rays: the object has no density cubes");
+  if (n == 0) return INOLF_OK;
+  RayBatch rb{};
+  rb.mode = 1;
+  rb.o = o;
+  rb.d = d;
+  rb.n = n;
+  return launch_render(obj->o, rb, INOLF_FP32, nullptr, k_out, t_out, nullptr, nullptr, workspace, workspace_bytes,
+                       stream, false, alpha_out, true);
 }

@@ -808,6 +808,8 @@ extern "C" inolf_status inolf_serve_add_object(inolf_server* s, const inolf_obje
   for (auto& m : s->slots)
     if (m.busy) return fail(INOLF_E_INVALID, "inolf_serve_add_object: requests are in flight");
   if ((int)s->objs.size() >= kServeMaxObjects) return fail(INOLF_E_INVALID, "inolf_serve_add_object: 16 objects max");
+  if (obj->o.variant)
+    return fail(INOLF_E_UNSUPPORTED, "inolf_serve_add_object: the serving loop composites mesh-proxy objects only");
   const Object& o = obj->o;
   ServeObj so{};
   so.nodes = (const float4*)o.nodes;

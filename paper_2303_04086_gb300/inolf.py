@@ -44,6 +44,13 @@ class HashStruct(ctypes.Structure):
                 ("phi", ctypes.POINTER(ctypes.c_uint32)), ("slot_of", ctypes.POINTER(ctypes.c_uint32))]
 
 
+class CubesDesc(ctypes.Structure):
+    _fields_ = [("b", ctypes.c_int32), ("r", ctypes.c_int32), ("n_cubes", ctypes.c_int64),
+                ("cells", ctypes.c_void_p), ("density", ctypes.c_void_p), ("diffuse", ctypes.c_void_p),
+                ("side", ctypes.c_float), ("step", ctypes.c_float), ("t_min", ctypes.c_float),
+                ("alpha_miss", ctypes.c_float)]
+
+
 class ObjectDesc(ctypes.Structure):
     _fields_ = [("n_vertices", ctypes.c_int32), ("n_triangles", ctypes.c_int32),
                 ("vertices", ctypes.c_void_p), ("triangles", ctypes.c_void_p),
@@ -52,7 +59,8 @@ class ObjectDesc(ctypes.Structure):
                 ("features_fp16", ctypes.c_int32),
                 ("w1", ctypes.c_void_p), ("w2", ctypes.c_void_p), ("w3", ctypes.c_void_p),
                 ("fp8_act_scale", ctypes.c_float * 3),
-                ("domain_lo", ctypes.c_float), ("domain_scale", ctypes.c_float)]
+                ("domain_lo", ctypes.c_float), ("domain_scale", ctypes.c_float),
+                ("cubes", ctypes.POINTER(CubesDesc))]
 
 
 def lib():
@@ -82,6 +90,7 @@ def lib():
     L.inolf_render.argtypes = [vp, vp, i32, i32, i32, i32, vp, vp, vp, vp, sz, vp]
     L.inolf_render_rays.argtypes = [vp, vp, vp, i64, i32, vp, vp, vp, vp, sz, vp]
     L.inolf_encode_rays.argtypes = [vp, vp, vp, i64, vp, vp, vp, sz, vp]
+    L.inolf_march_rays.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp, sz, vp]
     L.inolf_render_rays_noalloc.argtypes = [vp, vp, vp, i64, i32, vp, vp, vp, vp]
     L.inolf_calibrate_fp8.argtypes = [vp, vp, i32, i32, i32, vp, sz, vp]
     L.inolf_backward.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, sz, vp]
@@ -213,7 +222,8 @@ def build_hashes(scene, threads: int = 0, **kw) -> List[Hash]:
 
 def object_create(scene, hashes: Optional[List[Hash]] = None, fp16: Optional[bool] = None,
                   fp8_act_scale=(0.0, 0.0, 0.0), stream=None) -> Object:
-    """Upload a synth.Scene (mesh, per-level hash + features, MLP weights)."""
+    """Upload a synth.Scene (mesh, per-level hash + features, MLP weights; or,
+    for scenes with density cubes, the cubes in place of the mesh)."""
     if hashes is None:
         hashes = build_hashes(scene)
     L = scene.n_levels
@@ -239,8 +249,23 @@ def object_create(scene, hashes: Optional[List[Hash]] = None, fp16: Optional[boo
         d.fp8_act_scale[k] = float(fp8_act_scale[k])
     d.domain_lo = float(scene.domain_lo)
     d.domain_scale = float(np.float32(1.0 / scene.domain_side))
+    cubes = getattr(scene, "cubes", None)
+    keep = []
+    if cubes is not None:
+        cells = np.ascontiguousarray(cubes.cells, np.int32)
+        dens = np.ascontiguousarray(cubes.density, np.float32)
+        diff = np.ascontiguousarray(cubes.diffuse, np.float32)
+        keep = [cells, dens, diff]
+        c = CubesDesc()
+        c.b, c.r, c.n_cubes = int(cubes.b), int(cubes.r), len(cells)
+        c.cells, c.density, c.diffuse = cells.ctypes.data, dens.ctypes.data, diff.ctypes.data
+        c.side, c.step = float(cubes.side), float(cubes.step)
+        c.t_min, c.alpha_miss = float(cubes.t_min), float(cubes.alpha_miss)
+        keep.append(c)
+        d.cubes = ctypes.pointer(c)
     out = ctypes.c_void_p()
     _check(lib().inolf_object_create(ctypes.byref(d), _stream(stream), ctypes.byref(out)))
+    del keep
     return Object(out.value, L, scene.d_in, hashes)
 
 
@@ -318,6 +343,24 @@ def render_rays_noalloc(obj: Object, o, d, prec="fp32", rgba_out=None, tri_out=N
     _check(lib().inolf_render_rays_noalloc(obj.handle, _ptr(o), _ptr(d), n, p, _ptr(rgba_out), _ptr(tri_out),
                                            _ptr(t_out), _stream(stream)))
     return rgba_out
+
+
+def march_rays(obj: Object, o, d, k_out=None, t_out=None, alpha_out=None, workspace=None, stream=None):
+    """inolf_march_rays: hit sample k (-1 = miss), its t and alpha_c of the
+    density march (objects with density cubes).  Returns (k, t, alpha)."""
+    import torch
+    n = o.shape[0]
+    if k_out is None:
+        k_out = torch.empty(n, dtype=torch.int32, device=o.device)
+    if t_out is None:
+        t_out = torch.empty(n, dtype=torch.float32, device=o.device)
+    if alpha_out is None:
+        alpha_out = torch.empty(n, dtype=torch.float32, device=o.device)
+    if workspace is None:
+        workspace = _workspace(n, o.device)
+    _check(lib().inolf_march_rays(obj.handle, _ptr(o), _ptr(d), n, _ptr(k_out), _ptr(t_out), _ptr(alpha_out),
+                                  _ptr(workspace), workspace.numel() * workspace.element_size(), _stream(stream)))
+    return k_out, t_out, alpha_out
 
 
 def encode_rays(obj: Object, o, d, slots_out, feat_out, workspace=None, stream=None):
