@@ -49,6 +49,7 @@ def _args():
     ap.add_argument("--precisions", default="fp32,bf16,fp8")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-seconds", type=float, default=10.0)
+    ap.add_argument("--no-variant", action="store_true", help="skip the density-cube variant workload")
     return ap.parse_args()
 
 
@@ -411,6 +412,103 @@ def run_training(steps=40, batch=1 << 18, n_views=100, res=800, prec="bf16"):
             "views": n_views, "res": res}
 
 
+def run_variant(steps=3, warmup=3, views=N_VIEWS, precisions=("fp32", "bf16", "fp8"), oracle_pixels=100_000):
+    """The paper's decoupled variant (Sec. 4.2, Eqs. 4-7) on the same object
+    as a density shell: 64 ring views at 4K, hit points from the density march
+    (k_march), alpha_c input, c = c_d + t c_s.  Returns per-precision Mrays/s
+    with per-kernel times, the accuracy of view 0 against the oracle on a
+    pixel sample, and the march alone on 1080p frames."""
+    import torch
+    from paper_2303_04086_gb300 import inolf, synth
+    t0 = time.time()
+    scene = synth.full_density_scene(seed=0)
+    hashes = inolf.build_hashes(scene, slot_slack=SLOT_SLACK)
+    obj = inolf.object_create(scene, hashes)
+    prep_s = time.time() - t0
+    cams = synth.ring_cameras(views, RING_R)
+    W, H = W4K, H4K
+    n_rays = views * W * H
+    dev = torch.device("cuda", torch.cuda.current_device())
+    rgba = torch.empty((views, H, W, 4), dtype=torch.float32, device=dev)
+    ws = torch.empty((inolf.render_workspace_bytes(n_rays) + 15) // 16 * 4, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    kk = torch.empty((views, H, W), dtype=torch.int32, device=dev)
+    inolf.render(obj, cams, W, H, "fp32", rgba_out=rgba, tri_out=kk, workspace=ws)
+    torch.cuda.synchronize()
+    n_hit = int((kk >= 0).sum().item())
+    del kk
+    out = {"workload": ("displaced-sphere density shell (half-width 2 fine cells, optical depth 12), 128^3 base "
+                        "cells x 16^3 fine cells, %d cubes; L16 PSH N16-2048 over the voxels around possible hit "
+                        "points; MLP 49-64-64-4 with alpha_c; %d ring views r=2.5 at 3840x2160"
+                        % (scene.cubes.n, views)),
+           "prep_s": round(prep_s, 1), "rays_per_step": n_rays, "hit_rays_per_step": n_hit, "precisions": {}}
+    for prec in precisions:
+        if prec == "fp8":
+            inolf.calibrate_fp8(obj, cams[:1], W, H, workspace=ws)
+        for _ in range(warmup):
+            inolf.render(obj, cams, W, H, prec, rgba_out=rgba, workspace=ws, stream=stream)
+        torch.cuda.synchronize()
+        inolf.stats_reset()
+        inolf.stats_enable(True)
+        evs = []
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            inolf.render(obj, cams, W, H, prec, rgba_out=rgba, workspace=ws, stream=stream)
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        inolf.stats_enable(False)
+        ms = sum(e0.elapsed_time(e1) for e0, e1 in evs)
+        out["precisions"][prec] = {"value": n_rays * steps / (ms / 1e3) / 1e6, "unit": "Mrays/s",
+                                   "ms_per_step": ms / steps, "kernels": inolf.stats_read()}
+    # the march alone on 1080p frames (the paper times its hit estimation per 1080p image)
+    W2, H2 = 1920, 1080
+    o_views = 8
+    c8 = synth.ring_cameras(o_views, RING_R)
+    k8 = torch.empty((o_views, H2, W2), dtype=torch.int32, device=dev)
+    f8 = torch.empty((o_views, H2, W2, 4), dtype=torch.float32, device=dev)
+    for _ in range(3):
+        inolf.render(obj, c8, W2, H2, "bf16", rgba_out=f8, tri_out=k8, workspace=ws, stream=stream)
+    torch.cuda.synchronize()
+    inolf.stats_reset()
+    inolf.stats_enable(True)
+    for _ in range(5):
+        inolf.render(obj, c8, W2, H2, "bf16", rgba_out=f8, tri_out=k8, workspace=ws, stream=stream)
+    torch.cuda.synchronize()
+    inolf.stats_enable(False)
+    st = inolf.stats_read()
+    if "k_march" in st:
+        out["march_ms_per_1080p_frame"] = st["k_march"]["ms"] / (5 * o_views)
+    # accuracy of view 0 on a pixel sample against the oracle (FP32 argmax
+    # near-ties, a handful, are compared at the oracle's own decision anyway)
+    try:
+        import oracle
+        oracle.build()
+        orc = oracle.Oracle(scene)
+        rng = np.random.default_rng(7)
+        pix = np.sort(rng.choice(W * H, oracle_pixels, replace=False)).astype(np.int64)
+        ref = orc.render_variant_pixels(cams[0], W, H, pix)
+        hit = ref["k"] >= 0
+        pt = torch.from_numpy(pix).to(dev)
+        v0 = torch.empty((1, H, W, 4), dtype=torch.float32, device=dev)
+        for prec in precisions:
+            inolf.render(obj, cams[:1], W, H, prec, rgba_out=v0, workspace=ws)
+            got = v0.reshape(-1, 4)[pt].cpu().numpy()
+            mse = float(np.mean((got[hit] - ref["rgba"][hit]) ** 2))
+            out["precisions"][prec]["accuracy_vs_oracle"] = {
+                "psnr_db": 10 * math.log10(1.0 / mse) if mse > 0 else 99.0,
+                "max_abs": float(np.abs(got - ref["rgba"]).max()), "view": 0, "pixels": int(len(pix))}
+    except Exception as e:  # the accuracy check is a report, not the measurement
+        out["accuracy_error"] = str(e)[:200]
+    del rgba, ws, flush, obj, f8, k8
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -601,8 +699,14 @@ def run_native(a):
         out["accuracy_vs_oracle"] = fp32_acc
     if rank == 0 and not a.small:
         out["zoom_sweep"] = run_zoom_sweep(obj, W, H)
-    if rank == 0 and not a.no_serving and not a.small:
+    if rank == 0 and not a.small and not a.no_variant:
         del rgba, ws
+        torch.cuda.empty_cache()
+        out["variant"] = run_variant(steps=max(1, a.steps), warmup=max(1, a.warmup),
+                                     precisions=[p for p in ["fp32"] + list(precisions)
+                                                 if "unavailable" not in precisions.get(p, {})])
+    if rank == 0 and not a.no_serving and not a.small:
+        rgba = ws = None
         torch.cuda.empty_cache()
         out["serving"] = run_serving(seconds=a.serving_seconds, policy=1)
         out["serving_fifo"] = run_serving(seconds=a.serving_seconds, policy=0)

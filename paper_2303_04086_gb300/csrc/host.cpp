@@ -10,6 +10,7 @@
 #include <cstring>
 #include <new>
 #include <numeric>
+#include <thread>
 #include <vector>
 
 #include "inolf_internal.h"
@@ -425,48 +426,46 @@ inolf_status upload_weights(Object& o, const float* w1, const float* w2, const f
 static void destroy_object(Object& o) {
   auto f = [](void* p) { if (p) cudaFree(p); };
   f(o.nodes); f(o.tris); f(o.w_f32); f(o.w_bf16); f(o.w_fp8);
-  f((void*)o.cub.grid); f((void*)o.cub.dens); f((void*)o.cub.diff);
+  f((void*)o.cub.grid); f((void*)o.cub.dens); f((void*)o.cub.diff); f((void*)o.cub.fdist); f((void*)o.cub.bdist);
   for (int l = 0; l < o.L; ++l) { f((void*)o.lv[l].phi); f((void*)o.lv[l].table); }
   o = Object();
 }
 
-// Chebyshev (L-infinity) distance, in cells, from every cell of a b^3 grid to
-// the nearest listed cell, capped at `cap`: the 1-D distance along x, then
-// along y and z the minimum over the line of max(|offset|, previous pass),
-// which composes to min over listed cells of max(|dx|, |dy|, |dz|).
-static std::vector<int32_t> chebyshev_distance(const std::vector<uint8_t>& listed, int32_t b, int32_t cap) {
-  const int64_t n = (int64_t)b * b * b;
-  std::vector<int32_t> a(n), c(n);
-  auto at = [b](int64_t x, int64_t y, int64_t z) { return x + (int64_t)b * (y + (int64_t)b * z); };
-  for (int64_t z = 0; z < b; ++z)
-    for (int64_t y = 0; y < b; ++y) {
-      int32_t run = cap;
-      for (int64_t x = 0; x < b; ++x) {
-        run = listed[at(x, y, z)] ? 0 : std::min(cap, run + 1);
-        a[at(x, y, z)] = run;
-      }
-      run = cap;
-      for (int64_t x = b - 1; x >= 0; --x) {
-        run = listed[at(x, y, z)] ? 0 : std::min(cap, run + 1);
-        a[at(x, y, z)] = std::min(a[at(x, y, z)], run);
+// Octant distances of an n^3 grid of cells with obstacles: for every cell
+// and every octant s (bit q set: axis q decreasing, else increasing), the
+// largest D <= cap such that the block of D^3 cells that starts at the cell
+// and extends along s holds no obstacle (0 for an obstacle).  The block of
+// size D is empty exactly when the cell is empty and the blocks of size D - 1
+// of its 7 forward neighbours are, so one sweep against s per octant gives
+// D = 1 + min over those neighbours (cells beyond the grid do not constrain).
+// out: [8][n^3], cell x + n (y + n z).
+static void octant_distance(const uint8_t* obstacle, int32_t n, int32_t cap, uint8_t* out) {
+  const int64_t n3 = (int64_t)n * n * n;
+  for (int oct = 0; oct < 8; ++oct) {
+    const int32_t s[3] = {(oct & 1) ? -1 : 1, (oct & 2) ? -1 : 1, (oct & 4) ? -1 : 1};
+    uint8_t* D = out + (size_t)oct * n3;
+    for (int32_t iz = 0; iz < n; ++iz) {
+      const int32_t z = s[2] > 0 ? n - 1 - iz : iz;
+      for (int32_t iy = 0; iy < n; ++iy) {
+        const int32_t y = s[1] > 0 ? n - 1 - iy : iy;
+        for (int32_t ix = 0; ix < n; ++ix) {
+          const int32_t x = s[0] > 0 ? n - 1 - ix : ix;
+          const int64_t c = x + (int64_t)n * (y + (int64_t)n * z);
+          if (obstacle[c]) {
+            D[c] = 0;
+            continue;
+          }
+          int32_t m = cap;
+          for (int e = 1; e < 8; ++e) {
+            const int32_t nx = x + ((e & 1) ? s[0] : 0), ny = y + ((e & 2) ? s[1] : 0), nz = z + ((e & 4) ? s[2] : 0);
+            if (nx < 0 || ny < 0 || nz < 0 || nx >= n || ny >= n || nz >= n) continue;
+            m = std::min<int32_t>(m, D[nx + (int64_t)n * (ny + (int64_t)n * nz)]);
+          }
+          D[c] = (uint8_t)std::min<int32_t>(cap, m + 1);
+        }
       }
     }
-  auto line_pass = [&](const std::vector<int32_t>& in, std::vector<int32_t>& out, int axis) {
-    for (int64_t i = 0; i < b; ++i)
-      for (int64_t j = 0; j < b; ++j)
-        for (int64_t k = 0; k < b; ++k) {
-          auto idx = [&](int64_t m) { return axis == 1 ? at(i, m, j) : at(i, j, m); };
-          int32_t best = in[idx(k)];
-          for (int64_t off = 1; off < best && off < b; ++off) {
-            if (k - off >= 0) best = std::min(best, std::max((int32_t)off, in[idx(k - off)]));
-            if (k + off < b) best = std::min(best, std::max((int32_t)off, in[idx(k + off)]));
-          }
-          out[idx(k)] = best;
-        }
-  };
-  line_pass(a, c, 1);
-  line_pass(c, a, 2);
-  return a;
+  }
 }
 
 // Uploads the density / diffuse cubes and builds the base grid of cube
@@ -474,7 +473,7 @@ static std::vector<int32_t> chebyshev_distance(const std::vector<uint8_t>& liste
 static inolf_status create_cubes(Object& o, const inolf_cubes_desc& C, cudaStream_t st) {
   const int32_t b = C.b, r = C.r;
   const int64_t nb = (int64_t)b * b * b, nv = (int64_t)(r + 1) * (r + 1) * (r + 1);
-  std::vector<int32_t> grid(nb, -1);
+  std::vector<int32_t> grid(nb, -1);  // cube index, -1 for unlisted cells
   std::vector<uint8_t> listed(nb, 0);
   for (int64_t i = 0; i < C.n_cubes; ++i) {
     const int32_t x = C.cells[3 * i], y = C.cells[3 * i + 1], z = C.cells[3 * i + 2];
@@ -483,23 +482,62 @@ static inolf_status create_cubes(Object& o, const inolf_cubes_desc& C, cudaStrea
     listed[lin] = 1;
     grid[lin] = (int32_t)i;
   }
-  const int32_t cap = std::min<int32_t>(b, 255);
-  const std::vector<int32_t> dist = chebyshev_distance(listed, b, cap);
-  for (int64_t i = 0; i < nb; ++i)
-    if (!listed[i]) grid[i] = -std::max<int32_t>(1, dist[i]);
+  // empty space between the cubes: octant distances of the unlisted base cells
+  std::vector<uint8_t> bdist((size_t)8 * nb);
+  octant_distance(listed.data(), b, std::min<int32_t>(b, 255), bdist.data());
+  // inside each cube: octant distances (in fine cells, within the cube) of the
+  // cells that are not live -- a live cell has a vertex of non-zero density;
+  // a cell that is not live has sigma = 0 at every point, so the march skips
+  // blocks of such cells as it skips unlisted base cells.
+  const int64_t cpc = (int64_t)r * r * r;
+  const int64_t nfd = std::max<int64_t>(C.n_cubes * cpc, 1);
+  std::vector<uint8_t> fdist((size_t)8 * nfd, 0);
+  {
+    const int32_t fcap = std::min<int32_t>(r, 255);
+    const int nt = (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    auto work = [&](int tid) {
+      std::vector<uint8_t> dead((size_t)cpc), od((size_t)8 * cpc);
+      for (int64_t q = tid; q < C.n_cubes; q += nt) {
+        const float* blk = C.density + (size_t)(q * nv);
+        auto at = [&](int32_t i, int32_t j, int32_t k) { return blk[i + (r + 1) * (j + (r + 1) * k)]; };
+        for (int32_t k = 0; k < r; ++k)
+          for (int32_t j = 0; j < r; ++j)
+            for (int32_t i = 0; i < r; ++i) {
+              bool any = false;
+              for (int c = 0; c < 8 && !any; ++c) any = at(i + (c & 1), j + ((c >> 1) & 1), k + ((c >> 2) & 1)) > 0.0f;
+              dead[i + (size_t)r * (j + (size_t)r * k)] = any;  // live cells are the obstacles
+            }
+        octant_distance(dead.data(), r, fcap, od.data());
+        for (int oct = 0; oct < 8; ++oct)
+          std::memcpy(&fdist[(size_t)oct * nfd + (size_t)(q * cpc)], &od[(size_t)oct * cpc], (size_t)cpc);
+      }
+    };
+    std::vector<std::thread> th;
+    for (int t = 1; t < nt; ++t) th.emplace_back(work, t);
+    work(0);
+    for (auto& t : th) t.join();
+  }
   void* dg = nullptr;
   void* dd = nullptr;
   void* df = nullptr;
+  void* dz = nullptr;
+  void* db = nullptr;
   if (cudaMalloc(&dg, sizeof(int32_t) * nb) != cudaSuccess) return fail(INOLF_E_OOM, "cudaMalloc cube grid");
   o.cub.grid = (const int32_t*)dg;
+  if (cudaMalloc(&db, bdist.size()) != cudaSuccess) return fail(INOLF_E_OOM, "cudaMalloc base distances");
+  o.cub.bdist = (const uint8_t*)db;
   const size_t dbytes = sizeof(float) * (size_t)std::max<int64_t>(C.n_cubes * nv, 1);
   const size_t fbytes = sizeof(float4) * (size_t)std::max<int64_t>(C.n_cubes * nv, 1);
   if (cudaMalloc(&dd, dbytes) != cudaSuccess) return fail(INOLF_E_OOM, "cudaMalloc density cubes");
   o.cub.dens = (const float*)dd;
   if (cudaMalloc(&df, fbytes) != cudaSuccess) return fail(INOLF_E_OOM, "cudaMalloc diffuse cubes");
   o.cub.diff = (const float4*)df;
-  o.bytes += sizeof(int32_t) * nb + dbytes + fbytes;
+  if (cudaMalloc(&dz, fdist.size()) != cudaSuccess) return fail(INOLF_E_OOM, "cudaMalloc cube distances");
+  o.cub.fdist = (const uint8_t*)dz;
+  o.bytes += sizeof(int32_t) * nb + bdist.size() + dbytes + fbytes + fdist.size();
   if (cudaMemcpyAsync(dg, grid.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(db, bdist.data(), bdist.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(dz, fdist.data(), fdist.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
       (C.n_cubes > 0 &&
        (cudaMemcpyAsync(dd, C.density, sizeof(float) * C.n_cubes * nv, cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(df, C.diffuse, sizeof(float4) * C.n_cubes * nv, cudaMemcpyHostToDevice, st) !=
@@ -513,6 +551,7 @@ static inolf_status create_cubes(Object& o, const inolf_cubes_desc& C, cudaStrea
   while ((1 << c.rshift) < r) ++c.rshift;
   c.K = b * r;
   c.K_f = (float)c.K;
+  c.n_cubes = C.n_cubes;
   c.hi = o.lo + C.side;
   c.step = C.step;
   c.t_min = C.t_min;

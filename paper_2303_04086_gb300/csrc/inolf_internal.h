@@ -28,13 +28,19 @@ struct LevelDev {
 };
 
 // Density and diffuse texture cubes as the kernels see them (Sec. 4.2).
-// grid[x + b (y + b z)] of a base cell is its cube's index, or -D for an
-// unlisted cell whose nearest listed cube is D >= 1 base cells away in the
-// Chebyshev metric (every cell within D - 1 of it is unlisted too).
+// grid[x + b (y + b z)] of a base cell is its cube's index, or -1 when no
+// cube is listed there.  Octant distances (octant bit q set: axis q
+// decreasing): bdist[oct][cell] is the size D of the largest block of D^3
+// unlisted base cells that starts at the cell and extends along the octant;
+// fdist[oct][cube][fine cell] the same in fine cells within a cube for cells
+// that are not live (no vertex of non-zero density), 0 for live cells.
 struct CubesDev {
   const int32_t* grid;   // b^3
   const float* dens;     // n x (r+1)^3 sigma, x fastest
   const float4* diff;    // n x (r+1)^3 (c_d r, g, b, tint)
+  const uint8_t* bdist;  // 8 x b^3
+  const uint8_t* fdist;  // 8 x n x r^3
+  int64_t n_cubes;
   int32_t b, r, rshift;  // r = 1 << rshift
   int32_t K;             // fine cells per axis, b r
   float K_f;             // (float)K

@@ -490,11 +490,14 @@ __device__ __forceinline__ void fine_cell(const CubesDev& c, const float x[3], i
 // The march of one ray (Eq. 4): samples t_k = t0 + k step, sigma_k from the
 // cubes, w_k = T_k (1 - e_k), T_{k+1} = T_k e_k, e_k = exp(-sigma_k step),
 // stop once T < t_min; hit = first sample of largest w_k, alpha_c = 1 - T.
-// Samples in unlisted base cells have sigma = 0 and change nothing; the
-// march skips the ones that provably stay inside the empty block of base
-// cells around the current one (with a margin of kSkipMargin fine cells, far
-// above the FP32 error of the sample coordinates), so the samples it
-// evaluates, and therefore the result, are those of the plain loop.
+// Samples where sigma = 0 change nothing.  The octant distance fields mark,
+// for the ray's octant, a block of such samples that starts at the current
+// cell and extends the way the ray travels: unlisted base cells between the
+// cubes, or fine cells that are not live inside a cube (clipped to the cube).
+// The march skips the samples that provably stay inside that block (with a
+// margin of kSkipMargin fine cells, far above the FP32 error of the sample
+// coordinates), so the samples it evaluates, and therefore the result, are
+// those of the plain loop.
 __device__ __forceinline__ void march_ray(const CubesDev& c, float lo, float scale, const float o[3],
                                           const float d[3], int32_t& k_hit, float& t_hit, float& alpha) {
   k_hit = -1;
@@ -502,10 +505,17 @@ __device__ __forceinline__ void march_ray(const CubesDev& c, float lo, float sca
   alpha = 0.0f;
   float t0, t1;
   if (!cube_span(lo, c.hi, o, d, t0, t1)) return;
-  float du[3];  // fine cells advanced per sample along each axis
+  float inv_du[3];  // samples per fine cell along each axis (0: the ray does not move along it)
 #pragma unroll
-  for (int q = 0; q < 3; ++q) du[q] = fabsf(c.K_f * scale * d[q] * c.step);
-  const int32_t R1 = c.r + 1;
+  for (int q = 0; q < 3; ++q) {
+    const float du = fabsf(c.K_f * scale * d[q] * c.step);
+    inv_du[q] = du > 0.0f ? 1.0f / du : 0.0f;
+  }
+  const bool neg[3] = {d[0] < 0.0f, d[1] < 0.0f, d[2] < 0.0f};
+  const int32_t oct = (neg[0] ? 1 : 0) | (neg[1] ? 2 : 0) | (neg[2] ? 4 : 0);
+  const int32_t R1 = c.r + 1, r3 = c.r * c.r * c.r;
+  const uint8_t* bdist = c.bdist + (size_t)oct * c.b * c.b * c.b;
+  const uint8_t* fdist = c.fdist + (size_t)oct * c.n_cubes * r3;
   float T = 1.0f, wmax = 0.0f, tbest = 0.0f;
   int32_t kbest = -1;
   int32_t k = 0;
@@ -516,27 +526,36 @@ __device__ __forceinline__ void march_ray(const CubesDev& c, float lo, float sca
     int32_t ci[3];
     hit_unit_coords_ls(lo, scale, o, d, t, x);
     fine_cell(c, x, ci, f, u);
-    const int32_t bx = ci[0] >> c.rshift, by = ci[1] >> c.rshift, bz = ci[2] >> c.rshift;
-    const int32_t e = __ldg(c.grid + bx + c.b * (by + c.b * bz));
+    const int32_t bq[3] = {ci[0] >> c.rshift, ci[1] >> c.rshift, ci[2] >> c.rshift};
+    const int32_t lin = bq[0] + c.b * (bq[1] + c.b * bq[2]);
+    const int32_t e = __ldg(c.grid + lin);
+    const int32_t Db = __ldg(bdist + lin);
+    const int32_t lf[3] = {ci[0] - (bq[0] << c.rshift), ci[1] - (bq[1] << c.rshift), ci[2] - (bq[2] << c.rshift)};
+    // the face of the empty block the ray leaves through, per axis (fine cells)
+    int32_t D, face[3];
     if (e < 0) {
-      // every base cell within D - 1 of this one is empty: skip the samples
-      // that stay inside that block
-      const int32_t D = -e;
-      const int32_t bq[3] = {bx, by, bz};
+      D = Db;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) face[q] = (neg[q] ? bq[q] - D + 1 : bq[q] + D) * c.r;
+    } else {
+      D = __ldg(fdist + (size_t)e * r3 + lf[0] + c.r * (lf[1] + c.r * lf[2]));
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+        face[q] = neg[q] ? max(bq[q] * c.r, ci[q] - D + 1) : min((bq[q] + 1) * c.r, ci[q] + D);
+    }
+    if (D > 0) {
       float s = 1048576.0f;
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
-        if (du[q] > 0.0f) {
-          const float rem = d[q] > 0.0f ? __int2float_rn((bq[q] + D) * c.r) - u[q]
-                                        : u[q] - __int2float_rn((bq[q] - D + 1) * c.r);
-          s = fminf(s, (rem - kSkipMargin) / du[q]);
+        if (inv_du[q] > 0.0f) {
+          const float rem = neg[q] ? u[q] - __int2float_rn(face[q]) : __int2float_rn(face[q]) - u[q];
+          s = fminf(s, (rem - kSkipMargin) * inv_du[q]);
         }
       }
       k += 1 + (s >= 1.0f ? (int32_t)s : 0);
       continue;
     }
-    const float* v0 = c.dens + (size_t)e * R1 * R1 * R1 + (ci[0] - (bx << c.rshift)) +
-                      R1 * ((ci[1] - (by << c.rshift)) + R1 * (ci[2] - (bz << c.rshift)));
+    const float* v0 = c.dens + (size_t)e * R1 * R1 * R1 + lf[0] + R1 * (lf[1] + R1 * lf[2]);
     const float s000 = __ldg(v0), s100 = __ldg(v0 + 1);
     const float s010 = __ldg(v0 + R1), s110 = __ldg(v0 + R1 + 1);
     const float s001 = __ldg(v0 + R1 * R1), s101 = __ldg(v0 + R1 * R1 + 1);

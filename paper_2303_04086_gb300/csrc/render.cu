@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(256) k_trace(const __grid_constant__ Params p,
 // proxy trace: the density march of each ray, then the same compaction; the
 // hit record carries the hit sample's t and alpha_c goes alongside.
 // tri_out receives the hit sample k (-1 = miss), alpha_out alpha_c.
-__global__ void __launch_bounds__(256) k_march(const __grid_constant__ Params p, int32_t tiles_x, int32_t tiles_y) {
+__global__ void __launch_bounds__(256, 5) k_march(const __grid_constant__ Params p, int32_t tiles_x, int32_t tiles_y) {
   int64_t ray;
   float o[3], d[3];
   const bool valid = thread_ray(p, tiles_x, tiles_y, ray, o, d);
