@@ -50,6 +50,9 @@ def _args():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-seconds", type=float, default=10.0)
     ap.add_argument("--no-variant", action="store_true", help="skip the density-cube variant workload")
+    ap.add_argument("--variant-only", action="store_true",
+                    help="run only the density-cube variant workload (--views, --steps, --warmup, --precisions) "
+                         "and print its JSON (profiling)")
     return ap.parse_args()
 
 
@@ -486,6 +489,8 @@ def run_variant(steps=3, warmup=3, views=N_VIEWS, precisions=("fp32", "bf16", "f
     # accuracy of view 0 on a pixel sample against the oracle (FP32 argmax
     # near-ties, a handful, are compared at the oracle's own decision anyway)
     try:
+        if oracle_pixels <= 0:
+            raise RuntimeError("accuracy check skipped")
         import oracle
         oracle.build()
         orc = oracle.Oracle(scene)
@@ -723,6 +728,13 @@ def main():
     a = _args()
     if a.impl == "reference":
         run_reference(a)
+    elif a.variant_only:
+        from paper_2303_04086_gb300 import build
+        build.build()
+        out = run_variant(steps=max(1, a.steps), warmup=max(1, a.warmup), views=a.views,
+                          precisions=[p for p in a.precisions.split(",") if p],
+                          oracle_pixels=0 if a.no_cpu_baseline else 100_000)
+        print(json.dumps({"variant": out}))
     else:
         run_native(a)
 

@@ -305,6 +305,35 @@ __global__ void k_tables_to_fp16(const float2* __restrict__ src, __half2* __rest
     dst[i] = __floats2half2_rn(src[i].x, src[i].y);
 }
 
+// Unwrapped table: row X + S (Y + S Z) of the S = 2m sided copy holds the
+// canonical row (X mod m) + m ((Y mod m) + m (Z mod m)).
+template <class Row>
+__global__ void k_expand_table(const Row* __restrict__ src, Row* __restrict__ dst, uint32_t m, uint32_t S,
+                               uint64_t n) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t X = (uint32_t)(i % S), Y = (uint32_t)((i / S) % S), Z = (uint32_t)(i / ((uint64_t)S * S));
+    const uint32_t x = X >= m ? X - m : X, y = Y >= m ? Y - m : Y, z = Z >= m ? Z - m : Z;
+    dst[i] = src[x + (uint64_t)m * (y + (uint64_t)m * z)];
+  }
+}
+
+namespace inolf {
+inolf_status expand_level_table(Object& o, int l, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  const LevelDev& lv = o.lv[l];
+  const uint64_t n = (uint64_t)lv.S * lv.S * lv.S;
+  if (o.fp16)
+    k_expand_table<__half2><<<1024, 256, 0, st>>>((const __half2*)lv.table, (__half2*)lv.tablex, (uint32_t)lv.m,
+                                                  (uint32_t)lv.S, n);
+  else
+    k_expand_table<float2><<<1024, 256, 0, st>>>((const float2*)lv.table, (float2*)lv.tablex, (uint32_t)lv.m,
+                                                 (uint32_t)lv.S, n);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(INOLF_E_CUDA, std::string("k_expand_table: ") + cudaGetErrorString(e));
+  return INOLF_OK;
+}
+}  // namespace inolf
+
 extern "C" inolf_status inolf_object_load_params(inolf_object* obj, const float* const* tables_dev,
                                                  const float* w1_dev, const float* w2_dev, const float* w3_dev,
                                                  void* stream) {
@@ -324,6 +353,8 @@ extern "C" inolf_status inolf_object_load_params(inolf_object* obj, const float*
                  cudaSuccess) {
         return fail(INOLF_E_CUDA, "load_params: table copy failed");
       }
+      inolf_status es = inolf::expand_level_table(o, l, stream);
+      if (es != INOLF_OK) return es;
     }
   }
   if (w1_dev) {

@@ -427,7 +427,9 @@ static void destroy_object(Object& o) {
   auto f = [](void* p) { if (p) cudaFree(p); };
   f(o.nodes); f(o.tris); f(o.w_f32); f(o.w_bf16); f(o.w_fp8);
   f((void*)o.cub.grid); f((void*)o.cub.dens); f((void*)o.cub.diff); f((void*)o.cub.fdist); f((void*)o.cub.bdist);
-  for (int l = 0; l < o.L; ++l) { f((void*)o.lv[l].phi); f((void*)o.lv[l].table); }
+  for (int l = 0; l < o.L; ++l) {
+    f((void*)o.lv[l].phi); f((void*)o.lv[l].table); f((void*)o.lv[l].phix); f((void*)o.lv[l].tablex);
+  }
   o = Object();
 }
 
@@ -610,6 +612,10 @@ extern "C" inolf_status inolf_object_create(const inolf_object_desc* desc, void*
     if (!h || !h->phi || (h->n > 0 && (!h->slot_of || !D.features[l])) || h->m < 1 || h->m > 1024 || h->r < 1 ||
         D.resolution[l] < 1 || D.resolution[l] > (1 << 20))
       return fail(INOLF_E_INVALID, "inolf_object_create: bad hash / features of level " + std::to_string(l));
+    if (h->m > kMaxUnwrappedM)
+      return fail(INOLF_E_UNSUPPORTED, "inolf_object_create: hash-table side m = " + std::to_string(h->m) +
+                                           " of level " + std::to_string(l) + " exceeds " +
+                                           std::to_string(kMaxUnwrappedM) + " (unwrapped tables are 2m per side)");
   }
   inolf_object* obj = new (std::nothrow) inolf_object();
   if (!obj) return fail(INOLF_E_OOM, "inolf_object_create: oom");
@@ -746,8 +752,34 @@ extern "C" inolf_status inolf_object_create(const inolf_object_desc* desc, void*
     CUDA_TRY(cudaMalloc(&dt, table.size()));
     lv.table = dt;
     CUDA_TRY(cudaMemcpyAsync(dt, table.data(), table.size(), cudaMemcpyHostToDevice, st));
-    CUDA_TRY(cudaStreamSynchronize(st));
     o.bytes += sizeof(uint32_t) * R3 + table.size();
+    // unwrapped copies for the shade kernels: Phi of side r + 1 with offsets
+    // linearised in the 2m-sided table, and the table itself expanded on the device
+    lv.S = 2 * lv.m;
+    lv.R = lv.r + 1;
+    {
+      const int64_t R = lv.R, r = lv.r, S = lv.S;
+      std::vector<uint32_t> px((size_t)(R * R * R));
+      for (int64_t c = 0; c < R; ++c)
+        for (int64_t b2 = 0; b2 < R; ++b2)
+          for (int64_t a = 0; a < R; ++a) {
+            const uint32_t e = h->phi[(a % r) + r * ((b2 % r) + r * (c % r))];
+            const uint32_t fx = e & 1023u, fy = (e >> 10) & 1023u, fz = e >> 20;
+            px[(size_t)(a + R * (b2 + R * c))] = (uint32_t)(fx + S * (fy + S * (int64_t)fz));
+          }
+      void* dpx = nullptr;
+      CUDA_TRY(cudaMalloc(&dpx, px.size() * sizeof(uint32_t)));
+      lv.phix = (const uint32_t*)dpx;
+      CUDA_TRY(cudaMemcpyAsync(dpx, px.data(), px.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+      const size_t xbytes = (size_t)S * S * S * row_bytes;
+      void* dtx = nullptr;
+      CUDA_TRY(cudaMalloc(&dtx, xbytes));
+      lv.tablex = dtx;
+      o.bytes += px.size() * sizeof(uint32_t) + xbytes;
+      inolf_status es = expand_level_table(o, l, stream);
+      if (es != INOLF_OK) { destroy_object(o); delete obj; return es; }
+      CUDA_TRY(cudaStreamSynchronize(st));
+    }
   }
 
   inolf_status ws = upload_weights(o, D.w1, D.w2, D.w3, stream);

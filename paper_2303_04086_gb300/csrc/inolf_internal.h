@@ -25,7 +25,19 @@ struct LevelDev {
   float inv_r;            // 1/r rounded to FP32
   const uint32_t* phi;    // r^3 packed offsets
   const void* table;      // m^3 rows of F=2 features: float2 (FP32) or __half2 (FP16)
+  // Unwrapped copies used by the shade kernels: the table repeated to side
+  // S = 2m (row X + S (Y + S Z) holds slot (X mod m, Y mod m, Z mod m)) and
+  // Phi repeated to side R = r + 1 with each offset stored linearised in the
+  // S-sided table, so corner c + d of a cell reads Phi at h1(c) + d and its
+  // features at h0(c) + d + phi without any wrap-around.
+  const uint32_t* phix;   // R^3 linear offsets phi_x + S (phi_y + S phi_z)
+  const void* tablex;     // S^3 rows, same row type as `table`
+  int32_t S, R;
 };
+
+// Largest hash-table side the unwrapped layout supports: (2m)^3 rows must be
+// indexable with 32 bits.
+static constexpr int32_t kMaxUnwrappedM = 812;
 
 // Density and diffuse texture cubes as the kernels see them (Sec. 4.2).
 // grid[x + b (y + b z)] of a base cell is its cube's index, or -1 when no
@@ -117,6 +129,9 @@ size_t workspace_bytes(int64_t n_rays);
 // all weight formats (host.cpp); both reuse existing device buffers.
 inolf_status prepare_tc_weights(Object& obj, const float* w1, const float* w2, const float* w3, void* stream);
 inolf_status upload_weights(Object& obj, const float* w1, const float* w2, const float* w3, void* stream);
+
+// Fills level l's unwrapped table from its canonical table (backward.cu).
+inolf_status expand_level_table(Object& o, int l, void* stream);
 
 // Backward over explicit rays (render.cu + backward.cu).
 inolf_status launch_backward_rays(const Object& obj, const float* o, const float* d, int64_t n, const float* d_rgba,

@@ -415,6 +415,64 @@ __device__ __forceinline__ void finish_level(const LevelDev& lv, int fp16, const
   e1 = fmaf(f[2], by1 - by0, by0);
 }
 
+// The same two halves of Eq. 1 on the unwrapped copies (see LevelDev): the
+// corner c + d of the cell reads Phi at h1(c) + d (no wrap, Phi is repeated to
+// side r + 1) and its features at h0(c) + d + phi in the table repeated to
+// side 2m, where phi is stored linearised -- one add per corner between the
+// two dependent loads.  The features are those of the canonical slots.
+struct LevelFetchX {
+  uint32_t ph[8];
+  uint32_t base;  // h0(c) linearised in the 2m-sided table
+  float f[3];
+};
+
+__device__ __forceinline__ void fetch_phi_x(const LevelDev& lv, const float x[3], LevelFetchX& s) {
+  int32_t c[3];
+  cell_of(lv, x, c, s.f);
+  const uint32_t S = (uint32_t)lv.S, R = (uint32_t)lv.R;
+  s.base = (uint32_t)mod_small(c[0], lv.m, lv.inv_m) +
+           S * ((uint32_t)mod_small(c[1], lv.m, lv.inv_m) + S * (uint32_t)mod_small(c[2], lv.m, lv.inv_m));
+  const uint32_t q = (uint32_t)mod_small(c[0], lv.r, lv.inv_r) +
+                     R * ((uint32_t)mod_small(c[1], lv.r, lv.inv_r) + R * (uint32_t)mod_small(c[2], lv.r, lv.inv_r));
+  const uint32_t* ph = lv.phix + q;
+  const uint32_t R2 = R * R;
+  s.ph[0] = __ldg(ph);
+  s.ph[1] = __ldg(ph + 1);
+  s.ph[2] = __ldg(ph + R);
+  s.ph[3] = __ldg(ph + R + 1);
+  s.ph[4] = __ldg(ph + R2);
+  s.ph[5] = __ldg(ph + R2 + 1);
+  s.ph[6] = __ldg(ph + R2 + R);
+  s.ph[7] = __ldg(ph + R2 + R + 1);
+}
+
+__device__ __forceinline__ void finish_level_x(const LevelDev& lv, int fp16, const LevelFetchX& s, float& e0,
+                                               float& e1) {
+  const uint32_t S = (uint32_t)lv.S, S2 = S * S;
+  const uint32_t off[8] = {0u, 1u, S, S + 1u, S2, S2 + 1u, S2 + S, S2 + S + 1u};
+  float2 v[8];
+  if (fp16) {
+    const __half2* tb = reinterpret_cast<const __half2*>(lv.tablex) + s.base;
+#pragma unroll
+    for (int cc = 0; cc < 8; ++cc) v[cc] = __half22float2(__ldg(tb + (off[cc] + s.ph[cc])));
+  } else {
+    const float2* tb = reinterpret_cast<const float2*>(lv.tablex) + s.base;
+#pragma unroll
+    for (int cc = 0; cc < 8; ++cc) v[cc] = __ldg(tb + (off[cc] + s.ph[cc]));
+  }
+  const float* f = s.f;
+  float ax[4], bx[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    ax[k] = fmaf(f[0], v[2 * k + 1].x - v[2 * k].x, v[2 * k].x);
+    bx[k] = fmaf(f[0], v[2 * k + 1].y - v[2 * k].y, v[2 * k].y);
+  }
+  const float ay0 = fmaf(f[1], ax[1] - ax[0], ax[0]), ay1 = fmaf(f[1], ax[3] - ax[2], ax[2]);
+  const float by0 = fmaf(f[1], bx[1] - bx[0], bx[0]), by1 = fmaf(f[1], bx[3] - bx[2], bx[2]);
+  e0 = fmaf(f[2], ay1 - ay0, ay0);
+  e1 = fmaf(f[2], by1 - by0, by0);
+}
+
 // Eq. 1 slots of the 8 corners and the interpolated features of one level.
 __device__ __forceinline__ void encode_level(const LevelDev& lv, int fp16, const float x[3], uint32_t slots[8],
                                              float& e0, float& e1) {

@@ -94,17 +94,16 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_shade_tc(const __grid_constan
       ray_of(p, ray, o, d);
       hit_unit_coords(p, o, d, __uint_as_float(rec.y), x);
       // levels in pairs: Phi loads of the next level in flight, no state copies
-      LevelFetch fa, fb;
-      fetch_phi(p.lv[0], x, fa);
+      LevelFetchX fa, fb;
+      fetch_phi_x(p.lv[0], x, fa);
       for (int l = 0; l < p.L; l += 2) {
-        uint32_t slots[8];
         float e0, e1;
-        if (l + 1 < p.L) fetch_phi(p.lv[l + 1], x, fb);
-        finish_level(p.lv[l], p.fp16, fa, slots, e0, e1);
+        if (l + 1 < p.L) fetch_phi_x(p.lv[l + 1], x, fb);
+        finish_level_x(p.lv[l], p.fp16, fa, e0, e1);
         store_pair<kFP8>(A, row, 2u * l, chunks1, e0, e1, inv_sx);
         if (l + 1 >= p.L) break;
-        if (l + 2 < p.L) fetch_phi(p.lv[l + 2], x, fa);
-        finish_level(p.lv[l + 1], p.fp16, fb, slots, e0, e1);
+        if (l + 2 < p.L) fetch_phi_x(p.lv[l + 2], x, fa);
+        finish_level_x(p.lv[l + 1], p.fp16, fb, e0, e1);
         store_pair<kFP8>(A, row, 2u * (l + 1), chunks1, e0, e1, inv_sx);
       }
       float sh[16];

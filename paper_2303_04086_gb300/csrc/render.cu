@@ -339,18 +339,17 @@ __global__ void __launch_bounds__(kF32Threads, 3) k_shade_f32_tiled(const __grid
       ray_of(p, ray, o, d);
       hit_unit_coords(p, o, d, __uint_as_float(rec.y), x);
       // levels half, half + 2, ... with the next level's Phi loads in flight
-      LevelFetch fa, fb;
-      if (half < p.L) fetch_phi(p.lv[half], x, fa);
+      LevelFetchX fa, fb;
+      if (half < p.L) fetch_phi_x(p.lv[half], x, fa);
       for (int l = half; l < p.L; l += 4) {  // levels half, half + 2, ... in pairs, no state copies
-        uint32_t slots[8];
         float e0, e1;
-        if (l + 2 < p.L) fetch_phi(p.lv[l + 2], x, fb);
-        finish_level(p.lv[l], p.fp16, fa, slots, e0, e1);
+        if (l + 2 < p.L) fetch_phi_x(p.lv[l + 2], x, fb);
+        finish_level_x(p.lv[l], p.fp16, fa, e0, e1);
         act[(2 * l) * kF32Tile + ray_slot] = e0;
         act[(2 * l + 1) * kF32Tile + ray_slot] = e1;
         if (l + 2 >= p.L) break;
-        if (l + 4 < p.L) fetch_phi(p.lv[l + 4], x, fa);
-        finish_level(p.lv[l + 2], p.fp16, fb, slots, e0, e1);
+        if (l + 4 < p.L) fetch_phi_x(p.lv[l + 4], x, fa);
+        finish_level_x(p.lv[l + 2], p.fp16, fb, e0, e1);
         act[(2 * (l + 2)) * kF32Tile + ray_slot] = e0;
         act[(2 * (l + 2) + 1) * kF32Tile + ray_slot] = e1;
       }
