@@ -612,6 +612,9 @@ extern "C" inolf_status inolf_object_create(const inolf_object_desc* desc, void*
     if (!h || !h->phi || (h->n > 0 && (!h->slot_of || !D.features[l])) || h->m < 1 || h->m > 1024 || h->r < 1 ||
         D.resolution[l] < 1 || D.resolution[l] > (1 << 20))
       return fail(INOLF_E_INVALID, "inolf_object_create: bad hash / features of level " + std::to_string(l));
+    if (h->r >= 2048)
+      return fail(INOLF_E_UNSUPPORTED, "inolf_object_create: offset-table side r = " + std::to_string(h->r) +
+                                           " of level " + std::to_string(l) + " exceeds 2047");
     if (h->m > kMaxUnwrappedM)
       return fail(INOLF_E_UNSUPPORTED, "inolf_object_create: hash-table side m = " + std::to_string(h->m) +
                                            " of level " + std::to_string(l) + " exceeds " +
@@ -726,8 +729,9 @@ extern "C" inolf_status inolf_object_create(const inolf_object_desc* desc, void*
     lv.m = h->m;
     lv.r = h->r;
     lv.N_f = (float)lv.N;
-    lv.inv_m = 1.0f / (float)lv.m;
-    lv.inv_r = 1.0f / (float)lv.r;
+    auto magic = [](int64_t d) { return (uint32_t)std::min<uint64_t>(0xFFFFFFFFull, ((1ull << 32) + d - 1) / d); };
+    lv.magic_m = magic(lv.m);
+    lv.magic_r = magic(lv.r);
     const int64_t R3 = (int64_t)h->r * h->r * h->r;
     const int64_t M3 = (int64_t)h->m * h->m * h->m;
     o.rows[l] = M3;

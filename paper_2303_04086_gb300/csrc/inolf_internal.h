@@ -21,8 +21,8 @@ struct LevelDev {
   int32_t m;              // hash-table side
   int32_t r;              // offset-table side
   float N_f;              // (float)N
-  float inv_m;            // 1/m rounded to FP32 (fast exact modulo, see kernels)
-  float inv_r;            // 1/r rounded to FP32
+  uint32_t magic_m;       // ceil(2^32 / m) (2^32 - 1 for m = 1): a mod m by one high multiply
+  uint32_t magic_r;       // the same for r
   const uint32_t* phi;    // r^3 packed offsets
   const void* table;      // m^3 rows of F=2 features: float2 (FP32) or __half2 (FP16)
   // Unwrapped copies used by the shade kernels: the table repeated to side

@@ -315,14 +315,16 @@ __device__ __forceinline__ void hit_unit_coords(const Params& p, const float o[3
   hit_unit_coords_ls(p.lo, p.scale, o, d, t, x);
 }
 
-// a mod m for 0 <= a < 2^21 and m <= 2^10, with a float quotient estimate
-// (error < 0.25) corrected once in each direction.
-__device__ __forceinline__ int32_t mod_small(int32_t a, int32_t m, float inv_m) {
-  const int32_t q = __float2int_rz(__int2float_rn(a) * inv_m);
-  int32_t r = a - q * m;
-  r += (r < 0) ? m : 0;
-  r -= (r >= m) ? m : 0;
-  return r;
+// a mod m for 0 <= a < 2^21 and 1 <= m < 2048 by division by an invariant
+// integer (Granlund and Montgomery 1994): with magic = ceil(2^32 / m), the
+// high word of a * magic is floor(a/m + e), 0 <= e < a / 2^32 < 2^-11, and a/m
+// is never within 2^-11 below an integer when m < 2048, so the quotient is
+// exact; the one correction covers m = 1, whose magic is clamped to 2^32 - 1.
+__device__ __forceinline__ int32_t mod_small(int32_t a, int32_t m, uint32_t magic) {
+  const uint32_t q = __umulhi((uint32_t)a, magic);
+  uint32_t r = (uint32_t)a - q * (uint32_t)m;
+  r -= (r >= (uint32_t)m) ? (uint32_t)m : 0u;
+  return (int32_t)r;
 }
 
 // Cell of level `lv` (Sec. 4.1, p = floor(N x)): c = clamp(floor(u), 0, N-1),
@@ -355,17 +357,17 @@ __device__ __forceinline__ void fetch_phi(const LevelDev& lv, const float x[3], 
   int32_t qx[2], qy[2], qz[2];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    s.h0[k] = mod_small(c[k], m, lv.inv_m);
+    s.h0[k] = mod_small(c[k], m, lv.magic_m);
     s.h0n[k] = s.h0[k] + 1 == m ? 0 : s.h0[k] + 1;
   }
   {
-    const int32_t a = mod_small(c[0], r, lv.inv_r);
+    const int32_t a = mod_small(c[0], r, lv.magic_r);
     qx[0] = a;
     qx[1] = a + 1 == r ? 0 : a + 1;
-    const int32_t b = mod_small(c[1], r, lv.inv_r);
+    const int32_t b = mod_small(c[1], r, lv.magic_r);
     qy[0] = b * r;
     qy[1] = (b + 1 == r ? 0 : b + 1) * r;
-    const int32_t z = mod_small(c[2], r, lv.inv_r);
+    const int32_t z = mod_small(c[2], r, lv.magic_r);
     qz[0] = z * r * r;
     qz[1] = (z + 1 == r ? 0 : z + 1) * r * r;
   }
@@ -430,10 +432,10 @@ __device__ __forceinline__ void fetch_phi_x(const LevelDev& lv, const float x[3]
   int32_t c[3];
   cell_of(lv, x, c, s.f);
   const uint32_t S = (uint32_t)lv.S, R = (uint32_t)lv.R;
-  s.base = (uint32_t)mod_small(c[0], lv.m, lv.inv_m) +
-           S * ((uint32_t)mod_small(c[1], lv.m, lv.inv_m) + S * (uint32_t)mod_small(c[2], lv.m, lv.inv_m));
-  const uint32_t q = (uint32_t)mod_small(c[0], lv.r, lv.inv_r) +
-                     R * ((uint32_t)mod_small(c[1], lv.r, lv.inv_r) + R * (uint32_t)mod_small(c[2], lv.r, lv.inv_r));
+  s.base = (uint32_t)mod_small(c[0], lv.m, lv.magic_m) +
+           S * ((uint32_t)mod_small(c[1], lv.m, lv.magic_m) + S * (uint32_t)mod_small(c[2], lv.m, lv.magic_m));
+  const uint32_t q = (uint32_t)mod_small(c[0], lv.r, lv.magic_r) +
+                     R * ((uint32_t)mod_small(c[1], lv.r, lv.magic_r) + R * (uint32_t)mod_small(c[2], lv.r, lv.magic_r));
   const uint32_t* ph = lv.phix + q;
   const uint32_t R2 = R * R;
   s.ph[0] = __ldg(ph);

@@ -94,28 +94,25 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_shade_tc(const __grid_constan
       ray_of(p, ray, o, d);
       hit_unit_coords(p, o, d, __uint_as_float(rec.y), x);
       // levels in pairs: Phi loads of the next level in flight, no state copies
+      RowWriter<kFP8> rw(A, row, chunks1, inv_sx);
       LevelFetchX fa, fb;
       fetch_phi_x(p.lv[0], x, fa);
       for (int l = 0; l < p.L; l += 2) {
         float e0, e1;
         if (l + 1 < p.L) fetch_phi_x(p.lv[l + 1], x, fb);
         finish_level_x(p.lv[l], p.fp16, fa, e0, e1);
-        store_pair<kFP8>(A, row, 2u * l, chunks1, e0, e1, inv_sx);
+        rw.push(e0, e1);
         if (l + 1 >= p.L) break;
         if (l + 2 < p.L) fetch_phi_x(p.lv[l + 2], x, fa);
         finish_level_x(p.lv[l + 1], p.fp16, fb, e0, e1);
-        store_pair<kFP8>(A, row, 2u * (l + 1), chunks1, e0, e1, inv_sx);
+        rw.push(e0, e1);
       }
       float sh[16];
       sh16(p, d, sh);
 #pragma unroll
-      for (int i = 0; i < 8; ++i) store_pair<kFP8>(A, row, 2u * p.L + 2u * i, chunks1, sh[2 * i], sh[2 * i + 1], inv_sx);
-      uint32_t k0 = 2u * p.L + 16u;
-      if (p.variant) {  // alpha_c, the last input of F_s (Eq. 5), then zero padding
-        store_pair<kFP8>(A, row, k0, chunks1, p.hit_alpha[h], 0.f, inv_sx);
-        k0 += 2u;
-      }
-      for (uint32_t k = k0; k < K1; k += 2) store_pair<kFP8>(A, row, k, chunks1, 0.f, 0.f, 1.f);
+      for (int i = 0; i < 8; ++i) rw.push(sh[2 * i], sh[2 * i + 1]);
+      if (p.variant) rw.push(p.hit_alpha[h], 0.f);  // alpha_c, the last input of F_s (Eq. 5)
+      rw.pad_to(K1);
     } else {
       for (uint32_t c = 0; c < chunks1; ++c)
         *reinterpret_cast<uint4*>(A + tc::core_off(row, c, chunks1)) = make_uint4(0, 0, 0, 0);
@@ -154,7 +151,7 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_shade_tc(const __grid_constan
 static uint32_t round_up(uint32_t v, uint32_t m) { return (v + m - 1) / m * m; }
 
 // Weight blob in the operand layout (K-major core matrices, rows = output
-// neurons): [W1: 64 x K1][W2: 64 x 64][W3: 4 x 64 FP32 of the quantised values]
+// neurons): [W1: 64 x K1][W2: 64 x 64][W3^T: 64 x 4 FP32 of the quantised values]
 inolf_status prepare_tc_weights(Object& obj, const float* w1, const float* w2, const float* w3, void* stream) {
   const int din = obj.d_in, H = INOLF_HIDDEN, O = INOLF_OUT;
   cudaStream_t st = (cudaStream_t)stream;
@@ -178,8 +175,9 @@ inolf_status prepare_tc_weights(Object& obj, const float* w1, const float* w2, c
         __nv_bfloat16 v = __float2bfloat16_rn(w2[(size_t)n * H + k]);
         std::memcpy(&b2[tc::core_off(n, k / 8, ch2) + (k % 8) * 2], &v, 2);
       }
-    float* b3 = reinterpret_cast<float*>(b2 + (size_t)H * H * 2);
-    for (int i = 0; i < O * H; ++i) b3[i] = __bfloat162float(__float2bfloat16_rn(w3[i]));
+    float* b3 = reinterpret_cast<float*>(b2 + (size_t)H * H * 2);  // W3^T [64][4]
+    for (int o = 0; o < O; ++o)
+      for (int j = 0; j < H; ++j) b3[j * O + o] = __bfloat162float(__float2bfloat16_rn(w3[o * H + j]));
     if (!obj.w_bf16) {
       if (cudaMalloc(&obj.w_bf16, blob.size()) != cudaSuccess) return fail(INOLF_E_OOM, "cudaMalloc bf16 weights");
       obj.bytes += blob.size();
@@ -209,8 +207,9 @@ inolf_status prepare_tc_weights(Object& obj, const float* w1, const float* w2, c
     uint8_t* b2 = blob.data() + (size_t)H * K1;
     for (int n = 0; n < H; ++n)
       for (int k = 0; k < H; ++k) b2[tc::core_off(n, k / 16, ch2) + (k % 16)] = q(w2[(size_t)n * H + k], obj.fp8_w_scale[1]);
-    float* b3 = reinterpret_cast<float*>(b2 + (size_t)H * H);
-    for (int i = 0; i < O * H; ++i) b3[i] = dq(q(w3[i], obj.fp8_w_scale[2])) * obj.fp8_w_scale[2];
+    float* b3 = reinterpret_cast<float*>(b2 + (size_t)H * H);  // W3^T [64][4]
+    for (int o = 0; o < O; ++o)
+      for (int j = 0; j < H; ++j) b3[j * O + o] = dq(q(w3[o * H + j], obj.fp8_w_scale[2])) * obj.fp8_w_scale[2];
     if (!obj.w_fp8) {
       if (cudaMalloc(&obj.w_fp8, blob.size()) != cudaSuccess) return fail(INOLF_E_OOM, "cudaMalloc fp8 weights");
       obj.bytes += blob.size();

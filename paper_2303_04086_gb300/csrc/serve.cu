@@ -380,12 +380,16 @@ __global__ void __launch_bounds__(kServeThreads, 2) k_serve(const __grid_constan
           for (int a = 0; a < 3; ++a) ol[a] = __fsub_rn(o[a], ob.T[a]);
           hit_unit_coords_ls(ob.lo, ob.scale, ol, d, ht[q], x3);
           float x[kServeMaxDin];
-          for (int l = 0; l < ob.L; ++l) {
-            uint32_t slots[8];
-            float e0, e1;
-            encode_level(ob.lv[l], ob.fp16, x3, slots, e0, e1);
-            x[2 * l] = e0;
-            x[2 * l + 1] = e1;
+          {
+            LevelFetchX fa, fb;
+            fetch_phi_x(ob.lv[0], x3, fa);
+            for (int l = 0; l < ob.L; l += 2) {  // levels in pairs, the next level's Phi loads in flight
+              if (l + 1 < ob.L) fetch_phi_x(ob.lv[l + 1], x3, fb);
+              finish_level_x(ob.lv[l], ob.fp16, fa, x[2 * l], x[2 * l + 1]);
+              if (l + 1 >= ob.L) break;
+              if (l + 2 < ob.L) fetch_phi_x(ob.lv[l + 2], x3, fa);
+              finish_level_x(ob.lv[l + 1], ob.fp16, fb, x[2 * l + 2], x[2 * l + 3]);
+            }
           }
           sh16c(kp.shc, d, x + 2 * ob.L);
           s_rgba[tid * kServeMaxK + q] = mlp_f32(sWf, sWf + din * 16, sWf + din * 16 + 64 * 16, x, din);
@@ -419,11 +423,19 @@ __global__ void __launch_bounds__(kServeThreads, 2) k_serve(const __grid_constan
 #pragma unroll
             for (int a = 0; a < 3; ++a) ol[a] = __fsub_rn(po[a], ob.T[a]);
             hit_unit_coords_ls(ob.lo, ob.scale, ol, pd, th, x3);
-            for (int l = 0; l < ob.L; ++l) {
-              uint32_t slots[8];
-              float e0, e1;
-              encode_level(ob.lv[l], ob.fp16, x3, slots, e0, e1);
-              store_pair<false>(A, row, 2u * l, chunks1, e0, e1, 1.f);
+            {
+              LevelFetchX fa, fb;
+              fetch_phi_x(ob.lv[0], x3, fa);
+              for (int l = 0; l < ob.L; l += 2) {  // levels in pairs, the next level's Phi loads in flight
+                float e0, e1;
+                if (l + 1 < ob.L) fetch_phi_x(ob.lv[l + 1], x3, fb);
+                finish_level_x(ob.lv[l], ob.fp16, fa, e0, e1);
+                store_pair<false>(A, row, 2u * l, chunks1, e0, e1, 1.f);
+                if (l + 1 >= ob.L) break;
+                if (l + 2 < ob.L) fetch_phi_x(ob.lv[l + 2], x3, fa);
+                finish_level_x(ob.lv[l + 1], ob.fp16, fb, e0, e1);
+                store_pair<false>(A, row, 2u * (l + 1), chunks1, e0, e1, 1.f);
+              }
             }
             float sh[16];
             sh16c(kp.shc, pd, sh);

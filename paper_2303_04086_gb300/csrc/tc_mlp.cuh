@@ -1,6 +1,7 @@
 // Layers 1-3 of the MLP F_s on the tensor cores for 2 x 128 rows whose A1
 // operand rows are already in shared memory (shared by the render and serve
 // kernels).  256 threads; thread tid owns row tid & 127 of tile tid >> 7.
+// sW3 holds W3^T [64][4] (FP32 of the quantised weights), 16-byte aligned.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -40,6 +41,44 @@ __device__ __forceinline__ void store_pair(uint8_t* A, uint32_t row, uint32_t k,
   }
 }
 
+// Writes one row of an A operand tile as consecutive column pairs from column
+// 0 on, storing each 16-byte chunk (8 BF16 or 16 FP8 values) when it is
+// complete: one 16-byte store per chunk instead of one store per pair, and a
+// warp's stores fill whole core matrices (no shared-memory bank conflicts).
+template <bool kFP8>
+struct RowWriter {
+  uint8_t* A;
+  uint32_t row, chunks, n;  // n = pairs pushed so far
+  uint32_t w0, w1, w2, w3;
+  float inv_s;
+
+  __device__ __forceinline__ RowWriter(uint8_t* A_, uint32_t row_, uint32_t chunks_, float inv_s_)
+      : A(A_), row(row_), chunks(chunks_), n(0), w0(0), w1(0), w2(0), w3(0), inv_s(inv_s_) {}
+
+  __device__ __forceinline__ void push(float a, float b) {
+    if (kFP8) {  // 2-byte pairs shift through the 16-byte chunk
+      const uint32_t v = pack_fp8(a * inv_s, b * inv_s);
+      w0 = (w0 >> 16) | (w1 << 16);
+      w1 = (w1 >> 16) | (w2 << 16);
+      w2 = (w2 >> 16) | (w3 << 16);
+      w3 = (w3 >> 16) | (v << 16);
+      if ((++n & 7u) == 0) flush((n >> 3) - 1u);
+    } else {
+      w0 = w1;
+      w1 = w2;
+      w2 = w3;
+      w3 = pack_bf16(a, b);
+      if ((++n & 3u) == 0) flush((n >> 2) - 1u);
+    }
+  }
+  __device__ __forceinline__ void flush(uint32_t c) {
+    *reinterpret_cast<uint4*>(A + tc::core_off(row, c, chunks)) = make_uint4(w0, w1, w2, w3);
+  }
+  // zero pairs up to column K (a multiple of the chunk width)
+  __device__ __forceinline__ void pad_to(uint32_t K) {
+    while (2u * n < K) push(0.f, 0.f);
+  }
+};
 
 // Precision-dependent scales (FP8: per-tensor, amax / 448; BF16: unit).
 struct TcScales {
@@ -149,11 +188,11 @@ __device__ __forceinline__ bool tc_mlp_run(uint8_t* sA, const uint8_t* sB1, cons
     for (int j = 0; j < 16; ++j) {
       float a = fmaxf(v[j] * sc.mul2, 0.f);
       a = kFP8 ? round_fp8(a * sc.inv_sh2) * sc.sh2 : round_bf16(a);
-      const uint32_t col = c * 16u + (uint32_t)j;
-      out0 += sW3[0 * 64 + col] * a;
-      out1 += sW3[1 * 64 + col] * a;
-      out2 += sW3[2 * 64 + col] * a;
-      out3 += sW3[3 * 64 + col] * a;
+      const float4 w = reinterpret_cast<const float4*>(sW3)[c * 16u + (uint32_t)j];  // W3^T row
+      out0 += w.x * a;
+      out1 += w.y * a;
+      out2 += w.z * a;
+      out3 += w.w * a;
     }
   }
   out = make_float4(sigmoidf_(out0), sigmoidf_(out1), sigmoidf_(out2), sigmoidf_(out3));
