@@ -577,6 +577,14 @@ static inolf_status check_cubes(const inolf_cubes_desc& C) {
     return fail(INOLF_E_INVALID, "inolf_object_create: bad t_min / alpha_miss");
   for (int64_t i = 0; i < 3 * C.n_cubes; ++i)
     if (C.cells[i] < 0 || C.cells[i] >= C.b) return fail(INOLF_E_INVALID, "inolf_object_create: cube cell out of range");
+  {
+    std::vector<int64_t> lin((size_t)C.n_cubes);
+    for (int64_t i = 0; i < C.n_cubes; ++i)
+      lin[(size_t)i] = C.cells[3 * i] + (int64_t)C.b * (C.cells[3 * i + 1] + (int64_t)C.b * C.cells[3 * i + 2]);
+    std::sort(lin.begin(), lin.end());
+    if (std::adjacent_find(lin.begin(), lin.end()) != lin.end())
+      return fail(INOLF_E_INVALID, "inolf_object_create: cube listed twice");
+  }
   const int64_t nv = (int64_t)(C.r + 1) * (C.r + 1) * (C.r + 1);
   for (int64_t i = 0; i < C.n_cubes * nv; ++i)
     if (!(C.density[i] >= 0) || !std::isfinite(C.density[i]))

@@ -45,3 +45,93 @@ def test_render_rejects_bad_arguments_before_any_launch(lib):
     assert lib.inolf_render_rays(None, None, None, -1, 0, None, None, None, None, 0, None) == inolf.E_INVALID
     assert lib.inolf_object_create(None, None, None) == inolf.E_INVALID
     assert lib.inolf_render_workspace_bytes(1000) >= 8000
+
+
+def _cube_desc_scene():
+    from paper_2303_04086_gb300 import synth
+    return synth.tiny_density_scene(seed=0)
+
+
+def _create_status(scene, mutate_desc=None, mutate_cubes=None):
+    """inolf_object_create on a density-cube description, with one field
+    changed; the argument checks run before any device call."""
+    from paper_2303_04086_gb300 import inolf
+    L = scene.n_levels
+    hashes = [inolf.build_hash(synth_unpack(k), N) for k, N in zip(scene.keys, scene.resolutions)]
+    res = np.ascontiguousarray(scene.resolutions, np.int32)
+    feats = [np.ascontiguousarray(f, np.float32) for f in scene.features]
+    w = [np.ascontiguousarray(a, np.float32) for a in (scene.w1, scene.w2, scene.w3)]
+    hp = (ctypes.POINTER(inolf.HashStruct) * L)(*[h._h for h in hashes])
+    fp = (ctypes.c_void_p * L)(*[f.ctypes.data for f in feats])
+    c = scene.cubes
+    cells = np.ascontiguousarray(c.cells, np.int32)
+    dens = np.ascontiguousarray(c.density, np.float32)
+    diff = np.ascontiguousarray(c.diffuse, np.float32)
+    cd = inolf.CubesDesc()
+    cd.b, cd.r, cd.n_cubes = c.b, c.r, len(cells)
+    cd.cells, cd.density, cd.diffuse = cells.ctypes.data, dens.ctypes.data, diff.ctypes.data
+    cd.side, cd.step, cd.t_min, cd.alpha_miss = c.side, c.step, c.t_min, c.alpha_miss
+    d = inolf.ObjectDesc()
+    d.n_levels, d.n_features = L, 2
+    d.resolution = res.ctypes.data
+    d.hashes = ctypes.cast(hp, ctypes.c_void_p)
+    d.features = ctypes.cast(fp, ctypes.c_void_p)
+    d.w1, d.w2, d.w3 = w[0].ctypes.data, w[1].ctypes.data, w[2].ctypes.data
+    d.domain_lo, d.domain_scale = -1.5, float(np.float32(1 / 3))
+    d.cubes = ctypes.pointer(cd)
+    keep = (cells, dens, diff)
+    if mutate_cubes:
+        keep = keep + (mutate_cubes(cd, cells, dens),)
+    if mutate_desc:
+        mutate_desc(d)
+    out = ctypes.c_void_p()
+    st = inolf.lib().inolf_object_create(ctypes.byref(d), None, ctypes.byref(out))
+    del keep
+    return st
+
+
+def synth_unpack(keys):
+    from paper_2303_04086_gb300 import synth
+    return synth.unpack_keys(keys)
+
+
+@pytest.mark.parametrize("case", ["b_not_pow2", "r_not_pow2", "fine_grid_too_large", "cell_out_of_range",
+                                  "cube_twice", "negative_density", "nan_density", "zero_step", "step_too_small",
+                                  "t_min_zero", "alpha_miss_one", "mesh_given", "null_cells"])
+def test_cube_descriptions_are_checked_on_the_host(lib, case):
+    from paper_2303_04086_gb300 import inolf
+    scene = _cube_desc_scene()
+
+    def cubes(cd, cells, dens):
+        if case == "b_not_pow2":
+            cd.b = 12
+        elif case == "r_not_pow2":
+            cd.r = 6
+        elif case == "fine_grid_too_large":
+            cd.b, cd.r = 512, 16
+        elif case == "cell_out_of_range":
+            cells[0, 1] = cd.b
+        elif case == "cube_twice":
+            cells[1] = cells[0]
+        elif case == "negative_density":
+            dens[3, 5] = -1.0
+        elif case == "nan_density":
+            dens[2, 0] = np.nan
+        elif case == "zero_step":
+            cd.step = 0.0
+        elif case == "step_too_small":
+            cd.step = 1e-6
+        elif case == "t_min_zero":
+            cd.t_min = 0.0
+        elif case == "alpha_miss_one":
+            cd.alpha_miss = 1.0
+        elif case == "null_cells":
+            cd.cells = None
+        return None
+
+    def desc(d):
+        if case == "mesh_given":
+            d.n_vertices, d.n_triangles = 3, 1
+
+    st = _create_status(scene, mutate_desc=desc, mutate_cubes=cubes)
+    assert st == inolf.E_INVALID, (case, st, inolf.last_error())
