@@ -168,10 +168,10 @@ def make_workload(small: bool, views: int):
 
 # DRAM bytes (read + write) per hit ray of the current shade kernels, from one
 # ncu capture of a one-view launch of the full workload (cold L2), see
-# profiles/k_shade_f32_tiled_full_1view.md: 1.294 GB + 0.070 GB for 4 010 637
+# profiles/k_shade_f32_tiled_full_1view.md: 1.313 GB + 0.069 GB for 4 010 637
 # hit rays.  Traffic grows in proportion to the hit rays rendered, so a launch's
 # traffic is this figure times its hit rays.  None once the kernel changes.
-DRAM_BYTES_PER_HIT = {"k_shade_f32": (1.293669e9 + 70.448128e6) / 4010637}
+DRAM_BYTES_PER_HIT = {"k_shade_f32": (1.313405e9 + 68.739072e6) / 4010637}
 
 
 def algorithmic_bytes_per_hit(scene) -> int:
