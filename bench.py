@@ -619,15 +619,18 @@ def run_native(a):
             precisions[prec] = {"unavailable": str(e)}
 
     # end to end through the C ABI with host buffers: the cameras go from
-    # host memory into the launch, the full RGBA frame comes back to pinned
-    # host memory inside the timed region
+    # host memory into the launch, every RGBA frame comes back to pinned host
+    # memory inside the timed region (inolf_render_host: rendering of chunk
+    # c + 1 overlaps the copy of chunk c)
     host_out = torch.empty((nv, H, W, 4), dtype=torch.float32, pin_memory=True)
     host_cams = np.ascontiguousarray(cams, np.float32)
     e2e_steps = max(1, min(a.steps, 3))
+    vpc = 4
+    staging = torch.empty((2 * vpc * H * W * 4,), dtype=torch.float32, device=dev)
 
     def e2e_step():
-        inolf.render(obj, host_cams, W, H, "fp32", rgba_out=rgba, workspace=ws, stream=stream)
-        host_out.copy_(rgba, non_blocking=True)
+        inolf.render_host(obj, host_cams, W, H, "fp32", host_out=host_out, staging=staging, workspace=ws,
+                          stream=stream, views_per_chunk=vpc)
 
     e2e_step()
     torch.cuda.synchronize()
@@ -639,7 +642,7 @@ def run_native(a):
     e2e_s = _max_over_ranks(time.perf_counter() - t_e, world)
     e2e = {"value": n_rays * e2e_steps * world / e2e_s / 1e6, "unit": "Mrays/s",
            "h2d_bytes_per_step": int(host_cams.nbytes), "d2h_bytes_per_step": int(host_out.numel() * 4)}
-    del host_out
+    del host_out, staging
 
     # roofline of the dominant kernel (from CUDA events around each launch)
     top = max(stats, key=lambda k: stats[k]["ms"]) if stats else None

@@ -210,6 +210,22 @@ inolf_status inolf_render(const inolf_object* obj, const float* cams, int32_t n_
                           inolf_precision prec, float* rgba_out, int32_t* tri_out, float* t_out,
                           void* workspace, size_t workspace_bytes, void* stream);
 
+/* Renders n_views pinhole views into HOST memory, overlapping rendering with
+ * the device-to-host copies: views go in chunks into two halves of a caller-
+ * owned device staging buffer on `stream` while a library-owned stream copies
+ * the previous chunk out, so the copies hide behind the rendering (the frames
+ * a render farm hands to its encoder, Sec. 5.1).
+ *   rgba_host  host [n_views][H][W][4] FP32 (pinned memory for overlap; pageable
+ *              memory works but copies synchronously)
+ *   staging    device, 16-byte aligned; each half holds
+ *              floor(staging_bytes / 2 / (W H 16)) >= 1 views
+ *   workspace  as for inolf_render, for one chunk of views
+ * Returns after the last frame is in host memory.  Errors: INOLF_E_INVALID
+ * (including staging smaller than two views), INOLF_E_CUDA. */
+inolf_status inolf_render_host(const inolf_object* obj, const float* cams, int32_t n_views, int32_t W, int32_t H,
+                               inolf_precision prec, float* rgba_host, void* staging, size_t staging_bytes,
+                               void* workspace, size_t workspace_bytes, void* stream);
+
 /* Renders n explicit rays: o, d device [n][3] FP32 (d unit length, object
  * frame).  rgba_out device [n][4]; tri_out / t_out optional [n]. */
 inolf_status inolf_render_rays(const inolf_object* obj, const float* o, const float* d, int64_t n,

@@ -757,3 +757,60 @@ extern "C" inolf_status inolf_march_rays(const inolf_object* obj, const float* o
   return launch_render(obj->o, rb, INOLF_FP32, nullptr, k_out, t_out, nullptr, nullptr, workspace, workspace_bytes,
                        stream, false, alpha_out, true);
 }
+
+extern "C" inolf_status inolf_render_host(const inolf_object* obj, const float* cams, int32_t n_views, int32_t W,
+                                          int32_t H, inolf_precision prec, float* rgba_host, void* staging,
+                                          size_t staging_bytes, void* workspace, size_t workspace_bytes,
+                                          void* stream) {
+  clear_error();
+  if (!obj || !cams || !rgba_host || n_views < 0 || W <= 0 || H <= 0 || !staging || ((uintptr_t)staging & 15))
+    return fail(INOLF_E_INVALID, "inolf_render_host: bad argument");
+  if (n_views == 0) return INOLF_OK;
+  const size_t view_bytes = (size_t)W * H * 4 * sizeof(float);
+  const int64_t slot_views = (int64_t)(staging_bytes / 2 / view_bytes);
+  if (slot_views < 1) return fail(INOLF_E_INVALID, "inolf_render_host: staging holds less than two views");
+  cudaStream_t cs = (cudaStream_t)stream;
+  cudaStream_t xs = nullptr;
+  cudaEvent_t rendered[2] = {nullptr, nullptr}, copied[2] = {nullptr, nullptr};
+  inolf_status st = INOLF_OK;
+  if (cudaStreamCreateWithFlags(&xs, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(INOLF_E_CUDA, "inolf_render_host: cudaStreamCreate failed");
+  for (int k = 0; k < 2 && st == INOLF_OK; ++k)
+    if (cudaEventCreateWithFlags(&rendered[k], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&copied[k], cudaEventDisableTiming) != cudaSuccess)
+      st = fail(INOLF_E_CUDA, "inolf_render_host: cudaEventCreate failed");
+  // chunk c renders into staging slot c & 1 on the caller's stream while the
+  // copy stream moves chunk c - 1 to host memory; a slot is rendered into
+  // again only after its previous copy finished
+  for (int64_t v0 = 0, c = 0; st == INOLF_OK && v0 < n_views; v0 += slot_views, ++c) {
+    const int32_t nv = (int32_t)std::min<int64_t>(slot_views, n_views - v0);
+    const int slot = (int)(c & 1);
+    float* dst = reinterpret_cast<float*>((char*)staging + (size_t)slot * slot_views * view_bytes);
+    if (c >= 2 && cudaStreamWaitEvent(cs, copied[slot], 0) != cudaSuccess) {
+      st = fail(INOLF_E_CUDA, "inolf_render_host: cudaStreamWaitEvent failed");
+      break;
+    }
+    RayBatch rb{};
+    rb.mode = 0;
+    rb.cams = cams + 13 * v0;
+    rb.n_views = nv;
+    rb.W = W;
+    rb.H = H;
+    rb.n = (int64_t)nv * W * H;
+    st = launch_render(obj->o, rb, prec, dst, nullptr, nullptr, nullptr, nullptr, workspace, workspace_bytes, stream);
+    if (st != INOLF_OK) break;
+    if (cudaEventRecord(rendered[slot], cs) != cudaSuccess || cudaStreamWaitEvent(xs, rendered[slot], 0) != cudaSuccess ||
+        cudaMemcpyAsync(rgba_host + (size_t)v0 * W * H * 4, dst, (size_t)nv * view_bytes, cudaMemcpyDeviceToHost, xs) !=
+            cudaSuccess ||
+        cudaEventRecord(copied[slot], xs) != cudaSuccess)
+      st = fail(INOLF_E_CUDA, "inolf_render_host: copy scheduling failed");
+  }
+  const bool synced = cudaStreamSynchronize(xs) == cudaSuccess && cudaStreamSynchronize(cs) == cudaSuccess;
+  if (st == INOLF_OK && !synced) st = fail(INOLF_E_CUDA, "inolf_render_host: synchronisation failed");
+  for (int k = 0; k < 2; ++k) {
+    if (rendered[k]) cudaEventDestroy(rendered[k]);
+    if (copied[k]) cudaEventDestroy(copied[k]);
+  }
+  cudaStreamDestroy(xs);
+  return st;
+}

@@ -91,6 +91,7 @@ def lib():
     L.inolf_render_rays.argtypes = [vp, vp, vp, i64, i32, vp, vp, vp, vp, sz, vp]
     L.inolf_encode_rays.argtypes = [vp, vp, vp, i64, vp, vp, vp, sz, vp]
     L.inolf_march_rays.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp, sz, vp]
+    L.inolf_render_host.argtypes = [vp, vp, i32, i32, i32, i32, vp, vp, sz, vp, sz, vp]
     L.inolf_render_rays_noalloc.argtypes = [vp, vp, vp, i64, i32, vp, vp, vp, vp]
     L.inolf_calibrate_fp8.argtypes = [vp, vp, i32, i32, i32, vp, sz, vp]
     L.inolf_backward.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, sz, vp]
@@ -298,6 +299,27 @@ def render(obj: Object, cams: np.ndarray, W: int, H: int, prec="fp32", rgba_out=
                               _ptr(t_out), _ptr(workspace), workspace.numel() * workspace.element_size(),
                               _stream(stream)))
     return rgba_out
+
+
+def render_host(obj: Object, cams: np.ndarray, W: int, H: int, prec="fp32", host_out=None, staging=None,
+                workspace=None, stream=None, views_per_chunk: int = 4):
+    """inolf_render_host: render pinhole views into host memory (host_out: a
+    pinned CPU float32 tensor [n_views, H, W, 4], allocated when None) with the
+    device-to-host copies overlapped with rendering.  Returns host_out."""
+    import torch
+    cams = np.ascontiguousarray(cams, np.float32).reshape(-1, 13)
+    nv = len(cams)
+    if host_out is None:
+        host_out = torch.empty((nv, H, W, 4), dtype=torch.float32, pin_memory=True)
+    if staging is None:
+        staging = torch.empty((2 * max(1, views_per_chunk) * H * W * 4,), dtype=torch.float32, device="cuda")
+    if workspace is None:
+        workspace = _workspace(max(1, views_per_chunk) * W * H, staging.device)
+    p = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+    _check(lib().inolf_render_host(obj.handle, cams.ctypes.data, nv, W, H, p, _ptr(host_out), _ptr(staging),
+                                   staging.numel() * staging.element_size(), _ptr(workspace),
+                                   workspace.numel() * workspace.element_size(), _stream(stream)))
+    return host_out
 
 
 def render_rays(obj: Object, o, d, prec="fp32", rgba_out=None, tri_out=None, t_out=None, workspace=None,

@@ -149,3 +149,29 @@ def test_empty_batches(torch_cuda, tiny_obj):
     assert out.shape == (0, 4)
     with pytest.raises(inolf.InolfError):
         inolf.render(tiny_obj, np.zeros((1, 13), np.float32), 0, 4)
+
+
+@pytest.mark.parametrize("views_per_chunk,pinned", [(2, True), (1, True), (3, False)])
+def test_render_host_equals_device_render(torch_cuda, tiny, tiny_obj, views_per_chunk, pinned):
+    # frames rendered into host memory through the two staging halves (the
+    # copies of chunk c overlap the rendering of chunk c + 1) are the device
+    # render's, bit for bit; 7 views force slot reuse
+    import torch
+    from paper_2303_04086_gb300 import inolf
+    cams = synth.ring_cameras(7, 2.8)
+    W, H = 37, 23
+    dev = inolf.render(tiny_obj, cams, W, H).cpu().numpy()
+    host = torch.empty((7, H, W, 4), dtype=torch.float32, pin_memory=pinned)
+    staging = torch.empty((2 * views_per_chunk * H * W * 4,), dtype=torch.float32, device="cuda")
+    out = inolf.render_host(tiny_obj, cams, W, H, "fp32", host_out=host, staging=staging)
+    assert np.array_equal(out.numpy(), dev)
+
+
+def test_render_host_rejects_small_staging(torch_cuda, tiny, tiny_obj):
+    import torch
+    from paper_2303_04086_gb300 import inolf
+    cams = synth.ring_cameras(2, 2.8)
+    staging = torch.empty((37 * 23 * 4,), dtype=torch.float32, device="cuda")  # one view, not two
+    with pytest.raises(inolf.InolfError) as e:
+        inolf.render_host(tiny_obj, cams, 37, 23, "fp32", staging=staging)
+    assert e.value.status == inolf.E_INVALID
