@@ -301,6 +301,100 @@ __device__ __forceinline__ void closest_hit(const Params& p, const float o[3], c
   closest_hit_bvh(p.nodes, p.tris, p.counter + 1, o, d, best_id, best_t);
 }
 
+// Closest hit for the 32 rays of a warp traversed together (packet
+// traversal): the warp visits a node when any of its rays enters the node's
+// box within its own current best distance, every ray tests every triangle
+// of a visited leaf (warp-uniform loads), and a stacked subtree is skipped
+// only when no ray still wants it.  Each ray's result is the lexicographic
+// (t, id) minimum over the triangles it tested, which include every
+// triangle it can hit (its boxes are never rejected), so the result equals
+// the per-ray traversal's.  All control flow depends on warp votes only, so
+// the warp stays converged; lanes without a ray pass active = false.  Must
+// be called by all 32 lanes of the warp.
+__device__ __forceinline__ void closest_hit_packet(const float4* __restrict__ nodes, const float4* __restrict__ tris,
+                                                   uint32_t* err, bool active, const float o[3], const float d[3],
+                                                   int32_t& best_id, float& best_t) {
+  float inv[3], oi[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float dk = fabsf(d[k]) < 1e-20f ? copysignf(1e-20f, d[k]) : d[k];
+    inv[k] = 1.0f / dk;
+    oi[k] = o[k] * inv[k];
+  }
+  best_id = -1;
+  best_t = INFINITY;
+  int32_t st_idx[kStackDepth];  // the same in every lane
+  int32_t st_cnt[kStackDepth];
+  float st_t[kStackDepth];      // this lane's entry distance (INFINITY: not wanted)
+  int sp = 0;
+  int32_t cur = 0, cur_cnt = 0;  // inner node 0
+  for (int32_t guard = 0;; ++guard) {
+    if (guard > (1 << 22)) {  // warp-uniform
+      atomicOr(err, 2u);
+      break;
+    }
+    const float lim = best_id < 0 ? INFINITY : best_t * 1.00002f + 1e-5f;
+    if (cur_cnt == 0) {
+      const float4 nx = __ldg(nodes + 4 * cur + 0);
+      const float4 ny = __ldg(nodes + 4 * cur + 1);
+      const float4 nz = __ldg(nodes + 4 * cur + 2);
+      const int4 meta = __ldg(reinterpret_cast<const int4*>(nodes) + 4 * cur + 3);
+      float tl = box_enter(nx.x, nx.y, ny.x, ny.y, nz.x, nz.y, oi, inv, lim);
+      float tr = box_enter(nx.z, nx.w, ny.z, ny.w, nz.z, nz.w, oi, inv, lim);
+      if (!active || meta.x < 0) tl = INFINITY;
+      if (!active || meta.z < 0) tr = INFINITY;
+      const bool hl = tl != INFINITY, hr = tr != INFINITY;
+      const bool wl = __any_sync(0xffffffffu, hl), wr = __any_sync(0xffffffffu, hr);
+      if (wl && wr) {
+        // the child most rays enter first goes first
+        const uint32_t first_l = __ballot_sync(0xffffffffu, hl && (!hr || tl <= tr));
+        const uint32_t first_r = __ballot_sync(0xffffffffu, hr && (!hl || tr < tl));
+        const bool lfirst = __popc(first_l) >= __popc(first_r);
+        if (sp < kStackDepth) {
+          st_idx[sp] = lfirst ? meta.z : meta.x;
+          st_cnt[sp] = lfirst ? meta.w : meta.y;
+          st_t[sp] = lfirst ? tr : tl;
+          ++sp;
+        } else {
+          atomicOr(err, 1u);  // stack overflow: flagged, subtree skipped
+        }
+        cur = lfirst ? meta.x : meta.z;
+        cur_cnt = lfirst ? meta.y : meta.w;
+        continue;
+      } else if (wl || wr) {
+        cur = wl ? meta.x : meta.z;
+        cur_cnt = wl ? meta.y : meta.w;
+        continue;
+      }
+    } else {
+      for (int32_t k = 0; k < cur_cnt; ++k) {
+        const float4 a = __ldg(tris + 3 * (cur + k) + 0);
+        const float4 b = __ldg(tris + 3 * (cur + k) + 1);
+        const float4 c = __ldg(tris + 3 * (cur + k) + 2);
+        float t;
+        if (active && mt_hit(o, d, a, b, c, best_t, best_id >= 0, t)) {
+          const int32_t id = __float_as_int(a.w);
+          if (t < best_t || (t == best_t && id < best_id)) { best_t = t; best_id = id; }
+        }
+      }
+    }
+    // pop the next subtree that some ray of the warp still wants
+    bool found = false;
+    while (sp > 0) {
+      --sp;
+      const float lim2 = best_id < 0 ? INFINITY : best_t * 1.00002f + 1e-5f;
+      if (__any_sync(0xffffffffu, st_t[sp] <= lim2)) {
+        cur = st_idx[sp];
+        cur_cnt = st_cnt[sp];
+        found = true;
+        break;
+      }
+    }
+    if (!found) break;
+  }
+  if (best_id < 0) best_t = 0.0f;
+}
+
 // Scene-unit coordinates of the hit point: P = o + t d, x = (P - lo) * scale.
 __device__ __forceinline__ void hit_unit_coords_ls(float lo, float scale, const float o[3], const float d[3], float t,
                                                    float x[3]) {

@@ -86,7 +86,16 @@ __global__ void __launch_bounds__(256) k_trace(const __grid_constant__ Params p,
   const bool valid = thread_ray(p, tiles_x, tiles_y, ray, o, d);
   int32_t tri = -1;
   float t = 0.0f;
-  if (valid) closest_hit(p, o, d, tri, t);
+  if (p.mode == 0) {
+    // pinhole views: the 8 x 4 pixel block of a warp is coherent, traverse it as a packet
+    if (!valid) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) { o[k] = 0.0f; d[k] = 1.0f; }
+    }
+    closest_hit_packet(p.nodes, p.tris, p.counter + 1, valid, o, d, tri, t);
+  } else if (valid) {
+    closest_hit(p, o, d, tri, t);
+  }
   const bool hit = valid && tri >= 0;
   const uint32_t pos = compact_hit(p, hit);
   if (valid) {
