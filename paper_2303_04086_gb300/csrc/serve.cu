@@ -316,24 +316,28 @@ __global__ void __launch_bounds__(kServeThreads, 2) k_serve(const __grid_constan
     int nh = 0;
     const int i = (int)s_tx * kServeTile + (tid & 15), j = (int)s_ty * kServeTile + (tid >> 4);
     const bool valid = !s_skip && i < s_W && j < s_H;
-    float o[3], d[3];
-    if (valid) {
-      make_ray(s_cam, s_W, s_H, i, j, o, d);
-      for (int k = 0; k < kp.n_objs; ++k) {
-        const ServeObj& ob = kp.objs[k];
-        float ol[3];
+    float o[3] = {0.f, 0.f, 0.f}, d[3] = {1.f, 1.f, 1.f};
+    if (valid) make_ray(s_cam, s_W, s_H, i, j, o, d);
+    // every lane runs the object loop: a warp (16 x 2 pixels of the tile)
+    // traverses each object's BVH as one packet
+    for (int k = 0; k < kp.n_objs; ++k) {
+      const ServeObj& ob = kp.objs[k];
+      float ol[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) ol[a] = __fsub_rn(o[a], ob.T[a]);
-        {  // skip objects whose padded bounding sphere the ray misses
-          const float cx = ol[0] - ob.bs_c[0], cy = ol[1] - ob.bs_c[1], cz = ol[2] - ob.bs_c[2];
-          const float b = cx * d[0] + cy * d[1] + cz * d[2];
-          const float c2 = cx * cx + cy * cy + cz * cz - ob.bs_r2;
-          if (c2 > 0.f && (b > 0.f || b * b < c2)) continue;
-        }
-        int32_t id;
-        float t;
-        closest_hit_bvh(ob.nodes, ob.tris, &kp.st->err, ol, d, id, t);
-        if (id < 0) continue;
+      for (int a = 0; a < 3; ++a) ol[a] = __fsub_rn(o[a], ob.T[a]);
+      bool act = valid;
+      {  // skip objects whose padded bounding sphere the ray misses
+        const float cx = ol[0] - ob.bs_c[0], cy = ol[1] - ob.bs_c[1], cz = ol[2] - ob.bs_c[2];
+        const float b = cx * d[0] + cy * d[1] + cz * d[2];
+        const float c2 = cx * cx + cy * cy + cz * cz - ob.bs_r2;
+        if (c2 > 0.f && (b > 0.f || b * b < c2)) act = false;
+      }
+      if (!__any_sync(0xffffffffu, act)) continue;
+      int32_t id;
+      float t;
+      closest_hit_packet(ob.nodes, ob.tris, &kp.st->err, act, ol, d, id, t);
+      {
+        if (!act || id < 0) continue;
         // insert (t, k) into the sorted list (ties by object id: k increases)
         int pos = nh < kp.K ? nh : kp.K;
         while (pos > 0 && ht[pos - 1] > t) {
