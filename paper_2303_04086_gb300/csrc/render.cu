@@ -291,6 +291,18 @@ __global__ void __launch_bounds__(128) k_shade_f32(const __grid_constant__ Param
 static constexpr int kF32Tile = 128;
 static constexpr int kF32Threads = 256;
 
+// (c0, c1) += a * (w.x, w.y) as one packed FP32 instruction: two IEEE fused
+// multiply-adds rounded to nearest, the results of fmaf(a, w.x, c0), fmaf(a,
+// w.y, c1).
+__device__ __forceinline__ void fma2_rn(float& c0, float& c1, float a, float2 w) {
+  uint64_t c = ((uint64_t)__float_as_uint(c1) << 32) | __float_as_uint(c0);
+  const uint64_t av = ((uint64_t)__float_as_uint(a) << 32) | __float_as_uint(a);
+  const uint64_t wv = ((uint64_t)__float_as_uint(w.y) << 32) | __float_as_uint(w.x);
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(c) : "l"(av), "l"(wv));
+  c0 = __uint_as_float((uint32_t)c);
+  c1 = __uint_as_float((uint32_t)(c >> 32));
+}
+
 __device__ __forceinline__ void block_gemm_4x8(const float* __restrict__ act, const float* __restrict__ wT, int K,
                                                int r0, int c0, float acc[4][8]) {
   // act: [K][kF32Tile] (ray fastest), wT: [K][64] (neuron fastest)
@@ -304,11 +316,12 @@ __device__ __forceinline__ void block_gemm_4x8(const float* __restrict__ act, co
     const float4 w0 = *reinterpret_cast<const float4*>(wT + k * 64 + c0);
     const float4 w1 = *reinterpret_cast<const float4*>(wT + k * 64 + c0 + 4);
     const float av[4] = {a.x, a.y, a.z, a.w};
-    const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+    const float2 wp[4] = {make_float2(w0.x, w0.y), make_float2(w0.z, w0.w), make_float2(w1.x, w1.y),
+                          make_float2(w1.z, w1.w)};
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], wv[j], acc[i][j]);
+      for (int j = 0; j < 4; ++j) fma2_rn(acc[i][2 * j], acc[i][2 * j + 1], av[i], wp[j]);
   }
 }
 
