@@ -168,10 +168,10 @@ def make_workload(small: bool, views: int):
 
 # DRAM bytes (read + write) per hit ray of the current shade kernels, from one
 # ncu capture of a one-view launch of the full workload (cold L2), see
-# profiles/k_shade_f32_tiled_full_1view.md: 1.313 GB + 0.069 GB for 4 010 637
+# profiles/k_shade_f32_tiled_full_1view.md: 1.358 GB + 0.068 GB for 4 010 637
 # hit rays.  Traffic grows in proportion to the hit rays rendered, so a launch's
 # traffic is this figure times its hit rays.  None once the kernel changes.
-DRAM_BYTES_PER_HIT = {"k_shade_f32": (1.313405e9 + 68.739072e6) / 4010637}
+DRAM_BYTES_PER_HIT = {"k_shade_f32": (1.358243e9 + 67.909888e6) / 4010637}
 
 
 def algorithmic_bytes_per_hit(scene) -> int:
@@ -514,6 +514,65 @@ def run_variant(steps=3, warmup=3, views=N_VIEWS, precisions=("fp32", "bf16", "f
     return out
 
 
+def run_precision_sweep(steps=3, warmup=3, views=N_VIEWS, pixels_per_view=4000):
+    """The precision sweep on the tiny scene with FP16 feature tables: 64 ring
+    views at r = 3 and 3840x2160 rendered with the FP32, BF16 and FP8 MLPs
+    (Mrays/s each), and every view's PSNR / max-abs against the FP64 oracle on
+    a seeded pixel sample."""
+    import torch
+    import oracle
+    from paper_2303_04086_gb300 import inolf, synth
+    scene = synth.tiny_scene(seed=0, fp16=True)
+    obj = inolf.object_create(scene)
+    cams = synth.ring_cameras(views, 3.0)
+    W, H = W4K, H4K
+    n_rays = views * W * H
+    dev = torch.device("cuda", torch.cuda.current_device())
+    rgba = torch.empty((views, H, W, 4), dtype=torch.float32, device=dev)
+    ws = torch.empty((inolf.render_workspace_bytes(n_rays) + 15) // 16 * 4, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    inolf.calibrate_fp8(obj, cams[:1], W, H, workspace=ws)
+    oracle.build()
+    orc = oracle.Oracle(scene)
+    rng = np.random.default_rng(11)
+    samples = [np.sort(rng.choice(W * H, pixels_per_view, replace=False)).astype(np.int64) for _ in range(views)]
+    refs = [orc.render_pixels(cams[v], W, H, samples[v]) for v in range(views)]
+    out = {"workload": "icosphere-1280tri L4 N16-128, FP16 feature tables, MLP 24-64-64-4, %d ring views r=3 at "
+                       "3840x2160" % views,
+           "accuracy": "per view, %d seeded pixels, PSNR over the 4 channels of hit pixels" % pixels_per_view,
+           "precisions": {}}
+    for prec in ("fp32", "bf16", "fp8"):
+        for _ in range(warmup):
+            inolf.render(obj, cams, W, H, prec, rgba_out=rgba, workspace=ws, stream=stream)
+        torch.cuda.synchronize()
+        evs = []
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            inolf.render(obj, cams, W, H, prec, rgba_out=rgba, workspace=ws, stream=stream)
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        ms = sum(e0.elapsed_time(e1) for e0, e1 in evs)
+        flat = rgba.reshape(views, -1, 4)
+        psnrs, maxabs = [], 0.0
+        for v in range(views):
+            got = flat[v][torch.from_numpy(samples[v]).to(dev)].cpu().numpy()
+            hit = refs[v]["tri"] >= 0
+            mse = float(np.mean((got[hit] - refs[v]["rgba"][hit]) ** 2)) if hit.any() else 0.0
+            psnrs.append(10 * math.log10(1.0 / mse) if mse > 0 else 99.0)
+            maxabs = max(maxabs, float(np.abs(got - refs[v]["rgba"]).max()))
+        out["precisions"][prec] = {"value": n_rays * steps / (ms / 1e3) / 1e6, "unit": "Mrays/s",
+                                   "ms_per_step": ms / steps, "psnr_db_min": min(psnrs),
+                                   "psnr_db_median": float(np.median(psnrs)), "max_abs": maxabs}
+    del rgba, ws, flush, obj
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -713,6 +772,8 @@ def run_native(a):
         out["variant"] = run_variant(steps=max(1, a.steps), warmup=max(1, a.warmup),
                                      precisions=[p for p in ["fp32"] + list(precisions)
                                                  if "unavailable" not in precisions.get(p, {})])
+    if rank == 0 and not a.small and not a.no_variant:
+        out["precision_sweep"] = run_precision_sweep(steps=max(1, a.steps), warmup=max(1, a.warmup))
     if rank == 0 and not a.no_serving and not a.small:
         rgba = ws = None
         torch.cuda.empty_cache()
