@@ -184,6 +184,36 @@ def mlp_flops_per_hit(scene) -> int:
     return 2 * (64 * scene.d_in + 64 * 64 + 4 * 64)
 
 
+def kernel_rooflines(kernels, scene, n_rays, n_hit, steps, peaks):
+    """Every kernel of a timed run against its roofline: the shade kernels'
+    algorithmic gather + output bytes against the measured HBM copy bandwidth
+    and their MLP flops against the peak of their arithmetic (FP32 SIMT from
+    the unit counts, BF16 measured, FP8 = 2 x BF16, the nominal ratio); the
+    trace / march kernels' output bytes (16 B per miss, 8 B per hit record)
+    against HBM, with rays per second (their limit is ALU issue, see profiles/)."""
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    bf16 = peaks.get("bf16_tflops", 1900.0)
+    mlp_peak = {"k_shade_f32": 80.5, "k_shade_tc_bf16": bf16, "k_shade_tc_fp8": 2.0 * bf16}
+    out = {}
+    for name, st in kernels.items():
+        if not st.get("launches"):
+            continue
+        sec = st["ms"] / 1e3
+        per_step_launches = max(1, st["launches"] // max(1, steps))
+        if name.startswith("k_shade"):
+            byt = (algorithmic_bytes_per_hit(scene) + 24) * n_hit * steps
+            fl = mlp_flops_per_hit(scene) * n_hit * steps
+            out[name] = {"gbs": byt / sec / 1e9, "frac_hbm": byt / sec / 1e9 / hbm,
+                         "mlp_tflops": fl / sec / 1e12, "frac_mlp_peak": fl / sec / 1e12 / mlp_peak.get(name, bf16),
+                         "mlp_peak_tflops": mlp_peak.get(name, bf16), "launches_per_step": per_step_launches}
+        else:
+            byt = (16 * (n_rays - n_hit) + 8 * n_hit) * steps
+            out[name] = {"gbs": byt / sec / 1e9, "frac_hbm": byt / sec / 1e9 / hbm,
+                         "grays_per_s": n_rays * steps / sec / 1e9, "bound": "alu (issue)",
+                         "launches_per_step": per_step_launches}
+    return out
+
+
 def cpu_baseline(scene, cams, W, H, budget_s=12.0, orc=None):
     """The FP64 oracle as it stands, on a seeded pixel sample of view 0."""
     import oracle
@@ -762,6 +792,10 @@ def run_native(a):
            "e2e": e2e, "gpu_launches": int(sum(s["launches"] for s in stats.values())),
            "kernels": stats, "roofline": roof, "cpu_baseline": base, "clocks": clocks,
            "precisions": precisions, "hit_mrays_per_s": n_hit * a.steps * world / (ms / 1e3) / 1e6}
+    out["kernel_rooflines"] = {"fp32": kernel_rooflines(stats, scene, n_rays, n_hit, a.steps, peaks)}
+    for prec, pr in precisions.items():
+        if "kernels" in pr:
+            out["kernel_rooflines"][prec] = kernel_rooflines(pr["kernels"], scene, n_rays, n_hit, a.steps, peaks)
     if fp32_acc is not None:
         out["accuracy_vs_oracle"] = fp32_acc
     if rank == 0 and not a.small:
