@@ -336,8 +336,9 @@ inolf_status inolf_serve_create(const inolf_serve_params* params, inolf_server**
 
 /* Makes an object resident in the scene at a translation (object frame =
  * world - translation).  Up to 16 objects; only while no request is in
- * flight.  The object must outlive the server.  Objects with density cubes:
- * INOLF_E_UNSUPPORTED (the serving loop composites mesh-proxy objects). */
+ * flight.  The object must outlive the server.  Mesh-proxy objects and
+ * density-cube objects (hit by the march, alpha_c input, c = c_d + t c_s) can
+ * be mixed; every object's hits are composited by distance. */
 inolf_status inolf_serve_add_object(inolf_server* srv, const inolf_object* obj, const float translation[3]);
 
 /* Target frame rate of a viewer for policy 1 (default 50 Hz: one camera

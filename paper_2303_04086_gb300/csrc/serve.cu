@@ -48,7 +48,7 @@ static constexpr int kServeMaxK = 4;
 static constexpr int kServeTile = 16;
 static constexpr int kServeThreads = kServeTile * kServeTile;
 static constexpr int kServeMaxSlots = 256;
-static constexpr int kServeMaxDin = 2 * INOLF_MAX_LEVELS + INOLF_N_SH;
+static constexpr int kServeMaxDin = 2 * INOLF_MAX_LEVELS + INOLF_N_SH + 1;  // + alpha_c (density-cube objects)
 static constexpr unsigned long long kServeClaim = 16;  // tiles claimed per atomic
 
 struct ServeObj {
@@ -62,6 +62,8 @@ struct ServeObj {
   float lo, scale;
   float T[3];  // object placement: local = world - T
   float bs_c[3], bs_r2;  // bounding sphere of the proxy (local frame), padded
+  int32_t variant;       // 1: hit by the density march, alpha_c input, c = c_d + tint c_s
+  CubesDev cub;
   LevelDev lv[INOLF_MAX_LEVELS];
 };
 
@@ -190,7 +192,7 @@ __device__ __forceinline__ float4 mlp_f32(const float4* W1T, const float4* W2, c
 //   rgba of every hit      256 pixels x K float4
 //   hit list by object     256 x K u16 (pixel * K + rank)
 //   2 mbarriers + TMEM address slot
-static constexpr uint32_t kServeWBytes = (48 * 64 + 64 * 64 + 64 * 4) * 4;  // 30 720
+static constexpr uint32_t kServeWBytes = ((kServeMaxDin) * 64 + 64 * 64 + 64 * 4) * 4;  // 29 952
 static constexpr uint32_t kServeABytes = 2u * 128u * 64u * 2u;              // 32 768
 static constexpr size_t kServeSmem =
     kServeWBytes + kServeABytes + kServeThreads * kServeMaxK * 16 + kServeThreads * kServeMaxK * 2 + 64;
@@ -211,6 +213,7 @@ __global__ void __launch_bounds__(kServeThreads, 2) k_serve(const __grid_constan
   __shared__ float s_cam[13];
   __shared__ uint32_t s_cnt[kServeMaxObjects], s_off[kServeMaxObjects + 1];
   __shared__ float s_ht[kServeThreads * kServeMaxK];
+  __shared__ float s_ah[kServeThreads * kServeMaxK];  // alpha_c of each hit (density-cube objects)
   const int tid = threadIdx.x;
   const unsigned long long t_start = gtimer();
   if (tid == 0) {
@@ -311,7 +314,7 @@ __global__ void __launch_bounds__(kServeThreads, 2) k_serve(const __grid_constan
     if (s_cmd) break;
 
     // ---- trace every object, keep the K nearest hits of this pixel ----
-    float ht[kServeMaxK];
+    float ht[kServeMaxK], ha[kServeMaxK];
     int hk[kServeMaxK];
     int nh = 0;
     const int i = (int)s_tx * kServeTile + (tid & 15), j = (int)s_ty * kServeTile + (tid >> 4);
@@ -319,34 +322,41 @@ __global__ void __launch_bounds__(kServeThreads, 2) k_serve(const __grid_constan
     float o[3] = {0.f, 0.f, 0.f}, d[3] = {1.f, 1.f, 1.f};
     if (valid) make_ray(s_cam, s_W, s_H, i, j, o, d);
     // every lane runs the object loop: a warp (16 x 2 pixels of the tile)
-    // traverses each object's BVH as one packet
+    // traverses each mesh object's BVH as one packet; density-cube objects
+    // are marched ray by ray
     for (int k = 0; k < kp.n_objs; ++k) {
       const ServeObj& ob = kp.objs[k];
       float ol[3];
 #pragma unroll
       for (int a = 0; a < 3; ++a) ol[a] = __fsub_rn(o[a], ob.T[a]);
-      bool act = valid;
-      {  // skip objects whose padded bounding sphere the ray misses
-        const float cx = ol[0] - ob.bs_c[0], cy = ol[1] - ob.bs_c[1], cz = ol[2] - ob.bs_c[2];
-        const float b = cx * d[0] + cy * d[1] + cz * d[2];
-        const float c2 = cx * cx + cy * cy + cz * cz - ob.bs_r2;
-        if (c2 > 0.f && (b > 0.f || b * b < c2)) act = false;
-      }
-      if (!__any_sync(0xffffffffu, act)) continue;
-      int32_t id;
-      float t;
-      closest_hit_packet(ob.nodes, ob.tris, &kp.st->err, act, ol, d, id, t);
-      {
+      int32_t id = -1;
+      float t = 0.0f, ac = 0.0f;
+      if (ob.variant) {  // uniform: the density march of this ray (Eq. 4), no warp votes
+        if (valid) march_ray(ob.cub, ob.lo, ob.scale, ol, d, id, t, ac);
+        if (id < 0) continue;
+      } else {
+        bool act = valid;
+        {  // skip objects whose padded bounding sphere the ray misses
+          const float cx = ol[0] - ob.bs_c[0], cy = ol[1] - ob.bs_c[1], cz = ol[2] - ob.bs_c[2];
+          const float b = cx * d[0] + cy * d[1] + cz * d[2];
+          const float c2 = cx * cx + cy * cy + cz * cz - ob.bs_r2;
+          if (c2 > 0.f && (b > 0.f || b * b < c2)) act = false;
+        }
+        if (!__any_sync(0xffffffffu, act)) continue;
+        closest_hit_packet(ob.nodes, ob.tris, &kp.st->err, act, ol, d, id, t);
         if (!act || id < 0) continue;
+      }
+      {
         // insert (t, k) into the sorted list (ties by object id: k increases)
         int pos = nh < kp.K ? nh : kp.K;
         while (pos > 0 && ht[pos - 1] > t) {
-          if (pos < kp.K) { ht[pos] = ht[pos - 1]; hk[pos] = hk[pos - 1]; }
+          if (pos < kp.K) { ht[pos] = ht[pos - 1]; hk[pos] = hk[pos - 1]; ha[pos] = ha[pos - 1]; }
           --pos;
         }
         if (pos < kp.K) {
           ht[pos] = t;
           hk[pos] = k;
+          ha[pos] = ac;
           if (nh < kp.K) ++nh;
         }
       }
@@ -356,6 +366,7 @@ __global__ void __launch_bounds__(kServeThreads, 2) k_serve(const __grid_constan
     for (int q = 0; q < nh; ++q) {
       rank[q] = atomicAdd(&s_cnt[hk[q]], 1u);
       s_ht[tid * kServeMaxK + q] = ht[q];
+      s_ah[tid * kServeMaxK + q] = ha[q];
     }
     __syncthreads();
     if (tid == 0) {
@@ -396,7 +407,13 @@ __global__ void __launch_bounds__(kServeThreads, 2) k_serve(const __grid_constan
             }
           }
           sh16c(kp.shc, d, x + 2 * ob.L);
-          s_rgba[tid * kServeMaxK + q] = mlp_f32(sWf, sWf + din * 16, sWf + din * 16 + 64 * 16, x, din);
+          if (ob.variant) x[2 * ob.L + 16] = ha[q];  // alpha_c (Eq. 5)
+          float4 c = mlp_f32(sWf, sWf + din * 16, sWf + din * 16 + 64 * 16, x, din);
+          if (ob.variant) {  // c = c_d + tint c_s (Eq. 7)
+            const float4 dc = cube_diffuse(ob.cub, x3);
+            c = make_float4(fmaf(dc.w, c.x, dc.x), fmaf(dc.w, c.y, dc.y), fmaf(dc.w, c.z, dc.z), c.w);
+          }
+          s_rgba[tid * kServeMaxK + q] = c;
         }
         __syncthreads();
       } else {
@@ -417,6 +434,7 @@ __global__ void __launch_bounds__(kServeThreads, 2) k_serve(const __grid_constan
         for (uint32_t base = 0; base < cnt; base += kServeThreads) {
           const bool mine = base + (uint32_t)tid < cnt;
           uint32_t entry = 0;
+          float4 dc = make_float4(0.f, 0.f, 0.f, 0.f);
           if (mine) {
             entry = s_list[s_off[k] + base + tid];
             const int p = (int)(entry / kServeMaxK);
@@ -445,7 +463,13 @@ __global__ void __launch_bounds__(kServeThreads, 2) k_serve(const __grid_constan
             sh16c(kp.shc, pd, sh);
 #pragma unroll
             for (int u = 0; u < 8; ++u) store_pair<false>(A, row, 2u * ob.L + 2u * u, chunks1, sh[2 * u], sh[2 * u + 1], 1.f);
-            for (uint32_t kk = (uint32_t)din; kk < K1; kk += 2) store_pair<false>(A, row, kk, chunks1, 0.f, 0.f, 1.f);
+            uint32_t k0 = 2u * ob.L + 16u;
+            if (ob.variant) {  // alpha_c (Eq. 5); the diffuse of Eq. 7 is read now, used after the MLP
+              store_pair<false>(A, row, k0, chunks1, s_ah[entry], 0.f, 1.f);
+              k0 += 2u;
+              dc = cube_diffuse(ob.cub, x3);
+            }
+            for (uint32_t kk = k0; kk < K1; kk += 2) store_pair<false>(A, row, kk, chunks1, 0.f, 0.f, 1.f);
           } else {
             for (uint32_t c = 0; c < chunks1; ++c)
               *reinterpret_cast<uint4*>(A + tc::core_off(row, c, chunks1)) = make_uint4(0, 0, 0, 0);
@@ -456,7 +480,11 @@ __global__ void __launch_bounds__(kServeThreads, 2) k_serve(const __grid_constan
             broken = true;
             break;
           }
-          if (mine) s_rgba[entry] = rgba;
+          if (mine) {
+            if (ob.variant)
+              rgba = make_float4(fmaf(dc.w, rgba.x, dc.x), fmaf(dc.w, rgba.y, dc.y), fmaf(dc.w, rgba.z, dc.z), rgba.w);
+            s_rgba[entry] = rgba;
+          }
         }
       }
     }
@@ -824,8 +852,6 @@ extern "C" inolf_status inolf_serve_add_object(inolf_server* s, const inolf_obje
   for (auto& m : s->slots)
     if (m.busy) return fail(INOLF_E_INVALID, "inolf_serve_add_object: requests are in flight");
   if ((int)s->objs.size() >= kServeMaxObjects) return fail(INOLF_E_INVALID, "inolf_serve_add_object: 16 objects max");
-  if (obj->o.variant)
-    return fail(INOLF_E_UNSUPPORTED, "inolf_serve_add_object: the serving loop composites mesh-proxy objects only");
   const Object& o = obj->o;
   ServeObj so{};
   so.nodes = (const float4*)o.nodes;
@@ -843,6 +869,8 @@ extern "C" inolf_status inolf_serve_add_object(inolf_server* s, const inolf_obje
   for (int k = 0; k < 3; ++k) so.bs_c[k] = o.bsphere[k];
   so.bs_r2 = o.bsphere[3] * o.bsphere[3];
   for (int l = 0; l < o.L; ++l) so.lv[l] = o.lv[l];
+  so.variant = o.variant;
+  so.cub = o.cub;
   s->objs.push_back(so);
   s->objs_dirty = true;
   return INOLF_OK;

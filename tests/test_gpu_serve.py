@@ -262,3 +262,53 @@ def test_algorithm1_policy_serves_all_viewers(env):
     c = srv.counters()
     assert c["admitted"] == 13 and c["completed"] == 13 and c["denied"] == 0
     srv.close()
+
+
+def test_density_cube_object_served_like_render(env):
+    # the decoupled variant in the serving loop: one density-cube object
+    # equals inolf_render of it (FP32 exactly within TOL, BF16 within its
+    # tolerance), and composited among mesh objects its frame is the same
+    # alone and in the mix
+    torch, inolf, scenes, objs = env
+    dscene = synth.tiny_density_scene(seed=3)
+    dobj = inolf.object_create(dscene)
+    srv = inolf.Server(hbm_budget=64 << 20, max_slots=4, max_width=512, max_height=512)
+    srv.add_object(dobj, (0.0, 0.0, 0.0))
+    cam = synth.camera((0.4, -0.3, 3.0))
+    for prec, tol in (("fp32", TOL), ("bf16", 1e-2)):
+        t = srv.submit(cam, 96, 80, prec=prec)
+        st, res = _done(srv, t)
+        assert st == inolf.OK
+        got = srv.frame(res).cpu().numpy()
+        ref = inolf.render(dobj, cam[None], 96, 80, prec).cpu().numpy()[0]
+        # straight alpha out: compare colour where alpha > 0, alpha everywhere
+        m = ref[..., 3] > 0
+        assert np.abs(got[..., 3] - ref[..., 3]).max() <= tol
+        assert np.abs(got[m][:, :3] - ref[m][:, :3]).max() <= tol
+        srv.release(t)
+    srv.close()
+    mixed = inolf.Server(hbm_budget=256 << 20, max_slots=16, max_width=512, max_height=512)
+    mixed.add_object(objs[0], PLACES[1])
+    mixed.add_object(dobj, PLACES[0])
+    mixed.add_object(objs[1], PLACES[2])
+    cam2 = synth.camera((1.0, 1.5, 8.0), target=(0.0, 0.0, -0.5))
+    t = mixed.submit(cam2, 160, 120)
+    st, res = _done(mixed, t)
+    assert st == inolf.OK
+    alone = mixed.frame(res).cpu().numpy()
+    mixed.release(t)
+    assert (alone[..., 3] > 0).mean() > 0.05
+    rng = np.random.default_rng(2)
+    tickets = []
+    for k in range(9):
+        c = synth.camera(tuple(rng.uniform(-6, 6, 3) + np.array([0, 0, 9.0])))
+        tickets.append((mixed.submit(c, int(rng.integers(40, 200)), int(rng.integers(40, 200))), None))
+        if k == 4:
+            tickets.append((mixed.submit(cam2, 160, 120), "mine"))
+    for tk, tag in tickets:
+        st, res = _done(mixed, tk)
+        assert st == inolf.OK
+        if tag == "mine":
+            assert np.array_equal(mixed.frame(res).cpu().numpy(), alone)
+        mixed.release(tk)
+    mixed.close()
