@@ -185,22 +185,39 @@ __device__ __forceinline__ float4 mlp_f32(const float4* W1T, const float4* W2, c
   return make_float4(sigmoidf_(acc.x), sigmoidf_(acc.y), sigmoidf_(acc.z), sigmoidf_(acc.w));
 }
 
+// The density-cube path kept out of line, so that the march and the diffuse
+// lookup do not raise the register pressure of the mesh-object path.
+__device__ __noinline__ void serve_march(const CubesDev& c, float lo, float scale, const float* o, const float* d,
+                                         int32_t* k, float* t, float* alpha) {
+  march_ray(c, lo, scale, o, d, *k, *t, *alpha);
+}
+__device__ __noinline__ float4 serve_diffuse(const CubesDev& c, const float* x) { return cube_diffuse(c, x); }
+
 // Shared-memory plan of k_serve (dynamic part):
-//   [0, kServeWBytes)      FP32 weights of one object (FP32 requests) or its
+//   [0, serve_wbytes)      FP32 weights of one object (FP32 requests) or its
 //                           BF16 operand blob (BF16 requests)
 //   A tiles                2 x 128 rows x 64 BF16 (tensor-core operand)
 //   rgba of every hit      256 pixels x K float4
 //   hit list by object     256 x K u16 (pixel * K + rank)
 //   2 mbarriers + TMEM address slot
-static constexpr uint32_t kServeWBytes = ((kServeMaxDin) * 64 + 64 * 64 + 64 * 4) * 4;  // 29 952
-static constexpr uint32_t kServeABytes = 2u * 128u * 64u * 2u;              // 32 768
-static constexpr size_t kServeSmem =
-    kServeWBytes + kServeABytes + kServeThreads * kServeMaxK * 16 + kServeThreads * kServeMaxK * 2 + 64;
+// The kernel is compiled twice: for scenes of mesh objects only, and for
+// scenes that also hold density-cube objects (alpha_c input, d_in up to 49),
+// so that the mesh-only loop keeps its lean register and memory plan.
+// FP32 weights: (d_in 64 + 64 64 + 64 4) floats, rounded up to 1 KB so the
+// A tiles stay 1 KB aligned.
+__host__ __device__ constexpr uint32_t serve_wbytes(bool cubes) {
+  return (((cubes ? kServeMaxDin : kServeMaxDin - 1) * 64 + 64 * 64 + 64 * 4) * 4 + 1023) / 1024 * 1024;
+}
+static constexpr uint32_t kServeABytes = 2u * 128u * 64u * 2u;  // 32 768
+__host__ __device__ constexpr size_t serve_smem(bool cubes) {
+  return serve_wbytes(cubes) + kServeABytes + kServeThreads * kServeMaxK * 16 + kServeThreads * kServeMaxK * 2 + 64;
+}
 
+template <bool kCubes>
 __global__ void __launch_bounds__(kServeThreads, 2) k_serve(const __grid_constant__ ServeKParams kp) {
   extern __shared__ __align__(1024) uint8_t smem[];
   float4* sWf = reinterpret_cast<float4*>(smem);
-  uint8_t* sA = smem + kServeWBytes;
+  uint8_t* sA = smem + serve_wbytes(kCubes);
   float4* s_rgba = reinterpret_cast<float4*>(sA + kServeABytes);
   uint16_t* s_list = reinterpret_cast<uint16_t*>(s_rgba + kServeThreads * kServeMaxK);
   uint64_t* bars = reinterpret_cast<uint64_t*>(s_list + kServeThreads * kServeMaxK);  // [0] weights, [1] MMA
@@ -213,7 +230,7 @@ __global__ void __launch_bounds__(kServeThreads, 2) k_serve(const __grid_constan
   __shared__ float s_cam[13];
   __shared__ uint32_t s_cnt[kServeMaxObjects], s_off[kServeMaxObjects + 1];
   __shared__ float s_ht[kServeThreads * kServeMaxK];
-  __shared__ float s_ah[kServeThreads * kServeMaxK];  // alpha_c of each hit (density-cube objects)
+  __shared__ float s_ah[kCubes ? kServeThreads * kServeMaxK : 1];  // alpha_c of each hit (density-cube objects)
   const int tid = threadIdx.x;
   const unsigned long long t_start = gtimer();
   if (tid == 0) {
@@ -331,8 +348,8 @@ __global__ void __launch_bounds__(kServeThreads, 2) k_serve(const __grid_constan
       for (int a = 0; a < 3; ++a) ol[a] = __fsub_rn(o[a], ob.T[a]);
       int32_t id = -1;
       float t = 0.0f, ac = 0.0f;
-      if (ob.variant) {  // uniform: the density march of this ray (Eq. 4), no warp votes
-        if (valid) march_ray(ob.cub, ob.lo, ob.scale, ol, d, id, t, ac);
+      if (kCubes && ob.variant) {  // uniform: the density march of this ray (Eq. 4), no warp votes
+        if (valid) serve_march(ob.cub, ob.lo, ob.scale, ol, d, &id, &t, &ac);
         if (id < 0) continue;
       } else {
         bool act = valid;
@@ -350,13 +367,17 @@ __global__ void __launch_bounds__(kServeThreads, 2) k_serve(const __grid_constan
         // insert (t, k) into the sorted list (ties by object id: k increases)
         int pos = nh < kp.K ? nh : kp.K;
         while (pos > 0 && ht[pos - 1] > t) {
-          if (pos < kp.K) { ht[pos] = ht[pos - 1]; hk[pos] = hk[pos - 1]; ha[pos] = ha[pos - 1]; }
+          if (pos < kp.K) {
+            ht[pos] = ht[pos - 1];
+            hk[pos] = hk[pos - 1];
+            if (kCubes) ha[pos] = ha[pos - 1];
+          }
           --pos;
         }
         if (pos < kp.K) {
           ht[pos] = t;
           hk[pos] = k;
-          ha[pos] = ac;
+          if (kCubes) ha[pos] = ac;
           if (nh < kp.K) ++nh;
         }
       }
@@ -366,7 +387,7 @@ __global__ void __launch_bounds__(kServeThreads, 2) k_serve(const __grid_constan
     for (int q = 0; q < nh; ++q) {
       rank[q] = atomicAdd(&s_cnt[hk[q]], 1u);
       s_ht[tid * kServeMaxK + q] = ht[q];
-      s_ah[tid * kServeMaxK + q] = ha[q];
+      if (kCubes) s_ah[tid * kServeMaxK + q] = ha[q];
     }
     __syncthreads();
     if (tid == 0) {
@@ -394,7 +415,7 @@ __global__ void __launch_bounds__(kServeThreads, 2) k_serve(const __grid_constan
 #pragma unroll
           for (int a = 0; a < 3; ++a) ol[a] = __fsub_rn(o[a], ob.T[a]);
           hit_unit_coords_ls(ob.lo, ob.scale, ol, d, ht[q], x3);
-          float x[kServeMaxDin];
+          float x[kCubes ? kServeMaxDin : kServeMaxDin - 1];
           {
             LevelFetchX fa, fb;
             fetch_phi_x(ob.lv[0], x3, fa);
@@ -407,10 +428,10 @@ __global__ void __launch_bounds__(kServeThreads, 2) k_serve(const __grid_constan
             }
           }
           sh16c(kp.shc, d, x + 2 * ob.L);
-          if (ob.variant) x[2 * ob.L + 16] = ha[q];  // alpha_c (Eq. 5)
+          if (kCubes && ob.variant) x[2 * ob.L + 16] = ha[q];  // alpha_c (Eq. 5)
           float4 c = mlp_f32(sWf, sWf + din * 16, sWf + din * 16 + 64 * 16, x, din);
-          if (ob.variant) {  // c = c_d + tint c_s (Eq. 7)
-            const float4 dc = cube_diffuse(ob.cub, x3);
+          if (kCubes && ob.variant) {  // c = c_d + tint c_s (Eq. 7)
+            const float4 dc = serve_diffuse(ob.cub, x3);
             c = make_float4(fmaf(dc.w, c.x, dc.x), fmaf(dc.w, c.y, dc.y), fmaf(dc.w, c.z, dc.z), c.w);
           }
           s_rgba[tid * kServeMaxK + q] = c;
@@ -434,7 +455,6 @@ __global__ void __launch_bounds__(kServeThreads, 2) k_serve(const __grid_constan
         for (uint32_t base = 0; base < cnt; base += kServeThreads) {
           const bool mine = base + (uint32_t)tid < cnt;
           uint32_t entry = 0;
-          float4 dc = make_float4(0.f, 0.f, 0.f, 0.f);
           if (mine) {
             entry = s_list[s_off[k] + base + tid];
             const int p = (int)(entry / kServeMaxK);
@@ -464,10 +484,9 @@ __global__ void __launch_bounds__(kServeThreads, 2) k_serve(const __grid_constan
 #pragma unroll
             for (int u = 0; u < 8; ++u) store_pair<false>(A, row, 2u * ob.L + 2u * u, chunks1, sh[2 * u], sh[2 * u + 1], 1.f);
             uint32_t k0 = 2u * ob.L + 16u;
-            if (ob.variant) {  // alpha_c (Eq. 5); the diffuse of Eq. 7 is read now, used after the MLP
+            if (kCubes && ob.variant) {  // alpha_c (Eq. 5)
               store_pair<false>(A, row, k0, chunks1, s_ah[entry], 0.f, 1.f);
               k0 += 2u;
-              dc = cube_diffuse(ob.cub, x3);
             }
             for (uint32_t kk = k0; kk < K1; kk += 2) store_pair<false>(A, row, kk, chunks1, 0.f, 0.f, 1.f);
           } else {
@@ -481,8 +500,17 @@ __global__ void __launch_bounds__(kServeThreads, 2) k_serve(const __grid_constan
             break;
           }
           if (mine) {
-            if (ob.variant)
+            if (kCubes && ob.variant) {  // c = c_d + tint c_s (Eq. 7), diffuse read at the hit point
+              const int p = (int)(entry / kServeMaxK);
+              const int pi = (int)s_tx * kServeTile + (p & 15), pj = (int)s_ty * kServeTile + (p >> 4);
+              float po[3], pd[3], ol[3], x3[3];
+              make_ray(s_cam, s_W, s_H, pi, pj, po, pd);
+#pragma unroll
+              for (int a = 0; a < 3; ++a) ol[a] = __fsub_rn(po[a], ob.T[a]);
+              hit_unit_coords_ls(ob.lo, ob.scale, ol, pd, s_ht[entry], x3);
+              const float4 dc = serve_diffuse(ob.cub, x3);
               rgba = make_float4(fmaf(dc.w, rgba.x, dc.x), fmaf(dc.w, rgba.y, dc.y), fmaf(dc.w, rgba.z, dc.z), rgba.w);
+            }
             s_rgba[entry] = rgba;
           }
         }
@@ -570,7 +598,8 @@ struct inolf_server {
   cudaStream_t stream = nullptr;
   cudaEvent_t kernel_done = nullptr;
   bool launched = false;
-  int grid = 0;
+  int grid = 0;        // persistent CTAs of the mesh-only kernel
+  int grid_cubes = 0;  // and of the kernel that also serves density-cube objects
   // objects
   std::vector<ServeObj> objs;
   ServeObj* d_objs = nullptr;
@@ -652,7 +681,11 @@ static void serve_free(inolf_server* s) {
   delete s;
 }
 
-static size_t serve_smem_bytes() { return kServeSmem; }
+static bool scene_has_cubes(const inolf_server* s) {
+  for (const ServeObj& o : s->objs)
+    if (o.variant) return true;
+  return false;
+}
 
 // Launches the persistent kernel if it is not running (must hold s->mu).
 static inolf_status ensure_running(inolf_server* s) {
@@ -683,7 +716,10 @@ static inolf_status ensure_running(inolf_server* s) {
   sh_constants(kp.shc);
   {
     LaunchTimer lt("k_serve", s->stream);
-    k_serve<<<s->grid, kServeThreads, serve_smem_bytes(), s->stream>>>(kp);
+    if (scene_has_cubes(s))
+      k_serve<true><<<s->grid_cubes, kServeThreads, serve_smem(true), s->stream>>>(kp);
+    else
+      k_serve<false><<<s->grid, kServeThreads, serve_smem(false), s->stream>>>(kp);
   }
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(INOLF_E_CUDA, std::string("k_serve launch: ") + cudaGetErrorString(e));
@@ -813,11 +849,15 @@ extern "C" inolf_status inolf_serve_create(const inolf_serve_params* prm, inolf_
   s->slot_gen.assign(p.max_slots, 0);
   int sms = 1, occ = 1;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
-  cudaFuncSetAttribute(k_serve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)serve_smem_bytes());
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_serve, kServeThreads, serve_smem_bytes());
-  occ = std::max(1, std::min(occ, 4));  // each CTA holds 128 of the SM's 512 TMEM columns
-  if (p.ctas_per_sm > 0) occ = std::min(occ, p.ctas_per_sm);
-  s->grid = sms * occ;
+  auto grid_of = [&](const void* fn, size_t smem) {
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kServeThreads, smem);
+    occ = std::max(1, std::min(occ, 4));  // each CTA holds 128 of the SM's 512 TMEM columns
+    if (p.ctas_per_sm > 0) occ = std::min(occ, p.ctas_per_sm);
+    return sms * occ;
+  };
+  s->grid = grid_of((const void*)k_serve<false>, serve_smem(false));
+  s->grid_cubes = grid_of((const void*)k_serve<true>, serve_smem(true));
   cudaGetLastError();
   if (p.policy == 1 && inolf_sched_create(p.max_rays_in_flight, &s->sched) != INOLF_OK) return bad("scheduler");
   s->loop = std::thread(dispatcher, s);
