@@ -50,6 +50,8 @@ def _args():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-seconds", type=float, default=10.0)
     ap.add_argument("--no-variant", action="store_true", help="skip the density-cube variant workload")
+    ap.add_argument("--training-only", action="store_true",
+                    help="run only the differentiation workload and print its JSON (profiling)")
     ap.add_argument("--variant-only", action="store_true",
                     help="run only the density-cube variant workload (--views, --steps, --warmup, --precisions) "
                          "and print its JSON (profiling)")
@@ -433,16 +435,21 @@ def run_training(steps=40, batch=1 << 18, n_views=100, res=800, prec="bf16"):
         return loss
 
     for _ in range(3):
-        losses.append(float(one().detach()))
+        losses.append(one().detach())
     torch.cuda.synchronize()
+    inolf.stats_reset()
+    inolf.stats_enable(True)
     t0 = time.perf_counter()
-    for _ in range(steps):
-        losses.append(float(one().detach()))
+    for _ in range(steps):  # losses stay on the device: no host synchronisation inside the loop
+        losses.append(one().detach())
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
+    inolf.stats_enable(False)
+    kern = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / steps} for k, v in inolf.stats_read().items()}
+    losses = [float(x) for x in losses]
     return {"steps_per_s": steps / dt, "rays_per_step": batch, "mrays_per_s": steps * batch / dt / 1e6,
             "loss_first": losses[0], "loss_last": losses[-1], "forward": prec, "backward": "fp32",
-            "views": n_views, "res": res}
+            "views": n_views, "res": res, "kernels": kern}
 
 
 def run_variant(steps=3, warmup=3, views=N_VIEWS, precisions=("fp32", "bf16", "fp8"), oracle_pixels=100_000):
@@ -826,6 +833,10 @@ def main():
     a = _args()
     if a.impl == "reference":
         run_reference(a)
+    elif a.training_only:
+        from paper_2303_04086_gb300 import build
+        build.build()
+        print(json.dumps({"training": run_training(steps=max(1, a.steps))}))
     elif a.variant_only:
         from paper_2303_04086_gb300 import build
         build.build()

@@ -270,8 +270,9 @@ inolf_status inolf_backward(const inolf_object* obj, const float* o, const float
  * optimiser step): tables_dev (host array of n_levels device pointers, each
  * m_l^3 x 2 FP32 in slot order; NULL array or NULL entries keep a level) and
  * the three weight matrices (all or none; row-major FP32).  Tables are copied
- * on `stream`; new weights are read back, repacked for every precision
- * (FP8 weight scales recomputed) and uploaded, which synchronises `stream`. */
+ * on `stream`; new weights are repacked for every precision on the device
+ * (FP8 weight scales recomputed there), also on `stream`: the call does not
+ * synchronise, so it can sit inside a training loop. */
 inolf_status inolf_object_load_params(inolf_object* obj, const float* const* tables_dev, const float* w1_dev,
                                       const float* w2_dev, const float* w3_dev, void* stream);
 

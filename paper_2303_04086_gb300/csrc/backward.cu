@@ -357,15 +357,6 @@ extern "C" inolf_status inolf_object_load_params(inolf_object* obj, const float*
       if (es != INOLF_OK) return es;
     }
   }
-  if (w1_dev) {
-    const int din = o.d_in, H = INOLF_HIDDEN, O = INOLF_OUT;
-    std::vector<float> w1((size_t)H * din), w2((size_t)H * H), w3((size_t)O * H);
-    if (cudaMemcpyAsync(w1.data(), w1_dev, w1.size() * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaMemcpyAsync(w2.data(), w2_dev, w2.size() * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaMemcpyAsync(w3.data(), w3_dev, w3.size() * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess)
-      return fail(INOLF_E_CUDA, "load_params: weight readback failed");
-    return upload_weights(o, w1.data(), w2.data(), w3.data(), stream);
-  }
+  if (w1_dev) return inolf::pack_weights_device(o, w1_dev, w2_dev, w3_dev, stream);  // no host round trip
   return INOLF_OK;
 }

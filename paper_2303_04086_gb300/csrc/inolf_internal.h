@@ -82,7 +82,8 @@ struct Object {
   void* w_fp8 = nullptr;
   int32_t tc_k1_bf16 = 0, tc_k1_fp8 = 0;
   uint32_t tc_bytes_bf16 = 0, tc_bytes_fp8 = 0;
-  float fp8_w_scale[3] = {0, 0, 0};
+  float fp8_w_scale[3] = {0, 0, 0};  // host copy of the FP8 weight scales (refreshed on demand)
+  float* w_scale_dev = nullptr;       // device copy, read by the kernels
   float fp8_act_scale[3] = {0, 0, 0};
   // decoupled variant (density march, alpha_c input, diffuse cubes)
   int variant = 0;
@@ -128,6 +129,9 @@ size_t workspace_bytes(int64_t n_rays);
 // Weight repacking for the tensor-core paths (mlp_tc.cu) and the upload of
 // all weight formats (host.cpp); both reuse existing device buffers.
 inolf_status prepare_tc_weights(Object& obj, const float* w1, const float* w2, const float* w3, void* stream);
+// The same packing (FP32, BF16 and FP8 blobs, FP8 weight scales) on the
+// device from device weights, asynchronously on `stream` (mlp_tc.cu).
+inolf_status pack_weights_device(Object& obj, const float* w1, const float* w2, const float* w3, void* stream);
 inolf_status upload_weights(Object& obj, const float* w1, const float* w2, const float* w3, void* stream);
 
 // Fills level l's unwrapped table from its canonical table (backward.cu).

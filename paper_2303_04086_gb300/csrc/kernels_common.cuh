@@ -41,7 +41,7 @@ struct Params {
   const void* tc_w;                   // blob used by this launch
   int32_t tc_k1;
   uint32_t tc_wbytes;
-  float fp8_w_scale[3];
+  const float* fp8_w_scale;           // device [3]
   float fp8_act_scale[3];
   float shc[10];
   // outputs

@@ -220,6 +220,103 @@ inolf_status prepare_tc_weights(Object& obj, const float* w1, const float* w2, c
     obj.tc_k1_fp8 = (int32_t)K1;
     obj.tc_bytes_fp8 = (uint32_t)blob.size();
   }
+  if (!obj.w_scale_dev) {
+    if (cudaMalloc(&obj.w_scale_dev, 4 * sizeof(float)) != cudaSuccess) return fail(INOLF_E_OOM, "cudaMalloc scales");
+    obj.bytes += 4 * sizeof(float);
+  }
+  if (cudaMemcpyAsync(obj.w_scale_dev, obj.fp8_w_scale, 3 * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return fail(INOLF_E_CUDA, "upload fp8 weight scales");
+  return INOLF_OK;
+}
+
+// Device-side repacking of all weight formats from device FP32 weights (one
+// CTA; the MLP has ~7 500 weights): the per-tensor FP8 weight scales amax /
+// 448, the FP32 SIMT blob and the BF16 / FP8 operand blobs, each written
+// exactly as prepare_tc_weights and upload_weights write them on the host.
+__device__ float block_amax(const float* w, int n, float* red) {
+  float m = 0.f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmaxf(m, fabsf(w[i]));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  m = 0.f;
+  for (int k = 0; k < (int)(blockDim.x >> 5); ++k) m = fmaxf(m, red[k]);
+  return m;
+}
+
+__global__ void k_pack_weights(const float* __restrict__ w1, const float* __restrict__ w2,
+                               const float* __restrict__ w3, int din, uint32_t K1b, uint32_t K1f, float* f32,
+                               uint8_t* bf16, uint8_t* fp8, float* scales) {
+  constexpr int H = INOLF_HIDDEN, O = INOLF_OUT;
+  __shared__ float red[32];
+  const float a1 = block_amax(w1, H * din, red), a2 = block_amax(w2, H * H, red), a3 = block_amax(w3, O * H, red);
+  const float s1 = a1 > 0 ? a1 / 448.0f : 1.0f, s2 = a2 > 0 ? a2 / 448.0f : 1.0f, s3 = a3 > 0 ? a3 / 448.0f : 1.0f;
+  if (threadIdx.x == 0) {
+    scales[0] = s1;
+    scales[1] = s2;
+    scales[2] = s3;
+  }
+  auto q = [](float v, float sc) { return (uint8_t)__nv_cvt_float_to_fp8(v / sc, __NV_SATFINITE, __NV_E4M3); };
+  auto dq = [](uint8_t b) {
+    __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)b, __NV_E4M3);
+    return __half2float(__half(h));
+  };
+  const int tid = threadIdx.x, nt = blockDim.x;
+  // FP32: W1T [din][64] | W2 [64][64] | W3T [64][4]
+  for (int i = tid; i < H * din; i += nt) {
+    const int j = i / din, k = i - j * din;
+    f32[k * H + j] = w1[i];
+  }
+  for (int i = tid; i < H * H; i += nt) f32[din * H + i] = w2[i];
+  for (int i = tid; i < O * H; i += nt) {
+    const int j = i / H, k = i - j * H;
+    f32[din * H + H * H + k * O + j] = w3[i];
+  }
+  // BF16: W1 (64 x K1b, zero padded) | W2 (64 x 64) in core matrices | W3^T FP32 of the rounded values
+  const uint32_t ch1 = K1b / 8;
+  for (int i = tid; i < H * (int)K1b; i += nt) {
+    const int n = i / (int)K1b, k = i - n * (int)K1b;
+    const __nv_bfloat16 v = __float2bfloat16_rn(k < din ? w1[n * din + k] : 0.0f);
+    *reinterpret_cast<__nv_bfloat16*>(bf16 + tc::core_off(n, k / 8, ch1) + (k % 8) * 2) = v;
+  }
+  uint8_t* b2 = bf16 + (size_t)H * K1b * 2;
+  for (int i = tid; i < H * H; i += nt) {
+    const int n = i / H, k = i - n * H;
+    *reinterpret_cast<__nv_bfloat16*>(b2 + tc::core_off(n, k / 8, 8) + (k % 8) * 2) = __float2bfloat16_rn(w2[i]);
+  }
+  float* b3 = reinterpret_cast<float*>(b2 + (size_t)H * H * 2);
+  for (int i = tid; i < O * H; i += nt) {
+    const int o = i / H, j = i - o * H;
+    b3[j * O + o] = __bfloat162float(__float2bfloat16_rn(w3[i]));
+  }
+  // FP8 e4m3: W1 (64 x K1f, zero padded) | W2 | W3^T FP32 of the dequantised values
+  const uint32_t cf1 = K1f / 16;
+  for (int i = tid; i < H * (int)K1f; i += nt) {
+    const int n = i / (int)K1f, k = i - n * (int)K1f;
+    fp8[tc::core_off(n, k / 16, cf1) + (k % 16)] = k < din ? q(w1[n * din + k], s1) : (uint8_t)0;
+  }
+  uint8_t* f2 = fp8 + (size_t)H * K1f;
+  for (int i = tid; i < H * H; i += nt) {
+    const int n = i / H, k = i - n * H;
+    f2[tc::core_off(n, k / 16, 4) + (k % 16)] = q(w2[i], s2);
+  }
+  float* f3 = reinterpret_cast<float*>(f2 + (size_t)H * H);
+  for (int i = tid; i < O * H; i += nt) {
+    const int o = i / H, j = i - o * H;
+    f3[j * O + o] = dq(q(w3[i], s3)) * s3;
+  }
+}
+
+inolf_status pack_weights_device(Object& obj, const float* w1, const float* w2, const float* w3, void* stream) {
+  if (!obj.w_f32 || !obj.w_bf16 || !obj.w_fp8 || !obj.w_scale_dev)
+    return fail(INOLF_E_INVALID, "pack_weights_device: object weights not allocated");
+  k_pack_weights<<<1, 1024, 0, (cudaStream_t)stream>>>(w1, w2, w3, obj.d_in, (uint32_t)obj.tc_k1_bf16,
+                                                      (uint32_t)obj.tc_k1_fp8, obj.w_f32, (uint8_t*)obj.w_bf16,
+                                                      (uint8_t*)obj.w_fp8, obj.w_scale_dev);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(INOLF_E_CUDA, std::string("k_pack_weights: ") + cudaGetErrorString(e));
   return INOLF_OK;
 }
 

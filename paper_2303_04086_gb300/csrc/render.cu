@@ -469,10 +469,8 @@ static void fill_common(const Object& obj, Params& p) {
   p.tc_k1_fp8 = obj.tc_k1_fp8;
   p.tc_bytes_bf16 = obj.tc_bytes_bf16;
   p.tc_bytes_fp8 = obj.tc_bytes_fp8;
-  for (int k = 0; k < 3; ++k) {
-    p.fp8_w_scale[k] = obj.fp8_w_scale[k];
-    p.fp8_act_scale[k] = obj.fp8_act_scale[k];
-  }
+  p.fp8_w_scale = obj.w_scale_dev;
+  for (int k = 0; k < 3; ++k) p.fp8_act_scale[k] = obj.fp8_act_scale[k];
   sh_constants(p.shc);
   p.variant = obj.variant;
   p.cub = obj.cub;
@@ -741,10 +739,10 @@ extern "C" inolf_status inolf_calibrate_fp8(inolf_object* obj, const float* cams
 
 extern "C" inolf_status inolf_object_get_fp8_scales(const inolf_object* obj, float act[3], float weight[3]) {
   if (!obj || !act || !weight) return fail(INOLF_E_INVALID, "inolf_object_get_fp8_scales: NULL argument");
-  for (int k = 0; k < 3; ++k) {
-    act[k] = obj->o.fp8_act_scale[k];
-    weight[k] = obj->o.fp8_w_scale[k];
-  }
+  // the weight scales live on the device (repacked there by inolf_object_load_params)
+  if (cudaMemcpy(weight, obj->o.w_scale_dev, 3 * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(INOLF_E_CUDA, "inolf_object_get_fp8_scales: readback failed");
+  for (int k = 0; k < 3; ++k) act[k] = obj->o.fp8_act_scale[k];
   return INOLF_OK;
 }
 

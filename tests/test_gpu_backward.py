@@ -180,3 +180,22 @@ def test_training_reduces_l2_loss(env):
         opt.step()
         losses.append(float(loss))
     assert np.mean(losses[-5:]) < 0.5 * np.mean(losses[:5]), losses[::10]
+
+
+def test_device_weight_repacking_matches_host_packing(env, tiny):
+    # inolf_object_load_params repacks the weights on the device; loading the
+    # object's own weights back must reproduce the host-packed BF16 / FP8
+    # operand blobs and FP8 scales bit for bit (renders unchanged)
+    torch, inolf, _ = env
+    obj = inolf.object_create(tiny)
+    cam = synth.camera((0.2, -0.1, 3.0))
+    inolf.calibrate_fp8(obj, cam[None], 64, 64)
+    before = {p: inolf.render(obj, cam[None], 64, 64, p).cpu().numpy() for p in ("fp32", "bf16", "fp8")}
+    act0, w0 = obj.fp8_scales()
+    tables, w1, w2, w3 = obj.read_params()
+    inolf.load_params(obj, None, torch.from_numpy(w1).cuda(), torch.from_numpy(w2).cuda(),
+                      torch.from_numpy(w3).cuda())
+    act1, w1s = obj.fp8_scales()
+    assert np.array_equal(w0, w1s) and np.array_equal(act0, act1)
+    for p, ref in before.items():
+        assert np.array_equal(inolf.render(obj, cam[None], 64, 64, p).cpu().numpy(), ref), p
