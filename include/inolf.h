@@ -266,6 +266,15 @@ inolf_status inolf_backward(const inolf_object* obj, const float* o, const float
                             const float* d_rgba, float* const* grad_tables, float* grad_w1, float* grad_w2,
                             float* grad_w3, void* workspace, size_t workspace_bytes, void* stream);
 
+/* inolf_backward for rays whose forward pass already ran: tri and t (device
+ * [n]) are that pass's tri_out / t_out (inolf_render_rays on the same rays,
+ * the object's proxy unchanged since), and the hit list is compacted from them
+ * instead of tracing the rays again.  Same outputs as inolf_backward. */
+inolf_status inolf_backward_hits(const inolf_object* obj, const float* o, const float* d, int64_t n,
+                                 const int32_t* tri, const float* t, const float* d_rgba, float* const* grad_tables,
+                                 float* grad_w1, float* grad_w2, float* grad_w3, void* workspace,
+                                 size_t workspace_bytes, void* stream);
+
 /* Replaces the object's parameters from DEVICE buffers (e.g. after an
  * optimiser step): tables_dev (host array of n_levels device pointers, each
  * m_l^3 x 2 FP32 in slot order; NULL array or NULL entries keep a level) and

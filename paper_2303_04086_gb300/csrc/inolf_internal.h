@@ -140,7 +140,8 @@ inolf_status expand_level_table(Object& o, int l, void* stream);
 // Backward over explicit rays (render.cu + backward.cu).
 inolf_status launch_backward_rays(const Object& obj, const float* o, const float* d, int64_t n, const float* d_rgba,
                                   float* const* grad_tables, float* gw1, float* gw2, float* gw3, void* workspace,
-                                  size_t workspace_bytes, void* stream);
+                                  size_t workspace_bytes, void* stream, const int32_t* tri_in = nullptr,
+                                  const float* t_in = nullptr);
 
 }  // namespace inolf
 

@@ -110,6 +110,19 @@ __global__ void __launch_bounds__(256) k_trace(const __grid_constant__ Params p,
   }
 }
 
+// Hit list of explicit rays from a forward pass's per-ray results (closest
+// triangle, -1 = miss, and t), with the same compaction, for a backward pass
+// that does not trace again.
+__global__ void __launch_bounds__(256) k_hits_from_results(const __grid_constant__ Params p, const int32_t* tri,
+                                                          const float* t) {
+  const int64_t ray = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  const bool valid = ray < p.n_rays;
+  const int32_t id = valid ? tri[ray] : -1;
+  const bool hit = valid && id >= 0;
+  const uint32_t pos = compact_hit(p, hit);
+  if (hit) p.hits[pos] = make_uint2((uint32_t)ray, __float_as_uint(t[ray]));
+}
+
 // The decoupled variant's hit estimation (Sec. 4.2, Eq. 4) in place of the
 // proxy trace: the density march of each ray, then the same compaction; the
 // hit record carries the hit sample's t and alpha_c goes alongside.
@@ -616,7 +629,7 @@ inolf_status launch_backward(const Params& p, const BwdParams& b, cudaStream_t s
 
 inolf_status launch_backward_rays(const Object& obj, const float* o, const float* d, int64_t n, const float* d_rgba,
                                   float* const* grad_tables, float* gw1, float* gw2, float* gw3, void* workspace,
-                                  size_t ws_bytes, void* stream) {
+                                  size_t ws_bytes, void* stream, const int32_t* tri_in, const float* t_in) {
   cudaStream_t st = (cudaStream_t)stream;
   if (obj.variant)
     return fail(INOLF_E_UNSUPPORTED, "backward: objects with density cubes have no backward in this library");
@@ -642,11 +655,20 @@ inolf_status launch_backward_rays(const Object& obj, const float* o, const float
     p.ray_base = r0;
     p.n_rays = nr;
     if (cudaMemsetAsync(p.counter, 0, 8, st) != cudaSuccess) return fail(INOLF_E_CUDA, "cudaMemsetAsync failed");
-    {
-      LaunchTimer lt("k_trace", st);
-      k_trace<<<(unsigned)((nr + 255) / 256), 256, 0, st>>>(p, 0, 0);
+    inolf_status s;
+    if (tri_in) {  // the forward's hits: compact them instead of tracing again
+      {
+        LaunchTimer lt("k_hits_from_results", st);
+        k_hits_from_results<<<(unsigned)((nr + 255) / 256), 256, 0, st>>>(p, tri_in + r0, t_in + r0);
+      }
+      s = check_launch("k_hits_from_results");
+    } else {
+      {
+        LaunchTimer lt("k_trace", st);
+        k_trace<<<(unsigned)((nr + 255) / 256), 256, 0, st>>>(p, 0, 0);
+      }
+      s = check_launch("k_trace");
     }
-    inolf_status s = check_launch("k_trace");
     if (s != INOLF_OK) return s;
     s = launch_backward(p, b, st);
     if (s != INOLF_OK) return s;
@@ -669,7 +691,22 @@ extern "C" inolf_status inolf_backward(const inolf_object* obj, const float* o, 
     if (!grad_tables[l]) return fail(INOLF_E_INVALID, "inolf_backward: missing gradient table");
   if (n == 0) return INOLF_OK;
   return launch_backward_rays(obj->o, o, d, n, d_rgba, grad_tables, grad_w1, grad_w2, grad_w3, workspace,
-                              workspace_bytes, stream);
+                              workspace_bytes, stream, nullptr, nullptr);
+}
+
+extern "C" inolf_status inolf_backward_hits(const inolf_object* obj, const float* o, const float* d, int64_t n,
+                                            const int32_t* tri, const float* t, const float* d_rgba,
+                                            float* const* grad_tables, float* grad_w1, float* grad_w2,
+                                            float* grad_w3, void* workspace, size_t workspace_bytes, void* stream) {
+  clear_error();
+  if (!obj || n < 0 ||
+      (n > 0 && (!o || !d || !tri || !t || !d_rgba || !grad_tables || !grad_w1 || !grad_w2 || !grad_w3)))
+    return fail(INOLF_E_INVALID, "inolf_backward_hits: bad argument");
+  for (int l = 0; n > 0 && l < obj->o.L; ++l)
+    if (!grad_tables[l]) return fail(INOLF_E_INVALID, "inolf_backward_hits: missing gradient table");
+  if (n == 0) return INOLF_OK;
+  return launch_backward_rays(obj->o, o, d, n, d_rgba, grad_tables, grad_w1, grad_w2, grad_w3, workspace,
+                              workspace_bytes, stream, tri, t);
 }
 
 extern "C" size_t inolf_render_workspace_bytes(int64_t n_rays) { return inolf::workspace_bytes(n_rays); }

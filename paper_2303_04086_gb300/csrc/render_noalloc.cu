@@ -18,7 +18,9 @@
 
 // Hit-list scratch of the allocation-free path: a 256-byte header (hit
 // counter and error flags) followed by one 8-byte (ray, t) record per ray,
-// for at most INOLF_NOALLOC_MAX_RAYS rays: 8 MiB + 256 B in total.
+// for at most INOLF_NOALLOC_MAX_RAYS rays: 8 MiB + 256 B in total.  Objects
+// with density cubes need 12 bytes per ray (alpha_c alongside); for them the
+// array holds 699 050 rays per pass and larger batches take several passes.
 static constexpr size_t kNoAllocBytes = 256 + 8 * (size_t)INOLF_NOALLOC_MAX_RAYS;
 static __device__ __align__(256) unsigned char inolf_noalloc_scratch[kNoAllocBytes];
 

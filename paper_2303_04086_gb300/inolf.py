@@ -95,6 +95,7 @@ def lib():
     L.inolf_render_rays_noalloc.argtypes = [vp, vp, vp, i64, i32, vp, vp, vp, vp]
     L.inolf_calibrate_fp8.argtypes = [vp, vp, i32, i32, i32, vp, sz, vp]
     L.inolf_backward.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, sz, vp]
+    L.inolf_backward_hits.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
     L.inolf_object_load_params.argtypes = [vp, vp, vp, vp, vp, vp]
     L.inolf_object_get_fp8_scales.argtypes = [vp, vp, vp]
     _lib = L
@@ -426,13 +427,21 @@ def stats_read() -> dict:
 # ---------------------------------------------------------------------------
 # training: backward, parameter updates, autograd
 # ---------------------------------------------------------------------------
-def backward(obj: Object, o, d, d_rgba, grad_tables, gw1, gw2, gw3, workspace=None, stream=None):
+def backward(obj: Object, o, d, d_rgba, grad_tables, gw1, gw2, gw3, workspace=None, stream=None, tri=None,
+             t=None):
     """inolf_backward: accumulate (+=) dLoss/d(tables, W1, W2, W3) for rays
-    (o, d) given dLoss/dRGBA; all tensors on the device, FP32."""
+    (o, d) given dLoss/dRGBA; all tensors on the device, FP32.  With the
+    forward's tri / t (inolf_backward_hits) the rays are not traced again."""
     n = o.shape[0]
     if workspace is None:
         workspace = _workspace(n, o.device)
-    tp = (ctypes.c_void_p * obj.L)(*[t.data_ptr() for t in grad_tables])
+    tp = (ctypes.c_void_p * obj.L)(*[x.data_ptr() for x in grad_tables])
+    if tri is not None:
+        _check(lib().inolf_backward_hits(obj.handle, _ptr(o), _ptr(d), n, _ptr(tri), _ptr(t), _ptr(d_rgba),
+                                         ctypes.cast(tp, ctypes.c_void_p), _ptr(gw1), _ptr(gw2), _ptr(gw3),
+                                         _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                         _stream(stream)))
+        return
     _check(lib().inolf_backward(obj.handle, _ptr(o), _ptr(d), n, _ptr(d_rgba), ctypes.cast(tp, ctypes.c_void_p),
                                 _ptr(gw1), _ptr(gw2), _ptr(gw3), _ptr(workspace),
                                 workspace.numel() * workspace.element_size(), _stream(stream)))
@@ -460,18 +469,20 @@ def _render_fn():
         @staticmethod
         def forward(ctx, o, d, field, prec, w1, w2, w3, *tables):
             load_params(field.obj, tables, w1, w2, w3)
-            rgba = render_rays(field.obj, o, d, prec)
-            ctx.save_for_backward(o, d)
+            tri = torch.empty(o.shape[0], dtype=torch.int32, device=o.device)
+            t = torch.empty(o.shape[0], dtype=torch.float32, device=o.device)
+            rgba = render_rays(field.obj, o, d, prec, tri_out=tri, t_out=t)
+            ctx.save_for_backward(o, d, tri, t)
             ctx.field = field
             return rgba
 
         @staticmethod
         def backward(ctx, g):
-            o, d = ctx.saved_tensors
+            o, d, tri, t = ctx.saved_tensors
             f = ctx.field
-            gt = [torch.zeros_like(t) for t in f.tables]
+            gt = [torch.zeros_like(x) for x in f.tables]
             g1, g2, g3 = torch.zeros_like(f.w1), torch.zeros_like(f.w2), torch.zeros_like(f.w3)
-            backward(f.obj, o, d, g.contiguous(), gt, g1, g2, g3)
+            backward(f.obj, o, d, g.contiguous(), gt, g1, g2, g3, tri=tri, t=t)  # the forward's hits
             return (None, None, None, None, g1, g2, g3, *gt)
 
     return _RenderRays

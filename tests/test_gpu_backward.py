@@ -199,3 +199,31 @@ def test_device_weight_repacking_matches_host_packing(env, tiny):
     assert np.array_equal(w0, w1s) and np.array_equal(act0, act1)
     for p, ref in before.items():
         assert np.array_equal(inolf.render(obj, cam[None], 64, 64, p).cpu().numpy(), ref), p
+
+
+def test_backward_from_forward_hits_equals_backward(env, tiny):
+    # inolf_backward_hits (hit list compacted from the forward's tri / t) gives
+    # the gradients inolf_backward gives after tracing again
+    torch, inolf, _ = env
+    obj = inolf.object_create(tiny)
+    rng = np.random.default_rng(5)
+    eye = rng.normal(size=(3000, 3))
+    eye = 2.6 * eye / np.linalg.norm(eye, axis=1, keepdims=True)
+    dd = rng.uniform(-1.1, 1.1, size=(3000, 3)) - eye
+    dd /= np.linalg.norm(dd, axis=1, keepdims=True)
+    o = torch.from_numpy(eye.astype(np.float32)).cuda()
+    d = torch.from_numpy(dd.astype(np.float32)).cuda()
+    tri = torch.empty(3000, dtype=torch.int32, device="cuda")
+    t = torch.empty(3000, dtype=torch.float32, device="cuda")
+    inolf.render_rays(obj, o, d, "fp32", tri_out=tri, t_out=t)
+    g = torch.from_numpy(np.random.default_rng(1).normal(size=(3000, 4)).astype(np.float32)).cuda()
+    out = []
+    for kw in ({}, {"tri": tri, "t": t}):
+        gt = [torch.zeros((obj.table_rows(l), 2), dtype=torch.float32, device="cuda") for l in range(obj.L)]
+        gw = [torch.zeros(s, dtype=torch.float32, device="cuda") for s in ((64, obj.d_in), (64, 64), (4, 64))]
+        inolf.backward(obj, o, d, g, gt, *gw, **kw)
+        torch.cuda.synchronize()
+        out.append([x.cpu().numpy() for x in gt + gw])
+    # atomics add in any order: equal up to FP32 rounding of the sums
+    for a, b in zip(*out):
+        assert _rel_l2(a, b) < 1e-5

@@ -87,3 +87,21 @@ def test_noalloc_rejects_batches_beyond_the_limit(setup):
         inolf.NOALLOC_MAX_RAYS + 1, inolf.FP32, ctypes.c_void_p(rgba.data_ptr()), None, None, None)
     assert st == inolf.E_INVALID
     assert "limit" in inolf.last_error()
+
+
+def test_noalloc_serves_density_cube_objects(setup):
+    # an object of the decoupled variant keeps 12 bytes per hit-list entry
+    # (alpha_c alongside); the fixed array then holds fewer rays per pass, so
+    # a batch larger than that is rendered in several passes, still equal to
+    # the workspace-based entry point
+    torch, inolf, _ = setup
+    from paper_2303_04086_gb300 import synth
+    dobj = inolf.object_create(synth.tiny_density_scene(seed=1))
+    n = 900_000  # above the 699 050 rays one pass of the array holds for this object kind
+    o_np, d_np = _rays(n, 21)
+    o, d = torch.from_numpy(o_np).cuda(), torch.from_numpy(d_np).cuda()
+    ref = _call_workspace(torch, inolf, dobj, o, d)
+    got = _call_noalloc(torch, inolf, dobj, o, d)
+    assert np.array_equal(got[1], ref[1]) and np.array_equal(got[2].view(np.int32), ref[2].view(np.int32))
+    assert np.abs(got[0] - ref[0]).max() <= RGBA_TOL
+    assert (ref[1] >= 0).mean() > 0.2
