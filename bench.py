@@ -421,35 +421,60 @@ def run_training(steps=40, batch=1 << 18, n_views=100, res=800, prec="bf16"):
     d = a[..., None] * c[:, None, 3:6] + b[..., None] * c[:, None, 6:9] + c[:, None, 9:12]
     d = (d / d.norm(dim=-1, keepdim=True)).reshape(-1, 3).contiguous()
     o = c[:, None, 0:3].expand(-1, res * res, -1).reshape(-1, 3).contiguous()
-    opt = torch.optim.Adam(field.parameters(), lr=1e-2, betas=(0.9, 0.99), eps=1e-15)
-    gen = torch.Generator(device="cuda").manual_seed(0)
+    opt = torch.optim.Adam(field.parameters(), lr=1e-2, betas=(0.9, 0.99), eps=1e-15, capturable=True)
+    torch.manual_seed(0)
     losses = []
 
     def one():
-        idx = torch.randint(0, o.shape[0], (batch,), device="cuda", generator=gen)
+        idx = torch.randint(0, o.shape[0], (batch,), device="cuda")
         pred = field.render(o[idx], d[idx], prec)
         loss = ((pred - tgt[idx]) ** 2).sum(1).mean()
-        opt.zero_grad()
+        opt.zero_grad(set_to_none=False)
         loss.backward()
         opt.step()
-        return loss
+        return loss.detach()
 
-    for _ in range(3):
-        losses.append(one().detach())
+    # warm-up on a side stream (allocations, one-time kernel attributes), then
+    # the whole step -- sampling, inolf forward, inolf backward, Adam -- is
+    # captured once as a CUDA graph and replayed; eager steps if capture fails
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            losses.append(one())
+    torch.cuda.current_stream().wait_stream(side)
     torch.cuda.synchronize()
+    graph, static_loss = None, None
+    try:
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            static_loss = one()
+        torch.cuda.synchronize()
+    except Exception as e:  # eager fallback, reported
+        graph = None
+        capture_error = str(e)[:200]
+        torch.cuda.synchronize()
     inolf.stats_reset()
-    inolf.stats_enable(True)
+    inolf.stats_enable(graph is None)
     t0 = time.perf_counter()
     for _ in range(steps):  # losses stay on the device: no host synchronisation inside the loop
-        losses.append(one().detach())
+        if graph is not None:
+            graph.replay()
+            losses.append(static_loss.clone())
+        else:
+            losses.append(one())
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     inolf.stats_enable(False)
     kern = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / steps} for k, v in inolf.stats_read().items()}
     losses = [float(x) for x in losses]
-    return {"steps_per_s": steps / dt, "rays_per_step": batch, "mrays_per_s": steps * batch / dt / 1e6,
-            "loss_first": losses[0], "loss_last": losses[-1], "forward": prec, "backward": "fp32",
-            "views": n_views, "res": res, "kernels": kern}
+    out = {"steps_per_s": steps / dt, "rays_per_step": batch, "mrays_per_s": steps * batch / dt / 1e6,
+           "loss_first": losses[0], "loss_last": losses[-1], "forward": prec, "backward": "fp32",
+           "views": n_views, "res": res, "cuda_graph": graph is not None}
+    if graph is None:
+        out["kernels"] = kern
+        out["capture_error"] = capture_error
+    return out
 
 
 def run_variant(steps=3, warmup=3, views=N_VIEWS, precisions=("fp32", "bf16", "fp8"), oracle_pixels=100_000):
