@@ -28,6 +28,7 @@
 
 #include "inolf_internal.h"
 #include "kernels_common.cuh"
+#include "tc_ptx.cuh"
 
 namespace inolf {
 
@@ -338,6 +339,52 @@ __device__ __forceinline__ void block_gemm_4x8(const float* __restrict__ act, co
   }
 }
 
+// Input tile of one hit ray, written by its two gather threads (half 0 and
+// 1): features of levels half, half + 2, ... (each with the next level's Phi
+// loads in flight), the SH encoding and alpha_c (half 1), the diffuse colour
+// and tint of the variant (half 0), all into the [k][kF32Tile] FP32 tile;
+// invalid slots are zero.  Returns the ray index of the hit record.
+__device__ __forceinline__ int64_t gather_tile_f32(const Params& p, uint32_t h, bool valid, int ray_slot, int half,
+                                                   float* act, float* dif) {
+  if (!valid) {
+    for (int k = half; k < p.d_in; k += 2) act[k * kF32Tile + ray_slot] = 0.0f;
+    return 0;
+  }
+  const uint2 rec = p.hits[h];
+  const int64_t ray = rec.x;
+  float o[3], d[3], x[3];
+  ray_of(p, ray, o, d);
+  hit_unit_coords(p, o, d, __uint_as_float(rec.y), x);
+  LevelFetchX fa, fb;
+  if (half < p.L) fetch_phi_x(p.lv[half], x, fa);
+  for (int l = half; l < p.L; l += 4) {  // levels half, half + 2, ... in pairs, no state copies
+    float e0, e1;
+    if (l + 2 < p.L) fetch_phi_x(p.lv[l + 2], x, fb);
+    finish_level_x(p.lv[l], p.fp16, fa, e0, e1);
+    act[(2 * l) * kF32Tile + ray_slot] = e0;
+    act[(2 * l + 1) * kF32Tile + ray_slot] = e1;
+    if (l + 2 >= p.L) break;
+    if (l + 4 < p.L) fetch_phi_x(p.lv[l + 4], x, fa);
+    finish_level_x(p.lv[l + 2], p.fp16, fb, e0, e1);
+    act[(2 * (l + 2)) * kF32Tile + ray_slot] = e0;
+    act[(2 * (l + 2) + 1) * kF32Tile + ray_slot] = e1;
+  }
+  if (half == 1) {
+    float sh[16];
+    sh16(p, d, sh);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) act[(2 * p.L + k) * kF32Tile + ray_slot] = sh[k];
+    if (p.variant) act[(2 * p.L + 16) * kF32Tile + ray_slot] = p.hit_alpha[h];  // alpha_c (Eq. 5)
+  } else if (p.variant) {
+    const float4 dc = cube_diffuse(p.cub, x);
+    dif[0 * kF32Tile + ray_slot] = dc.x;
+    dif[1 * kF32Tile + ray_slot] = dc.y;
+    dif[2 * kF32Tile + ray_slot] = dc.z;
+    dif[3 * kF32Tile + ray_slot] = dc.w;
+  }
+  return ray;
+}
+
 __global__ void __launch_bounds__(kF32Threads, 3) k_shade_f32_tiled(const __grid_constant__ Params p) {
   extern __shared__ float4 smem4[];
   float* sm = reinterpret_cast<float*>(smem4);
@@ -365,45 +412,7 @@ __global__ void __launch_bounds__(kF32Threads, 3) k_shade_f32_tiled(const __grid
   for (uint32_t base = blockIdx.x * kF32Tile; base < total; base += gridDim.x * kF32Tile) {
     const uint32_t h = base + (uint32_t)ray_slot;
     const bool valid = h < total;
-    int64_t ray = 0;
-    float o[3], d[3];
-    if (valid) {
-      const uint2 rec = p.hits[h];
-      ray = rec.x;
-      float x[3];
-      ray_of(p, ray, o, d);
-      hit_unit_coords(p, o, d, __uint_as_float(rec.y), x);
-      // levels half, half + 2, ... with the next level's Phi loads in flight
-      LevelFetchX fa, fb;
-      if (half < p.L) fetch_phi_x(p.lv[half], x, fa);
-      for (int l = half; l < p.L; l += 4) {  // levels half, half + 2, ... in pairs, no state copies
-        float e0, e1;
-        if (l + 2 < p.L) fetch_phi_x(p.lv[l + 2], x, fb);
-        finish_level_x(p.lv[l], p.fp16, fa, e0, e1);
-        act[(2 * l) * kF32Tile + ray_slot] = e0;
-        act[(2 * l + 1) * kF32Tile + ray_slot] = e1;
-        if (l + 2 >= p.L) break;
-        if (l + 4 < p.L) fetch_phi_x(p.lv[l + 4], x, fa);
-        finish_level_x(p.lv[l + 2], p.fp16, fb, e0, e1);
-        act[(2 * (l + 2)) * kF32Tile + ray_slot] = e0;
-        act[(2 * (l + 2) + 1) * kF32Tile + ray_slot] = e1;
-      }
-      if (half == 1) {
-        float sh[16];
-        sh16(p, d, sh);
-#pragma unroll
-        for (int k = 0; k < 16; ++k) act[(2 * p.L + k) * kF32Tile + ray_slot] = sh[k];
-        if (p.variant) act[(2 * p.L + 16) * kF32Tile + ray_slot] = p.hit_alpha[h];  // alpha_c (Eq. 5)
-      } else if (p.variant) {
-        const float4 dc = cube_diffuse(p.cub, x);
-        dif[0 * kF32Tile + ray_slot] = dc.x;
-        dif[1 * kF32Tile + ray_slot] = dc.y;
-        dif[2 * kF32Tile + ray_slot] = dc.z;
-        dif[3 * kF32Tile + ray_slot] = dc.w;
-      }
-    } else {
-      for (int k = half; k < din; k += 2) act[k * kF32Tile + ray_slot] = 0.0f;
-    }
+    const int64_t ray = gather_tile_f32(p, h, valid, ray_slot, half, act, dif);
     __syncthreads();
     float acc[4][8];
     block_gemm_4x8(act, W1T, din, r0, c0, acc);
@@ -443,6 +452,175 @@ __global__ void __launch_bounds__(kF32Threads, 3) k_shade_f32_tiled(const __grid
       }
     }
     __syncthreads();  // before the next tile overwrites the activations
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_shade_f32_ws: the FP32 shade of k_shade_f32_tiled with the gather and the
+// MLP on separate warps, so that the latency-bound gather of some tiles runs
+// beside the FMA-bound MLP of others.  One persistent CTA per SM:
+//   * kWsTeams gather teams of 256 threads (two per ray, as in
+//     gather_tile_f32) fill a ring of kWsSlots input tiles in shared memory;
+//     local tile k goes to slot k % kWsSlots and is gathered by team
+//     k % kWsTeams;
+//   * 256 MLP threads take the tiles in order: layer 1 from the slot (which
+//     is released right after it), layers 2 and 3 through a private hidden
+//     tile, RGBA out.
+// Slot hand-over uses two mbarriers per slot (full: 256 gather arrivals,
+// empty: 256 MLP arrivals), every wait bounded by the global timer; a group
+// whose wait runs out flags bit 4 of the workspace error word and stops, and
+// the others then run out in turn.  Group-internal barriers are named
+// barriers (id 1: MLP threads, 2 + t: team t).
+// ---------------------------------------------------------------------------
+static constexpr int kWsTeams = 2;
+static constexpr int kWsSlots = 4;
+static constexpr int kWsThreads = 256 * (kWsTeams + 1);
+static constexpr uint64_t kRingWaitLimitNs = 2000000000ull;  // 2 s; one tile takes microseconds
+// Register split (setmaxnreg): the CTA is launched with kWsLaunchRegs per
+// thread (the host checks the compiled count before every launch); the
+// gather warpgroups give registers back, the MLP warpgroups take them.
+static constexpr int kWsLaunchRegs = 80;
+static constexpr int kWsGatherRegs = 64;
+static constexpr int kWsMlpRegs = 112;
+static_assert(kWsTeams * 256 * kWsGatherRegs + 256 * kWsMlpRegs <= kWsThreads * kWsLaunchRegs,
+              "register split exceeds the CTA's launch allocation");
+static_assert(kWsThreads * kWsLaunchRegs <= 65536, "launch allocation exceeds the register file");
+
+__device__ __forceinline__ void named_sync(uint32_t id, uint32_t n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+// OR of v over the n threads of named barrier id (all of them must call it)
+__device__ __forceinline__ bool named_any(bool v, uint32_t id, uint32_t n) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, %2, %3, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(id), "r"(n)
+      : "memory");
+  return r != 0;
+}
+
+// shared-memory floats of one ring slot: inputs [d_in][tile], diffuse
+// [4][tile], ray ids [tile]
+__host__ __device__ constexpr int ws_slot_floats(int din) { return (din + 5) * kF32Tile; }
+
+__global__ void __launch_bounds__(kWsThreads, 1) k_shade_f32_ws(const __grid_constant__ Params p) {
+  extern __shared__ float4 smem4[];
+  float* sm = reinterpret_cast<float*>(smem4);
+  const int din = p.d_in;
+  float* W1T = sm;              // [din][64]
+  float* W2T = W1T + din * 64;  // [64][64] (W2 transposed: [in][out])
+  float* W3 = W2T + 64 * 64;    // [4][64]
+  float* hid = W3 + 4 * 64;     // [64][kF32Tile] hidden activations (MLP threads)
+  float* ring = hid + 64 * kF32Tile;
+  const int slot_floats = ws_slot_floats(din);
+  uint64_t* full = reinterpret_cast<uint64_t*>(ring + kWsSlots * slot_floats);
+  uint64_t* empty = full + kWsSlots;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int s = 0; s < kWsSlots; ++s) {
+      tc::mbar_init(&full[s], 256);
+      tc::mbar_init(&empty[s], 256);
+    }
+    tc::fence_mbar_init();
+  }
+  {
+    const float* g = p.w_f32;
+    for (int k = tid; k < din * 64; k += kWsThreads) W1T[k] = g[k];
+    const float* g2 = g + din * 64;  // W2 [out][in]
+    for (int k = tid; k < 64 * 64; k += kWsThreads) W2T[(k & 63) * 64 + (k >> 6)] = g2[k];
+    const float* g3 = g2 + 64 * 64;  // W3T [in][4]
+    for (int k = tid; k < 64 * 4; k += kWsThreads) W3[(k & 3) * 64 + (k >> 2)] = g3[k];
+  }
+  __syncthreads();
+  const uint32_t total = *p.counter;
+  const uint32_t n_tiles = (total + kF32Tile - 1) / kF32Tile;
+  const uint32_t n_k = blockIdx.x < n_tiles ? (n_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0u;
+  const int group = tid >> 8, gt = tid & 255;
+  const int ray_slot = gt & (kF32Tile - 1), half = gt >> 7;
+
+  if (group < kWsTeams) {  // ---- gather team ----
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kWsGatherRegs));
+    for (uint32_t k = (uint32_t)group; k < n_k; k += kWsTeams) {
+      const uint32_t s = k % kWsSlots;
+      if (k >= (uint32_t)kWsSlots) {  // the MLP threads released the tile k - kWsSlots
+        const bool ok = tc::mbar_wait(&empty[s], (k / kWsSlots - 1u) & 1u, kRingWaitLimitNs);
+        if (named_any(!ok, 2u + (uint32_t)group, 256u)) {
+          if (gt == 0) atomicOr(p.counter + 1, 4u);
+          break;
+        }
+      }
+      float* in = ring + s * slot_floats;
+      float* dif = in + din * kF32Tile;
+      uint32_t* rid = reinterpret_cast<uint32_t*>(dif + 4 * kF32Tile);
+      const uint32_t h = (blockIdx.x + k * gridDim.x) * kF32Tile + (uint32_t)ray_slot;
+      const int64_t ray = gather_tile_f32(p, h, h < total, ray_slot, half, in, dif);
+      if (half == 0) rid[ray_slot] = (uint32_t)ray;
+      tc::mbar_arrive(&full[s]);
+    }
+    return;
+  }
+
+  // ---- MLP threads: block of rays r0..r0+3, neurons c0..c0+7 ----
+  asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kWsMlpRegs));
+  const int r0 = (gt & 31) * 4, c0 = (gt >> 5) * 8;
+  for (uint32_t k = 0; k < n_k; ++k) {
+    const uint32_t s = k % kWsSlots;
+    const bool ok = tc::mbar_wait(&full[s], (k / kWsSlots) & 1u, kRingWaitLimitNs);
+    if (named_any(!ok, 1u, 256u)) {
+      if (gt == 0) atomicOr(p.counter + 1, 4u);
+      break;
+    }
+    const float* in = ring + s * slot_floats;
+    const float* dif = in + din * kF32Tile;
+    const uint32_t* rid = reinterpret_cast<const uint32_t*>(dif + 4 * kF32Tile);
+    const uint32_t h = (blockIdx.x + k * gridDim.x) * kF32Tile + (uint32_t)ray_slot;
+    const bool valid = h < total;
+    // what layer 3 needs from the slot, read before the slot is released
+    const uint32_t ray = valid ? rid[ray_slot] : 0u;
+    float tint = 0.f, dc0 = 0.f, dc1 = 0.f;
+    if (p.variant && valid) {
+      tint = dif[3 * kF32Tile + ray_slot];
+      dc0 = dif[(2 * half) * kF32Tile + ray_slot];
+      dc1 = dif[1 * kF32Tile + ray_slot];
+    }
+    float acc[4][8];
+    block_gemm_4x8(in, W1T, din, r0, c0, acc);
+    if (k + kWsSlots < n_k) tc::mbar_arrive(&empty[s]);
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      *reinterpret_cast<float4*>(hid + (c0 + j) * kF32Tile + r0) =
+          make_float4(fmaxf(acc[0][j], 0.f), fmaxf(acc[1][j], 0.f), fmaxf(acc[2][j], 0.f), fmaxf(acc[3][j], 0.f));
+    named_sync(1u, 256u);
+    block_gemm_4x8(hid, W2T, 64, r0, c0, acc);
+    named_sync(1u, 256u);
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      *reinterpret_cast<float4*>(hid + (c0 + j) * kF32Tile + r0) =
+          make_float4(fmaxf(acc[0][j], 0.f), fmaxf(acc[1][j], 0.f), fmaxf(acc[2][j], 0.f), fmaxf(acc[3][j], 0.f));
+    named_sync(1u, 256u);
+    {  // layer 3: output channel pair (2 half, 2 half + 1) of ray ray_slot
+      float z0 = 0.f, z1 = 0.f;
+      const float* w0 = W3 + (2 * half) * 64;
+      const float* w1 = w0 + 64;
+#pragma unroll 8
+      for (int j = 0; j < 64; ++j) {
+        const float a = hid[j * kF32Tile + ray_slot];
+        z0 = fmaf(w0[j], a, z0);
+        z1 = fmaf(w1[j], a, z1);
+      }
+      if (valid) {
+        float* out = reinterpret_cast<float*>(p.rgba + (p.ray_base + (int64_t)ray));
+        float2 v = make_float2(sigmoidf_(z0), sigmoidf_(z1));
+        if (p.variant) {  // c = c_d + tint c_s (Eq. 7); alpha stays F_s's
+          v.x = fmaf(tint, v.x, dc0);
+          if (half == 0) v.y = fmaf(tint, v.y, dc1);
+        }
+        *reinterpret_cast<float2*>(out + 2 * half) = v;
+      }
+    }
+    named_sync(1u, 256u);  // the hidden tile is read before the next tile's layer 1 overwrites it
   }
 }
 
@@ -552,6 +730,19 @@ inolf_status launch_render(const Object& obj, const RayBatch& rays, inolf_precis
     cudaGetLastError();
   });
   const int f32_grid = sm_count() * f32_ctas;
+  const size_t smem_ws = (size_t)(obj.d_in * 64 + 64 * 64 + 4 * 64 + 64 * kF32Tile + kWsSlots * ws_slot_floats(obj.d_in)) *
+                             sizeof(float) + 2 * kWsSlots * sizeof(uint64_t);
+  static std::once_flag ws_once;
+  static bool ws_ok = false;  // compiled with the register count its split assumes
+  std::call_once(ws_once, [&] {
+    cudaFuncAttributes fa{};
+    ws_ok = cudaFuncGetAttributes(&fa, k_shade_f32_ws) == cudaSuccess && fa.numRegs == kWsLaunchRegs;
+    const int din_max = 2 * INOLF_MAX_LEVELS + 17;
+    const size_t mx = (size_t)(din_max * 64 + 64 * 64 + 4 * 64 + 64 * kF32Tile + kWsSlots * ws_slot_floats(din_max)) *
+                          sizeof(float) + 2 * kWsSlots * sizeof(uint64_t);
+    cudaFuncSetAttribute(k_shade_f32_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
+    cudaGetLastError();
+  });
 
   auto run_chunk = [&](int64_t n_chunk, int32_t tiles_x, int32_t tiles_y, int64_t trace_blocks) -> inolf_status {
     if (cudaMemsetAsync(counter, 0, 8, st) != cudaSuccess) return fail(INOLF_E_CUDA, "cudaMemsetAsync failed");
@@ -585,7 +776,8 @@ inolf_status launch_render(const Object& obj, const RayBatch& rays, inolf_precis
     if (prec == INOLF_FP32) {
       {
         LaunchTimer lt("k_shade_f32", st);
-        k_shade_f32_tiled<<<f32_grid, kF32Threads, smem_f32_tiled, st>>>(p);
+        if (ws_ok) k_shade_f32_ws<<<sm_count(), kWsThreads, smem_ws, st>>>(p);
+        else k_shade_f32_tiled<<<f32_grid, kF32Threads, smem_f32_tiled, st>>>(p);
       }
       return check_launch("k_shade_f32");
     }
