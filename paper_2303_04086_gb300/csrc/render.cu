@@ -317,9 +317,11 @@ __device__ __forceinline__ void fma2_rn(float& c0, float& c1, float a, float2 w)
   c1 = __uint_as_float((uint32_t)(c >> 32));
 }
 
+// acc[i][j] = sum_k act[k][r0 + i] wT[k][n_j]: act [K][kF32Tile] (ray
+// fastest), wT [K][64]; the 8 neurons n_j sit at columns w0 .. w0 + 3 and
+// w1 .. w1 + 3 of wT (c0 and c0 + 4 in the natural layout).
 __device__ __forceinline__ void block_gemm_4x8(const float* __restrict__ act, const float* __restrict__ wT, int K,
-                                               int r0, int c0, float acc[4][8]) {
-  // act: [K][kF32Tile] (ray fastest), wT: [K][64] (neuron fastest)
+                                               int r0, int w0c, int w1c, float acc[4][8]) {
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -327,8 +329,8 @@ __device__ __forceinline__ void block_gemm_4x8(const float* __restrict__ act, co
 #pragma unroll 4
   for (int k = 0; k < K; ++k) {
     const float4 a = *reinterpret_cast<const float4*>(act + k * kF32Tile + r0);
-    const float4 w0 = *reinterpret_cast<const float4*>(wT + k * 64 + c0);
-    const float4 w1 = *reinterpret_cast<const float4*>(wT + k * 64 + c0 + 4);
+    const float4 w0 = *reinterpret_cast<const float4*>(wT + k * 64 + w0c);
+    const float4 w1 = *reinterpret_cast<const float4*>(wT + k * 64 + w1c);
     const float av[4] = {a.x, a.y, a.z, a.w};
     const float2 wp[4] = {make_float2(w0.x, w0.y), make_float2(w0.z, w0.w), make_float2(w1.x, w1.y),
                           make_float2(w1.z, w1.w)};
@@ -415,14 +417,14 @@ __global__ void __launch_bounds__(kF32Threads, 3) k_shade_f32_tiled(const __grid
     const int64_t ray = gather_tile_f32(p, h, valid, ray_slot, half, act, dif);
     __syncthreads();
     float acc[4][8];
-    block_gemm_4x8(act, W1T, din, r0, c0, acc);
+    block_gemm_4x8(act, W1T, din, r0, c0, c0 + 4, acc);
     __syncthreads();  // every thread has read the inputs
 #pragma unroll
     for (int j = 0; j < 8; ++j)
       *reinterpret_cast<float4*>(act + (c0 + j) * kF32Tile + r0) =
           make_float4(fmaxf(acc[0][j], 0.f), fmaxf(acc[1][j], 0.f), fmaxf(acc[2][j], 0.f), fmaxf(acc[3][j], 0.f));
     __syncthreads();
-    block_gemm_4x8(act, W2T, 64, r0, c0, acc);
+    block_gemm_4x8(act, W2T, 64, r0, c0, c0 + 4, acc);
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < 8; ++j)
@@ -458,33 +460,39 @@ __global__ void __launch_bounds__(kF32Threads, 3) k_shade_f32_tiled(const __grid
 // ---------------------------------------------------------------------------
 // k_shade_f32_ws: the FP32 shade of k_shade_f32_tiled with the gather and the
 // MLP on separate warps, so that the latency-bound gather of some tiles runs
-// beside the FMA-bound MLP of others.  One persistent CTA per SM:
-//   * kWsTeams gather teams of 256 threads (two per ray, as in
+// beside the FMA-bound MLP of others.  One persistent CTA of 768 threads per
+// SM:
+//   * kWsTeams = 2 gather teams of 256 threads (two per ray, as in
 //     gather_tile_f32) fill a ring of kWsSlots input tiles in shared memory;
 //     local tile k goes to slot k % kWsSlots and is gathered by team
 //     k % kWsTeams;
-//   * 256 MLP threads take the tiles in order: layer 1 from the slot (which
-//     is released right after it), layers 2 and 3 through a private hidden
-//     tile, RGBA out.
+//   * 256 MLP threads take the tiles in order.  Warp w owns rays
+//     16 w .. 16 w + 15 and all 64 neurons; lane l computes the 4-ray x
+//     8-neuron block (rays 16 w + 4 (l & 3) .., neurons 8 (l >> 2) ..).
+//     Layer 1 reads the slot (released right after it), layer 2 a private
+//     hidden tile; layer 3 is folded into layer 2's epilogue: each lane
+//     forms the partial sums of its 8 neurons for its 4 rays x 4 outputs,
+//     and the 8 lanes of a ray group add them by a butterfly over lane bits
+//     2..4 that leaves each lane one ray's channel pair.
+// The staged W1^T and W2^T rows are permuted so that the first and second
+// float4 of the 8 neuron octets are 128 contiguous bytes each: every shared-
+// memory load of the layer loops is one wavefront.
 // Slot hand-over uses two mbarriers per slot (full: 256 gather arrivals,
 // empty: 256 MLP arrivals), every wait bounded by the global timer; a group
 // whose wait runs out flags bit 4 of the workspace error word and stops, and
 // the others then run out in turn.  Group-internal barriers are named
-// barriers (id 1: MLP threads, 2 + t: team t).
+// barriers (id 1: MLP threads, 2 + t: team t).  Registers are split with
+// setmaxnreg: the CTA is launched with kWsLaunchRegs per thread (the host
+// checks the compiled count before launching), the gather warpgroups give
+// registers back and the MLP warpgroups take them.
 // ---------------------------------------------------------------------------
-static constexpr int kWsTeams = 2;
-static constexpr int kWsSlots = 4;
-static constexpr int kWsThreads = 256 * (kWsTeams + 1);
-static constexpr uint64_t kRingWaitLimitNs = 2000000000ull;  // 2 s; one tile takes microseconds
-// Register split (setmaxnreg): the CTA is launched with kWsLaunchRegs per
-// thread (the host checks the compiled count before every launch); the
-// gather warpgroups give registers back, the MLP warpgroups take them.
-static constexpr int kWsLaunchRegs = 80;
-static constexpr int kWsGatherRegs = 64;
-static constexpr int kWsMlpRegs = 112;
-static_assert(kWsTeams * 256 * kWsGatherRegs + 256 * kWsMlpRegs <= kWsThreads * kWsLaunchRegs,
+static constexpr int kWsTeams = 2, kWsSlots = 4, kWsMlp = 256;
+static constexpr int kWsThreads = 256 * kWsTeams + kWsMlp;
+static constexpr int kWsLaunchRegs = 80, kWsGatherRegs = 64, kWsMlpRegs = 112;
+static_assert(kWsTeams * 256 * kWsGatherRegs + kWsMlp * kWsMlpRegs <= kWsThreads * kWsLaunchRegs,
               "register split exceeds the CTA's launch allocation");
 static_assert(kWsThreads * kWsLaunchRegs <= 65536, "launch allocation exceeds the register file");
+static constexpr uint64_t kRingWaitLimitNs = 2000000000ull;  // 2 s; one tile takes microseconds
 
 __device__ __forceinline__ void named_sync(uint32_t id, uint32_t n) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
@@ -504,15 +512,35 @@ __device__ __forceinline__ bool named_any(bool v, uint32_t id, uint32_t n) {
 // shared-memory floats of one ring slot: inputs [d_in][tile], diffuse
 // [4][tile], ray ids [tile]
 __host__ __device__ constexpr int ws_slot_floats(int din) { return (din + 5) * kF32Tile; }
+__host__ __device__ constexpr size_t ws_smem_bytes(int din) {
+  return (size_t)(din * 64 + 64 * 64 + 4 * 64 + 64 * kF32Tile + kWsSlots * ws_slot_floats(din)) * sizeof(float) +
+         2 * kWsSlots * sizeof(uint64_t);
+}
+// column of neuron c in the permuted W^T rows: octet c / 8, float4 half (c / 4) & 1
+__device__ __forceinline__ int ws_wcol(int c) { return ((c >> 2) & 1) * 32 + (c >> 3) * 4 + (c & 3); }
+
+// Adds v over the lanes that differ in lane bit `bit`, keeping the half of
+// the n values selected by that bit (reduce-scatter step): v[0 .. n/2) is
+// the kept half afterwards.
+template <int n>
+__device__ __forceinline__ void butterfly_keep(float (&v)[16], int bit) {
+  const bool hi = (threadIdx.x >> bit) & 1;
+#pragma unroll
+  for (int m = 0; m < n / 2; ++m) {
+    const float mine = hi ? v[n / 2 + m] : v[m];
+    const float give = hi ? v[m] : v[n / 2 + m];
+    v[m] = mine + __shfl_xor_sync(0xffffffffu, give, 1 << bit);
+  }
+}
 
 __global__ void __launch_bounds__(kWsThreads, 1) k_shade_f32_ws(const __grid_constant__ Params p) {
   extern __shared__ float4 smem4[];
   float* sm = reinterpret_cast<float*>(smem4);
   const int din = p.d_in;
-  float* W1T = sm;              // [din][64]
-  float* W2T = W1T + din * 64;  // [64][64] (W2 transposed: [in][out])
-  float* W3 = W2T + 64 * 64;    // [4][64]
-  float* hid = W3 + 4 * 64;     // [64][kF32Tile] hidden activations (MLP threads)
+  float* W1T = sm;              // [din][64], permuted columns
+  float* W2T = W1T + din * 64;  // [64][64] (W2 transposed: [in][out]), permuted columns
+  float* W3T = W2T + 64 * 64;   // [64][4]
+  float* hid = W3T + 4 * 64;    // [64][kF32Tile] hidden activations (MLP threads)
   float* ring = hid + 64 * kF32Tile;
   const int slot_floats = ws_slot_floats(din);
   uint64_t* full = reinterpret_cast<uint64_t*>(ring + kWsSlots * slot_floats);
@@ -521,32 +549,32 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_shade_f32_ws(const __grid_con
   if (tid == 0) {
     for (int s = 0; s < kWsSlots; ++s) {
       tc::mbar_init(&full[s], 256);
-      tc::mbar_init(&empty[s], 256);
+      tc::mbar_init(&empty[s], kWsMlp);
     }
     tc::fence_mbar_init();
   }
   {
-    const float* g = p.w_f32;
-    for (int k = tid; k < din * 64; k += kWsThreads) W1T[k] = g[k];
+    const float* g = p.w_f32;  // W1^T [din][64]
+    for (int k = tid; k < din * 64; k += kWsThreads) W1T[(k & ~63) + ws_wcol(k & 63)] = g[k];
     const float* g2 = g + din * 64;  // W2 [out][in]
-    for (int k = tid; k < 64 * 64; k += kWsThreads) W2T[(k & 63) * 64 + (k >> 6)] = g2[k];
-    const float* g3 = g2 + 64 * 64;  // W3T [in][4]
-    for (int k = tid; k < 64 * 4; k += kWsThreads) W3[(k & 3) * 64 + (k >> 2)] = g3[k];
+    for (int k = tid; k < 64 * 64; k += kWsThreads) W2T[(k & 63) * 64 + ws_wcol(k >> 6)] = g2[k];
+    const float* g3 = g2 + 64 * 64;  // W3^T [in][4]
+    for (int k = tid; k < 64 * 4; k += kWsThreads) W3T[k] = g3[k];
   }
   __syncthreads();
   const uint32_t total = *p.counter;
   const uint32_t n_tiles = (total + kF32Tile - 1) / kF32Tile;
   const uint32_t n_k = blockIdx.x < n_tiles ? (n_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0u;
-  const int group = tid >> 8, gt = tid & 255;
-  const int ray_slot = gt & (kF32Tile - 1), half = gt >> 7;
 
-  if (group < kWsTeams) {  // ---- gather team ----
+  if (tid < 256 * kWsTeams) {  // ---- gather team tid / 256 ----
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kWsGatherRegs));
-    for (uint32_t k = (uint32_t)group; k < n_k; k += kWsTeams) {
+    const int team = tid >> 8, gt = tid & 255;
+    const int ray_slot = gt & (kF32Tile - 1), half = gt >> 7;
+    for (uint32_t k = (uint32_t)team; k < n_k; k += kWsTeams) {
       const uint32_t s = k % kWsSlots;
       if (k >= (uint32_t)kWsSlots) {  // the MLP threads released the tile k - kWsSlots
         const bool ok = tc::mbar_wait(&empty[s], (k / kWsSlots - 1u) & 1u, kRingWaitLimitNs);
-        if (named_any(!ok, 2u + (uint32_t)group, 256u)) {
+        if (named_any(!ok, 2u + (uint32_t)team, 256u)) {
           if (gt == 0) atomicOr(p.counter + 1, 4u);
           break;
         }
@@ -562,65 +590,70 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_shade_f32_ws(const __grid_con
     return;
   }
 
-  // ---- MLP threads: block of rays r0..r0+3, neurons c0..c0+7 ----
+  // ---- MLP threads ----
   asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kWsMlpRegs));
-  const int r0 = (gt & 31) * 4, c0 = (gt >> 5) * 8;
+  const int mt = tid - 256 * kWsTeams, lane = mt & 31, warp = mt >> 5;
+  const int r0 = warp * 16 + (lane & 3) * 4, nb = lane >> 2, c0 = nb * 8;
+  // after the butterfly: ray r0 + out_i, channels 2 out_cp, 2 out_cp + 1
+  const int out_i = ((lane >> 4) & 1) * 2 + ((lane >> 3) & 1), out_cp = (lane >> 2) & 1;
+  const int out_ray = r0 + out_i;
   for (uint32_t k = 0; k < n_k; ++k) {
     const uint32_t s = k % kWsSlots;
     const bool ok = tc::mbar_wait(&full[s], (k / kWsSlots) & 1u, kRingWaitLimitNs);
-    if (named_any(!ok, 1u, 256u)) {
-      if (gt == 0) atomicOr(p.counter + 1, 4u);
+    if (named_any(!ok, 1u, (uint32_t)kWsMlp)) {
+      if (mt == 0) atomicOr(p.counter + 1, 4u);
       break;
     }
     const float* in = ring + s * slot_floats;
     const float* dif = in + din * kF32Tile;
     const uint32_t* rid = reinterpret_cast<const uint32_t*>(dif + 4 * kF32Tile);
-    const uint32_t h = (blockIdx.x + k * gridDim.x) * kF32Tile + (uint32_t)ray_slot;
+    const uint32_t h = (blockIdx.x + k * gridDim.x) * kF32Tile + (uint32_t)out_ray;
     const bool valid = h < total;
-    // what layer 3 needs from the slot, read before the slot is released
-    const uint32_t ray = valid ? rid[ray_slot] : 0u;
-    float tint = 0.f, dc0 = 0.f, dc1 = 0.f;
+    // what the output needs from the slot, read before the slot is released
+    const uint32_t ray = valid ? rid[out_ray] : 0u;
+    float dc0 = 0.f, dc1 = 0.f, tint = 0.f;
     if (p.variant && valid) {
-      tint = dif[3 * kF32Tile + ray_slot];
-      dc0 = dif[(2 * half) * kF32Tile + ray_slot];
-      dc1 = dif[1 * kF32Tile + ray_slot];
+      dc0 = dif[(2 * out_cp) * kF32Tile + out_ray];
+      dc1 = dif[(2 * out_cp + 1) * kF32Tile + out_ray];  // unused for the alpha channel
+      tint = dif[3 * kF32Tile + out_ray];
     }
     float acc[4][8];
-    block_gemm_4x8(in, W1T, din, r0, c0, acc);
+    block_gemm_4x8(in, W1T, din, r0, nb * 4, 32 + nb * 4, acc);
     if (k + kWsSlots < n_k) tc::mbar_arrive(&empty[s]);
 #pragma unroll
     for (int j = 0; j < 8; ++j)
       *reinterpret_cast<float4*>(hid + (c0 + j) * kF32Tile + r0) =
           make_float4(fmaxf(acc[0][j], 0.f), fmaxf(acc[1][j], 0.f), fmaxf(acc[2][j], 0.f), fmaxf(acc[3][j], 0.f));
-    named_sync(1u, 256u);
-    block_gemm_4x8(hid, W2T, 64, r0, c0, acc);
-    named_sync(1u, 256u);
+    named_sync(1u, (uint32_t)kWsMlp);
+    block_gemm_4x8(hid, W2T, 64, r0, nb * 4, 32 + nb * 4, acc);
+    // layer 3 partial sums of this lane's 8 neurons: v[4 i + c], ray r0 + i, output c
+    float v[16];
 #pragma unroll
-    for (int j = 0; j < 8; ++j)
-      *reinterpret_cast<float4*>(hid + (c0 + j) * kF32Tile + r0) =
-          make_float4(fmaxf(acc[0][j], 0.f), fmaxf(acc[1][j], 0.f), fmaxf(acc[2][j], 0.f), fmaxf(acc[3][j], 0.f));
-    named_sync(1u, 256u);
-    {  // layer 3: output channel pair (2 half, 2 half + 1) of ray ray_slot
-      float z0 = 0.f, z1 = 0.f;
-      const float* w0 = W3 + (2 * half) * 64;
-      const float* w1 = w0 + 64;
-#pragma unroll 8
-      for (int j = 0; j < 64; ++j) {
-        const float a = hid[j * kF32Tile + ray_slot];
-        z0 = fmaf(w0[j], a, z0);
-        z1 = fmaf(w1[j], a, z1);
-      }
-      if (valid) {
-        float* out = reinterpret_cast<float*>(p.rgba + (p.ray_base + (int64_t)ray));
-        float2 v = make_float2(sigmoidf_(z0), sigmoidf_(z1));
-        if (p.variant) {  // c = c_d + tint c_s (Eq. 7); alpha stays F_s's
-          v.x = fmaf(tint, v.x, dc0);
-          if (half == 0) v.y = fmaf(tint, v.y, dc1);
-        }
-        *reinterpret_cast<float2*>(out + 2 * half) = v;
+    for (int q = 0; q < 16; ++q) v[q] = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float4 w = *reinterpret_cast<const float4*>(W3T + (c0 + j) * 4);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float a = fmaxf(acc[i][j], 0.f);
+        v[4 * i + 0] = fmaf(w.x, a, v[4 * i + 0]);
+        v[4 * i + 1] = fmaf(w.y, a, v[4 * i + 1]);
+        v[4 * i + 2] = fmaf(w.z, a, v[4 * i + 2]);
+        v[4 * i + 3] = fmaf(w.w, a, v[4 * i + 3]);
       }
     }
-    named_sync(1u, 256u);  // the hidden tile is read before the next tile's layer 1 overwrites it
+    butterfly_keep<16>(v, 4);  // rays (0, 1) or (2, 3)
+    butterfly_keep<8>(v, 3);   // one ray
+    butterfly_keep<4>(v, 2);   // one channel pair: v[0], v[1]
+    if (valid) {
+      float2 o = make_float2(sigmoidf_(v[0]), sigmoidf_(v[1]));
+      if (p.variant) {  // c = c_d + tint c_s (Eq. 7); alpha stays F_s's
+        o.x = fmaf(tint, o.x, dc0);
+        if (out_cp == 0) o.y = fmaf(tint, o.y, dc1);
+      }
+      *reinterpret_cast<float2*>(reinterpret_cast<float*>(p.rgba + (p.ray_base + (int64_t)ray)) + 2 * out_cp) = o;
+    }
+    named_sync(1u, (uint32_t)kWsMlp);  // layer 2 has read the hidden tile before the next tile's layer 1 writes it
   }
 }
 
@@ -730,16 +763,13 @@ inolf_status launch_render(const Object& obj, const RayBatch& rays, inolf_precis
     cudaGetLastError();
   });
   const int f32_grid = sm_count() * f32_ctas;
-  const size_t smem_ws = (size_t)(obj.d_in * 64 + 64 * 64 + 4 * 64 + 64 * kF32Tile + kWsSlots * ws_slot_floats(obj.d_in)) *
-                             sizeof(float) + 2 * kWsSlots * sizeof(uint64_t);
+  const size_t smem_ws = ws_smem_bytes(obj.d_in);
   static std::once_flag ws_once;
   static bool ws_ok = false;  // compiled with the register count its split assumes
   std::call_once(ws_once, [&] {
     cudaFuncAttributes fa{};
     ws_ok = cudaFuncGetAttributes(&fa, k_shade_f32_ws) == cudaSuccess && fa.numRegs == kWsLaunchRegs;
-    const int din_max = 2 * INOLF_MAX_LEVELS + 17;
-    const size_t mx = (size_t)(din_max * 64 + 64 * 64 + 4 * 64 + 64 * kF32Tile + kWsSlots * ws_slot_floats(din_max)) *
-                          sizeof(float) + 2 * kWsSlots * sizeof(uint64_t);
+    const size_t mx = ws_smem_bytes(2 * INOLF_MAX_LEVELS + 17);
     cudaFuncSetAttribute(k_shade_f32_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
     cudaGetLastError();
   });
