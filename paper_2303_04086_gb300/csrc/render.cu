@@ -478,10 +478,12 @@ __global__ void __launch_bounds__(kF32Threads, 3) k_shade_f32_tiled(const __grid
 // float4 of the 8 neuron octets are 128 contiguous bytes each: every shared-
 // memory load of the layer loops is one wavefront.
 // Slot hand-over uses two mbarriers per slot (full: 256 gather arrivals,
-// empty: 256 MLP arrivals), every wait bounded by the global timer; a group
+// empty: 256 MLP arrivals), every wait bounded by the global timer; a warp
 // whose wait runs out flags bit 4 of the workspace error word and stops, and
-// the others then run out in turn.  Group-internal barriers are named
-// barriers (id 1: MLP threads, 2 + t: team t).  Registers are split with
+// the others then run out in turn.  No other barrier joins warps: a gather
+// warp writes its own rays of a tile, and an MLP warp's hidden activations
+// are its own 16 columns of the hidden tile, so every warp runs at its own
+// pace between the slot barriers.  Registers are split with
 // setmaxnreg: the CTA is launched with kWsLaunchRegs per thread (the host
 // checks the compiled count before launching), the gather warpgroups give
 // registers back and the MLP warpgroups take them.
@@ -493,21 +495,6 @@ static_assert(kWsTeams * 256 * kWsGatherRegs + kWsMlp * kWsMlpRegs <= kWsThreads
               "register split exceeds the CTA's launch allocation");
 static_assert(kWsThreads * kWsLaunchRegs <= 65536, "launch allocation exceeds the register file");
 static constexpr uint64_t kRingWaitLimitNs = 2000000000ull;  // 2 s; one tile takes microseconds
-
-__device__ __forceinline__ void named_sync(uint32_t id, uint32_t n) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
-}
-// OR of v over the n threads of named barrier id (all of them must call it)
-__device__ __forceinline__ bool named_any(bool v, uint32_t id, uint32_t n) {
-  uint32_t r;
-  asm volatile(
-      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, %2, %3, p;\n\t"
-      "selp.u32 %0, 1, 0, q;\n\t}\n"
-      : "=r"(r)
-      : "r"((uint32_t)v), "r"(id), "r"(n)
-      : "memory");
-  return r != 0;
-}
 
 // shared-memory floats of one ring slot: inputs [d_in][tile], diffuse
 // [4][tile], ray ids [tile]
@@ -574,8 +561,8 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_shade_f32_ws(const __grid_con
       const uint32_t s = k % kWsSlots;
       if (k >= (uint32_t)kWsSlots) {  // the MLP threads released the tile k - kWsSlots
         const bool ok = tc::mbar_wait(&empty[s], (k / kWsSlots - 1u) & 1u, kRingWaitLimitNs);
-        if (named_any(!ok, 2u + (uint32_t)team, 256u)) {
-          if (gt == 0) atomicOr(p.counter + 1, 4u);
+        if (__any_sync(0xffffffffu, !ok)) {
+          if ((gt & 31) == 0) atomicOr(p.counter + 1, 4u);
           break;
         }
       }
@@ -600,8 +587,8 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_shade_f32_ws(const __grid_con
   for (uint32_t k = 0; k < n_k; ++k) {
     const uint32_t s = k % kWsSlots;
     const bool ok = tc::mbar_wait(&full[s], (k / kWsSlots) & 1u, kRingWaitLimitNs);
-    if (named_any(!ok, 1u, (uint32_t)kWsMlp)) {
-      if (mt == 0) atomicOr(p.counter + 1, 4u);
+    if (__any_sync(0xffffffffu, !ok)) {
+      if (lane == 0) atomicOr(p.counter + 1, 4u);
       break;
     }
     const float* in = ring + s * slot_floats;
@@ -624,7 +611,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_shade_f32_ws(const __grid_con
     for (int j = 0; j < 8; ++j)
       *reinterpret_cast<float4*>(hid + (c0 + j) * kF32Tile + r0) =
           make_float4(fmaxf(acc[0][j], 0.f), fmaxf(acc[1][j], 0.f), fmaxf(acc[2][j], 0.f), fmaxf(acc[3][j], 0.f));
-    named_sync(1u, (uint32_t)kWsMlp);
+    __syncwarp();  // the warp's own 16 hidden columns
     block_gemm_4x8(hid, W2T, 64, r0, nb * 4, 32 + nb * 4, acc);
     // layer 3 partial sums of this lane's 8 neurons: v[4 i + c], ray r0 + i, output c
     float v[16];
@@ -653,7 +640,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_shade_f32_ws(const __grid_con
       }
       *reinterpret_cast<float2*>(reinterpret_cast<float*>(p.rgba + (p.ray_base + (int64_t)ray)) + 2 * out_cp) = o;
     }
-    named_sync(1u, (uint32_t)kWsMlp);  // layer 2 has read the hidden tile before the next tile's layer 1 writes it
+    __syncwarp();  // layer 2 has read the hidden columns before the next tile's layer 1 writes them
   }
 }
 
