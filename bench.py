@@ -170,10 +170,10 @@ def make_workload(small: bool, views: int):
 
 # DRAM bytes (read + write) per hit ray of the current shade kernels, from one
 # ncu capture of a one-view launch of the full workload (cold L2), see
-# profiles/k_shade_f32_tiled_full_1view.md: 1.358 GB + 0.068 GB for 4 010 637
+# profiles/k_shade_f32_ws_full_1view.md: 1.104 GB + 0.065 GB for 4 010 637
 # hit rays.  Traffic grows in proportion to the hit rays rendered, so a launch's
 # traffic is this figure times its hit rays.  None once the kernel changes.
-DRAM_BYTES_PER_HIT = {"k_shade_f32": (1.358243e9 + 67.909888e6) / 4010637}
+DRAM_BYTES_PER_HIT = {"k_shade_f32": (1.103592e9 + 65.239040e6) / 4010637}
 
 
 def algorithmic_bytes_per_hit(scene) -> int:
