@@ -216,6 +216,30 @@ def kernel_rooflines(kernels, scene, n_rays, n_hit, steps, peaks):
     return out
 
 
+def add_probed_rooflines(rooflines, probed, scene, n_rays, n_hit, steps, kernels_by_prec, tstats):
+    """The same kernels against the microbenchmarked peaks (inolf_probe_peaks):
+    the PSH gather's random loads (16 per level and hit ray: 8 Phi + 8 table
+    entries) against the L2 random-read rate, the FP32 SIMT MLP against the
+    packed-FMA rate, and the trace kernel's BVH node visits per second (node
+    visits per ray from inolf_trace_stats on view 0)."""
+    for prec, kern in kernels_by_prec.items():
+        for name, st in kern.items():
+            if not st.get("launches") or name not in rooflines.get(prec, {}):
+                continue
+            sec = st["ms"] / 1e3
+            r = rooflines[prec][name]
+            if name.startswith("k_shade"):
+                loads = 16 * scene.n_levels * n_hit * steps / sec / 1e9
+                r["gather_gloads_per_s"] = loads
+                r["frac_l2_random_read_probe"] = loads / probed["l2_gather_gsps"]
+                if name == "k_shade_f32":
+                    r["frac_fp32_fma_probe"] = r["mlp_tflops"] / probed["fp32_tflops"]
+            elif name == "k_trace" and tstats:
+                r["node_visits_per_ray"] = tstats["node_visits_per_ray"]
+                r["triangle_tests_per_ray"] = tstats["triangle_tests_per_ray"]
+                r["gnode_visits_per_s"] = tstats["node_visits_per_ray"] * n_rays * steps / sec / 1e9
+
+
 def cpu_baseline(scene, cams, W, H, budget_s=12.0, orc=None):
     """The FP64 oracle as it stands, on a seeded pixel sample of view 0."""
     import oracle
@@ -828,6 +852,17 @@ def run_native(a):
     for prec, pr in precisions.items():
         if "kernels" in pr:
             out["kernel_rooflines"][prec] = kernel_rooflines(pr["kernels"], scene, n_rays, n_hit, a.steps, peaks)
+    if rank == 0:
+        try:  # measurement aids outside the timed region; the bench line stands without them
+            probed = inolf.probe_peaks()
+            tstats = inolf.trace_stats(obj, cams[:1], W, H)
+            by_prec = {"fp32": stats}
+            by_prec.update({k: v["kernels"] for k, v in precisions.items() if "kernels" in v})
+            add_probed_rooflines(out["kernel_rooflines"], probed, scene, n_rays, n_hit, a.steps, by_prec, tstats)
+            out["peaks_probed"] = probed
+            out["trace_stats_view0"] = tstats
+        except Exception as e:  # noqa: BLE001
+            out["peaks_probed"] = {"error": str(e)[:200]}
     if fp32_acc is not None:
         out["accuracy_vs_oracle"] = fp32_acc
     if rank == 0 and not a.small:

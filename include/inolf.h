@@ -461,6 +461,35 @@ inolf_status inolf_stats_reset(void);
  * entries in out (host), the number of kernels in *n. */
 inolf_status inolf_stats_read(inolf_kernel_stat* out, int32_t max, int32_t* n);
 
+/* Traversal statistics of the closest-hit BVH step (Sec. 4.2's hit point on
+ * the proxy mesh) for n_views pinhole views of W x H pixels, as rendered by
+ * inolf_render: the trace kernel alone runs, each warp's 8 x 4-pixel packet
+ * counting its own steps.  out (host, 5 entries): [0] rays, [1] hit rays,
+ * [2] inner-node visits summed over packets, [3] triangle tests summed over
+ * packets, [4] packets.  Every ray of a packet takes all of its packet's
+ * steps, so [2] / [4] is the node visits per ray.  cams is host memory as for
+ * inolf_render; workspace as for inolf_render (>= the size for the rays of
+ * one view).  Synchronises `stream`.  E_INVALID for objects without a proxy
+ * mesh (density cubes). */
+inolf_status inolf_trace_stats(const inolf_object* obj, const float* cams, int32_t n_views, int32_t W, int32_t H,
+                               int64_t* out, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Device peaks measured by microbenchmarks, the denominators of the rooflines
+ * that the HBM copy and BF16 GEMM figures do not cover:
+ *   l2_read_gbs     streaming 16-byte reads of an L2-resident 32 MB buffer,
+ *                   bypassing L1 (GB/s);
+ *   l2_gather_gsps  independent random 8-byte reads of the same buffer,
+ *                   bypassing L1: one 32-byte sector each (G reads/s);
+ *   fp32_tflops     packed FP32 fused multiply-adds (fma.rn.f32x2) on
+ *                   registers (TFLOP/s, 2 flop per multiply-add).
+ * Allocates and frees a 32 MB device buffer; synchronises `stream`. */
+typedef struct {
+  double l2_read_gbs;
+  double l2_gather_gsps;
+  double fp32_tflops;
+} inolf_peaks;
+inolf_status inolf_probe_peaks(inolf_peaks* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -14,7 +14,8 @@ LIB = os.path.join(HERE, "libinolf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O3", "--cudart", "shared",
                      "-diag-suppress", "177"]
-SOURCES = ["host.cpp", "render.cu", "mlp_tc.cu", "stats.cpp", "render_noalloc.cu", "backward.cu", "serve.cu", "sched.cpp"]
+SOURCES = ["host.cpp", "render.cu", "mlp_tc.cu", "stats.cpp", "render_noalloc.cu", "backward.cu", "serve.cu", "sched.cpp",
+           "probes.cu"]
 
 
 def _nvcc() -> str:

@@ -122,7 +122,7 @@ struct RayBatch {
 inolf_status launch_render(const Object& obj, const RayBatch& rays, inolf_precision prec, float* rgba,
                            int32_t* tri_out, float* t_out, uint32_t* slots_out, float* feat_out,
                            void* workspace, size_t workspace_bytes, void* stream, bool amax = false,
-                           float* alpha_out = nullptr, bool hits_only = false);
+                           float* alpha_out = nullptr, bool hits_only = false, bool count_trace = false);
 
 size_t workspace_bytes(int64_t n_rays);
 

@@ -311,9 +311,14 @@ __device__ __forceinline__ void closest_hit(const Params& p, const float o[3], c
 // the per-ray traversal's.  All control flow depends on warp votes only, so
 // the warp stays converged; lanes without a ray pass active = false.  Must
 // be called by all 32 lanes of the warp.
+// kCount: also returns the warp's inner-node visits and triangle tests (the
+// same in every lane: the packet moves as one).
+template <bool kCount = false>
 __device__ __forceinline__ void closest_hit_packet(const float4* __restrict__ nodes, const float4* __restrict__ tris,
                                                    uint32_t* err, bool active, const float o[3], const float d[3],
-                                                   int32_t& best_id, float& best_t) {
+                                                   int32_t& best_id, float& best_t, uint32_t* n_inner = nullptr,
+                                                   uint32_t* n_tests = nullptr) {
+  uint32_t visits = 0, tests = 0;
   float inv[3], oi[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
@@ -335,6 +340,7 @@ __device__ __forceinline__ void closest_hit_packet(const float4* __restrict__ no
     }
     const float lim = best_id < 0 ? INFINITY : best_t * 1.00002f + 1e-5f;
     if (cur_cnt == 0) {
+      if (kCount) ++visits;
       const float4 nx = __ldg(nodes + 4 * cur + 0);
       const float4 ny = __ldg(nodes + 4 * cur + 1);
       const float4 nz = __ldg(nodes + 4 * cur + 2);
@@ -367,6 +373,7 @@ __device__ __forceinline__ void closest_hit_packet(const float4* __restrict__ no
         continue;
       }
     } else {
+      if (kCount) tests += (uint32_t)cur_cnt;
       for (int32_t k = 0; k < cur_cnt; ++k) {
         const float4 a = __ldg(tris + 3 * (cur + k) + 0);
         const float4 b = __ldg(tris + 3 * (cur + k) + 1);
@@ -393,6 +400,10 @@ __device__ __forceinline__ void closest_hit_packet(const float4* __restrict__ no
     if (!found) break;
   }
   if (best_id < 0) best_t = 0.0f;
+  if (kCount) {
+    *n_inner = visits;
+    *n_tests = tests;
+  }
 }
 
 // Scene-unit coordinates of the hit point: P = o + t d, x = (P - lo) * scale.

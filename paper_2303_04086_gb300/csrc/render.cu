@@ -81,6 +81,11 @@ __device__ __forceinline__ uint32_t compact_hit(const Params& p, bool hit) {
   return s_base + s_warp[warp] + __popc(mask & ((1u << lane) - 1u));
 }
 
+// Workspace words 8 .. 13 (three uint64): with kCount, k_trace adds each
+// packet's inner-node visits, triangle tests and hit rays there.
+static constexpr int kTraceCountWord = 8;
+
+template <bool kCount>
 __global__ void __launch_bounds__(256) k_trace(const __grid_constant__ Params p, int32_t tiles_x, int32_t tiles_y) {
   int64_t ray;
   float o[3], d[3];
@@ -93,7 +98,17 @@ __global__ void __launch_bounds__(256) k_trace(const __grid_constant__ Params p,
 #pragma unroll
       for (int k = 0; k < 3; ++k) { o[k] = 0.0f; d[k] = 1.0f; }
     }
-    closest_hit_packet(p.nodes, p.tris, p.counter + 1, valid, o, d, tri, t);
+    uint32_t visits = 0, tests = 0;
+    closest_hit_packet<kCount>(p.nodes, p.tris, p.counter + 1, valid, o, d, tri, t, &visits, &tests);
+    if (kCount) {
+      const uint32_t hits = __popc(__ballot_sync(0xffffffffu, valid && tri >= 0));
+      if ((threadIdx.x & 31) == 0) {
+        unsigned long long* c = reinterpret_cast<unsigned long long*>(p.counter + kTraceCountWord);
+        atomicAdd(c + 0, (unsigned long long)visits);
+        atomicAdd(c + 1, (unsigned long long)tests);
+        atomicAdd(c + 2, (unsigned long long)hits);
+      }
+    }
   } else if (valid) {
     closest_hit(p, o, d, tri, t);
   }
@@ -707,7 +722,7 @@ inolf_status launch_shade_tc(const Params& p, inolf_precision prec, cudaStream_t
 inolf_status launch_render(const Object& obj, const RayBatch& rays, inolf_precision prec, float* rgba,
                            int32_t* tri_out, float* t_out, uint32_t* slots_out, float* feat_out,
                            void* workspace, size_t ws_bytes, void* stream, bool amax, float* alpha_out,
-                           bool hits_only) {
+                           bool hits_only, bool count_trace) {
   cudaStream_t st = (cudaStream_t)stream;
   if (!workspace || ws_bytes < workspace_bytes(1) || ((uintptr_t)workspace & 15))
     return fail(INOLF_E_INVALID, "render: workspace missing, too small or not 16-byte aligned");
@@ -774,7 +789,8 @@ inolf_status launch_render(const Object& obj, const RayBatch& rays, inolf_precis
     } else {
       {
         LaunchTimer lt("k_trace", st);
-        k_trace<<<(unsigned)trace_blocks, 256, 0, st>>>(p, tiles_x, tiles_y);
+        if (count_trace) k_trace<true><<<(unsigned)trace_blocks, 256, 0, st>>>(p, tiles_x, tiles_y);
+        else k_trace<false><<<(unsigned)trace_blocks, 256, 0, st>>>(p, tiles_x, tiles_y);
       }
       inolf_status s = check_launch("k_trace");
       if (s != INOLF_OK) return s;
@@ -874,7 +890,7 @@ inolf_status launch_backward_rays(const Object& obj, const float* o, const float
     } else {
       {
         LaunchTimer lt("k_trace", st);
-        k_trace<<<(unsigned)((nr + 255) / 256), 256, 0, st>>>(p, 0, 0);
+        k_trace<false><<<(unsigned)((nr + 255) / 256), 256, 0, st>>>(p, 0, 0);
       }
       s = check_launch("k_trace");
     }
@@ -936,6 +952,41 @@ extern "C" inolf_status inolf_render(const inolf_object* obj, const float* cams,
   rb.n = (int64_t)n_views * W * H;
   return launch_render(obj->o, rb, prec, rgba_out, tri_out, t_out, nullptr, nullptr, workspace, workspace_bytes,
                        stream);
+}
+
+extern "C" inolf_status inolf_trace_stats(const inolf_object* obj, const float* cams, int32_t n_views, int32_t W,
+                                          int32_t H, int64_t* out, void* workspace, size_t workspace_bytes,
+                                          void* stream) {
+  clear_error();
+  if (!obj || !cams || !out || n_views <= 0 || W <= 0 || H <= 0)
+    return fail(INOLF_E_INVALID, "inolf_trace_stats: bad argument");
+  if (obj->o.variant) return fail(INOLF_E_INVALID, "inolf_trace_stats: the object has no proxy mesh");
+  if (!workspace || workspace_bytes < inolf::workspace_bytes(1) || ((uintptr_t)workspace & 15))
+    return fail(INOLF_E_INVALID, "inolf_trace_stats: workspace missing, too small or not 16-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  uint64_t* dev = reinterpret_cast<uint64_t*>(static_cast<uint32_t*>(workspace) + kTraceCountWord);
+  if (cudaMemsetAsync(dev, 0, 3 * sizeof(uint64_t), st) != cudaSuccess)
+    return fail(INOLF_E_CUDA, "cudaMemsetAsync failed");
+  RayBatch rb{};
+  rb.mode = 0;
+  rb.cams = cams;
+  rb.n_views = n_views;
+  rb.W = W;
+  rb.H = H;
+  rb.n = (int64_t)n_views * W * H;
+  inolf_status s = launch_render(obj->o, rb, INOLF_FP32, nullptr, nullptr, nullptr, nullptr, nullptr, workspace,
+                                 workspace_bytes, stream, false, nullptr, true, true);
+  if (s != INOLF_OK) return s;
+  uint64_t h[3] = {0, 0, 0};
+  if (cudaMemcpyAsync(h, dev, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return fail(INOLF_E_CUDA, "inolf_trace_stats: reading the counters failed");
+  out[0] = rb.n;
+  out[1] = (int64_t)h[2];
+  out[2] = (int64_t)h[0];
+  out[3] = (int64_t)h[1];
+  out[4] = (int64_t)n_views * ((W + 15) / 16) * ((H + 15) / 16) * 8;  // 8 x 4-ray packets
+  return INOLF_OK;
 }
 
 extern "C" inolf_status inolf_render_rays(const inolf_object* obj, const float* o, const float* d, int64_t n,

@@ -51,6 +51,11 @@ class CubesDesc(ctypes.Structure):
                 ("alpha_miss", ctypes.c_float)]
 
 
+class Peaks(ctypes.Structure):
+    _fields_ = [("l2_read_gbs", ctypes.c_double), ("l2_gather_gsps", ctypes.c_double),
+                ("fp32_tflops", ctypes.c_double)]
+
+
 class ObjectDesc(ctypes.Structure):
     _fields_ = [("n_vertices", ctypes.c_int32), ("n_triangles", ctypes.c_int32),
                 ("vertices", ctypes.c_void_p), ("triangles", ctypes.c_void_p),
@@ -92,6 +97,8 @@ def lib():
     L.inolf_encode_rays.argtypes = [vp, vp, vp, i64, vp, vp, vp, sz, vp]
     L.inolf_march_rays.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp, sz, vp]
     L.inolf_render_host.argtypes = [vp, vp, i32, i32, i32, i32, vp, vp, sz, vp, sz, vp]
+    L.inolf_trace_stats.argtypes = [vp, vp, i32, i32, i32, vp, vp, sz, vp]
+    L.inolf_probe_peaks.argtypes = [ctypes.POINTER(Peaks), vp]
     L.inolf_render_rays_noalloc.argtypes = [vp, vp, vp, i64, i32, vp, vp, vp, vp]
     L.inolf_calibrate_fp8.argtypes = [vp, vp, i32, i32, i32, vp, sz, vp]
     L.inolf_backward.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, sz, vp]
@@ -300,6 +307,29 @@ def render(obj: Object, cams: np.ndarray, W: int, H: int, prec="fp32", rgba_out=
                               _ptr(t_out), _ptr(workspace), workspace.numel() * workspace.element_size(),
                               _stream(stream)))
     return rgba_out
+
+
+def trace_stats(obj: Object, cams: np.ndarray, W: int, H: int, workspace=None, stream=None) -> dict:
+    """inolf_trace_stats: rays, hit rays, BVH inner-node visits and triangle
+    tests of the closest-hit packets of pinhole views (cams: host [n, 13])."""
+    cams = np.ascontiguousarray(cams, np.float32).reshape(-1, 13)
+    nv = len(cams)
+    if workspace is None:
+        workspace = _workspace(min(nv, 16) * W * H, "cuda")
+    out = np.zeros(5, np.int64)
+    _check(lib().inolf_trace_stats(obj.handle, cams.ctypes.data, nv, W, H, out.ctypes.data, _ptr(workspace),
+                                   workspace.numel() * workspace.element_size(), _stream(stream)))
+    rays, hits, inner, tests, packets = (int(v) for v in out)
+    return {"rays": rays, "hit_rays": hits, "inner_node_visits": inner, "triangle_tests": tests, "packets": packets,
+            "node_visits_per_ray": inner / max(packets, 1), "triangle_tests_per_ray": tests / max(packets, 1)}
+
+
+def probe_peaks(stream=None) -> dict:
+    """inolf_probe_peaks: L2 streaming-read GB/s, L2 random 8-byte reads
+    (G/s) and packed FP32 FMA TFLOP/s measured by microbenchmarks."""
+    pk = Peaks()
+    _check(lib().inolf_probe_peaks(ctypes.byref(pk), _stream(stream)))
+    return {"l2_read_gbs": pk.l2_read_gbs, "l2_gather_gsps": pk.l2_gather_gsps, "fp32_tflops": pk.fp32_tflops}
 
 
 def render_host(obj: Object, cams: np.ndarray, W: int, H: int, prec="fp32", host_out=None, staging=None,

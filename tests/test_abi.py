@@ -45,6 +45,9 @@ def test_render_rejects_bad_arguments_before_any_launch(lib):
     assert lib.inolf_render_rays(None, None, None, -1, 0, None, None, None, None, 0, None) == inolf.E_INVALID
     assert lib.inolf_object_create(None, None, None) == inolf.E_INVALID
     assert lib.inolf_render_workspace_bytes(1000) >= 8000
+    # the measurement aids check their arguments on the host too
+    assert lib.inolf_trace_stats(None, None, 1, 4, 4, None, None, 0, None) == inolf.E_INVALID
+    assert lib.inolf_probe_peaks(None, None) == inolf.E_INVALID
 
 
 def _cube_desc_scene():
