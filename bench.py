@@ -825,15 +825,21 @@ def run_native(a):
         ref = orc.render_pixels(cams[0], W, H)
         hit = ref["tri"] >= 0
         v0 = torch.empty((1, H, W, 4), dtype=torch.float32, device=dev)
+        tri0 = torch.empty((1, H, W), dtype=torch.int32, device=dev)
         for prec in ["fp32"] + list(precisions):
             if "unavailable" in precisions.get(prec, {}):
                 continue
-            inolf.render(obj, cams[:1], W, H, prec, rgba_out=v0, workspace=ws)
+            inolf.render(obj, cams[:1], W, H, prec, rgba_out=v0, tri_out=tri0 if prec == "fp32" else None,
+                         workspace=ws)
             got = v0.cpu().numpy().reshape(-1, 4)
             mse = float(np.mean((got[hit] - ref["rgba"][hit]) ** 2))
             acc = {"psnr_db": 10 * math.log10(1.0 / mse) if mse > 0 else 99.0,
                    "max_abs": float(np.abs(got - ref["rgba"]).max()), "view": 0}
             if prec == "fp32":
+                # hit triangle ids against the oracle's, and the rays whose winning hit
+                # lies within 1e-6 (barycentric) of a triangle edge
+                acc["tri_id_mismatches"] = int((tri0.cpu().numpy().ravel() != ref["tri"]).sum())
+                acc["near_edge_rays"] = int(np.asarray(ref["near_edge"]).sum())
                 fp32_acc = acc
             else:
                 precisions[prec]["accuracy_vs_oracle"] = acc

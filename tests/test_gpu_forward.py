@@ -109,6 +109,39 @@ def test_explicit_rays_match_oracle(torch_cuda, tiny, tiny_obj, tiny_oracle, n):
     assert np.abs(rgba - ref["rgba"]).max() <= RGBA_TOL
 
 
+def test_edge_and_vertex_rays_are_counted_and_exact(torch_cuda, tiny, tiny_obj, tiny_oracle, record_property):
+    # rays aimed at edge midpoints, vertices and centroids of 200 triangles:
+    # the winning hit of most lies within 1e-6 (barycentric) of an edge.  They
+    # are counted and reported, and the triangle id and t still match the
+    # oracle bit for bit (both sides take the same FP32 test).
+    import torch
+    from paper_2303_04086_gb300 import inolf
+    V, F = tiny.vertices.astype(np.float64), tiny.triangles
+    rng = np.random.default_rng(11)
+    tg = []
+    for f in rng.choice(len(F), 200, replace=False):
+        a, b, c = V[F[f]]
+        tg += [(a + b) / 2, (b + c) / 2, (c + a) / 2, a, (a + b + c) / 3]
+    tg = np.array(tg)
+    eye = tg * 2.5 + rng.normal(scale=0.05, size=tg.shape)
+    d = tg - eye
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    o, d = eye.astype(np.float32), d.astype(np.float32)
+    n = len(o)
+    tri = torch.empty(n, dtype=torch.int32, device="cuda")
+    t = torch.empty(n, dtype=torch.float32, device="cuda")
+    rgba = inolf.render_rays(tiny_obj, torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda(), tri_out=tri,
+                             t_out=t).cpu().numpy()
+    ref = tiny_oracle.render_rays(o, d)
+    n_edge = int(ref["near_edge"].sum())
+    record_property("near_edge_rays", n_edge)
+    print(f"near-edge rays: {n_edge} of {n}")
+    assert n_edge > n // 2
+    assert np.array_equal(tri.cpu().numpy(), ref["tri"])
+    assert np.array_equal(t.cpu().numpy().view(np.int32), ref["t"].view(np.int32))
+    assert np.abs(rgba - ref["rgba"]).max() <= RGBA_TOL
+
+
 def test_encode_slots_and_features(torch_cuda, tiny, tiny_obj, tiny_oracle, tiny_cam):
     import torch
     from paper_2303_04086_gb300 import inolf

@@ -54,12 +54,15 @@ def _sample(view, n, seed):
 
 
 @pytest.mark.parametrize("view", [0, 17, 40, 63])
-def test_full_views_sampled(full, rendered, full_oracle, view):
+def test_full_views_sampled(full, rendered, full_oracle, view, record_property):
     torch, inolf, scene, obj, cams = full
     rgba, tri, t = rendered
     pix = _sample(view, 3000, view)
     ref = full_oracle.render_pixels(cams[view], W, H, pix)
     assert ref["missing"] == 0
+    # rays whose winning hit lies within 1e-6 (barycentric) of an edge: counted,
+    # reported, and held to the same bit-exact bar as the rest
+    record_property("near_edge_rays", int(np.asarray(ref["near_edge"]).sum()))
     pt = torch.from_numpy(pix).cuda()
     g_tri = tri[view].reshape(-1)[pt].cpu().numpy()
     g_t = t[view].reshape(-1)[pt].cpu().numpy()
