@@ -6,12 +6,15 @@
 //            lexicographic (t, triangle id) minimum), then warp-ballot
 //            compaction of the hitting rays into a dense hit list
 //            (one global atomic per CTA).  Misses write RGBA = 0.
-//   k_shade  persistent over the hit list, one thread per hit ray: the
+//   k_shade  persistent over the hit list in tiles of 128 hit rays: the
 //            Sec. 4.1 grid vertex of the hit point on every level, Eq. 1
 //            perfect-hash slots of the 8 voxel corners, feature gather,
 //            trilinear interpolation, SH view encoding and the MLP F_s of
-//            Eq. 3 with weights resident in shared memory.  Tensor-core
-//            variants of the MLP live in mlp_tc.cu.
+//            Eq. 3 with weights resident in shared memory.  FP32:
+//            k_shade_f32_ws (gather and MLP on separate warps; k_shade_f32_tiled
+//            where the register split cannot be used); per-ray k_shade_f32
+//            for stage outputs and FP8 calibration.  Tensor-core variants of
+//            the MLP live in mlp_tc.cu.
 //
 // The FP32 steps that decide integers (ray generation, triangle test, hit
 // point, cell index) are written with explicit round-to-nearest intrinsics
