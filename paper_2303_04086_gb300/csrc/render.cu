@@ -493,8 +493,8 @@ __global__ void __launch_bounds__(kF32Threads, 3) k_shade_f32_tiled(const __grid
 //     and the 8 lanes of a ray group add them by a butterfly over lane bits
 //     2..4 that leaves each lane one ray's channel pair.
 // The staged W1^T and W2^T rows are permuted so that the first and second
-// float4 of the 8 neuron octets are 128 contiguous bytes each: every shared-
-// memory load of the layer loops is one wavefront.
+// float4 of the 8 neuron octets are 128 contiguous bytes each: a warp's
+// float4 weight load reads 8 distinct, bank-disjoint 16-byte chunks.
 // Slot hand-over uses two mbarriers per slot (full: 256 gather arrivals,
 // empty: 256 MLP arrivals), every wait bounded by the global timer; a warp
 // whose wait runs out flags bit 4 of the workspace error word and stops, and
