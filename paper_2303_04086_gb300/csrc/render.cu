@@ -521,6 +521,8 @@ __host__ __device__ constexpr size_t ws_smem_bytes(int din) {
   return (size_t)(din * 64 + 64 * 64 + 4 * 64 + 64 * kF32Tile + kWsSlots * ws_slot_floats(din)) * sizeof(float) +
          2 * kWsSlots * sizeof(uint64_t);
 }
+static_assert(ws_smem_bytes(2 * INOLF_MAX_LEVELS + 17) <= 227 * 1024,
+              "the largest input tile (16 levels, alpha_c) must fit one CTA's shared memory");
 // column of neuron c in the permuted W^T rows: octet c / 8, float4 half (c / 4) & 1
 __device__ __forceinline__ int ws_wcol(int c) { return ((c >> 2) & 1) * 32 + (c >> 3) * 4 + (c & 3); }
 
