@@ -272,19 +272,7 @@ def serving_workload(seed: int = 0):
     overlap in a 10 m cube; 32 viewers on a 12 m sphere around the cube
     centre, each with its resolution drawn from 720p / 1080p / 4K."""
     from paper_2303_04086_gb300 import synth
-    rng = np.random.default_rng(seed)
-    places = []
-    while len(places) < 12:
-        p = rng.uniform(-4.0, 4.0, size=3)  # centres keep the r = 1.1 proxies inside the 10 m cube
-        if all(np.linalg.norm(p - q) > 2.3 for q in places):
-            places.append(p)
-    scenes = [synth.tiny_scene(seed=s) for s in range(12)]
-    res = [(1280, 720), (1920, 1080), (3840, 2160)]
-    viewers = []
-    for v in range(32):
-        d = rng.normal(size=3)
-        viewers.append({"dir": d / np.linalg.norm(d), "res": res[rng.integers(0, 3)]})
-    return scenes, [tuple(map(float, p)) for p in places], viewers
+    return synth.serving_scene(seed)
 
 
 def run_serving(seconds=10.0, warmup=1.0, rate_hz=50.0, seed=0, prec="bf16", policy=1,

@@ -30,7 +30,11 @@
  *      delta)) (Eq. 4) through a density field given as texture cubes, the
  *      coarse opacity alpha_c = sum_i w_i is an extra input of F_s (Eq. 5),
  *      and the colour is c = c_d + t c_s (Eq. 7) with (c_d, t) read from
- *      diffuse texture cubes at the hit point.
+ *      diffuse texture cubes at the hit point;
+ *  10. the depth fusion of several objects' renders of one frame (the frame
+ *      composer of Sec. 5.1): per ray, the K nearest hits over all objects by
+ *      (t, object index), composited front to back with the straight-alpha
+ *      over operator.
  *
  * Every FP32 step is written as separate IEEE operations; this file must be
  * compiled with -ffp-contract=off (no fused multiply-add), so that the same
@@ -1091,6 +1095,67 @@ int64_t orc_render_variant_pixels(const void* hs, const void* hc, const float* c
     missing += render_variant_one(s, c, o, d, rgba + 4 * i, k ? k + i : 0, t ? t + i : 0, alpha ? alpha + i : 0);
   }
   return missing;
+}
+
+/* ------------------------------------------------------------------------ */
+/* 10. Depth fusion of several objects (the frame composer of Sec. 5.1,     */
+/*     which merges the per-object renders of a frame "according to the     */
+/*     depth").  Reading: objects are placed by translation, so a ray's t is */
+/*     the same in the world and in each object's frame; the ray's hits on   */
+/*     all objects are ordered by (t, object index), the first K are kept,   */
+/*     and they are composited front to back with the straight-alpha "over"  */
+/*     operator,                                                             */
+/*         C <- C + (1 - A) a c,   A <- A + (1 - A) a,                       */
+/*     starting from C = 0, A = 0.  The pixel stores the straight colour     */
+/*     C / A and the coverage A, or (0, 0, 0, 0) when A = 0.                 */
+/*     Inputs, per object k and ray r (object-major): hit[k][r] (non-zero =  */
+/*     hit), t[k][r], rgba[k][r][4] straight RGBA of that object's render.   */
+/*     Output out[r][4]; used[r] (optional) = hits composited (<= K).        */
+/* ------------------------------------------------------------------------ */
+#define ORC_MAX_OBJECTS 64
+
+void orc_composite(int32_t n_obj, int64_t n, const int32_t* hit, const float* t, const double* rgba, int32_t K,
+                   double* out, int32_t* used) {
+#pragma omp parallel for schedule(static)
+  for (int64_t r = 0; r < n; ++r) {
+    int32_t order[ORC_MAX_OBJECTS];
+    int32_t m = 0;
+    /* insertion into a list sorted by (t, object index) */
+    for (int32_t k = 0; k < n_obj && k < ORC_MAX_OBJECTS; ++k) {
+      if (!hit[(int64_t)k * n + r]) continue;
+      const float tk = t[(int64_t)k * n + r];
+      int32_t pos = m;
+      while (pos > 0) {
+        const int32_t q = order[pos - 1];
+        const float tq = t[(int64_t)q * n + r];
+        if (tq < tk || (tq == tk && q < k)) break;
+        order[pos] = q;
+        --pos;
+      }
+      order[pos] = k;
+      ++m;
+    }
+    if (m > K) m = K;
+    double C[3] = {0.0, 0.0, 0.0}, A = 0.0;
+    for (int32_t i = 0; i < m; ++i) {
+      const double* c = rgba + ((int64_t)order[i] * n + r) * 4;
+      const double w = (1.0 - A) * c[3];
+      C[0] += w * c[0];
+      C[1] += w * c[1];
+      C[2] += w * c[2];
+      A += w;
+    }
+    double* o = out + r * 4;
+    if (A > 0.0) {
+      o[0] = C[0] / A;
+      o[1] = C[1] / A;
+      o[2] = C[2] / A;
+      o[3] = A;
+    } else {
+      o[0] = o[1] = o[2] = o[3] = 0.0;
+    }
+    if (used) used[r] = m;
+  }
 }
 
 int32_t orc_max_threads(void) {

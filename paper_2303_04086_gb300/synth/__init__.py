@@ -373,3 +373,26 @@ def full_density_scene(seed: int = 0, n_levels: int = 16, top: int = 2048, b: in
     res = full_resolutions(n_levels, 16, top)
     return _density_scene(seed, 1.0, amp, b, r, res, w_cells, opacity, fp16,
                           {"name": "displaced-shell-b%d-r%d-L%d" % (b, r, n_levels), "seed": seed})
+
+
+def serving_scene(seed: int = 0, n_objects: int = 12, n_viewers: int = 32):
+    """The multi-viewer serving workload: ``n_objects`` tiny scenes (seeds
+    0 .. n_objects - 1) placed by translation without bounding-sphere overlap
+    (centres more than 2.3 apart, uniform in [-4, 4]^3, so the r <= 1.1
+    proxies stay inside a 10 m cube), and ``n_viewers`` viewers, each a unit
+    direction (the viewer sits at 12 m along it, looking at the origin) with a
+    resolution drawn from 1280x720 / 1920x1080 / 3840x2160.  Returns
+    (scenes, translations, viewers)."""
+    rng = np.random.default_rng(seed)
+    places = []
+    while len(places) < n_objects:
+        p = rng.uniform(-4.0, 4.0, size=3)
+        if all(np.linalg.norm(p - q) > 2.3 for q in places):
+            places.append(p)
+    scenes = [tiny_scene(seed=s) for s in range(n_objects)]
+    res = [(1280, 720), (1920, 1080), (3840, 2160)]
+    viewers = []
+    for _ in range(n_viewers):
+        d = rng.normal(size=3)
+        viewers.append({"dir": d / np.linalg.norm(d), "res": res[rng.integers(0, 3)]})
+    return scenes, [tuple(map(float, p)) for p in places], viewers

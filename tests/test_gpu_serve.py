@@ -104,29 +104,11 @@ def test_multi_object_composite_matches_oracle(env):
     got = srv.frame(res).cpu().numpy().reshape(-1, 4)
     srv.release(t)
     srv.close()
-    # FP64 reference: every object in its local frame, (t, id)-ordered over
+    # FP64 reference: the oracle's depth fusion of the objects' renders
     o, d = oracle.raygen(cam, W, H)
-    per = []
-    for sc, pl in zip(scenes, PLACES):
-        ol = (o - np.float32(pl)).astype(np.float32)   # the same FP32 subtraction
-        r = oracle.Oracle(sc).render_rays(ol, d)
-        per.append(r)
-    ref = np.zeros((W * H, 4))
-    nhit = 0
-    for px in range(W * H):
-        hits = sorted((per[k]["t"][px], k) for k in range(len(per)) if per[k]["tri"][px] >= 0)[:4]
-        C, A = np.zeros(3), 0.0
-        for _, k in hits:
-            c = per[k]["rgba"][px]
-            w = (1 - A) * c[3]
-            C += w * c[:3]
-            A += w
-        if A > 0:
-            ref[px, :3] = C / A
-            ref[px, 3] = A
-        nhit += len(hits) > 1
-    assert nhit > 20  # some pixels see more than one object
-    assert np.abs(got - ref).max() <= TOL
+    ref = oracle.render_scene([oracle.Oracle(sc) for sc in scenes], PLACES, o, d, K=4)
+    assert (ref["used"] > 1).sum() > 20  # some pixels see more than one object
+    assert np.abs(got - ref["rgba"]).max() <= TOL
 
 
 def test_admission_by_budget_and_slots(env):
@@ -222,21 +204,8 @@ def test_bf16_serving_matches_render_and_oracle(env):
     srv.close()
     got = frames[0].reshape(-1, 4)
     o, d = oracle.raygen(cam, W, H)
-    per = [oracle.Oracle(sc).render_rays((o - np.float32(pl)).astype(np.float32), d)
-           for sc, pl in zip(scenes, PLACES)]
-    ref = np.zeros((W * H, 4))
-    for px in range(W * H):
-        hits = sorted((per[k]["t"][px], k) for k in range(len(per)) if per[k]["tri"][px] >= 0)[:4]
-        C, A = np.zeros(3), 0.0
-        for _, k in hits:
-            c = per[k]["rgba"][px]
-            w = (1 - A) * c[3]
-            C += w * c[:3]
-            A += w
-        if A > 0:
-            ref[px, :3] = C / A
-            ref[px, 3] = A
-    assert np.abs(got - ref).max() <= 1e-2
+    ref = oracle.render_scene([oracle.Oracle(sc) for sc in scenes], PLACES, o, d, K=4)
+    assert np.abs(got - ref["rgba"]).max() <= 1e-2
 
 
 def test_algorithm1_policy_serves_all_viewers(env):
@@ -312,3 +281,48 @@ def test_density_cube_object_served_like_render(env):
             assert np.array_equal(mixed.frame(res).cpu().numpy(), alone)
         mixed.release(tk)
     mixed.close()
+
+
+def _psnr(got, ref):
+    mse = float(np.mean((got - ref) ** 2))
+    return 10 * np.log10(1.0 / mse) if mse > 0 else 99.0
+
+
+def test_twelve_objects_4k_against_oracle_composite():
+    # the serving workload's scene (12 objects, placement of synth.serving_scene)
+    # at 4K: a BF16 request with K = 4 against the oracle's depth fusion at the
+    # BF16 bar, and an FP32 request with K = 2, where the cut drops real hits,
+    # at the FP32 bar; 20 000 seeded pixels each
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2303_04086_gb300 import build, inolf
+    build.build()
+    scenes, places, viewers = synth.serving_scene(0)
+    objs = [inolf.object_create(sc) for sc in scenes]
+    orcs = [oracle.Oracle(sc) for sc in scenes]
+    W, H = 3840, 2160
+    rng = np.random.default_rng(5)
+    pix = np.sort(rng.choice(W * H, 20000, replace=False)).astype(np.int64)
+    for v, prec, K in ((4, "bf16", 4), (8, "fp32", 2)):
+        srv = inolf.Server(hbm_budget=512 << 20, max_slots=4, max_width=W, max_height=H, max_hits=K)
+        for ob, pl in zip(objs, places):
+            srv.add_object(ob, pl)
+        cam = synth.camera(tuple(12.0 * viewers[v]["dir"]))
+        t = srv.submit(cam, W, H, prec)
+        st, res = _done(srv, t)
+        assert st == inolf.OK
+        got = srv.frame(res).reshape(-1, 4)[torch.from_numpy(pix).cuda()].cpu().numpy()
+        srv.release(t)
+        srv.close()
+        o, d = oracle.raygen(cam, W, H, pix)
+        ref = oracle.render_scene(orcs, places, o, d, K=K)
+        hit = ref["used"] > 0
+        assert hit.sum() > 3000 and (ref["used"] > 1).sum() > 300
+        assert np.array_equal(got[~hit], np.zeros_like(got[~hit]))
+        if prec == "bf16":
+            assert _psnr(got[hit], ref["rgba"][hit]) >= 45.0
+            assert np.abs(got - ref["rgba"]).max() <= 1e-2
+        else:
+            assert (ref["hits"] > K).sum() > 100  # the cut is exercised
+            assert np.abs(got - ref["rgba"]).max() <= TOL
