@@ -168,12 +168,32 @@ def make_workload(small: bool, views: int):
     return scene, cams, W4K, H4K, {"workload": desc}
 
 
-# DRAM bytes (read + write) per hit ray of the current shade kernels, from one
-# ncu capture of a one-view launch of the full workload (cold L2), see
-# profiles/k_shade_f32_ws_full_1view.md: 1.104 GB + 0.065 GB for 4 010 637
-# hit rays.  Traffic grows in proportion to the hit rays rendered, so a launch's
-# traffic is this figure times its hit rays.  None once the kernel changes.
-DRAM_BYTES_PER_HIT = {"k_shade_f32": (1.103592e9 + 65.239040e6) / 4010637}
+# Per-hit-ray counters of the FP32 shade kernel on the full workload, from one
+# ncu capture of one 4K view (one launch, cold L2; the capture command sits in
+# the profile summary of that kernel): DRAM bytes read + written, and the
+# 32-byte sectors L2 served to L1 (lts__t_sectors_srcunit_tex_op_read.sum).
+# Both grow in proportion to the hit rays rendered.  Each figure is keyed by a
+# hash of the kernel's sources; once they change the figure prints as null
+# until it is captured again.
+SHADE_SOURCES = ["render.cu", "kernels_common.cuh", "tc_ptx.cuh", "inolf_internal.h"]
+SHADE_COUNTERS = {"k_shade_f32": {"src_sha": None, "dram_bytes_per_hit": None, "l2_sectors_per_hit": None}}
+
+
+def shade_source_sha() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in SHADE_SOURCES:
+        with open(os.path.join(ROOT, "paper_2303_04086_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def shade_counters(kernel: str) -> dict:
+    """The stored per-hit counters of `kernel`, or {} when they are stale."""
+    c = SHADE_COUNTERS.get(kernel)
+    if not c or c["src_sha"] != shade_source_sha():
+        return {}
+    return c
 
 
 def algorithmic_bytes_per_hit(scene) -> int:
@@ -218,10 +238,11 @@ def kernel_rooflines(kernels, scene, n_rays, n_hit, steps, peaks):
 
 def add_probed_rooflines(rooflines, probed, scene, n_rays, n_hit, steps, kernels_by_prec, tstats):
     """The same kernels against the microbenchmarked peaks (inolf_probe_peaks):
-    the PSH gather's random loads (16 per level and hit ray: 8 Phi + 8 table
-    entries) against the L2 random-read rate, the FP32 SIMT MLP against the
-    packed-FMA rate, and the trace kernel's BVH node visits per second (node
-    visits per ray from inolf_trace_stats on view 0)."""
+    the PSH gather's load rate (16 per level and hit ray: 8 Phi + 8 table
+    entries; L1 serves most of them, so the ratio to the L2 random-read rate
+    can exceed 1), the FP32 SIMT MLP against the packed-FMA rate, and the
+    trace kernel's BVH node visits per second (node visits per ray from
+    inolf_trace_stats on view 0)."""
     for prec, kern in kernels_by_prec.items():
         for name, st in kern.items():
             if not st.get("launches") or name not in rooflines.get(prec, {}):
@@ -229,9 +250,12 @@ def add_probed_rooflines(rooflines, probed, scene, n_rays, n_hit, steps, kernels
             sec = st["ms"] / 1e3
             r = rooflines[prec][name]
             if name.startswith("k_shade"):
+                # all 16 loads per level and hit ray, most of them L1 hits: a
+                # rate, not a fraction of the L2 probe (that one needs the
+                # L2-served sectors, see the roofline entry)
                 loads = 16 * scene.n_levels * n_hit * steps / sec / 1e9
                 r["gather_gloads_per_s"] = loads
-                r["frac_l2_random_read_probe"] = loads / probed["l2_gather_gsps"]
+                r["gather_loads_per_l2_random_read"] = loads / probed["l2_gather_gsps"]
                 if name == "k_shade_f32":
                     r["frac_fp32_fma_probe"] = r["mlp_tflops"] / probed["fp32_tflops"]
             elif name == "k_trace" and tstats:
@@ -240,31 +264,73 @@ def add_probed_rooflines(rooflines, probed, scene, n_rays, n_hit, steps, kernels
                 r["gnode_visits_per_s"] = tstats["node_visits_per_ray"] * n_rays * steps / sec / 1e9
 
 
-def cpu_baseline(scene, cams, W, H, budget_s=12.0, orc=None):
-    """The FP64 oracle as it stands, on a seeded pixel sample of view 0."""
+ORACLE_BATCH_RAYS = 1_000_000
+
+
+def time_oracle_batches(orc, cams, W, H, n_batches, warmup=1, batch_rays=ORACLE_BATCH_RAYS, seed=0,
+                        budget_s=None):
+    """The FP64 oracle as it stands on seeded batches of the workload: batch
+    b renders `batch_rays` random pixels (sorted) of view b mod len(cams).
+    The first `warmup` batches are not timed.  Stops after n_batches timed
+    batches, or earlier once budget_s seconds are spent.  Returns (rays,
+    seconds, per-batch seconds).  Both CPU legs of this file time the oracle
+    through this function, so their figures are comparable."""
+    rng = np.random.default_rng(seed)
+    rays, secs, per = 0, 0.0, []
+    n = min(batch_rays, W * H)
+    for b in range(warmup + n_batches):
+        pix = np.sort(rng.choice(W * H, n, replace=False)).astype(np.int64)
+        t0 = time.perf_counter()
+        orc.render_pixels(cams[b % len(cams)], W, H, pix)
+        dt = time.perf_counter() - t0
+        if b >= warmup:
+            rays += n
+            secs += dt
+            per.append(dt)
+            if budget_s is not None and secs >= budget_s:
+                break
+    return rays, secs, per
+
+
+def cpu_baseline(scene, cams, W, H, budget_s=10.0, orc=None):
+    """The FP64 oracle as it stands on the machine's host cores: batches of 10^6
+    seeded random pixels cycling through the views (all cores, about
+    budget_s seconds), the same on one thread (one batch of 10^5 pixels),
+    and full frames of the tiny scene (one 128x128 view at distance 3) and of
+    the precision-sweep scene (FP16 tables, one 3840x2160 ring view at r = 3)."""
     import oracle
     if orc is None:
         oracle.build()
         orc = oracle.Oracle(scene)
-    rng = np.random.default_rng(0)
-    n = 2000
-    spent = 0.0
-    total_rays = 0
-    rounds = 0
-    while spent < budget_s and n <= W * H and rounds < 8:
-        rounds += 1
-        pix = np.sort(rng.choice(W * H, n, replace=False)).astype(np.int64)
+    cores = oracle.max_threads()
+    rays, secs, _ = time_oracle_batches(orc, cams, W, H, n_batches=1000, warmup=1, budget_s=budget_s)
+    rate = rays / secs
+    out = {"value": rate / 1e6, "unit": "Mrays/s", "cores": cores, "kind": "oracle",
+           "sample": f"{rays} rays in batches of {min(ORACLE_BATCH_RAYS, W * H)} seeded random pixels of views 1, 2, ... "
+                     f"({W}x{H}; one untimed warm-up batch of view 0), FP64 oracle, {secs:.1f} s of CPU work "
+                     f"on {cores} threads"}
+    try:
+        oracle.set_threads(1)
+        r1, s1, _ = time_oracle_batches(orc, cams, W, H, n_batches=1, warmup=0, batch_rays=100_000, seed=1)
+        out["value_1thread"] = r1 / s1 / 1e6
+        out["sample_1thread"] = f"{r1} seeded random pixels of view 0 on 1 thread, {s1:.1f} s"
+    finally:
+        oracle.set_threads(cores)
+    from paper_2303_04086_gb300 import synth
+    frames = {}
+    for name, sc, cam, fw, fh in (
+            ("tiny_128x128", synth.tiny_scene(seed=0), synth.camera((0.0, 0.0, 3.0)), 128, 128),
+            ("tiny_fp16_3840x2160", synth.tiny_scene(seed=0, fp16=True), synth.ring_cameras(1, 3.0)[0],
+             3840, 2160)):
+        o2 = oracle.Oracle(sc)
+        o2.render_pixels(cam, min(fw, 64), min(fh, 64))  # warm-up
         t0 = time.perf_counter()
-        orc.render_pixels(cams[0], W, H, pix)
+        o2.render_pixels(cam, fw, fh)
         dt = time.perf_counter() - t0
-        spent += dt
-        total_rays += n
-        if dt < 0.5 * (budget_s - spent):
-            n = min(W * H, n * 4)
-    rate = total_rays / spent
-    return {"value": rate / 1e6, "unit": "Mrays/s", "cores": oracle.max_threads(), "kind": "oracle",
-            "sample": f"{total_rays} rays: seeded random pixel subsets (2000, x4 per round) of view 0 "
-                      f"({W}x{H}), FP64 oracle, {spent:.1f} s of CPU work"}
+        frames[name] = {"rays": fw * fh, "seconds": dt, "mrays_per_s": fw * fh / dt / 1e6, "cores": cores}
+        del o2
+    out["full_frames"] = frames
+    return out
 
 
 def serving_workload(seed: int = 0):
@@ -648,28 +714,20 @@ def run_precision_sweep(steps=3, warmup=3, views=N_VIEWS, pixels_per_view=4000):
 
 
 def run_reference(a):
+    """The oracle as it stands (the reference of this project), one batch of
+    10^6 seeded random pixels per step, views cycling, on the host cores."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     scene, cams, W, H, cfg = make_workload(a.small, a.views)
-    per_step = []
     import oracle
     oracle.build()
     orc = oracle.Oracle(scene)
-    rng = np.random.default_rng(0)
-    n = 20000 if not a.small else 20000
-    for s in range(a.warmup + a.steps):
-        pix = np.sort(rng.choice(W * H, min(n, W * H), replace=False)).astype(np.int64)
-        t0 = time.perf_counter()
-        orc.render_pixels(cams[s % len(cams)], W, H, pix)
-        dt = time.perf_counter() - t0
-        if s >= a.warmup:
-            per_step.append((len(pix), dt))
-    rays = sum(r for r, _ in per_step)
-    secs = sum(t for _, t in per_step)
+    rays, secs, _ = time_oracle_batches(orc, cams, W, H, n_batches=a.steps, warmup=a.warmup)
     val = rays / secs / 1e6
     cfg = dict(cfg)
-    cfg["sample"] = f"{n} seeded random pixels per step of the 4K views"
+    cfg["sample"] = (f"{min(ORACLE_BATCH_RAYS, W * H)} seeded random pixels per step, step s on view s mod "
+                     f"{len(cams)} ({W}x{H}), FP64 oracle on {oracle.max_threads()} threads")
     out = {"impl": "reference", "metric": "i-NOLF Mrays/s at 4K (FP32 plain)", "value": val, "unit": "Mrays/s",
            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * secs / a.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -784,22 +842,34 @@ def run_native(a):
         st = stats[top]
         avg_s = st["ms"] / 1e3 / st["launches"]
         hits_per_launch = n_hit / max(1, st["launches"] // a.steps) if a.steps else n_hit
+        peak = peaks.get("hbm_gbs", 6800.0)
         if top.startswith("k_shade"):
+            # the gather's algorithmic bytes over the measured HBM copy rate (the
+            # contract's fraction); the kernel is bound by the latency of its
+            # dependent L1/L2 gathers, so the DRAM bytes it actually moves and
+            # the L2-served sectors against the probed L2 random-read rate are
+            # reported beside it
             byt = algorithmic_bytes_per_hit(scene) * hits_per_launch + 16 * hits_per_launch + 8 * hits_per_launch
             achieved = byt / avg_s / 1e9
-            peak = peaks.get("hbm_gbs", 6800.0)
-            tpb = DRAM_BYTES_PER_HIT.get(top) if not a.small else None
-            roof = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak, "traffic": tpb * hits_per_launch if tpb else None,
+            cnt = shade_counters(top) if not a.small else {}
+            dram = cnt.get("dram_bytes_per_hit")
+            l2s = cnt.get("l2_sectors_per_hit")
+            roof = {"kernel": top, "bound": "latency (dependent L1/L2 gather loads)", "achieved": achieved,
+                    "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": "measured",
+                    "traffic": dram * hits_per_launch if dram else None,
                     "algorithmic_bytes_per_launch": byt,
+                    "frac_algorithmic_of_hbm": achieved / peak,
+                    "frac_dram_of_hbm": dram * hits_per_launch / avg_s / 1e9 / peak if dram else None,
+                    "l2_sectors_per_launch": l2s * hits_per_launch if l2s else None,
+                    "frac_l2_served_of_l2_random_probe": None,
+                    "counters_src_sha": shade_source_sha(),
                     "mlp_tflops": mlp_flops_per_hit(scene) * hits_per_launch / avg_s / 1e12,
                     "mlp_frac_of_fp32_peak": mlp_flops_per_hit(scene) * hits_per_launch / avg_s / 80.5e12}
         else:
             rays_per_launch = n_rays / max(1, st["launches"] // a.steps)
             byt = 16 * rays_per_launch + 8 * hits_per_launch
             achieved = byt / avg_s / 1e9
-            peak = peaks.get("hbm_gbs", 6800.0)
-            roof = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            roof = {"kernel": top, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "GB/s",
                     "frac": achieved / peak, "traffic": None}
 
     base = None
@@ -854,6 +924,11 @@ def run_native(a):
             by_prec.update({k: v["kernels"] for k, v in precisions.items() if "kernels" in v})
             add_probed_rooflines(out["kernel_rooflines"], probed, scene, n_rays, n_hit, a.steps, by_prec, tstats)
             out["peaks_probed"] = probed
+            if roof and roof.get("l2_sectors_per_launch"):
+                st = stats[roof["kernel"]]
+                avg_s = st["ms"] / 1e3 / st["launches"]
+                roof["frac_l2_served_of_l2_random_probe"] = (roof["l2_sectors_per_launch"] / avg_s / 1e9 /
+                                                             probed["l2_gather_gsps"])
             out["trace_stats_view0"] = tstats
         except Exception as e:  # noqa: BLE001
             out["peaks_probed"] = {"error": str(e)[:200]}

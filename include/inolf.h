@@ -58,6 +58,7 @@ typedef int inolf_status;
 #define INOLF_E_UNKNOWN_TICKET (-7) /* serve_poll: no such request */
 #define INOLF_E_UNSUPPORTED (-8)   /* valid request this build cannot serve */
 #define INOLF_E_CANCELLED (-9)     /* serve_poll: the request was cancelled */
+#define INOLF_E_DEVICE (-10)       /* a kernel reported an internal failure (inolf_workspace_flags) */
 
 #define INOLF_MAX_LEVELS 16
 #define INOLF_HIDDEN 64
@@ -209,6 +210,47 @@ size_t inolf_render_workspace_bytes(int64_t n_rays);
 inolf_status inolf_render(const inolf_object* obj, const float* cams, int32_t n_views, int32_t W, int32_t H,
                           inolf_precision prec, float* rgba_out, int32_t* tri_out, float* t_out,
                           void* workspace, size_t workspace_bytes, void* stream);
+
+/* Device-side failure flags.  The kernels of a call OR these bits into word 1
+ * of the workspace header (the call zeroes the word when it starts); the
+ * results of the rays concerned are incomplete:
+ *   INOLF_FLAG_STACK_OVERFLOW   a BVH traversal stack overflowed (a subtree
+ *                               was skipped; the BVH is deeper than 48)
+ *   INOLF_FLAG_TRAVERSAL_LIMIT  a traversal exceeded 2^22 steps (malformed BVH)
+ *   INOLF_FLAG_WAIT_TIMEOUT     a bounded wait in a shade kernel ran out (a
+ *                               pipeline hand-over or a tensor-core completion);
+ *                               some hit rays were not shaded */
+#define INOLF_FLAG_STACK_OVERFLOW 1u
+#define INOLF_FLAG_TRAVERSAL_LIMIT 2u
+#define INOLF_FLAG_WAIT_TIMEOUT 4u
+
+/* Reads the failure flags of the last call that used `workspace` (device
+ * memory, as passed to that call; NULL = the fixed scratch of
+ * inolf_render_rays_noalloc on the current device).  Synchronises `stream`
+ * (the stream of that call) first.  *flags receives the bits above.  Returns
+ * INOLF_OK when no bit is set, INOLF_E_TIMEOUT when INOLF_FLAG_WAIT_TIMEOUT is
+ * set, INOLF_E_DEVICE for the traversal bits (the message names them),
+ * INOLF_E_INVALID for a NULL flags pointer, INOLF_E_CUDA when the read fails.
+ * The asynchronous calls (inolf_render, inolf_render_rays, inolf_backward, ...)
+ * leave the check to the caller; the synchronising ones (inolf_render_host,
+ * inolf_calibrate_fp8, inolf_trace_stats, inolf_render_rays_noalloc) make it
+ * themselves and return its status. */
+inolf_status inolf_workspace_flags(const void* workspace, uint32_t* flags, void* stream);
+
+/* Limit of the bounded hand-over waits between the gather and MLP warps of
+ * the warp-specialised shade kernels, for all later launches of the process
+ * (ns; 0 restores the default of 2 s).  A wait that runs out sets
+ * INOLF_FLAG_WAIT_TIMEOUT and the kernel returns.  Errors: INOLF_E_INVALID for
+ * ns < 0. */
+inolf_status inolf_set_wait_limit_ns(int64_t ns);
+
+/* Fault injection for tests of the failure path (process-wide, 0 = off):
+ * with INOLF_INJECT_RING_STALL the gather warps of the warp-specialised shade
+ * kernels never hand their tiles over, so every hand-over wait runs out (after
+ * the limit of inolf_set_wait_limit_ns) and the call's flags report
+ * INOLF_FLAG_WAIT_TIMEOUT.  No GPU fault is involved: every wait is bounded. */
+#define INOLF_INJECT_RING_STALL 1u
+inolf_status inolf_set_fault_injection(uint32_t mask);
 
 /* Renders n_views pinhole views into HOST memory, overlapping rendering with
  * the device-to-host copies: views go in chunks into two halves of a caller-
@@ -437,6 +479,10 @@ inolf_status inolf_sched_wait_ns(inolf_sched* s, uint32_t viewer, int64_t* w_ns,
  *     itself.  Calls whose GPU work overlaps in time (other streams or host
  *     threads) race on the array and produce wrong results: order them, e.g.
  *     on one stream.
+ *   - The call synchronises `stream` before it returns, so that it can read
+ *     the device-side failure flags of its kernels from the array (where the
+ *     caller cannot reach them) and report them: INOLF_E_TIMEOUT or
+ *     INOLF_E_DEVICE as inolf_workspace_flags describes.
  * o, d, rgba_out, tri_out, t_out, prec and stream are as for
  * inolf_render_rays. */
 inolf_status inolf_render_rays_noalloc(const inolf_object* obj, const float* o, const float* d, int64_t n,

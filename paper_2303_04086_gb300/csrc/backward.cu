@@ -273,17 +273,19 @@ static size_t bwd_smem_bytes() {
 }
 
 inolf_status launch_backward(const Params& p, const BwdParams& b, cudaStream_t st) {
-  static int grid = 0;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    int dev = 0, sms = 1, occ = 1;
-    cudaGetDevice(&dev);
+  const int dev = device_index();
+  if (dev < 0) return fail(INOLF_E_UNSUPPORTED, "k_backward: no current device, or an index beyond 63");
+  static int grid_dev[kMaxDevices];
+  static std::once_flag once[kMaxDevices];
+  std::call_once(once[dev], [dev] {
+    int sms = 1, occ = 1;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaFuncSetAttribute(k_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem_bytes());
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_backward, kBThreads, bwd_smem_bytes());
-    grid = sms * std::max(1, occ);
+    grid_dev[dev] = sms * std::max(1, occ);
     cudaGetLastError();
   });
+  const int grid = grid_dev[dev];
   {
     LaunchTimer lt("k_backward", st);
     k_backward<<<grid, kBThreads, bwd_smem_bytes(), st>>>(p, b);

@@ -15,6 +15,22 @@ namespace inolf {
 inolf_status fail(inolf_status st, const std::string& msg);
 void clear_error();
 
+// The library may run on several devices of one process; kernel attributes
+// and grid sizes are set up once per device (index < kMaxDevices), with that
+// device current.  device_index() returns the current device, or -1 when it
+// cannot be read or lies beyond kMaxDevices.
+static constexpr int kMaxDevices = 64;
+int device_index();
+
+// Failure flags of a call (word 1 of the workspace header, INOLF_FLAG_*):
+// synchronises `stream`, reads the word and turns it into a status (message
+// prefixed by `what`).  ws = NULL reads the allocation-free scratch.
+inolf_status read_device_flags(const void* ws, void* stream, uint32_t* flags);
+inolf_status flags_status(uint32_t flags, const char* what);
+// Device address of the allocation-free scratch on the current device
+// (render_noalloc.cu).
+inolf_status noalloc_scratch_address(void** out);
+
 // Per-level encoder description as the kernels see it.
 struct LevelDev {
   int32_t N;              // cells per axis
@@ -119,10 +135,13 @@ struct RayBatch {
   int64_t n;               // total rays
 };
 
+// clear_flags: zero the header's failure flags first (false when a caller
+// accumulates the flags of several launch_render calls, e.g. chunks of views).
 inolf_status launch_render(const Object& obj, const RayBatch& rays, inolf_precision prec, float* rgba,
                            int32_t* tri_out, float* t_out, uint32_t* slots_out, float* feat_out,
                            void* workspace, size_t workspace_bytes, void* stream, bool amax = false,
-                           float* alpha_out = nullptr, bool hits_only = false, bool count_trace = false);
+                           float* alpha_out = nullptr, bool hits_only = false, bool count_trace = false,
+                           bool clear_flags = true);
 
 size_t workspace_bytes(int64_t n_rays);
 

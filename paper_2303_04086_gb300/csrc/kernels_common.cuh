@@ -54,8 +54,11 @@ struct Params {
   int32_t variant;
   CubesDev cub;
   float* alpha_out;    // march stage output (inolf_march_rays), or NULL
+  // bounded waits and test fault injection (process-wide settings)
+  uint64_t wait_ns;    // limit of the gather/MLP hand-over waits
+  uint32_t inject;     // INOLF_INJECT_* bits
   // workspace
-  uint32_t* counter;   // [0] hit count, [1] error flags, [4..6] activation amax bits
+  uint32_t* counter;   // [0] hit count, [1] error flags (INOLF_FLAG_*), [4..6] activation amax bits
   uint2* hits;         // (ray index in launch, t bits)
   float* hit_alpha;    // variant: alpha_c of each hit-list entry
 };
@@ -236,7 +239,7 @@ __device__ __forceinline__ void closest_hit_bvh(const float4* __restrict__ nodes
   // against a malformed node array (flagged, traversal stops)
   for (int32_t guard = 0;; ++guard) {
     if (guard > (1 << 22)) {
-      atomicOr(err, 2u);
+      atomicOr(err, INOLF_FLAG_TRAVERSAL_LIMIT);
       break;
     }
     const float lim = best_id < 0 ? INFINITY : best_t * 1.00002f + 1e-5f;
@@ -257,7 +260,7 @@ __device__ __forceinline__ void closest_hit_bvh(const float4* __restrict__ nodes
           st_t[sp] = lfirst ? tr : tl;
           ++sp;
         } else {
-          atomicOr(err, 1u);  // stack overflow: flagged, subtree skipped
+          atomicOr(err, INOLF_FLAG_STACK_OVERFLOW);  // flagged, subtree skipped
         }
         cur = lfirst ? meta.x : meta.z;
         cur_cnt = lfirst ? meta.y : meta.w;
@@ -335,7 +338,7 @@ __device__ __forceinline__ void closest_hit_packet(const float4* __restrict__ no
   int32_t cur = 0, cur_cnt = 0;  // inner node 0
   for (int32_t guard = 0;; ++guard) {
     if (guard > (1 << 22)) {  // warp-uniform
-      atomicOr(err, 2u);
+      atomicOr(err, INOLF_FLAG_TRAVERSAL_LIMIT);
       break;
     }
     const float lim = best_id < 0 ? INFINITY : best_t * 1.00002f + 1e-5f;
@@ -362,7 +365,7 @@ __device__ __forceinline__ void closest_hit_packet(const float4* __restrict__ no
           st_t[sp] = lfirst ? tr : tl;
           ++sp;
         } else {
-          atomicOr(err, 1u);  // stack overflow: flagged, subtree skipped
+          atomicOr(err, INOLF_FLAG_STACK_OVERFLOW);  // flagged, subtree skipped
         }
         cur = lfirst ? meta.x : meta.z;
         cur_cnt = lfirst ? meta.y : meta.w;

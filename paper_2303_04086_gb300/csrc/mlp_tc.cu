@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_shade_tc(const __grid_constan
     }
   }
   if (bad) {
-    if (tid == 0) atomicOr(p.counter + 1, 4u);
+    if (tid == 0) atomicOr(p.counter + 1, INOLF_FLAG_WAIT_TIMEOUT);
     tc::mbar_wait(&bars[1], phase, kWaitLimitNs);  // let MMAs still in flight finish
   }
   __syncthreads();
@@ -336,11 +336,14 @@ inolf_status launch_shade_tc(const Params& p_in, inolf_precision prec, cudaStrea
   p.tc_wbytes = fp8 ? p.tc_bytes_fp8 : p.tc_bytes_bf16;
   if (!p.tc_w || p.tc_wbytes == 0 || (p.tc_wbytes & 15u)) return fail(INOLF_E_INVALID, "tensor-core weights missing");
   const size_t smem = tc_smem_bytes(p.tc_wbytes, fp8);
-  static int grid_bf16 = 0, grid_fp8 = 0;
-  static std::once_flag once;
-  std::call_once(once, [&] {
-    int dev = 0, sms = 1, regs_sm = 65536, smem_sm = 0;
-    cudaGetDevice(&dev);
+  const int dev = device_index();
+  if (dev < 0) return fail(INOLF_E_UNSUPPORTED, "k_shade_tc: no current device, or an index beyond 63");
+  static int grid_bf16_dev[kMaxDevices], grid_fp8_dev[kMaxDevices];
+  static std::once_flag once[kMaxDevices];
+  std::call_once(once[dev], [&] {
+    int sms = 1, regs_sm = 65536, smem_sm = 0;
+    int& grid_bf16 = grid_bf16_dev[dev];
+    int& grid_fp8 = grid_fp8_dev[dev];
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
     cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
@@ -365,7 +368,7 @@ inolf_status launch_shade_tc(const Params& p_in, inolf_precision prec, cudaStrea
     cudaGetLastError();
   });
   if (smem > (size_t)tc_smem_bytes(kMaxTcWeightBytes, fp8)) return fail(INOLF_E_INVALID, "tensor-core weights too large");
-  const int grid = fp8 ? grid_fp8 : grid_bf16;
+  const int grid = fp8 ? grid_fp8_dev[dev] : grid_bf16_dev[dev];
   {
     LaunchTimer lt(fp8 ? "k_shade_tc_fp8" : "k_shade_tc_bf16", st);
     if (fp8) k_shade_tc<true><<<grid, kTcThreads, smem, st>>>(p);

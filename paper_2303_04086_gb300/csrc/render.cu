@@ -24,6 +24,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -496,9 +497,9 @@ __global__ void __launch_bounds__(kF32Threads, 3) k_shade_f32_tiled(const __grid
 // float4 of the 8 neuron octets are 128 contiguous bytes each: a warp's
 // float4 weight load reads 8 distinct, bank-disjoint 16-byte chunks.
 // Slot hand-over uses two mbarriers per slot (full: 256 gather arrivals,
-// empty: 256 MLP arrivals), every wait bounded by the global timer; a warp
-// whose wait runs out flags bit 4 of the workspace error word and stops, and
-// the others then run out in turn.  No other barrier joins warps: a gather
+// empty: 256 MLP arrivals), every wait bounded by the global timer (limit
+// p.wait_ns); a warp whose wait runs out sets INOLF_FLAG_WAIT_TIMEOUT in the
+// workspace error word and stops, and the others then run out in turn.  No other barrier joins warps: a gather
 // warp writes its own rays of a tile, and an MLP warp's hidden activations
 // are its own 16 columns of the hidden tile, so every warp runs at its own
 // pace between the slot barriers.  Registers are split with
@@ -512,7 +513,7 @@ static constexpr int kWsLaunchRegs = 80, kWsGatherRegs = 64, kWsMlpRegs = 112;
 static_assert(kWsTeams * 256 * kWsGatherRegs + kWsMlp * kWsMlpRegs <= kWsThreads * kWsLaunchRegs,
               "register split exceeds the CTA's launch allocation");
 static_assert(kWsThreads * kWsLaunchRegs <= 65536, "launch allocation exceeds the register file");
-static constexpr uint64_t kRingWaitLimitNs = 2000000000ull;  // 2 s; one tile takes microseconds
+static constexpr uint64_t kRingWaitLimitNs = 2000000000ull;  // default hand-over limit: 2 s; a tile takes microseconds
 
 // shared-memory floats of one ring slot: inputs [d_in][tile], diffuse
 // [4][tile], ray ids [tile]
@@ -580,9 +581,9 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_shade_f32_ws(const __grid_con
     for (uint32_t k = (uint32_t)team; k < n_k; k += kWsTeams) {
       const uint32_t s = k % kWsSlots;
       if (k >= (uint32_t)kWsSlots) {  // the MLP threads released the tile k - kWsSlots
-        const bool ok = tc::mbar_wait(&empty[s], (k / kWsSlots - 1u) & 1u, kRingWaitLimitNs);
+        const bool ok = tc::mbar_wait(&empty[s], (k / kWsSlots - 1u) & 1u, p.wait_ns);
         if (__any_sync(0xffffffffu, !ok)) {
-          if ((gt & 31) == 0) atomicOr(p.counter + 1, 4u);
+          if ((gt & 31) == 0) atomicOr(p.counter + 1, INOLF_FLAG_WAIT_TIMEOUT);
           break;
         }
       }
@@ -592,7 +593,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_shade_f32_ws(const __grid_con
       const uint32_t h = (blockIdx.x + k * gridDim.x) * kF32Tile + (uint32_t)ray_slot;
       const int64_t ray = gather_tile_f32(p, h, h < total, ray_slot, half, in, dif);
       if (half == 0) rid[ray_slot] = (uint32_t)ray;
-      tc::mbar_arrive(&full[s]);
+      if (!(p.inject & INOLF_INJECT_RING_STALL)) tc::mbar_arrive(&full[s]);  // injected stall: never handed over
     }
     return;
   }
@@ -606,9 +607,9 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_shade_f32_ws(const __grid_con
   const int out_ray = r0 + out_i;
   for (uint32_t k = 0; k < n_k; ++k) {
     const uint32_t s = k % kWsSlots;
-    const bool ok = tc::mbar_wait(&full[s], (k / kWsSlots) & 1u, kRingWaitLimitNs);
+    const bool ok = tc::mbar_wait(&full[s], (k / kWsSlots) & 1u, p.wait_ns);
     if (__any_sync(0xffffffffu, !ok)) {
-      if (lane == 0) atomicOr(p.counter + 1, 4u);
+      if (lane == 0) atomicOr(p.counter + 1, INOLF_FLAG_WAIT_TIMEOUT);
       break;
     }
     const float* in = ring + s * slot_floats;
@@ -672,16 +673,24 @@ static constexpr size_t kWsHeader = 256;
 size_t workspace_bytes(int64_t n_rays) { return kWsHeader + (size_t)std::max<int64_t>(n_rays, 1) * 12; }
 static size_t workspace_bytes_min() { return workspace_bytes(1); }
 
+std::atomic<int64_t> g_wait_ns{0};     // inolf_set_wait_limit_ns (0 = default)
+std::atomic<uint32_t> g_inject{0};     // inolf_set_fault_injection
+
+int device_index() {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  return dev >= 0 && dev < kMaxDevices ? dev : -1;
+}
+
 static int sm_count() {
-  static int n = 0;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 1;
+  static int n[kMaxDevices] = {};
+  static std::once_flag once[kMaxDevices];
+  const int dev = std::max(device_index(), 0);
+  std::call_once(once[dev], [dev] {
+    cudaDeviceGetAttribute(&n[dev], cudaDevAttrMultiProcessorCount, dev);
+    if (n[dev] <= 0) n[dev] = 1;
   });
-  return n;
+  return n[dev];
 }
 
 static void fill_common(const Object& obj, Params& p) {
@@ -705,6 +714,9 @@ static void fill_common(const Object& obj, Params& p) {
   sh_constants(p.shc);
   p.variant = obj.variant;
   p.cub = obj.cub;
+  const int64_t w = g_wait_ns.load();
+  p.wait_ns = w > 0 ? (uint64_t)w : kRingWaitLimitNs;
+  p.inject = g_inject.load();
 }
 
 // Hit list (cap records) and, for the variant, the alpha_c array after it.
@@ -722,15 +734,45 @@ static inolf_status check_launch(const char* what) {
   return INOLF_OK;
 }
 
+inolf_status flags_status(uint32_t flags, const char* what) {
+  if (!flags) return INOLF_OK;
+  std::string m = std::string(what) + ": device-side failure flags 0x" + std::to_string(flags) + " (";
+  if (flags & INOLF_FLAG_WAIT_TIMEOUT) m += " a bounded wait in a shade kernel ran out;";
+  if (flags & INOLF_FLAG_STACK_OVERFLOW) m += " a BVH traversal stack overflowed;";
+  if (flags & INOLF_FLAG_TRAVERSAL_LIMIT) m += " a BVH traversal exceeded its step limit;";
+  m += " the results of the rays concerned are incomplete)";
+  return fail((flags & INOLF_FLAG_WAIT_TIMEOUT) ? INOLF_E_TIMEOUT : INOLF_E_DEVICE, m);
+}
+
+inolf_status read_device_flags(const void* ws, void* stream, uint32_t* flags) {
+  cudaStream_t st = (cudaStream_t)stream;
+  const void* hdr = ws;
+  if (!hdr) {
+    void* sc = nullptr;
+    inolf_status s = noalloc_scratch_address(&sc);
+    if (s != INOLF_OK) return s;
+    hdr = sc;
+  }
+  uint32_t f = 0;
+  if (cudaMemcpyAsync(&f, static_cast<const uint32_t*>(hdr) + 1, sizeof(f), cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return fail(INOLF_E_CUDA, "reading the device failure flags failed");
+  *flags = f;
+  return INOLF_OK;
+}
+
 inolf_status launch_shade_tc(const Params& p, inolf_precision prec, cudaStream_t st);  // mlp_tc.cu
 
 inolf_status launch_render(const Object& obj, const RayBatch& rays, inolf_precision prec, float* rgba,
                            int32_t* tri_out, float* t_out, uint32_t* slots_out, float* feat_out,
                            void* workspace, size_t ws_bytes, void* stream, bool amax, float* alpha_out,
-                           bool hits_only, bool count_trace) {
+                           bool hits_only, bool count_trace, bool clear_flags) {
   cudaStream_t st = (cudaStream_t)stream;
   if (!workspace || ws_bytes < workspace_bytes(1) || ((uintptr_t)workspace & 15))
     return fail(INOLF_E_INVALID, "render: workspace missing, too small or not 16-byte aligned");
+  const int dev = device_index();
+  if (dev < 0) return fail(INOLF_E_UNSUPPORTED, "render: no current device, or a device index beyond 63");
   const bool encode = slots_out != nullptr;
   if (!encode && prec != INOLF_FP32 && prec != INOLF_BF16 && prec != INOLF_FP8)
     return fail(INOLF_E_INVALID, "render: unknown precision");
@@ -749,8 +791,8 @@ inolf_status launch_render(const Object& obj, const RayBatch& rays, inolf_precis
   p.alpha_out = alpha_out;
 
   const size_t smem_f32 = (size_t)(obj.d_in * 64 + 64 * 64 + 64 * 4) * sizeof(float);
-  static std::once_flag attr_once;
-  std::call_once(attr_once, [&] {
+  static std::once_flag attr_once[kMaxDevices];
+  std::call_once(attr_once[dev], [&] {
     cudaFuncSetAttribute(k_shade_f32<kShade>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     cudaFuncSetAttribute(k_shade_f32<kShade>, cudaFuncAttributePreferredSharedMemoryCarveout, 50);
     cudaFuncSetAttribute(k_shade_f32<kAmax>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
@@ -758,9 +800,10 @@ inolf_status launch_render(const Object& obj, const RayBatch& rays, inolf_precis
   const int shade_grid = sm_count() * 8;
   const size_t smem_f32_tiled =
       (size_t)(obj.d_in * 64 + 64 * 64 + 4 * 64 + 64 * kF32Tile + (obj.variant ? 4 * kF32Tile : 0)) * sizeof(float);
-  static std::once_flag tiled_once;
-  static int f32_ctas = 1;
-  std::call_once(tiled_once, [&] {
+  static std::once_flag tiled_once[kMaxDevices];
+  static int f32_ctas_dev[kMaxDevices];
+  std::call_once(tiled_once[dev], [&] {
+    int& f32_ctas = f32_ctas_dev[dev];
     // the largest configuration: 16 levels, alpha_c input and the diffuse tile
     const size_t mx =
         (size_t)((2 * INOLF_MAX_LEVELS + 17) * 64 + 64 * 64 + 4 * 64 + 64 * kF32Tile + 4 * kF32Tile) * sizeof(float);
@@ -769,20 +812,26 @@ inolf_status launch_render(const Object& obj, const RayBatch& rays, inolf_precis
     if (f32_ctas < 1) f32_ctas = 1;
     cudaGetLastError();
   });
-  const int f32_grid = sm_count() * f32_ctas;
+  const int f32_grid = sm_count() * f32_ctas_dev[dev];
   const size_t smem_ws = ws_smem_bytes(obj.d_in);
-  static std::once_flag ws_once;
-  static bool ws_ok = false;  // compiled with the register count its split assumes
-  std::call_once(ws_once, [&] {
+  static std::once_flag ws_once[kMaxDevices];
+  static bool ws_ok_dev[kMaxDevices];  // compiled with the register count its split assumes
+  std::call_once(ws_once[dev], [&] {
     cudaFuncAttributes fa{};
-    ws_ok = cudaFuncGetAttributes(&fa, k_shade_f32_ws) == cudaSuccess && fa.numRegs == kWsLaunchRegs;
+    ws_ok_dev[dev] = cudaFuncGetAttributes(&fa, k_shade_f32_ws) == cudaSuccess && fa.numRegs == kWsLaunchRegs;
     const size_t mx = ws_smem_bytes(2 * INOLF_MAX_LEVELS + 17);
     cudaFuncSetAttribute(k_shade_f32_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
     cudaGetLastError();
   });
 
+  const bool ws_ok = ws_ok_dev[dev];
+  // the hit counter restarts with every chunk; the failure flags (word 1)
+  // accumulate over the call
+  bool first_chunk = clear_flags;
   auto run_chunk = [&](int64_t n_chunk, int32_t tiles_x, int32_t tiles_y, int64_t trace_blocks) -> inolf_status {
-    if (cudaMemsetAsync(counter, 0, 8, st) != cudaSuccess) return fail(INOLF_E_CUDA, "cudaMemsetAsync failed");
+    if (cudaMemsetAsync(counter, 0, first_chunk ? 8 : 4, st) != cudaSuccess)
+      return fail(INOLF_E_CUDA, "cudaMemsetAsync failed");
+    first_chunk = false;
     (void)n_chunk;
     if (obj.variant) {
       {
@@ -884,7 +933,9 @@ inolf_status launch_backward_rays(const Object& obj, const float* o, const float
     p.rd = d + 3 * r0;
     p.ray_base = r0;
     p.n_rays = nr;
-    if (cudaMemsetAsync(p.counter, 0, 8, st) != cudaSuccess) return fail(INOLF_E_CUDA, "cudaMemsetAsync failed");
+    // hit counter per chunk, failure flags (word 1) once per call
+    if (cudaMemsetAsync(p.counter, 0, r0 == 0 ? 8 : 4, st) != cudaSuccess)
+      return fail(INOLF_E_CUDA, "cudaMemsetAsync failed");
     inolf_status s;
     if (tri_in) {  // the forward's hits: compact them instead of tracing again
       {
@@ -941,6 +992,28 @@ extern "C" inolf_status inolf_backward_hits(const inolf_object* obj, const float
 
 extern "C" size_t inolf_render_workspace_bytes(int64_t n_rays) { return inolf::workspace_bytes(n_rays); }
 
+extern "C" inolf_status inolf_workspace_flags(const void* workspace, uint32_t* flags, void* stream) {
+  clear_error();
+  if (!flags) return fail(INOLF_E_INVALID, "inolf_workspace_flags: NULL flags");
+  *flags = 0;
+  inolf_status s = read_device_flags(workspace, stream, flags);
+  if (s != INOLF_OK) return s;
+  return flags_status(*flags, "inolf_workspace_flags");
+}
+
+extern "C" inolf_status inolf_set_wait_limit_ns(int64_t ns) {
+  clear_error();
+  if (ns < 0) return fail(INOLF_E_INVALID, "inolf_set_wait_limit_ns: negative limit");
+  g_wait_ns.store(ns);
+  return INOLF_OK;
+}
+
+extern "C" inolf_status inolf_set_fault_injection(uint32_t mask) {
+  clear_error();
+  g_inject.store(mask);
+  return INOLF_OK;
+}
+
 extern "C" inolf_status inolf_render(const inolf_object* obj, const float* cams, int32_t n_views, int32_t W,
                                      int32_t H, inolf_precision prec, float* rgba_out, int32_t* tri_out,
                                      float* t_out, void* workspace, size_t workspace_bytes, void* stream) {
@@ -986,6 +1059,11 @@ extern "C" inolf_status inolf_trace_stats(const inolf_object* obj, const float* 
   if (cudaMemcpyAsync(h, dev, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return fail(INOLF_E_CUDA, "inolf_trace_stats: reading the counters failed");
+  uint32_t flags = 0;
+  s = read_device_flags(workspace, stream, &flags);
+  if (s != INOLF_OK) return s;
+  s = flags_status(flags, "inolf_trace_stats");
+  if (s != INOLF_OK) return s;
   out[0] = rb.n;
   out[1] = (int64_t)h[2];
   out[2] = (int64_t)h[0];
@@ -1027,10 +1105,13 @@ extern "C" inolf_status inolf_calibrate_fp8(inolf_object* obj, const float* cams
   inolf_status s = launch_render(obj->o, rb, INOLF_FP32, nullptr, nullptr, nullptr, nullptr, nullptr, workspace,
                                  workspace_bytes, stream, true);
   if (s != INOLF_OK) return s;
-  uint32_t bits[3];
+  uint32_t bits[3], flags = 0;
   if (cudaMemcpyAsync(bits, hdr + 4, sizeof(bits), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(&flags, hdr + 1, sizeof(flags), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return fail(INOLF_E_CUDA, "inolf_calibrate_fp8: readback failed");
+  s = flags_status(flags, "inolf_calibrate_fp8");
+  if (s != INOLF_OK) return s;
   for (int k = 0; k < 3; ++k) {
     float a;
     std::memcpy(&a, &bits[k], 4);
@@ -1119,7 +1200,8 @@ extern "C" inolf_status inolf_render_host(const inolf_object* obj, const float* 
     rb.W = W;
     rb.H = H;
     rb.n = (int64_t)nv * W * H;
-    st = launch_render(obj->o, rb, prec, dst, nullptr, nullptr, nullptr, nullptr, workspace, workspace_bytes, stream);
+    st = launch_render(obj->o, rb, prec, dst, nullptr, nullptr, nullptr, nullptr, workspace, workspace_bytes, stream,
+                       false, nullptr, false, false, /*clear_flags=*/c == 0);
     if (st != INOLF_OK) break;
     if (cudaEventRecord(rendered[slot], cs) != cudaSuccess || cudaStreamWaitEvent(xs, rendered[slot], 0) != cudaSuccess ||
         cudaMemcpyAsync(rgba_host + (size_t)v0 * W * H * 4, dst, (size_t)nv * view_bytes, cudaMemcpyDeviceToHost, xs) !=
@@ -1129,6 +1211,11 @@ extern "C" inolf_status inolf_render_host(const inolf_object* obj, const float* 
   }
   const bool synced = cudaStreamSynchronize(xs) == cudaSuccess && cudaStreamSynchronize(cs) == cudaSuccess;
   if (st == INOLF_OK && !synced) st = fail(INOLF_E_CUDA, "inolf_render_host: synchronisation failed");
+  if (st == INOLF_OK) {  // device-side failures of any chunk
+    uint32_t flags = 0;
+    st = read_device_flags(workspace, stream, &flags);
+    if (st == INOLF_OK) st = flags_status(flags, "inolf_render_host");
+  }
   for (int k = 0; k < 2; ++k) {
     if (rendered[k]) cudaEventDestroy(rendered[k]);
     if (copied[k]) cudaEventDestroy(copied[k]);

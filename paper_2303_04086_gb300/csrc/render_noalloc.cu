@@ -32,24 +32,23 @@ __global__ void k_noalloc_clear_header() {
   if (threadIdx.x < 64) reinterpret_cast<uint32_t*>(inolf_noalloc_scratch)[threadIdx.x] = 0u;
 }
 
-constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-void* g_scratch[kMaxDevices] = {};
+void* g_scratch[inolf::kMaxDevices] = {};
+
+}  // namespace
 
 // Device address of the scratch array on the current device.  In host code
 // the symbol names a host-side stand-in, not device memory, so the address
 // is looked up once per device with cudaGetSymbolAddress while that device is
 // current, then cached.
-inolf_status scratch_address(void** out) {
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return inolf::fail(INOLF_E_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices)
-    return inolf::fail(INOLF_E_UNSUPPORTED, "inolf_render_rays_noalloc: device index beyond 63");
+inolf_status inolf::noalloc_scratch_address(void** out) {
+  const int dev = inolf::device_index();
+  if (dev < 0)
+    return inolf::fail(INOLF_E_UNSUPPORTED, "inolf_render_rays_noalloc: no current device, or an index beyond 63");
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_scratch[dev]) {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, inolf_noalloc_scratch);
+    cudaError_t e = cudaGetSymbolAddress(&p, inolf_noalloc_scratch);
     if (e != cudaSuccess || !p)
       return inolf::fail(INOLF_E_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
     g_scratch[dev] = p;
@@ -57,8 +56,6 @@ inolf_status scratch_address(void** out) {
   *out = g_scratch[dev];
   return INOLF_OK;
 }
-
-}  // namespace
 
 extern "C" inolf_status inolf_render_rays_noalloc(const inolf_object* obj, const float* o, const float* d,
                                                   int64_t n, inolf_precision prec, float* rgba_out,
@@ -73,7 +70,7 @@ extern "C" inolf_status inolf_render_rays_noalloc(const inolf_object* obj, const
                                             " rays; split the batch or use inolf_render_rays");
   if (n == 0) return INOLF_OK;
   void* ws = nullptr;
-  inolf_status s = scratch_address(&ws);
+  inolf_status s = inolf::noalloc_scratch_address(&ws);
   if (s != INOLF_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
   k_noalloc_clear_header<<<1, 64, 0, st>>>();
@@ -84,6 +81,12 @@ extern "C" inolf_status inolf_render_rays_noalloc(const inolf_object* obj, const
   rb.o = o;
   rb.d = d;
   rb.n = n;
-  return inolf::launch_render(obj->o, rb, prec, rgba_out, tri_out, t_out, nullptr, nullptr, ws, kNoAllocBytes,
-                              stream);
+  s = inolf::launch_render(obj->o, rb, prec, rgba_out, tri_out, t_out, nullptr, nullptr, ws, kNoAllocBytes, stream);
+  if (s != INOLF_OK) return s;
+  // the failure flags sit in the scratch header, out of the caller's reach,
+  // and the next call clears them: read them now (this synchronises `stream`)
+  uint32_t flags = 0;
+  s = inolf::read_device_flags(ws, stream, &flags);
+  if (s != INOLF_OK) return s;
+  return inolf::flags_status(flags, "inolf_render_rays_noalloc");
 }

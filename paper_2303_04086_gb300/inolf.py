@@ -19,8 +19,10 @@ LIB_PATH = os.path.join(HERE, "libinolf.so")
 
 OK, PENDING = 0, 1
 (E_INVALID, E_OOM, E_CUDA, E_BUDGET, E_TIMEOUT, E_HASH_FAILED, E_UNKNOWN_TICKET, E_UNSUPPORTED,
- E_CANCELLED) = range(-1, -10, -1)
+ E_CANCELLED, E_DEVICE) = range(-1, -11, -1)
 REQ_TEST_DROP_DESCRIPTOR = 1
+FLAG_STACK_OVERFLOW, FLAG_TRAVERSAL_LIMIT, FLAG_WAIT_TIMEOUT = 1, 2, 4
+INJECT_RING_STALL = 1
 FP32, BF16, FP8 = 0, 1, 2
 PRECISIONS = {"fp32": FP32, "bf16": BF16, "fp8": FP8}
 MAX_LEVELS = 16
@@ -105,6 +107,9 @@ def lib():
     L.inolf_backward_hits.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
     L.inolf_object_load_params.argtypes = [vp, vp, vp, vp, vp, vp]
     L.inolf_object_get_fp8_scales.argtypes = [vp, vp, vp]
+    L.inolf_workspace_flags.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32), vp]
+    L.inolf_set_wait_limit_ns.argtypes = [i64]
+    L.inolf_set_fault_injection.argtypes = [ctypes.c_uint32]
     _lib = L
     return L
 
@@ -133,6 +138,43 @@ def _stream(stream) -> Optional[int]:
     if stream is None:
         return torch.cuda.current_stream().cuda_stream
     return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+_check_flags = False
+
+
+def check_device_flags(on: bool = True):
+    """When on, every asynchronous render / backward wrapper below waits for
+    its call and raises InolfError if a kernel set a failure flag (see
+    workspace_flags).  Off by default: the check synchronises the stream."""
+    global _check_flags
+    _check_flags = bool(on)
+
+
+def workspace_flags(workspace=None, stream=None) -> int:
+    """inolf_workspace_flags: the INOLF_FLAG_* bits the kernels of the last
+    call on `workspace` set (None = the allocation-free scratch); synchronises
+    the stream.  Returns the bits; a non-zero value is not raised."""
+    f = ctypes.c_uint32(0)
+    st = lib().inolf_workspace_flags(_ptr(workspace), ctypes.byref(f), _stream(stream))
+    if st < 0 and f.value == 0:
+        raise InolfError(st, last_error())
+    return int(f.value)
+
+
+def _after(workspace, stream):
+    if _check_flags:
+        _check(lib().inolf_workspace_flags(_ptr(workspace), ctypes.byref(ctypes.c_uint32(0)), _stream(stream)))
+
+
+def set_wait_limit_ns(ns: int):
+    """Limit of the warp-specialised shade kernels' hand-over waits (0 = 2 s)."""
+    _check(lib().inolf_set_wait_limit_ns(int(ns)))
+
+
+def set_fault_injection(mask: int):
+    """Test-only fault injection (INJECT_RING_STALL), process-wide; 0 = off."""
+    _check(lib().inolf_set_fault_injection(int(mask)))
 
 
 # ---------------------------------------------------------------------------
@@ -306,6 +348,7 @@ def render(obj: Object, cams: np.ndarray, W: int, H: int, prec="fp32", rgba_out=
     _check(lib().inolf_render(obj.handle, cams.ctypes.data, nv, W, H, p, _ptr(rgba_out), _ptr(tri_out),
                               _ptr(t_out), _ptr(workspace), workspace.numel() * workspace.element_size(),
                               _stream(stream)))
+    _after(workspace, stream)
     return rgba_out
 
 
@@ -366,6 +409,7 @@ def render_rays(obj: Object, o, d, prec="fp32", rgba_out=None, tri_out=None, t_o
     _check(lib().inolf_render_rays(obj.handle, _ptr(o), _ptr(d), n, p, _ptr(rgba_out), _ptr(tri_out),
                                    _ptr(t_out), _ptr(workspace), workspace.numel() * workspace.element_size(),
                                    _stream(stream)))
+    _after(workspace, stream)
     return rgba_out
 
 
@@ -413,6 +457,7 @@ def march_rays(obj: Object, o, d, k_out=None, t_out=None, alpha_out=None, worksp
         workspace = _workspace(n, o.device)
     _check(lib().inolf_march_rays(obj.handle, _ptr(o), _ptr(d), n, _ptr(k_out), _ptr(t_out), _ptr(alpha_out),
                                   _ptr(workspace), workspace.numel() * workspace.element_size(), _stream(stream)))
+    _after(workspace, stream)
     return k_out, t_out, alpha_out
 
 
@@ -425,6 +470,7 @@ def encode_rays(obj: Object, o, d, slots_out, feat_out, workspace=None, stream=N
     _check(lib().inolf_encode_rays(obj.handle, _ptr(o), _ptr(d), n, _ptr(slots_out), _ptr(feat_out),
                                    _ptr(workspace), workspace.numel() * workspace.element_size(),
                                    _stream(stream)))
+    _after(workspace, stream)
 
 
 # ---------------------------------------------------------------------------
@@ -471,10 +517,12 @@ def backward(obj: Object, o, d, d_rgba, grad_tables, gw1, gw2, gw3, workspace=No
                                          ctypes.cast(tp, ctypes.c_void_p), _ptr(gw1), _ptr(gw2), _ptr(gw3),
                                          _ptr(workspace), workspace.numel() * workspace.element_size(),
                                          _stream(stream)))
+        _after(workspace, stream)
         return
     _check(lib().inolf_backward(obj.handle, _ptr(o), _ptr(d), n, _ptr(d_rgba), ctypes.cast(tp, ctypes.c_void_p),
                                 _ptr(gw1), _ptr(gw2), _ptr(gw3), _ptr(workspace),
                                 workspace.numel() * workspace.element_size(), _stream(stream)))
+    _after(workspace, stream)
 
 
 def load_params(obj: Object, tables=None, w1=None, w2=None, w3=None, stream=None):

@@ -22,6 +22,17 @@ def _host_builds():
     oracle.build()
 
 
+@pytest.fixture(scope="session", autouse=True)
+def _device_flag_checks():
+    """Every asynchronous render / backward call made through the Python
+    binding in the tests waits for its kernels and fails on a device-side
+    failure flag (a traversal overflow, a bounded wait that ran out)."""
+    from paper_2303_04086_gb300 import inolf
+    inolf.check_device_flags(True)
+    yield
+    inolf.check_device_flags(False)
+
+
 @pytest.fixture(scope="session")
 def tiny():
     from paper_2303_04086_gb300 import synth

@@ -48,6 +48,10 @@ def test_render_rejects_bad_arguments_before_any_launch(lib):
     # the measurement aids check their arguments on the host too
     assert lib.inolf_trace_stats(None, None, 1, 4, 4, None, None, 0, None) == inolf.E_INVALID
     assert lib.inolf_probe_peaks(None, None) == inolf.E_INVALID
+    assert lib.inolf_workspace_flags(None, None, None) == inolf.E_INVALID
+    assert lib.inolf_set_wait_limit_ns(-1) == inolf.E_INVALID
+    assert lib.inolf_set_wait_limit_ns(0) == inolf.OK
+    assert lib.inolf_set_fault_injection(0) == inolf.OK
 
 
 def _cube_desc_scene():

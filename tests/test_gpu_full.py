@@ -105,3 +105,42 @@ def test_full_slots_all_levels(full, full_oracle):
         expect = oracle.psh_slots(h.phi, h.m, h.r, coords).reshape(n, 8)
         assert np.array_equal(slots[:, l, :], expect), l
     assert np.abs(feats.cpu().numpy() - r["E"][hit, :2 * L]).max() <= 1e-6
+
+
+def _psnr(a, b):
+    mse = float(np.mean((a - b) ** 2))
+    return 99.0 if mse == 0 else 10.0 * np.log10(1.0 / mse)
+
+
+def test_full_bf16_fp8_sampled(full, full_oracle):
+    # the tensor-core MLP at the benchmark's configuration (L = 16, d_in = 48,
+    # layer 1 padded to K = 48 for BF16 and K = 64 for FP8): two 4K views,
+    # 3000 sampled pixels each plus the silhouette patch, against the FP64
+    # oracle at the precision bars (BF16 >= 45 dB and <= 1e-2 max-abs, FP8
+    # >= 38 dB; PSNR over the 4 channels of hit pixels)
+    torch, inolf, scene, obj, cams = full
+    assert scene.d_in == 48
+    inolf.calibrate_fp8(obj, cams[:1], W, H)  # view 0, FP32 path, then frozen
+    views = [0, 40]
+    sel = cams[views]
+    got = {}
+    for prec in ("bf16", "fp8"):
+        tri = torch.empty((len(views), H, W), dtype=torch.int32, device="cuda")
+        rgba = inolf.render(obj, sel, W, H, prec, tri_out=tri)
+        torch.cuda.synchronize()
+        got[prec] = (rgba, tri)
+    for k, v in enumerate(views):
+        pix = _sample(v, 3000, 100 + v)
+        ref = full_oracle.render_pixels(cams[v], W, H, pix)
+        hit = ref["tri"] >= 0
+        assert 0.2 < hit.mean() < 0.9
+        pt = torch.from_numpy(pix).cuda()
+        for prec, bar in (("bf16", 45.0), ("fp8", 38.0)):
+            rgba, tri = got[prec]
+            assert np.array_equal(tri[k].reshape(-1)[pt].cpu().numpy(), ref["tri"])
+            g = rgba[k].reshape(-1, 4)[pt].cpu().numpy()
+            assert np.all(g[~hit] == 0)
+            p, err = _psnr(g[hit], ref["rgba"][hit]), float(np.abs(g - ref["rgba"]).max())
+            assert p >= bar, (prec, v, p, err)
+            if prec == "bf16":
+                assert err <= 1e-2, (v, p, err)

@@ -9,6 +9,9 @@ caller-provided workspace.  Two calls in a row, with different rays, must each
 match the workspace-based entry point (triangle ids and t bit-exact, RGBA within
 the 1e-4 max-abs tolerance of the other parity tests), which also shows that the
 second call is not disturbed by what the first left in the shared array.
+The BF16 and FP8 paths read the same array and must match inolf_render_rays
+at their precision; a warmed-up call through the Python wrapper with
+preallocated outputs must leave the device's allocations unchanged.
 
 This file is named so that pytest collects it last."""
 import ctypes
@@ -76,6 +79,35 @@ def test_noalloc_matches_workspace_entry_point_twice(setup):
         assert np.isfinite(got[0]).all()
         assert np.abs(got[0] - ref[0]).max() <= RGBA_TOL, f"call {call}: RGBA differs"
         assert (ref[1] >= 0).mean() > 0.2
+
+
+def test_noalloc_lower_precisions_and_no_device_allocation(setup):
+    # the BF16 and FP8 tensor-core shade kernels read the same scratch hit list;
+    # through the Python wrapper with preallocated outputs, a warmed-up call
+    # leaves both torch's allocator and the device's free memory unchanged
+    torch, inolf, obj = setup
+    from paper_2303_04086_gb300 import synth
+    inolf.calibrate_fp8(obj, synth.ring_cameras(1, 3.0), 256, 256)
+    n = 5003
+    o_np, d_np = _rays(n, 13)
+    o, d = torch.from_numpy(o_np).cuda(), torch.from_numpy(d_np).cuda()
+    for prec in ("bf16", "fp8"):
+        ref = inolf.render_rays(obj, o, d, prec)
+        out = torch.full((n, 4), float("nan"), dtype=torch.float32, device="cuda")
+        tri = torch.empty((n,), dtype=torch.int32, device="cuda")
+        for _ in range(2):  # warm-up: kernels loaded, library set-up done
+            inolf.render_rays_noalloc(obj, o, d, prec, rgba_out=out, tri_out=tri)
+        torch.cuda.synchronize()
+        used, free = torch.cuda.memory_allocated(), torch.cuda.mem_get_info()[0]
+        out.fill_(float("nan"))
+        got = inolf.render_rays_noalloc(obj, o, d, prec, rgba_out=out, tri_out=tri)
+        torch.cuda.synchronize()
+        assert torch.cuda.memory_allocated() == used
+        assert torch.cuda.mem_get_info()[0] == free
+        assert got.data_ptr() == out.data_ptr()
+        assert bool(torch.isfinite(out).all())
+        assert float((out - ref).abs().max()) <= RGBA_TOL, prec
+        assert inolf.workspace_flags(None) == 0
 
 
 def test_noalloc_rejects_batches_beyond_the_limit(setup):
