@@ -52,6 +52,8 @@ def _args():
     ap.add_argument("--no-variant", action="store_true", help="skip the density-cube variant workload")
     ap.add_argument("--training-only", action="store_true",
                     help="run only the differentiation workload and print its JSON (profiling)")
+    ap.add_argument("--serving-only", action="store_true",
+                    help="run only the serving workload (policy 1) and print its JSON (profiling)")
     ap.add_argument("--variant-only", action="store_true",
                     help="run only the density-cube variant workload (--views, --steps, --warmup, --precisions) "
                          "and print its JSON (profiling)")
@@ -401,7 +403,18 @@ def run_serving(seconds=10.0, warmup=1.0, rate_hz=50.0, seed=0, prec="bf16", pol
         time.sleep(0.0002)
     wall = time.perf_counter() - t0 - warmup
     counters = srv.counters()
+    prof = srv.profile()
     srv.close()
+    work = sum(prof[k] for k in ("trace_cycles", "shade_cycles", "composite_cycles", "done_cycles"))
+    phases = {k.replace("_cycles", ""): prof[k] / max(1, work)
+              for k in ("trace_cycles", "shade_cycles", "composite_cycles", "done_cycles")}
+    profile = {"phase_share_of_work": phases,
+               "claim_and_idle_cycles_per_work_cycle": prof["claim_cycles"] / max(1, work),
+               "cycles_per_tile": work / max(1, prof["tiles"]),
+               "hits_per_tile": prof["hits"] / max(1, prof["tiles"]),
+               "mlp_batches_per_tile": prof["mlp_batches"] / max(1, prof["tiles"]),
+               "rows_used_per_256_row_batch": prof["hits"] / max(1, prof["mlp_batches"]),
+               "raw": prof}
     lat_ms = np.array(lat) * 1e3
     return {"viewers": len(viewers), "objects": len(objs), "rate_hz_per_viewer": rate_hz, "seconds": seconds,
             "frames": frames, "frames_per_s": frames / wall, "mrays_per_s": rays_done / wall / 1e6,
@@ -410,6 +423,7 @@ def run_serving(seconds=10.0, warmup=1.0, rate_hz=50.0, seed=0, prec="bf16", pol
             "refused": refused, "submitted": submitted, "precision": prec,
             "policy": "algorithm1" if policy == 1 else "arrival-order",
             "max_rays_in_flight": max_rays_in_flight if policy == 1 else None, "counters": counters,
+            "kernel_profile": profile,
             "note": "latency = arrival time -> completion seen by the poller; refused = admission (slots/HBM "
                     "budget) full at arrival"}
 
@@ -543,14 +557,21 @@ def run_training(steps=40, batch=1 << 18, n_views=100, res=800, prec="bf16"):
             losses.append(one())
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
+    if graph is not None:  # per-kernel times from a few eager steps with launch events (outside the timed loop)
+        inolf.stats_enable(True)
+        for _ in range(5):
+            one()
+        torch.cuda.synchronize()
+        n_kern = 5
+    else:
+        n_kern = steps
     inolf.stats_enable(False)
-    kern = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / steps} for k, v in inolf.stats_read().items()}
+    kern = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / n_kern} for k, v in inolf.stats_read().items()}
     losses = [float(x) for x in losses]
     out = {"steps_per_s": steps / dt, "rays_per_step": batch, "mrays_per_s": steps * batch / dt / 1e6,
            "loss_first": losses[0], "loss_last": losses[-1], "forward": prec, "backward": "fp32",
-           "views": n_views, "res": res, "cuda_graph": graph is not None}
+           "views": n_views, "res": res, "cuda_graph": graph is not None, "kernels": kern}
     if graph is None:
-        out["kernels"] = kern
         out["capture_error"] = capture_error
     return out
 
@@ -966,6 +987,10 @@ def main():
         from paper_2303_04086_gb300 import build
         build.build()
         print(json.dumps({"training": run_training(steps=max(1, a.steps))}))
+    elif a.serving_only:
+        from paper_2303_04086_gb300 import build
+        build.build()
+        print(json.dumps({"serving": run_serving(seconds=a.serving_seconds, policy=1)}))
     elif a.variant_only:
         from paper_2303_04086_gb300 import build
         build.build()

@@ -231,7 +231,8 @@ inolf_status inolf_render(const inolf_object* obj, const float* cams, int32_t n_
  * INOLF_OK when no bit is set, INOLF_E_TIMEOUT when INOLF_FLAG_WAIT_TIMEOUT is
  * set, INOLF_E_DEVICE for the traversal bits (the message names them),
  * INOLF_E_INVALID for a NULL flags pointer, INOLF_E_CUDA when the read fails.
- * The asynchronous calls (inolf_render, inolf_render_rays, inolf_backward, ...)
+ * A call without work (no rays) launches nothing and leaves the word as it
+ * was.  The asynchronous calls (inolf_render, inolf_render_rays, inolf_backward, ...)
  * leave the check to the caller; the synchronising ones (inolf_render_host,
  * inolf_calibrate_fp8, inolf_trace_stats, inolf_render_rays_noalloc) make it
  * themselves and return its status. */
@@ -425,6 +426,17 @@ inolf_status inolf_serve_destroy(inolf_server* srv);
  * budget), denied by the starvation state (policy 1), completed. */
 inolf_status inolf_serve_counters(inolf_server* srv, int64_t* admitted, int64_t* refused, int64_t* denied,
                                   int64_t* completed);
+
+/* Profile of the request loop (measurement support, no paper counterpart),
+ * summed over the persistent CTAs, which add their figures when they exit:
+ * the call first waits for the kernel to go idle and return.  out (host, 9
+ * entries): SM clock cycles spent in [0] claiming tiles and reading request
+ * descriptors (including waiting for work), [1] tracing every object and
+ * ordering the hits, [2] shading (weights staged, encoding, MLP), [3]
+ * compositing and storing, [4] completion; then [5] tiles, [6] hits shaded,
+ * [7] MLP batches (256-row tensor-core passes or FP32 passes of one object),
+ * [8] weight stagings.  reset != 0 zeroes the counters after reading. */
+inolf_status inolf_serve_profile(inolf_server* srv, int64_t* out, int32_t reset);
 
 /* ------------------------------------------------------------------------ */
 /* Multi-user scheduling policy (Sec. 6.2, Algorithm 1, Eq. 13), host-only.  */

@@ -26,6 +26,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -736,7 +737,9 @@ static inolf_status check_launch(const char* what) {
 
 inolf_status flags_status(uint32_t flags, const char* what) {
   if (!flags) return INOLF_OK;
-  std::string m = std::string(what) + ": device-side failure flags 0x" + std::to_string(flags) + " (";
+  char hex[16];
+  std::snprintf(hex, sizeof(hex), "0x%x", flags);
+  std::string m = std::string(what) + ": device-side failure flags " + hex + " (";
   if (flags & INOLF_FLAG_WAIT_TIMEOUT) m += " a bounded wait in a shade kernel ran out;";
   if (flags & INOLF_FLAG_STACK_OVERFLOW) m += " a BVH traversal stack overflowed;";
   if (flags & INOLF_FLAG_TRAVERSAL_LIMIT) m += " a BVH traversal exceeded its step limit;";

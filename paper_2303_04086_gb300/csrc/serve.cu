@@ -92,12 +92,29 @@ struct ServeCtl {  // mapped host memory
   uint32_t pad;
 };
 
+// Profile of the request loop (inolf_serve_profile), summed over CTAs when
+// each persistent CTA exits: SM cycles per phase, then event counts.
+enum ServeProf {
+  kProfClaim = 0,   // claiming tiles and reading request descriptors (includes waiting for work)
+  kProfTrace,       // ray generation, every object's proxy traced, K nearest hits sorted and grouped
+  kProfShade,       // per object: weights staged, encoding gathered, MLP
+  kProfComposite,   // front-to-back compositing and the frame store
+  kProfDone,        // completion counting and publication
+  kProfTiles,       // tiles processed
+  kProfHits,        // hits shaded (<= K per pixel)
+  kProfBatches,     // MLP batches (one 256-row tensor-core pass, or one FP32 pass of an object)
+  kProfWeightLoads, // weight stagings into shared memory
+  kProfCount
+};
+
 struct ServeDevState {  // device memory
   unsigned long long head;           // tiles claimed so far
   unsigned long long last_activity;  // global timer of the last claim
   uint32_t tiles_done[kServeMaxSlots];
   int32_t status[kServeMaxSlots];
   uint32_t err;
+  uint32_t pad;
+  unsigned long long prof[kProfCount];
 };
 
 struct ServeKParams {
@@ -185,6 +202,11 @@ __device__ __forceinline__ float4 mlp_f32(const float4* W1T, const float4* W2, c
   return make_float4(sigmoidf_(acc.x), sigmoidf_(acc.y), sigmoidf_(acc.z), sigmoidf_(acc.w));
 }
 
+// Pixel of thread t within a 16 x 16 tile: each warp covers an 8 x 4 block
+// (the 8 warps tile 2 x 4 blocks), so that a warp's rays are coherent packets.
+__device__ __forceinline__ int serve_px(int t) { return ((t >> 5) & 1) * 8 + (t & 7); }
+__device__ __forceinline__ int serve_py(int t) { return (t >> 6) * 4 + ((t >> 3) & 3); }
+
 // The density-cube path kept out of line, so that the march and the diffuse
 // lookup do not raise the register pressure of the mesh-object path.
 __device__ __noinline__ void serve_march(const CubesDev& c, float lo, float scale, const float* o, const float* d,
@@ -231,11 +253,14 @@ __global__ void __launch_bounds__(kServeThreads, 2) k_serve(const __grid_constan
   __shared__ uint32_t s_cnt[kServeMaxObjects], s_off[kServeMaxObjects + 1];
   __shared__ float s_ht[kServeThreads * kServeMaxK];
   __shared__ float s_ah[kCubes ? kServeThreads * kServeMaxK : 1];  // alpha_c of each hit (density-cube objects)
+  __shared__ uint4 s_ring[kServeClaim][2];                           // ring entries of the claimed batch
+  __shared__ int s_wcache;  // object (+ 1000 for FP32 weights) whose weights are staged, -1: none
   const int tid = threadIdx.x;
   const unsigned long long t_start = gtimer();
   if (tid == 0) {
     s_have = 0;
     s_slot = 0xFFFFFFFFu;
+    s_wcache = -1;
     tc::mbar_init(&bars[0], 1);
     tc::mbar_init(&bars[1], 1);
     tc::fence_mbar_init();
@@ -250,46 +275,92 @@ __global__ void __launch_bounds__(kServeThreads, 2) k_serve(const __grid_constan
   bool broken = false;
 
   unsigned long long batch_next = 0, batch_end = 0;  // tiles claimed but not yet processed (thread 0)
+  unsigned long long prof[kProfCount] = {};          // thread 0's phase cycles and counts
+  long long clk = clock64();
+  auto lap = [&](int phase) {
+    if (tid == 0) {
+      const long long now = clock64();
+      prof[phase] += (unsigned long long)(now - clk);
+      clk = now;
+    }
+  };
+  // completion counts not yet published (thread 0): tiles of one request
+  // generation finished by this CTA since its last flush
+  uint32_t pend_slot = 0, pend_gen = 0, pend_n = 0, pend_total = 0;
+  auto flush_done = [&]() {  // thread 0, after a CTA barrier that follows the frame stores
+    if (!pend_n) return;
+    // bar.sync orders the CTA's frame writes before thread 0's device-scope
+    // fence and counter update; the CTA that completes the request observes
+    // every other CTA's update and issues the one system-scope fence before
+    // the completion record, which makes the whole frame visible to the host
+    __threadfence();
+    const uint32_t n = atomicAdd(&kp.st->tiles_done[pend_slot], pend_n) + pend_n;
+    if (n == pend_total) {
+      const int status = atomicExch(&kp.st->status[pend_slot], 0);
+      kp.st->tiles_done[pend_slot] = 0;
+      __threadfence_system();
+      *(volatile int32_t*)&kp.done[pend_slot].status = status;
+      st_rel_sys_u32(&kp.done[pend_slot].gen, pend_gen);
+    }
+    pend_n = 0;
+  };
+  unsigned long long batch_start = 0;
   while (!broken) {
     // ---- claim a batch of up to kServeClaim published tiles (thread 0), bounded idle wait ----
-    if (tid == 0) {
-      int cmd = 1;
-      if (batch_next < batch_end) {
-        s_idx = batch_next++;
-        cmd = 0;
-      }
-      while (cmd) {
-        if (ld_vol_u32(&kp.ctl->stop)) break;
-        const unsigned long long pub = ld_acq_sys_u64(&kp.ctl->published);
-        unsigned long long h = *(volatile unsigned long long*)&kp.st->head;
-        bool claimed = false;
-        while (h < pub) {  // one CAS claims min(kServeClaim, pub - h) consecutive tiles
-          const unsigned long long n = min((unsigned long long)kServeClaim, pub - h);
-          const unsigned long long prev = atomicCAS(&kp.st->head, h, h + n);
-          if (prev == h) {
-            s_idx = h;
-            batch_next = h + 1;
-            batch_end = h + n;
-            claimed = true;
+    if (tid < 32) {
+      int fresh = 0;  // a new batch was claimed: warp 0 copies its ring entries
+      if (tid == 0) {
+        int cmd = 1;
+        if (batch_next < batch_end) {
+          s_idx = batch_next++;
+          cmd = 0;
+        }
+        while (cmd) {
+          if (ld_vol_u32(&kp.ctl->stop)) break;
+          const unsigned long long pub = ld_acq_sys_u64(&kp.ctl->published);
+          unsigned long long h = *(volatile unsigned long long*)&kp.st->head;
+          bool claimed = false;
+          while (h < pub) {  // one CAS claims min(kServeClaim, pub - h) consecutive tiles
+            const unsigned long long n = min((unsigned long long)kServeClaim, pub - h);
+            const unsigned long long prev = atomicCAS(&kp.st->head, h, h + n);
+            if (prev == h) {
+              s_idx = h;
+              batch_start = h;
+              batch_next = h + 1;
+              batch_end = h + n;
+              claimed = true;
+              break;
+            }
+            h = prev;
+          }
+          if (claimed) {
+            cmd = 0;
+            fresh = 1;
+            atomicMax(&kp.st->last_activity, gtimer());
             break;
           }
-          h = prev;
+          const unsigned long long now = gtimer();
+          const unsigned long long last =
+              max(*(volatile unsigned long long*)&kp.st->last_activity, t_start);
+          if (now > last + kp.idle_limit_ns) break;  // idle: exit, the host relaunches on new work
+          __nanosleep(1000);
         }
-        if (claimed) {
-          cmd = 0;
-          atomicMax(&kp.st->last_activity, gtimer());
-          break;
-        }
-        const unsigned long long now = gtimer();
-        const unsigned long long last =
-            max(*(volatile unsigned long long*)&kp.st->last_activity, t_start);
-        if (now > last + kp.idle_limit_ns) break;  // idle: exit, the host relaunches on new work
-        __nanosleep(1000);
+        s_cmd = cmd;
       }
-      s_cmd = cmd;
-      if (cmd == 0) {
-        const ServeTile* e = kp.ring + (s_idx % kp.ring_cap);
-        const uint4 e0 = ld_vol_v4(e), e1 = ld_vol_v4(reinterpret_cast<const uint4*>(e) + 1);
+      // the ring lives in mapped host memory: one round trip for the whole batch
+      fresh = __shfl_sync(0xffffffffu, fresh, 0);
+      if (fresh) {
+        const unsigned long long b0 = __shfl_sync(0xffffffffu, batch_start, 0);
+        const unsigned long long nb = __shfl_sync(0xffffffffu, batch_end - batch_start, 0);
+        if ((unsigned long long)tid < nb) {
+          const ServeTile* e = kp.ring + ((b0 + (unsigned long long)tid) % kp.ring_cap);
+          s_ring[tid][0] = ld_vol_v4(e);
+          s_ring[tid][1] = ld_vol_v4(reinterpret_cast<const uint4*>(e) + 1);
+        }
+      }
+      __syncwarp();
+      if (tid == 0 && s_cmd == 0) {
+        const uint4 e0 = s_ring[s_idx - batch_start][0], e1 = s_ring[s_idx - batch_start][1];
         const bool same = e0.x == s_slot && e0.y == s_gen && s_have;  // descriptor cached from the last tile
         s_slot = e0.x;
         s_gen = e0.y;
@@ -328,13 +399,14 @@ __global__ void __launch_bounds__(kServeThreads, 2) k_serve(const __grid_constan
     }
     if (tid < kServeMaxObjects) s_cnt[tid] = 0;
     __syncthreads();
+    lap(kProfClaim);
     if (s_cmd) break;
 
     // ---- trace every object, keep the K nearest hits of this pixel ----
     float ht[kServeMaxK], ha[kServeMaxK];
     int hk[kServeMaxK];
     int nh = 0;
-    const int i = (int)s_tx * kServeTile + (tid & 15), j = (int)s_ty * kServeTile + (tid >> 4);
+    const int i = (int)s_tx * kServeTile + serve_px(tid), j = (int)s_ty * kServeTile + serve_py(tid);
     const bool valid = !s_skip && i < s_W && j < s_H;
     float o[3] = {0.f, 0.f, 0.f}, d[3] = {1.f, 1.f, 1.f};
     if (valid) make_ray(s_cam, s_W, s_H, i, j, o, d);
@@ -399,6 +471,11 @@ __global__ void __launch_bounds__(kServeThreads, 2) k_serve(const __grid_constan
     for (int q = 0; q < nh; ++q) s_list[s_off[hk[q]] + rank[q]] = (uint16_t)(tid * kServeMaxK + q);
     __syncthreads();
 
+    lap(kProfTrace);
+    if (tid == 0) {
+      prof[kProfTiles] += 1;
+      prof[kProfHits] += s_off[kServeMaxObjects];
+    }
     // ---- shade the hits object by object ----
     for (int k = 0; k < kp.n_objs && !broken; ++k) {
       const uint32_t cnt = s_cnt[k];
@@ -406,9 +483,17 @@ __global__ void __launch_bounds__(kServeThreads, 2) k_serve(const __grid_constan
       const ServeObj& ob = kp.objs[k];
       const int din = ob.d_in;
       if (s_prec == INOLF_FP32) {
+        // the object's FP32 weights, unless they are still staged from the last pass
+        const bool need = s_wcache != 1000 + k;
         const int nw4 = (din * 64 + 64 * 64 + 64 * 4) / 4;
-        for (int q = tid; q < nw4; q += kServeThreads) sWf[q] = reinterpret_cast<const float4*>(ob.w_f32)[q];
+        if (tid == 0) {
+          prof[kProfWeightLoads] += need ? 1 : 0;
+          prof[kProfBatches] += 1;
+        }
+        if (need)
+          for (int q = tid; q < nw4; q += kServeThreads) sWf[q] = reinterpret_cast<const float4*>(ob.w_f32)[q];
         __syncthreads();
+        if (tid == 0 && need) s_wcache = 1000 + k;
         for (int q = 0; q < nh; ++q) {
           if (hk[q] != k) continue;
           float ol[3], x3[3];
@@ -438,15 +523,23 @@ __global__ void __launch_bounds__(kServeThreads, 2) k_serve(const __grid_constan
         }
         __syncthreads();
       } else {
-        // BF16 tensor-core MLP: stage the object's operand blob by one bulk copy
+        // BF16 tensor-core MLP: stage the object's operand blob by one bulk copy,
+        // unless it is still staged from the last pass
         const uint32_t K1 = (uint32_t)ob.tc_k1_bf16, chunks1 = K1 / 8u;
-        if (tid == 0) {
-          tc::mbar_arrive_expect_tx(&bars[0], ob.tc_bytes_bf16);
-          tc::bulk_g2s(smem, ob.w_bf16, ob.tc_bytes_bf16, &bars[0]);
+        const bool need = s_wcache != k;
+        bool okw = true;
+        if (need) {
+          if (tid == 0) {
+            tc::fence_async_smem();  // after generic writes (FP32 weights) to the same bytes
+            tc::mbar_arrive_expect_tx(&bars[0], ob.tc_bytes_bf16);
+            tc::bulk_g2s(smem, ob.w_bf16, ob.tc_bytes_bf16, &bars[0]);
+            prof[kProfWeightLoads] += 1;
+          }
+          okw = tc::mbar_wait(&bars[0], w_phase, kWaitLimitNs);
+          w_phase ^= 1u;
         }
-        const bool okw = tc::mbar_wait(&bars[0], w_phase, kWaitLimitNs);
-        w_phase ^= 1u;
         if (__syncthreads_or(!okw)) { broken = true; break; }
+        if (tid == 0 && need) s_wcache = k;
         const uint8_t* sB1 = smem;
         const uint8_t* sB2 = smem + 64u * K1 * 2u;
         const float* sW3 = reinterpret_cast<const float*>(sB2 + 64u * 64u * 2u);
@@ -459,7 +552,7 @@ __global__ void __launch_bounds__(kServeThreads, 2) k_serve(const __grid_constan
             entry = s_list[s_off[k] + base + tid];
             const int p = (int)(entry / kServeMaxK);
             const float th = s_ht[entry];
-            const int pi = (int)s_tx * kServeTile + (p & 15), pj = (int)s_ty * kServeTile + (p >> 4);
+            const int pi = (int)s_tx * kServeTile + serve_px(p), pj = (int)s_ty * kServeTile + serve_py(p);
             float po[3], pd[3], ol[3], x3[3];
             make_ray(s_cam, s_W, s_H, pi, pj, po, pd);
 #pragma unroll
@@ -495,6 +588,7 @@ __global__ void __launch_bounds__(kServeThreads, 2) k_serve(const __grid_constan
           }
           float4 rgba;
           const TcScales sc = TcScales::make(false, nullptr, nullptr);
+          if (tid == 0) prof[kProfBatches] += 1;
           if (!tc_mlp_run<false>(sA, sB1, sB2, sW3, K1, tmem, &bars[1], mma_phase, sc, rgba)) {
             broken = true;
             break;
@@ -502,7 +596,7 @@ __global__ void __launch_bounds__(kServeThreads, 2) k_serve(const __grid_constan
           if (mine) {
             if (kCubes && ob.variant) {  // c = c_d + tint c_s (Eq. 7), diffuse read at the hit point
               const int p = (int)(entry / kServeMaxK);
-              const int pi = (int)s_tx * kServeTile + (p & 15), pj = (int)s_ty * kServeTile + (p >> 4);
+              const int pi = (int)s_tx * kServeTile + serve_px(p), pj = (int)s_ty * kServeTile + serve_py(p);
               float po[3], pd[3], ol[3], x3[3];
               make_ray(s_cam, s_W, s_H, pi, pj, po, pd);
 #pragma unroll
@@ -518,6 +612,7 @@ __global__ void __launch_bounds__(kServeThreads, 2) k_serve(const __grid_constan
     }
     __syncthreads();
 
+    lap(kProfShade);
     // ---- composite front to back, straight alpha out ----
     if (valid && !broken) {
       float C0 = 0.f, C1 = 0.f, C2 = 0.f, A = 0.f;
@@ -533,27 +628,34 @@ __global__ void __launch_bounds__(kServeThreads, 2) k_serve(const __grid_constan
       reinterpret_cast<float4*>(s_out)[(size_t)j * s_W + i] = px;
     }
     __syncthreads();
-    // ---- tile done; the last tile of the request publishes its completion ----
-    // (bar.sync orders the CTA's frame writes before thread 0's device-scope
-    // fence and counter update; the CTA that completes the request observes
-    // every other tile's update and issues the one system-scope fence before
-    // the completion record, which makes the whole frame visible to the host)
+    lap(kProfComposite);
+    // ---- tile done: its count joins this CTA's pending completions, which are
+    // published (one fence) when the next tile belongs to another request or
+    // the claimed batch is used up; the last tile of a request publishes it ----
     if (tid == 0) {
-      __threadfence();
       const uint32_t slot = s_slot;
       const int st = broken ? INOLF_E_TIMEOUT : s_status;
       if (broken) atomicOr(&kp.st->err, 4u);
       if (st) atomicCAS(&kp.st->status[slot], 0, st);
-      const uint32_t n = atomicAdd(&kp.st->tiles_done[slot], 1u) + 1u;
-      if (n == s_tiles_total) {
-        const int status = atomicExch(&kp.st->status[slot], 0);
-        kp.st->tiles_done[slot] = 0;
-        __threadfence_system();
-        *(volatile int32_t*)&kp.done[slot].status = status;
-        st_rel_sys_u32(&kp.done[slot].gen, s_gen);
+      if (pend_n && (pend_slot != slot || pend_gen != s_gen)) flush_done();
+      pend_slot = slot;
+      pend_gen = s_gen;
+      pend_total = s_tiles_total;
+      ++pend_n;
+      bool keep = !broken && batch_next < batch_end;
+      if (keep) {
+        const uint4 nx = s_ring[batch_next - batch_start][0];
+        keep = nx.x == slot && nx.y == s_gen;
       }
+      if (!keep) flush_done();
     }
     __syncthreads();
+    lap(kProfDone);
+  }
+  if (tid == 0) {
+    flush_done();  // normally nothing is pending here
+    for (int k = 0; k < kProfCount; ++k)
+      if (prof[k]) atomicAdd(&kp.st->prof[k], prof[k]);
   }
   if (broken) {  // let tensor-core work still in flight finish before freeing TMEM
     tc::mbar_wait(&bars[1], mma_phase ^ 1u, kWaitLimitNs);
@@ -882,6 +984,23 @@ extern "C" inolf_status inolf_serve_counters(inolf_server* s, int64_t* admitted,
   if (refused) *refused = s->n_refused;
   if (denied) *denied = s->n_denied;
   if (completed) *completed = s->n_completed;
+  return INOLF_OK;
+}
+
+extern "C" inolf_status inolf_serve_profile(inolf_server* s, int64_t* out, int32_t reset) {
+  clear_error();
+  if (!s || !out) return fail(INOLF_E_INVALID, "inolf_serve_profile: NULL argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  // the persistent CTAs add their counters when they exit: wait until the
+  // kernel has gone idle and returned
+  if (s->launched && cudaEventSynchronize(s->kernel_done) != cudaSuccess)
+    return fail(INOLF_E_CUDA, "inolf_serve_profile: waiting for the kernel failed");
+  unsigned long long v[kProfCount];
+  if (cudaMemcpy(v, s->d_st->prof, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(INOLF_E_CUDA, "inolf_serve_profile: read failed");
+  for (int k = 0; k < kProfCount; ++k) out[k] = (int64_t)v[k];
+  if (reset && cudaMemset(s->d_st->prof, 0, sizeof(v)) != cudaSuccess)
+    return fail(INOLF_E_CUDA, "inolf_serve_profile: reset failed");
   return INOLF_OK;
 }
 

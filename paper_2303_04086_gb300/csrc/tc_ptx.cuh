@@ -34,7 +34,8 @@ __device__ __forceinline__ uint64_t desc_kmajor(uint32_t saddr, uint32_t lbo, ui
 
 // Instruction descriptor: D in FP32 (bits 4-5 = 1), A/B formats (bits 7-9,
 // 10-12), both operands K-major (bits 15, 16 = 0), N >> 3 (bits 17-22),
-// M >> 4 (bits 24-28).  kind::f16: format 1 = BF16; kind::f8f6f4: 0 = E4M3.
+// M >> 4 (bits 24-28).  kind::f16: format 1 = BF16; kind::f8f6f4: 0 = E4M3;
+// kind::tf32: 2 = TF32.
 __host__ __device__ constexpr uint32_t idesc(uint32_t M, uint32_t N, uint32_t ab_format) {
   return (1u << 4) | (ab_format << 7) | (ab_format << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
 }
@@ -55,6 +56,23 @@ __device__ __forceinline__ void mma_fp8(uint32_t tmem_d, uint64_t adesc, uint64_
       "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
       "l"(adesc), "l"(bdesc), "r"(id), "r"(accumulate)
       : "memory");
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t id,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(id), "r"(accumulate)
+      : "memory");
+}
+
+// x rounded to nearest TF32 (10 explicit mantissa bits; the low 13 bits of
+// the result are zero), as an FP32 value.
+__device__ __forceinline__ float round_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
 }
 
 // Arrives once on the mbarrier when all previously issued MMAs of this

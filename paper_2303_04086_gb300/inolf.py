@@ -162,8 +162,9 @@ def workspace_flags(workspace=None, stream=None) -> int:
     return int(f.value)
 
 
-def _after(workspace, stream):
-    if _check_flags:
+def _after(workspace, stream, launched=True):
+    # a call without work (n = 0) launches nothing and leaves the flag word as it was
+    if _check_flags and launched:
         _check(lib().inolf_workspace_flags(_ptr(workspace), ctypes.byref(ctypes.c_uint32(0)), _stream(stream)))
 
 
@@ -348,7 +349,7 @@ def render(obj: Object, cams: np.ndarray, W: int, H: int, prec="fp32", rgba_out=
     _check(lib().inolf_render(obj.handle, cams.ctypes.data, nv, W, H, p, _ptr(rgba_out), _ptr(tri_out),
                               _ptr(t_out), _ptr(workspace), workspace.numel() * workspace.element_size(),
                               _stream(stream)))
-    _after(workspace, stream)
+    _after(workspace, stream, nv > 0)
     return rgba_out
 
 
@@ -409,7 +410,7 @@ def render_rays(obj: Object, o, d, prec="fp32", rgba_out=None, tri_out=None, t_o
     _check(lib().inolf_render_rays(obj.handle, _ptr(o), _ptr(d), n, p, _ptr(rgba_out), _ptr(tri_out),
                                    _ptr(t_out), _ptr(workspace), workspace.numel() * workspace.element_size(),
                                    _stream(stream)))
-    _after(workspace, stream)
+    _after(workspace, stream, n > 0)
     return rgba_out
 
 
@@ -457,7 +458,7 @@ def march_rays(obj: Object, o, d, k_out=None, t_out=None, alpha_out=None, worksp
         workspace = _workspace(n, o.device)
     _check(lib().inolf_march_rays(obj.handle, _ptr(o), _ptr(d), n, _ptr(k_out), _ptr(t_out), _ptr(alpha_out),
                                   _ptr(workspace), workspace.numel() * workspace.element_size(), _stream(stream)))
-    _after(workspace, stream)
+    _after(workspace, stream, n > 0)
     return k_out, t_out, alpha_out
 
 
@@ -470,7 +471,7 @@ def encode_rays(obj: Object, o, d, slots_out, feat_out, workspace=None, stream=N
     _check(lib().inolf_encode_rays(obj.handle, _ptr(o), _ptr(d), n, _ptr(slots_out), _ptr(feat_out),
                                    _ptr(workspace), workspace.numel() * workspace.element_size(),
                                    _stream(stream)))
-    _after(workspace, stream)
+    _after(workspace, stream, n > 0)
 
 
 # ---------------------------------------------------------------------------
@@ -517,12 +518,12 @@ def backward(obj: Object, o, d, d_rgba, grad_tables, gw1, gw2, gw3, workspace=No
                                          ctypes.cast(tp, ctypes.c_void_p), _ptr(gw1), _ptr(gw2), _ptr(gw3),
                                          _ptr(workspace), workspace.numel() * workspace.element_size(),
                                          _stream(stream)))
-        _after(workspace, stream)
+        _after(workspace, stream, n > 0)
         return
     _check(lib().inolf_backward(obj.handle, _ptr(o), _ptr(d), n, _ptr(d_rgba), ctypes.cast(tp, ctypes.c_void_p),
                                 _ptr(gw1), _ptr(gw2), _ptr(gw3), _ptr(workspace),
                                 workspace.numel() * workspace.element_size(), _stream(stream)))
-    _after(workspace, stream)
+    _after(workspace, stream, n > 0)
 
 
 def load_params(obj: Object, tables=None, w1=None, w2=None, w3=None, stream=None):
@@ -645,6 +646,7 @@ class Server:
         L.inolf_serve_destroy.argtypes = [vp]
         L.inolf_serve_set_viewer.argtypes = [vp, ctypes.c_uint32, ctypes.c_double]
         L.inolf_serve_counters.argtypes = [vp] + [ctypes.POINTER(ctypes.c_int64)] * 4
+        L.inolf_serve_profile.argtypes = [vp, vp, ctypes.c_int32]
         prm = ServeParams(hbm_budget, max_slots, max_width, max_height, max_hits, wait_limit_ns, idle_limit_ns,
                           ctas_per_sm, policy, max_rays_in_flight)
         h = vp()
@@ -704,6 +706,17 @@ class Server:
         v = [ctypes.c_int64() for _ in range(4)]
         _check(lib().inolf_serve_counters(self._h, *[ctypes.byref(x) for x in v]))
         return dict(zip(("admitted", "refused", "denied", "completed"), (x.value for x in v)))
+
+    PROFILE_KEYS = ("claim_cycles", "trace_cycles", "shade_cycles", "composite_cycles", "done_cycles", "tiles",
+                    "hits", "mlp_batches", "weight_stagings")
+
+    def profile(self, reset: bool = False) -> dict:
+        """inolf_serve_profile: SM cycles per phase of the request loop and
+        event counts, summed over the persistent CTAs (waits for the kernel to
+        go idle)."""
+        v = np.zeros(len(self.PROFILE_KEYS), np.int64)
+        _check(lib().inolf_serve_profile(self._h, v.ctypes.data, 1 if reset else 0))
+        return dict(zip(self.PROFILE_KEYS, (int(x) for x in v)))
 
     def release(self, ticket: int):
         _check(lib().inolf_serve_release(self._h, ticket))
