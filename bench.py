@@ -358,6 +358,9 @@ def run_serving(seconds=10.0, warmup=1.0, rate_hz=50.0, seed=0, prec="bf16", pol
     for o, p in zip(objs, places):
         srv.add_object(o, p)
     rng = np.random.default_rng(seed + 1)
+    inolf.stats_reset()
+    inolf.stats_enable(True)  # events around each persistent-kernel launch: the device's busy time
+    t_submit = t_poll = 0.0
     events = [(rng.exponential(1.0 / rate_hz), v) for v in range(len(viewers))]
     heapq.heapify(events)
     inflight = {}
@@ -378,7 +381,11 @@ def run_serving(seconds=10.0, warmup=1.0, rate_hz=50.0, seed=0, prec="bf16", pol
             cam = synth.camera(tuple(12.0 * dv))
             W, H = vw["res"]
             try:
-                t = srv.submit(cam, W, H, prec, viewer_id=v)
+                ts0 = time.perf_counter()
+                try:
+                    t = srv.submit(cam, W, H, prec, viewer_id=v)
+                finally:
+                    t_submit += time.perf_counter() - ts0
                 inflight[t] = (ta, W * H)
                 submitted += 1
             except inolf.InolfError as e:
@@ -388,7 +395,9 @@ def run_serving(seconds=10.0, warmup=1.0, rate_hz=50.0, seed=0, prec="bf16", pol
                     refused += 1
             heapq.heappush(events, (ta + rng.exponential(1.0 / rate_hz), v))
         for t in list(inflight):
+            tp0 = time.perf_counter()
             st, res = srv.poll(t)
+            t_poll += time.perf_counter() - tp0
             if st == inolf.PENDING:
                 continue
             ta, npx = inflight.pop(t)
@@ -405,6 +414,8 @@ def run_serving(seconds=10.0, warmup=1.0, rate_hz=50.0, seed=0, prec="bf16", pol
     counters = srv.counters()
     prof = srv.profile()
     srv.close()
+    inolf.stats_enable(False)
+    ks = inolf.stats_read().get("k_serve", {"launches": 0, "ms": 0.0})
     work = sum(prof[k] for k in ("trace_cycles", "shade_cycles", "composite_cycles", "done_cycles"))
     phases = {k.replace("_cycles", ""): prof[k] / max(1, work)
               for k in ("trace_cycles", "shade_cycles", "composite_cycles", "done_cycles")}
@@ -414,6 +425,9 @@ def run_serving(seconds=10.0, warmup=1.0, rate_hz=50.0, seed=0, prec="bf16", pol
                "hits_per_tile": prof["hits"] / max(1, prof["tiles"]),
                "mlp_batches_per_tile": prof["mlp_batches"] / max(1, prof["tiles"]),
                "rows_used_per_256_row_batch": prof["hits"] / max(1, prof["mlp_batches"]),
+               "kernel_launches": ks["launches"], "kernel_busy_s": ks["ms"] / 1e3, "persistent_ctas": prof["ctas"],
+               "sm_mhz_implied": (prof["claim_cycles"] + work) / max(1, prof["ctas"]) / max(1e-9, ks["ms"] / 1e3) / 1e6,
+               "host_submit_s": t_submit, "host_poll_s": t_poll, "wall_s_incl_warmup": wall + warmup,
                "raw": prof}
     lat_ms = np.array(lat) * 1e3
     return {"viewers": len(viewers), "objects": len(objs), "rate_hz_per_viewer": rate_hz, "seconds": seconds,

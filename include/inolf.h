@@ -253,13 +253,16 @@ inolf_status inolf_set_wait_limit_ns(int64_t ns);
 #define INOLF_INJECT_RING_STALL 1u
 inolf_status inolf_set_fault_injection(uint32_t mask);
 
-/* Renders n_views pinhole views into HOST memory, overlapping rendering with
- * the device-to-host copies: views go in chunks into two halves of a caller-
- * owned device staging buffer on `stream` while a library-owned stream copies
- * the previous chunk out, so the copies hide behind the rendering (the frames
- * a render farm hands to its encoder, Sec. 5.1).
- *   rgba_host  host [n_views][H][W][4] FP32 (pinned memory for overlap; pageable
- *              memory works but copies synchronously)
+/* Renders n_views pinhole views into HOST memory (the frames a render farm
+ * hands to its encoder, Sec. 5.1).  When rgba_host is pinned memory mapped
+ * into the device's address space (cudaHostAlloc / cudaHostRegister with a
+ * device pointer, 16-byte aligned), the kernels store the frames straight
+ * into it over the GPU-host link and the staging buffer is not used.
+ * Otherwise views go in chunks into two halves of a caller-owned device
+ * staging buffer on `stream` while a library-owned stream copies the previous
+ * chunk out, so the copies hide behind the rendering.
+ *   rgba_host  host [n_views][H][W][4] FP32 (pinned memory; pageable memory
+ *              works but copies synchronously)
  *   staging    device, 16-byte aligned; each half holds
  *              floor(staging_bytes / 2 / (W H 16)) >= 1 views
  *   workspace  as for inolf_render, for one chunk of views
@@ -429,13 +432,14 @@ inolf_status inolf_serve_counters(inolf_server* srv, int64_t* admitted, int64_t*
 
 /* Profile of the request loop (measurement support, no paper counterpart),
  * summed over the persistent CTAs, which add their figures when they exit:
- * the call first waits for the kernel to go idle and return.  out (host, 9
- * entries): SM clock cycles spent in [0] claiming tiles and reading request
+ * the call first waits for the kernel to go idle and return.  out (host):
+ * SM clock cycles spent in [0] claiming tiles and reading request
  * descriptors (including waiting for work), [1] tracing every object and
  * ordering the hits, [2] shading (weights staged, encoding, MLP), [3]
  * compositing and storing, [4] completion; then [5] tiles, [6] hits shaded,
  * [7] MLP batches (256-row tensor-core passes or FP32 passes of one object),
- * [8] weight stagings.  reset != 0 zeroes the counters after reading. */
+ * [8] weight stagings, [9] persistent CTAs per launch (out holds 10
+ * entries).  reset != 0 zeroes the counters after reading. */
 inolf_status inolf_serve_profile(inolf_server* srv, int64_t* out, int32_t reset);
 
 /* ------------------------------------------------------------------------ */

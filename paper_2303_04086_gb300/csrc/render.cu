@@ -1164,6 +1164,18 @@ extern "C" inolf_status inolf_march_rays(const inolf_object* obj, const float* o
                        stream, false, alpha_out, true);
 }
 
+// Device address of a host buffer the device can store to directly (pinned
+// and mapped into the device's address space, 16-byte aligned), or NULL.
+static float* mapped_host_target(float* host) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer || ((uintptr_t)a.devicePointer & 15)) return nullptr;
+  return static_cast<float*>(a.devicePointer);
+}
+
 extern "C" inolf_status inolf_render_host(const inolf_object* obj, const float* cams, int32_t n_views, int32_t W,
                                           int32_t H, inolf_precision prec, float* rgba_host, void* staging,
                                           size_t staging_bytes, void* workspace, size_t workspace_bytes,
@@ -1172,9 +1184,28 @@ extern "C" inolf_status inolf_render_host(const inolf_object* obj, const float* 
   if (!obj || !cams || !rgba_host || n_views < 0 || W <= 0 || H <= 0 || !staging || ((uintptr_t)staging & 15))
     return fail(INOLF_E_INVALID, "inolf_render_host: bad argument");
   if (n_views == 0) return INOLF_OK;
+
   const size_t view_bytes = (size_t)W * H * 4 * sizeof(float);
   const int64_t slot_views = (int64_t)(staging_bytes / 2 / view_bytes);
   if (slot_views < 1) return fail(INOLF_E_INVALID, "inolf_render_host: staging holds less than two views");
+  if (float* direct = mapped_host_target(rgba_host)) {
+    // pinned, mapped host memory: the kernels store the frames straight into it
+    // (over the GPU-host link), with no staging copy
+    RayBatch rb{};
+    rb.mode = 0;
+    rb.cams = cams;
+    rb.n_views = n_views;
+    rb.W = W;
+    rb.H = H;
+    rb.n = (int64_t)n_views * W * H;
+    inolf_status st = launch_render(obj->o, rb, prec, direct, nullptr, nullptr, nullptr, nullptr, workspace,
+                                    workspace_bytes, stream);
+    if (st != INOLF_OK) return st;
+    uint32_t flags = 0;
+    st = read_device_flags(workspace, stream, &flags);  // synchronises `stream`
+    if (st != INOLF_OK) return st;
+    return flags_status(flags, "inolf_render_host");
+  }
   cudaStream_t cs = (cudaStream_t)stream;
   cudaStream_t xs = nullptr;
   cudaEvent_t rendered[2] = {nullptr, nullptr}, copied[2] = {nullptr, nullptr};

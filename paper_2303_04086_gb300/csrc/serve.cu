@@ -953,6 +953,9 @@ extern "C" inolf_status inolf_serve_create(const inolf_serve_params* prm, inolf_
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
   auto grid_of = [&](const void* fn, size_t smem) {
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the whole unified L1 / shared storage may go to shared memory, so that two
+    // CTAs of ~84 KB fit one SM (with the default split only one does)
+    cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kServeThreads, smem);
     occ = std::max(1, std::min(occ, 4));  // each CTA holds 128 of the SM's 512 TMEM columns
     if (p.ctas_per_sm > 0) occ = std::min(occ, p.ctas_per_sm);
@@ -999,6 +1002,7 @@ extern "C" inolf_status inolf_serve_profile(inolf_server* s, int64_t* out, int32
   if (cudaMemcpy(v, s->d_st->prof, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess)
     return fail(INOLF_E_CUDA, "inolf_serve_profile: read failed");
   for (int k = 0; k < kProfCount; ++k) out[k] = (int64_t)v[k];
+  out[kProfCount] = scene_has_cubes(s) ? s->grid_cubes : s->grid;  // persistent CTAs per launch
   if (reset && cudaMemset(s->d_st->prof, 0, sizeof(v)) != cudaSuccess)
     return fail(INOLF_E_CUDA, "inolf_serve_profile: reset failed");
   return INOLF_OK;

@@ -186,9 +186,10 @@ def test_empty_batches(torch_cuda, tiny_obj):
 
 @pytest.mark.parametrize("views_per_chunk,pinned", [(2, True), (1, True), (3, False)])
 def test_render_host_equals_device_render(torch_cuda, tiny, tiny_obj, views_per_chunk, pinned):
-    # frames rendered into host memory through the two staging halves (the
-    # copies of chunk c overlap the rendering of chunk c + 1) are the device
-    # render's, bit for bit; 7 views force slot reuse
+    # frames rendered into host memory are the device render's, bit for bit:
+    # pinned memory is stored to directly by the kernels; pageable memory goes
+    # through the two staging halves (the copies of chunk c overlap the
+    # rendering of chunk c + 1; 7 views force slot reuse)
     import torch
     from paper_2303_04086_gb300 import inolf
     cams = synth.ring_cameras(7, 2.8)
