@@ -426,6 +426,7 @@ def run_serving(seconds=10.0, warmup=1.0, rate_hz=50.0, seed=0, prec="bf16", pol
                "mlp_batches_per_tile": prof["mlp_batches"] / max(1, prof["tiles"]),
                "rows_used_per_256_row_batch": prof["hits"] / max(1, prof["mlp_batches"]),
                "kernel_launches": ks["launches"], "kernel_busy_s": ks["ms"] / 1e3, "persistent_ctas": prof["ctas"],
+               "launch_plan": {k: prof[k] for k in ("regs_per_thread", "static_smem", "dynamic_smem", "ctas_per_sm")},
                "sm_mhz_implied": (prof["claim_cycles"] + work) / max(1, prof["ctas"]) / max(1e-9, ks["ms"] / 1e3) / 1e6,
                "host_submit_s": t_submit, "host_poll_s": t_poll, "wall_s_incl_warmup": wall + warmup,
                "raw": prof}

@@ -438,7 +438,9 @@ inolf_status inolf_serve_counters(inolf_server* srv, int64_t* admitted, int64_t*
  * ordering the hits, [2] shading (weights staged, encoding, MLP), [3]
  * compositing and storing, [4] completion; then [5] tiles, [6] hits shaded,
  * [7] MLP batches (256-row tensor-core passes or FP32 passes of one object),
- * [8] weight stagings, [9] persistent CTAs per launch (out holds 10
+ * [8] weight stagings, [9] persistent CTAs per launch, and the launch plan of
+ * the mesh-only kernel: [10] registers per thread, [11] static and [12]
+ * dynamic shared-memory bytes per CTA, [13] CTAs per SM (out holds 14
  * entries).  reset != 0 zeroes the counters after reading. */
 inolf_status inolf_serve_profile(inolf_server* srv, int64_t* out, int32_t reset);
 

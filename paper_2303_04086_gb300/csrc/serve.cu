@@ -700,6 +700,7 @@ struct inolf_server {
   cudaStream_t stream = nullptr;
   cudaEvent_t kernel_done = nullptr;
   bool launched = false;
+  int occ_diag[4] = {0, 0, 0, 0};  // mesh-only kernel: registers, static / dynamic shared bytes, CTAs per SM
   int grid = 0;        // persistent CTAs of the mesh-only kernel
   int grid_cubes = 0;  // and of the kernel that also serves density-cube objects
   // objects
@@ -949,19 +950,34 @@ extern "C" inolf_status inolf_serve_create(const inolf_serve_params* prm, inolf_
   s->free_blocks[0] = p.hbm_budget;
   s->slots.resize(p.max_slots);
   s->slot_gen.assign(p.max_slots, 0);
-  int sms = 1, occ = 1;
+  int sms = 1, regs_sm = 65536, smem_sm = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+  cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, s->device);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, s->device);
+  // resident CTAs per SM from the kernel's registers, shared memory and tensor
+  // memory (the occupancy query reports one CTA for this tensor-memory kernel;
+  // a CTA that does not fit only starts when another exits, and no CTA waits
+  // on another, so an over-estimate is harmless)
   auto grid_of = [&](const void* fn, size_t smem) {
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    // the whole unified L1 / shared storage may go to shared memory, so that two
-    // CTAs of ~84 KB fit one SM (with the default split only one does)
-    cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kServeThreads, smem);
-    occ = std::max(1, std::min(occ, 4));  // each CTA holds 128 of the SM's 512 TMEM columns
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, fn);
+    const int regs_warp = ((std::max(fa.numRegs, 1) * 32 + 255) / 256) * 256;  // allocated per warp in units of 256
+    const int by_regs = regs_sm / (regs_warp * (kServeThreads / 32));
+    const int by_smem = (int)(smem_sm / (smem + fa.sharedSizeBytes + 1024));
+    int occ = std::max(1, std::min(std::min(by_regs, by_smem), 4));  // each CTA holds 128 of 512 TMEM columns
     if (p.ctas_per_sm > 0) occ = std::min(occ, p.ctas_per_sm);
     return sms * occ;
   };
   s->grid = grid_of((const void*)k_serve<false>, serve_smem(false));
+  {
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, (const void*)k_serve<false>);
+    s->occ_diag[0] = fa.numRegs;
+    s->occ_diag[1] = (int)fa.sharedSizeBytes;
+    s->occ_diag[2] = (int)serve_smem(false);
+    s->occ_diag[3] = s->grid / std::max(1, sms);
+  }
   s->grid_cubes = grid_of((const void*)k_serve<true>, serve_smem(true));
   cudaGetLastError();
   if (p.policy == 1 && inolf_sched_create(p.max_rays_in_flight, &s->sched) != INOLF_OK) return bad("scheduler");
@@ -1003,6 +1019,7 @@ extern "C" inolf_status inolf_serve_profile(inolf_server* s, int64_t* out, int32
     return fail(INOLF_E_CUDA, "inolf_serve_profile: read failed");
   for (int k = 0; k < kProfCount; ++k) out[k] = (int64_t)v[k];
   out[kProfCount] = scene_has_cubes(s) ? s->grid_cubes : s->grid;  // persistent CTAs per launch
+  for (int k = 0; k < 4; ++k) out[kProfCount + 1 + k] = s->occ_diag[k];
   if (reset && cudaMemset(s->d_st->prof, 0, sizeof(v)) != cudaSuccess)
     return fail(INOLF_E_CUDA, "inolf_serve_profile: reset failed");
   return INOLF_OK;

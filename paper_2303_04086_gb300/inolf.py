@@ -708,7 +708,8 @@ class Server:
         return dict(zip(("admitted", "refused", "denied", "completed"), (x.value for x in v)))
 
     PROFILE_KEYS = ("claim_cycles", "trace_cycles", "shade_cycles", "composite_cycles", "done_cycles", "tiles",
-                    "hits", "mlp_batches", "weight_stagings", "ctas")
+                    "hits", "mlp_batches", "weight_stagings", "ctas", "regs_per_thread", "static_smem",
+                    "dynamic_smem", "ctas_per_sm")
 
     def profile(self, reset: bool = False) -> dict:
         """inolf_serve_profile: SM cycles per phase of the request loop and
