@@ -218,7 +218,7 @@ def kernel_rooflines(kernels, scene, n_rays, n_hit, steps, peaks):
     and their MLP flops against the peak of their arithmetic (FP32 SIMT from
     the unit counts, BF16 measured, FP8 = 2 x BF16, the nominal ratio); the
     trace / march kernels' output bytes (16 B per miss, 8 B per hit record)
-    against HBM, with rays per second (their limit is ALU issue, see profiles/)."""
+    against HBM, with rays per second (their limit is ALU issue, as ncu shows)."""
     hbm = peaks.get("hbm_gbs", 6800.0)
     bf16 = peaks.get("bf16_tflops", 1900.0)
     mlp_peak = {"k_shade_f32": 80.5, "k_shade_tc_bf16": bf16, "k_shade_tc_fp8": 2.0 * bf16}
