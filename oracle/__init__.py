@@ -218,16 +218,23 @@ def composite(hit, t, rgba, K: int = 4):
 def render_scene(orcs, translations, o, d, K: int = 4):
     """World rays o, d [n][3] (FP32) against objects placed by translation:
     each object sees the ray in its own frame (o - T, one FP32 subtraction
-    per axis), renders it (closest hit + one query), and the results are
-    fused by :func:`composite`.  Returns a dict with ``rgba`` [n][4], ``used``
+    per axis), renders it (closest hit + one query, or the density march of
+    the decoupled variant for objects with cubes), and the results are fused
+    by :func:`composite`.  Returns a dict with ``rgba`` [n][4], ``used``
     (hits composited), ``hits`` (hits before the K cut) and the per-object
     results ``per``."""
     o = _f32(o); d = _f32(d)
     per = []
     for orc, T in zip(orcs, translations):
         ol = (o - np.asarray(T, np.float32)).astype(np.float32)
-        per.append(orc.render_rays(ol, d))
-    hit = np.stack([r["tri"] >= 0 for r in per])
+        if orc.cubes is None:  # mesh proxy: closest hit, one query
+            r = orc.render_rays(ol, d)
+            r["hit"] = r["tri"] >= 0
+        else:  # decoupled variant: density march, alpha_c input, c = c_d + t c_s
+            r = orc.render_variant_rays(ol, d)
+            r["hit"] = r["k"] >= 0
+        per.append(r)
+    hit = np.stack([r["hit"] for r in per])
     t = np.stack([r["t"] for r in per])
     rgba = np.stack([r["rgba"] for r in per])
     out, used = composite(hit, t, rgba, K)

@@ -326,3 +326,42 @@ def test_twelve_objects_4k_against_oracle_composite():
         else:
             assert (ref["hits"] > K).sum() > 100  # the cut is exercised
             assert np.abs(got - ref["rgba"]).max() <= TOL
+
+
+def test_mixed_mesh_and_density_objects_against_oracle_composite(env):
+    # a density-cube object (the decoupled variant) between two mesh objects,
+    # FP32: the served composite against the oracle's fusion of its variant
+    # render and the mesh renders.  Pixels whose march is ambiguous in FP32
+    # (two best weights within 1e-5, the stop test or the miss test within
+    # rounding, see test_gpu_variant.py) are left out and counted.
+    torch, inolf, scenes, objs = env
+    dscene = synth.tiny_density_scene(seed=3)
+    dobj = inolf.object_create(dscene)
+    places = [PLACES[1], PLACES[0], PLACES[2]]
+    srv = inolf.Server(hbm_budget=64 << 20, max_slots=4, max_width=256, max_height=256)
+    srv.add_object(objs[0], places[0])
+    srv.add_object(dobj, places[1])
+    srv.add_object(objs[1], places[2])
+    cam = synth.camera((1.0, 1.5, 8.0), target=(0.0, 0.0, -0.5))
+    W, H = 200, 150
+    t = srv.submit(cam, W, H)
+    st, res = _done(srv, t)
+    assert st == inolf.OK
+    got = srv.frame(res).cpu().numpy().reshape(-1, 4)
+    srv.release(t)
+    srv.close()
+    orcs = [oracle.Oracle(scenes[0]), oracle.Oracle(dscene), oracle.Oracle(scenes[1])]
+    o, d = oracle.raygen(cam, W, H)
+    ref = oracle.render_scene(orcs, places, o, d, K=4)
+    c = orcs[1].cubes
+    m = c.march((o - np.float32(places[1])).astype(np.float32), d)
+    tie = 1e-5
+    ambiguous = (((m["k2"] >= 0) & (m["w2"] >= m["wmax"] * (1 - tie))) |
+                 (np.abs(m["T_prev"] - c.c.t_min) <= 1e-4 * c.c.t_min) |
+                 (np.abs((1.0 - m["alpha"].astype(np.float64)) - c.c.t_min) <= 1e-3 * c.c.t_min) |
+                 (np.abs(m["alpha"] - c.c.alpha_miss) <= tie))
+    assert ambiguous.mean() < 0.01
+    keep = ~ambiguous
+    assert ref["per"][1]["hit"][keep].sum() > 500          # the density object is seen
+    assert (ref["used"][keep] > 1).sum() > 50              # and overlaps a mesh object
+    assert np.abs(got[keep] - ref["rgba"][keep]).max() <= TOL
