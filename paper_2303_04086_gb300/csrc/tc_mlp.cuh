@@ -81,16 +81,19 @@ struct RowWriter {
 };
 
 // Precision-dependent scales (FP8: per-tensor, amax / 448; BF16: unit).
+// A layer's accumulator dequantises with mul = s_in s_w and the next layer's
+// input quantises with 1 / s_next; both are positive, so ReLU commutes with
+// them and the two multiplications fold into one (q1, q2).  The last layer's
+// input scale sh2 is applied once to the 4 dot products instead of to each of
+// the 64 inputs.
 struct TcScales {
-  float inv_sx, mul1, inv_sh1, mul2, sh2, inv_sh2;
+  float inv_sx, q1, q2, sh2;
   __device__ static TcScales make(bool fp8, const float act[3], const float w[3]) {
     TcScales s;
     s.inv_sx = fp8 ? 1.0f / act[0] : 1.0f;
-    s.mul1 = fp8 ? act[0] * w[0] : 1.0f;
-    s.inv_sh1 = fp8 ? 1.0f / act[1] : 1.0f;
-    s.mul2 = fp8 ? act[1] * w[1] : 1.0f;
+    s.q1 = fp8 ? (act[0] * w[0]) / act[1] : 1.0f;
+    s.q2 = fp8 ? (act[1] * w[1]) / act[2] : 1.0f;
     s.sh2 = fp8 ? act[2] : 1.0f;
-    s.inv_sh2 = fp8 ? 1.0f / act[2] : 1.0f;
     return s;
   }
 };
@@ -142,10 +145,10 @@ __device__ __forceinline__ bool tc_mlp_run(uint8_t* sA, const uint8_t* sB1, cons
       uint32_t w[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const float a0 = fmaxf(v[4 * q + 0] * sc.mul1, 0.f) * sc.inv_sh1;
-        const float a1 = fmaxf(v[4 * q + 1] * sc.mul1, 0.f) * sc.inv_sh1;
-        const float a2 = fmaxf(v[4 * q + 2] * sc.mul1, 0.f) * sc.inv_sh1;
-        const float a3 = fmaxf(v[4 * q + 3] * sc.mul1, 0.f) * sc.inv_sh1;
+        const float a0 = fmaxf(v[4 * q + 0] * sc.q1, 0.f);
+        const float a1 = fmaxf(v[4 * q + 1] * sc.q1, 0.f);
+        const float a2 = fmaxf(v[4 * q + 2] * sc.q1, 0.f);
+        const float a3 = fmaxf(v[4 * q + 3] * sc.q1, 0.f);
         w[q] = (uint32_t)pack_fp8(a0, a1) | ((uint32_t)pack_fp8(a2, a3) << 16);
       }
       *reinterpret_cast<uint4*>(A + tc::core_off(row, c, chunks2)) = make_uint4(w[0], w[1], w[2], w[3]);
@@ -186,14 +189,20 @@ __device__ __forceinline__ bool tc_mlp_run(uint8_t* sA, const uint8_t* sB1, cons
     tc::tmem_ld16(tmem + lane_base + t * 64u + c * 16u, v);
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
-      float a = fmaxf(v[j] * sc.mul2, 0.f);
-      a = kFP8 ? round_fp8(a * sc.inv_sh2) * sc.sh2 : round_bf16(a);
+      // FP8: the quantised input in units of sh2; BF16: the rounded input
+      const float a = kFP8 ? round_fp8(fmaxf(v[j] * sc.q2, 0.f)) : round_bf16(fmaxf(v[j], 0.f));
       const float4 w = reinterpret_cast<const float4*>(sW3)[c * 16u + (uint32_t)j];  // W3^T row
       out0 += w.x * a;
       out1 += w.y * a;
       out2 += w.z * a;
       out3 += w.w * a;
     }
+  }
+  if (kFP8) {
+    out0 *= sc.sh2;
+    out1 *= sc.sh2;
+    out2 *= sc.sh2;
+    out3 *= sc.sh2;
   }
   out = make_float4(sigmoidf_(out0), sigmoidf_(out1), sigmoidf_(out2), sigmoidf_(out3));
   tc::fence_before();
