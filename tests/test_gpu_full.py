@@ -144,3 +144,34 @@ def test_full_bf16_fp8_sampled(full, full_oracle):
             assert p >= bar, (prec, v, p, err)
             if prec == "bf16":
                 assert err <= 1e-2, (v, p, err)
+
+
+def test_full_backward_against_oracle_gradient(full, full_oracle):
+    # the backward at the benchmark's configuration (16 levels, d_in = 48: the
+    # weight-gradient MMA at its widest, N = 64 + 48) against the oracle's
+    # analytic FP64 gradient on 400 hit rays of view 3
+    torch, inolf, scene, obj, cams = full
+    pix = _sample(3, 1500, 33)
+    o, d = oracle.raygen(cams[3], W, H, pix)
+    r = full_oracle.render_rays(o, d)
+    hit = np.nonzero(r["tri"] >= 0)[0][:400]
+    assert len(hit) == 400
+    o, d = o[hit], d[hit]
+    g = np.random.default_rng(5).normal(size=(len(o), 4)) / len(o)
+    L = scene.n_levels
+    gt = [torch.zeros((obj.table_rows(l), 2), dtype=torch.float32, device="cuda") for l in range(L)]
+    gw = [torch.zeros((64, scene.d_in), device="cuda"), torch.zeros((64, 64), device="cuda"),
+          torch.zeros((4, 64), device="cuda")]
+    inolf.backward(obj, torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda(),
+                   torch.from_numpy(g.astype(np.float32)).cuda(), gt, *gw)
+    torch.cuda.synchronize()
+    r1, r2, r3, rf = full_oracle.backward(o, d, g)
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+    for a, b in zip([x.cpu().numpy() for x in gw], (r1, r2, r3)):
+        assert rel(a, b) <= 1e-4
+    for l in range(L):
+        got = gt[l].cpu().numpy()[obj.hashes[l].slot_of]  # slot order -> key order
+        assert rel(got, rf[l]) <= 1e-4, l
