@@ -11,9 +11,11 @@
 //   3. each warp reads its 32 rows of D1 (tcgen05.ld), applies ReLU and the
 //      quantisation of the next layer's input and writes A2 in place of A1;
 //   4. D2 = A2 W2^T on the tensor cores;
-//   5. each thread reads its row of D2, applies ReLU, quantises, multiplies by
-//      W3 (4 x 64, CUDA cores: N = 4 is below the tensor-core minimum) and
-//      writes sigmoid(.) as RGBA.
+//   5. each warp reads its rows of D2, applies ReLU and the last layer's
+//      quantisation and writes A3 in place of A2;
+//   6. D3 = A3 W3^T on the tensor cores with W3 padded to 16 rows (the
+//      smallest N of an M = 128 MMA); each thread reads the 4 outputs of its
+//      row and writes sigmoid(.) as RGBA.
 // The weights of all three layers are staged once per CTA into shared memory
 // by one bulk (TMA) copy from a blob laid out on the host in the operand
 // format.  Every mbarrier wait is bounded by a global-timer limit; on expiry
@@ -40,6 +42,7 @@ namespace inolf {
 
 static constexpr int kTcThreads = 256;
 static constexpr uint32_t kTmemCols = 128;  // 2 tiles x 64 FP32 columns
+static constexpr int kW3Rows = 16;          // W3 padded to the smallest N of an M = 128 MMA
 
 template <bool kFP8>
 __global__ void __launch_bounds__(kTcThreads, 4) k_shade_tc(const __grid_constant__ Params p) {
@@ -50,7 +53,7 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_shade_tc(const __grid_constan
   const uint32_t wbytes = p.tc_wbytes;
   uint8_t* sB1 = smem;
   uint8_t* sB2 = smem + 64u * K1 * ES;
-  const float* sW3 = reinterpret_cast<const float*>(sB2 + 64u * 64u * ES);
+  const uint8_t* sB3 = sB2 + 64u * 64u * ES;  // W3 as a 16-row operand
   uint8_t* sA = smem + ((wbytes + 1023u) & ~1023u);
   constexpr uint32_t tile_bytes = 128u * 64u * ES;
   uint64_t* bars = reinterpret_cast<uint64_t*>(sA + 2 * tile_bytes);  // [0] weights, [1] MMA
@@ -118,7 +121,7 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_shade_tc(const __grid_constan
         *reinterpret_cast<uint4*>(A + tc::core_off(row, c, chunks1)) = make_uint4(0, 0, 0, 0);
     }
     float4 rgba;
-    if (!tc_mlp_run<kFP8>(sA, sB1, sB2, sW3, K1, tmem, &bars[1], phase, sc, rgba)) {
+    if (!tc_mlp_run<kFP8>(sA, sB1, sB2, sB3, K1, tmem, &bars[1], phase, sc, rgba)) {
       bad = true;
       break;
     }
@@ -136,7 +139,9 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_shade_tc(const __grid_constan
   }
   if (bad) {
     if (tid == 0) atomicOr(p.counter + 1, INOLF_FLAG_WAIT_TIMEOUT);
-    tc::mbar_wait(&bars[1], phase, kWaitLimitNs);  // let MMAs still in flight finish
+    // let MMAs still in flight finish: the failed wait already flipped `phase`,
+    // so the phase in flight has parity phase ^ 1
+    tc::mbar_wait(&bars[1], phase ^ 1u, kWaitLimitNs);
   }
   __syncthreads();
   if (warp == 0) {
@@ -151,7 +156,7 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_shade_tc(const __grid_constan
 static uint32_t round_up(uint32_t v, uint32_t m) { return (v + m - 1) / m * m; }
 
 // Weight blob in the operand layout (K-major core matrices, rows = output
-// neurons): [W1: 64 x K1][W2: 64 x 64][W3^T: 64 x 4 FP32 of the quantised values]
+// neurons): [W1: 64 x K1][W2: 64 x 64][W3: 16 x 64, rows 4..15 zero]
 inolf_status prepare_tc_weights(Object& obj, const float* w1, const float* w2, const float* w3, void* stream) {
   const int din = obj.d_in, H = INOLF_HIDDEN, O = INOLF_OUT;
   cudaStream_t st = (cudaStream_t)stream;
@@ -163,7 +168,7 @@ inolf_status prepare_tc_weights(Object& obj, const float* w1, const float* w2, c
   // ---- BF16 ----
   {
     const uint32_t K1 = round_up((uint32_t)din, 16), ch1 = K1 / 8, ch2 = 8;
-    std::vector<uint8_t> blob((size_t)H * K1 * 2 + (size_t)H * H * 2 + (size_t)O * H * 4, 0);
+    std::vector<uint8_t> blob((size_t)H * K1 * 2 + (size_t)H * H * 2 + (size_t)kW3Rows * H * 2, 0);
     for (int n = 0; n < H; ++n)
       for (int k = 0; k < din; ++k) {
         __nv_bfloat16 v = __float2bfloat16_rn(w1[(size_t)n * din + k]);
@@ -175,9 +180,12 @@ inolf_status prepare_tc_weights(Object& obj, const float* w1, const float* w2, c
         __nv_bfloat16 v = __float2bfloat16_rn(w2[(size_t)n * H + k]);
         std::memcpy(&b2[tc::core_off(n, k / 8, ch2) + (k % 8) * 2], &v, 2);
       }
-    float* b3 = reinterpret_cast<float*>(b2 + (size_t)H * H * 2);  // W3^T [64][4]
-    for (int o = 0; o < O; ++o)
-      for (int j = 0; j < H; ++j) b3[j * O + o] = __bfloat162float(__float2bfloat16_rn(w3[o * H + j]));
+    uint8_t* b3 = b2 + (size_t)H * H * 2;  // W3: 16 rows (4 outputs, 12 zero rows) x 64
+    for (int n = 0; n < O; ++n)
+      for (int k = 0; k < H; ++k) {
+        __nv_bfloat16 v = __float2bfloat16_rn(w3[(size_t)n * H + k]);
+        std::memcpy(&b3[tc::core_off(n, k / 8, ch2) + (k % 8) * 2], &v, 2);
+      }
     if (!obj.w_bf16) {
       if (cudaMalloc(&obj.w_bf16, blob.size()) != cudaSuccess) return fail(INOLF_E_OOM, "cudaMalloc bf16 weights");
       obj.bytes += blob.size();
@@ -196,20 +204,16 @@ inolf_status prepare_tc_weights(Object& obj, const float* w1, const float* w2, c
     obj.fp8_w_scale[1] = s2 > 0 ? s2 / 448.0f : 1.0f;
     obj.fp8_w_scale[2] = s3 > 0 ? s3 / 448.0f : 1.0f;
     auto q = [](float v, float s) { return (uint8_t)__nv_cvt_float_to_fp8(v / s, __NV_SATFINITE, __NV_E4M3); };
-    auto dq = [](uint8_t b) {
-      __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)b, __NV_E4M3);
-      return __half2float(__half(h));
-    };
-    std::vector<uint8_t> blob((size_t)H * K1 + (size_t)H * H + (size_t)O * H * 4, 0);
+    std::vector<uint8_t> blob((size_t)H * K1 + (size_t)H * H + (size_t)kW3Rows * H, 0);
     for (int n = 0; n < H; ++n)
       for (int k = 0; k < din; ++k)
         blob[tc::core_off(n, k / 16, ch1) + (k % 16)] = q(w1[(size_t)n * din + k], obj.fp8_w_scale[0]);
     uint8_t* b2 = blob.data() + (size_t)H * K1;
     for (int n = 0; n < H; ++n)
       for (int k = 0; k < H; ++k) b2[tc::core_off(n, k / 16, ch2) + (k % 16)] = q(w2[(size_t)n * H + k], obj.fp8_w_scale[1]);
-    float* b3 = reinterpret_cast<float*>(b2 + (size_t)H * H);  // W3^T [64][4]
-    for (int o = 0; o < O; ++o)
-      for (int j = 0; j < H; ++j) b3[j * O + o] = dq(q(w3[o * H + j], obj.fp8_w_scale[2])) * obj.fp8_w_scale[2];
+    uint8_t* b3 = b2 + (size_t)H * H;  // W3: 16 rows (4 outputs, 12 zero rows) x 64
+    for (int n = 0; n < O; ++n)
+      for (int k = 0; k < H; ++k) b3[tc::core_off(n, k / 16, ch2) + (k % 16)] = q(w3[(size_t)n * H + k], obj.fp8_w_scale[2]);
     if (!obj.w_fp8) {
       if (cudaMalloc(&obj.w_fp8, blob.size()) != cudaSuccess) return fail(INOLF_E_OOM, "cudaMalloc fp8 weights");
       obj.bytes += blob.size();
@@ -233,7 +237,8 @@ inolf_status prepare_tc_weights(Object& obj, const float* w1, const float* w2, c
 // Device-side repacking of all weight formats from device FP32 weights (one
 // CTA; the MLP has ~7 500 weights): the per-tensor FP8 weight scales amax /
 // 448, the FP32 SIMT blob and the BF16 / FP8 operand blobs, each written
-// exactly as prepare_tc_weights and upload_weights write them on the host.
+// exactly as prepare_tc_weights and upload_weights write them on the host
+// (the zero rows of W3 included).
 __device__ float block_amax(const float* w, int n, float* red) {
   float m = 0.f;
   for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmaxf(m, fabsf(w[i]));
@@ -259,10 +264,6 @@ __global__ void k_pack_weights(const float* __restrict__ w1, const float* __rest
     scales[2] = s3;
   }
   auto q = [](float v, float sc) { return (uint8_t)__nv_cvt_float_to_fp8(v / sc, __NV_SATFINITE, __NV_E4M3); };
-  auto dq = [](uint8_t b) {
-    __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)b, __NV_E4M3);
-    return __half2float(__half(h));
-  };
   const int tid = threadIdx.x, nt = blockDim.x;
   // FP32: W1T [din][64] | W2 [64][64] | W3T [64][4]
   for (int i = tid; i < H * din; i += nt) {
@@ -286,10 +287,11 @@ __global__ void k_pack_weights(const float* __restrict__ w1, const float* __rest
     const int n = i / H, k = i - n * H;
     *reinterpret_cast<__nv_bfloat16*>(b2 + tc::core_off(n, k / 8, 8) + (k % 8) * 2) = __float2bfloat16_rn(w2[i]);
   }
-  float* b3 = reinterpret_cast<float*>(b2 + (size_t)H * H * 2);
-  for (int i = tid; i < O * H; i += nt) {
-    const int o = i / H, j = i - o * H;
-    b3[j * O + o] = __bfloat162float(__float2bfloat16_rn(w3[i]));
+  uint8_t* b3 = b2 + (size_t)H * H * 2;  // rows 4..15 stay zero
+  for (int i = tid; i < kW3Rows * H; i += nt) {
+    const int n = i / H, k = i - n * H;
+    *reinterpret_cast<__nv_bfloat16*>(b3 + tc::core_off(n, k / 8, 8) + (k % 8) * 2) =
+        __float2bfloat16_rn(n < O ? w3[i] : 0.0f);
   }
   // FP8 e4m3: W1 (64 x K1f, zero padded) | W2 | W3^T FP32 of the dequantised values
   const uint32_t cf1 = K1f / 16;
@@ -302,10 +304,10 @@ __global__ void k_pack_weights(const float* __restrict__ w1, const float* __rest
     const int n = i / H, k = i - n * H;
     f2[tc::core_off(n, k / 16, 4) + (k % 16)] = q(w2[i], s2);
   }
-  float* f3 = reinterpret_cast<float*>(f2 + (size_t)H * H);
-  for (int i = tid; i < O * H; i += nt) {
-    const int o = i / H, j = i - o * H;
-    f3[j * O + o] = dq(q(w3[i], s3)) * s3;
+  uint8_t* f3 = f2 + (size_t)H * H;
+  for (int i = tid; i < kW3Rows * H; i += nt) {
+    const int n = i / H, k = i - n * H;
+    f3[tc::core_off(n, k / 16, 4) + (k % 16)] = n < O ? q(w3[i], s3) : (uint8_t)0;
   }
 }
 
@@ -320,8 +322,8 @@ inolf_status pack_weights_device(Object& obj, const float* w1, const float* w2, 
   return INOLF_OK;
 }
 
-// Largest weight blob: K1 = 64 (BF16: 64 x 64 x 2 + 64 x 64 x 2 + 4 x 64 x 4 bytes).
-static constexpr uint32_t kMaxTcWeightBytes = 17408;
+// Largest weight blob: K1 = 64 (BF16: 64 x 64 x 2 + 64 x 64 x 2 + 16 x 64 x 2 bytes).
+static constexpr uint32_t kMaxTcWeightBytes = 18432;
 
 static size_t tc_smem_bytes(uint32_t wbytes, bool fp8) {
   const size_t tile = 128u * 64u * (fp8 ? 1u : 2u);

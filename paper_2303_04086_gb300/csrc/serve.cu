@@ -542,7 +542,7 @@ __global__ void __launch_bounds__(kServeThreads, 2) k_serve(const __grid_constan
         if (tid == 0 && need) s_wcache = k;
         const uint8_t* sB1 = smem;
         const uint8_t* sB2 = smem + 64u * K1 * 2u;
-        const float* sW3 = reinterpret_cast<const float*>(sB2 + 64u * 64u * 2u);
+        const uint8_t* sB3 = sB2 + 64u * 64u * 2u;  // W3 as a 16-row operand
         const uint32_t t = (uint32_t)tid >> 7, row = (uint32_t)tid & 127u;
         uint8_t* A = sA + t * (128u * 64u * 2u);
         for (uint32_t base = 0; base < cnt; base += kServeThreads) {
@@ -589,7 +589,7 @@ __global__ void __launch_bounds__(kServeThreads, 2) k_serve(const __grid_constan
           float4 rgba;
           const TcScales sc = TcScales::make(false, nullptr, nullptr);
           if (tid == 0) prof[kProfBatches] += 1;
-          if (!tc_mlp_run<false>(sA, sB1, sB2, sW3, K1, tmem, &bars[1], mma_phase, sc, rgba)) {
+          if (!tc_mlp_run<false>(sA, sB1, sB2, sB3, K1, tmem, &bars[1], mma_phase, sc, rgba)) {
             broken = true;
             break;
           }

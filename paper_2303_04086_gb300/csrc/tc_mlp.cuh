@@ -1,7 +1,8 @@
 // Layers 1-3 of the MLP F_s on the tensor cores for 2 x 128 rows whose A1
 // operand rows are already in shared memory (shared by the render and serve
 // kernels).  256 threads; thread tid owns row tid & 127 of tile tid >> 7.
-// sW3 holds W3^T [64][4] (FP32 of the quantised weights), 16-byte aligned.
+// sB3 holds W3 as a 16-row operand (rows 4..15 zero: N = 16 is the smallest
+// N of an M = 128 MMA), K-major like W2.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -87,24 +88,25 @@ struct RowWriter {
 // input scale sh2 is applied once to the 4 dot products instead of to each of
 // the 64 inputs.
 struct TcScales {
-  float inv_sx, q1, q2, sh2;
+  float inv_sx, q1, q2, o3;
   __device__ static TcScales make(bool fp8, const float act[3], const float w[3]) {
     TcScales s;
     s.inv_sx = fp8 ? 1.0f / act[0] : 1.0f;
     s.q1 = fp8 ? (act[0] * w[0]) / act[1] : 1.0f;
     s.q2 = fp8 ? (act[1] * w[1]) / act[2] : 1.0f;
-    s.sh2 = fp8 ? act[2] : 1.0f;
+    s.o3 = fp8 ? act[2] * w[2] : 1.0f;  // dequantises the last layer's accumulator
     return s;
   }
 };
 
 // Steps after the A1 rows are written: D1 = A1 W1^T (tcgen05, TMEM), ReLU and
-// quantisation into A2 (in place of A1), D2 = A2 W2^T, ReLU, quantisation,
-// W3 on the CUDA cores and sigmoid.  Every thread of the CTA must call it;
-// `out` receives the thread's row.  Returns false (uniformly) when an MMA
-// completion wait ran out.
+// quantisation into A2 (in place of A1), D2 = A2 W2^T, ReLU and quantisation
+// into A3 (in place of A2), D3 = A3 W3^T (N = 16, the 4 outputs in columns
+// 0..3) and sigmoid.  Every thread of the CTA must call it; `out` receives
+// the thread's row.  Returns false (uniformly) when an MMA completion wait ran
+// out.
 template <bool kFP8>
-__device__ __forceinline__ bool tc_mlp_run(uint8_t* sA, const uint8_t* sB1, const uint8_t* sB2, const float* sW3,
+__device__ __forceinline__ bool tc_mlp_run(uint8_t* sA, const uint8_t* sB1, const uint8_t* sB2, const uint8_t* sB3,
                                            uint32_t K1, uint32_t tmem, uint64_t* bar, uint32_t& phase,
                                            const TcScales& sc, float4& out) {
   constexpr uint32_t ES = kFP8 ? 1u : 2u;
@@ -115,96 +117,70 @@ __device__ __forceinline__ bool tc_mlp_run(uint8_t* sA, const uint8_t* sB1, cons
   const uint32_t t = (uint32_t)tid >> 7, row = (uint32_t)tid & 127u;
   uint8_t* A = sA + t * tile_bytes;
   const uint32_t lane_base = ((uint32_t)(warp & 3) * 32u) << 16;
-  const uint32_t id = tc::idesc(128, 64, kFP8 ? 0u : 1u);
+  const uint32_t fmt = kFP8 ? 0u : 1u;
+  const uint32_t id = tc::idesc(128, 64, fmt), id3 = tc::idesc(128, 16, fmt);
+  // D (+)= A B^T for both tiles (thread 0), committed to `bar`, then waited for
+  auto mma = [&](const uint8_t* sB, uint32_t chunks, uint32_t idesc) -> bool {
+    if (tid == 0) {
+      tc::fence_after();
+      for (uint32_t tt = 0; tt < 2; ++tt) {
+        const uint32_t a0 = tc::smem_u32(sA + tt * tile_bytes), b0 = tc::smem_u32(sB);
+        for (uint32_t s = 0; s < chunks / KSTEP_CHUNKS; ++s) {
+          const uint64_t ad = tc::desc_kmajor(a0 + s * 256u, 128u, chunks * 128u);
+          const uint64_t bd = tc::desc_kmajor(b0 + s * 256u, 128u, chunks * 128u);
+          if (kFP8) tc::mma_fp8(tmem + tt * 64u, ad, bd, idesc, s > 0);
+          else tc::mma_bf16(tmem + tt * 64u, ad, bd, idesc, s > 0);
+        }
+      }
+      tc::mma_commit(bar);
+    }
+    const bool ok = tc::mbar_wait(bar, phase, kWaitLimitNs);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) return false;
+    tc::fence_after();
+    return true;
+  };
+  // this thread's TMEM row (64 columns) -> ReLU (FP8: times `scale`, then
+  // quantised) -> the next layer's A operand row, in place
+  auto next_input = [&](float scale) {
+#pragma unroll 1
+    for (uint32_t c = 0; c < 4; ++c) {
+      float v[16];
+      tc::tmem_ld16(tmem + lane_base + t * 64u + c * 16u, v);
+      if (kFP8) {
+        uint32_t w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float a0 = fmaxf(v[4 * q + 0] * scale, 0.f);
+          const float a1 = fmaxf(v[4 * q + 1] * scale, 0.f);
+          const float a2 = fmaxf(v[4 * q + 2] * scale, 0.f);
+          const float a3 = fmaxf(v[4 * q + 3] * scale, 0.f);
+          w[q] = (uint32_t)pack_fp8(a0, a1) | ((uint32_t)pack_fp8(a2, a3) << 16);
+        }
+        *reinterpret_cast<uint4*>(A + tc::core_off(row, c, chunks2)) = make_uint4(w[0], w[1], w[2], w[3]);
+      } else {
+        uint32_t w[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) w[q] = pack_bf16(fmaxf(v[2 * q], 0.f), fmaxf(v[2 * q + 1], 0.f));
+        *reinterpret_cast<uint4*>(A + tc::core_off(row, 2 * c, chunks2)) = make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4*>(A + tc::core_off(row, 2 * c + 1, chunks2)) = make_uint4(w[4], w[5], w[6], w[7]);
+      }
+    }
+    tc::fence_before();
+    tc::fence_async_smem();
+    __syncthreads();
+  };
   tc::fence_async_smem();
   __syncthreads();
-  // ---- D1 = A1 W1^T ----
-  if (tid == 0) {
-    tc::fence_after();
-    for (uint32_t tt = 0; tt < 2; ++tt) {
-      const uint32_t a0 = tc::smem_u32(sA + tt * tile_bytes), b0 = tc::smem_u32(sB1);
-      for (uint32_t s = 0; s < chunks1 / KSTEP_CHUNKS; ++s) {
-        const uint64_t ad = tc::desc_kmajor(a0 + s * 256u, 128u, chunks1 * 128u);
-        const uint64_t bd = tc::desc_kmajor(b0 + s * 256u, 128u, chunks1 * 128u);
-        if (kFP8) tc::mma_fp8(tmem + tt * 64u, ad, bd, id, s > 0);
-        else tc::mma_bf16(tmem + tt * 64u, ad, bd, id, s > 0);
-      }
-    }
-    tc::mma_commit(bar);
-  }
-  bool ok = tc::mbar_wait(bar, phase, kWaitLimitNs);
-  phase ^= 1u;
-  if (__syncthreads_or(!ok)) return false;
-  tc::fence_after();
-  // ---- ReLU, quantise -> A2 row ----
-#pragma unroll 1
-  for (uint32_t c = 0; c < 4; ++c) {
-    float v[16];
-    tc::tmem_ld16(tmem + lane_base + t * 64u + c * 16u, v);
-    if (kFP8) {
-      uint32_t w[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float a0 = fmaxf(v[4 * q + 0] * sc.q1, 0.f);
-        const float a1 = fmaxf(v[4 * q + 1] * sc.q1, 0.f);
-        const float a2 = fmaxf(v[4 * q + 2] * sc.q1, 0.f);
-        const float a3 = fmaxf(v[4 * q + 3] * sc.q1, 0.f);
-        w[q] = (uint32_t)pack_fp8(a0, a1) | ((uint32_t)pack_fp8(a2, a3) << 16);
-      }
-      *reinterpret_cast<uint4*>(A + tc::core_off(row, c, chunks2)) = make_uint4(w[0], w[1], w[2], w[3]);
-    } else {
-      uint32_t w[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) w[q] = pack_bf16(fmaxf(v[2 * q], 0.f), fmaxf(v[2 * q + 1], 0.f));
-      *reinterpret_cast<uint4*>(A + tc::core_off(row, 2 * c, chunks2)) = make_uint4(w[0], w[1], w[2], w[3]);
-      *reinterpret_cast<uint4*>(A + tc::core_off(row, 2 * c + 1, chunks2)) = make_uint4(w[4], w[5], w[6], w[7]);
-    }
-  }
-  tc::fence_before();
-  tc::fence_async_smem();
-  __syncthreads();
-  // ---- D2 = A2 W2^T ----
-  if (tid == 0) {
-    tc::fence_after();
-    for (uint32_t tt = 0; tt < 2; ++tt) {
-      const uint32_t a0 = tc::smem_u32(sA + tt * tile_bytes), b0 = tc::smem_u32(sB2);
-      for (uint32_t s = 0; s < chunks2 / KSTEP_CHUNKS; ++s) {
-        const uint64_t ad = tc::desc_kmajor(a0 + s * 256u, 128u, chunks2 * 128u);
-        const uint64_t bd = tc::desc_kmajor(b0 + s * 256u, 128u, chunks2 * 128u);
-        if (kFP8) tc::mma_fp8(tmem + tt * 64u, ad, bd, id, s > 0);
-        else tc::mma_bf16(tmem + tt * 64u, ad, bd, id, s > 0);
-      }
-    }
-    tc::mma_commit(bar);
-  }
-  ok = tc::mbar_wait(bar, phase, kWaitLimitNs);
-  phase ^= 1u;
-  if (__syncthreads_or(!ok)) return false;
-  tc::fence_after();
-  // ---- ReLU, quantise, W3, sigmoid ----
-  float out0 = 0.f, out1 = 0.f, out2 = 0.f, out3 = 0.f;
-#pragma unroll 1
-  for (uint32_t c = 0; c < 4; ++c) {
-    float v[16];
-    tc::tmem_ld16(tmem + lane_base + t * 64u + c * 16u, v);
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      // FP8: the quantised input in units of sh2; BF16: the rounded input
-      const float a = kFP8 ? round_fp8(fmaxf(v[j] * sc.q2, 0.f)) : round_bf16(fmaxf(v[j], 0.f));
-      const float4 w = reinterpret_cast<const float4*>(sW3)[c * 16u + (uint32_t)j];  // W3^T row
-      out0 += w.x * a;
-      out1 += w.y * a;
-      out2 += w.z * a;
-      out3 += w.w * a;
-    }
-  }
-  if (kFP8) {
-    out0 *= sc.sh2;
-    out1 *= sc.sh2;
-    out2 *= sc.sh2;
-    out3 *= sc.sh2;
-  }
-  out = make_float4(sigmoidf_(out0), sigmoidf_(out1), sigmoidf_(out2), sigmoidf_(out3));
+  if (!mma(sB1, chunks1, id)) return false;  // D1 = A1 W1^T
+  next_input(sc.q1);                         // A2
+  if (!mma(sB2, chunks2, id)) return false;  // D2 = A2 W2^T
+  next_input(sc.q2);                         // A3
+  if (!mma(sB3, chunks2, id3)) return false; // D3 = A3 W3^T (columns 0..3)
+  float v[16];
+  tc::tmem_ld16(tmem + lane_base + t * 64u, v);
+  out = make_float4(sigmoidf_(v[0] * sc.o3), sigmoidf_(v[1] * sc.o3), sigmoidf_(v[2] * sc.o3),
+                    sigmoidf_(v[3] * sc.o3));
   tc::fence_before();
   __syncthreads();
   return true;
