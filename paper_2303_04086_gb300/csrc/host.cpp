@@ -779,6 +779,9 @@ extern "C" inolf_status inolf_object_create(const inolf_object_desc* desc, void*
             const uint32_t fx = e & 1023u, fy = (e >> 10) & 1023u, fz = e >> 20;
             px[(size_t)(a + R * (b2 + R * c))] = (uint32_t)(fx + S * (fy + S * (int64_t)fz));
           }
+      // padded with zeros to a multiple of 16 bytes, so that one bulk copy of
+      // the whole table (a multiple of 16 bytes) stays inside the allocation
+      px.resize((px.size() + 3) / 4 * 4, 0u);
       void* dpx = nullptr;
       CUDA_TRY(cudaMalloc(&dpx, px.size() * sizeof(uint32_t)));
       lv.phix = (const uint32_t*)dpx;

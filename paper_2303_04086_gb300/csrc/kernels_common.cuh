@@ -57,6 +57,10 @@ struct Params {
   // bounded waits and test fault injection (process-wide settings)
   uint64_t wait_ns;    // limit of the gather/MLP hand-over waits
   uint32_t inject;     // INOLF_INJECT_* bits
+  // offset tables of levels 0 .. phis_levels - 1 staged in shared memory by
+  // k_shade_f32_ws (word offsets of each level's copy, 16-byte aligned)
+  int32_t phis_levels;
+  uint32_t phis_off[INOLF_MAX_LEVELS + 1];
   // workspace
   uint32_t* counter;   // [0] hit count, [1] error flags (INOLF_FLAG_*), [4..6] activation amax bits
   uint2* hits;         // (ray index in launch, t bits)
@@ -536,16 +540,20 @@ struct LevelFetchX {
   float f[3];
 };
 
-__device__ __forceinline__ void fetch_phi_x(const LevelDev& lv, const float x[3], LevelFetchX& s) {
+// Cell, fractions, h0 and the offset-table index q of corner 0 of x's cell.
+__device__ __forceinline__ uint32_t phi_index_x(const LevelDev& lv, const float x[3], LevelFetchX& s) {
   int32_t c[3];
   cell_of(lv, x, c, s.f);
   const uint32_t S = (uint32_t)lv.S, R = (uint32_t)lv.R;
   s.base = (uint32_t)mod_small(c[0], lv.m, lv.magic_m) +
            S * ((uint32_t)mod_small(c[1], lv.m, lv.magic_m) + S * (uint32_t)mod_small(c[2], lv.m, lv.magic_m));
-  const uint32_t q = (uint32_t)mod_small(c[0], lv.r, lv.magic_r) +
-                     R * ((uint32_t)mod_small(c[1], lv.r, lv.magic_r) + R * (uint32_t)mod_small(c[2], lv.r, lv.magic_r));
-  const uint32_t* ph = lv.phix + q;
-  const uint32_t R2 = R * R;
+  return (uint32_t)mod_small(c[0], lv.r, lv.magic_r) +
+         R * ((uint32_t)mod_small(c[1], lv.r, lv.magic_r) + R * (uint32_t)mod_small(c[2], lv.r, lv.magic_r));
+}
+
+__device__ __forceinline__ void fetch_phi_x(const LevelDev& lv, const float x[3], LevelFetchX& s) {
+  const uint32_t R = (uint32_t)lv.R, R2 = R * R;
+  const uint32_t* ph = lv.phix + phi_index_x(lv, x, s);
   s.ph[0] = __ldg(ph);
   s.ph[1] = __ldg(ph + 1);
   s.ph[2] = __ldg(ph + R);
@@ -554,6 +562,21 @@ __device__ __forceinline__ void fetch_phi_x(const LevelDev& lv, const float x[3]
   s.ph[5] = __ldg(ph + R2 + 1);
   s.ph[6] = __ldg(ph + R2 + R);
   s.ph[7] = __ldg(ph + R2 + R + 1);
+}
+
+// The same fetch from `phx`, a copy of lv.phix staged in shared memory.
+__device__ __forceinline__ void fetch_phi_x_from(const LevelDev& lv, const uint32_t* phx, const float x[3],
+                                                 LevelFetchX& s) {
+  const uint32_t R = (uint32_t)lv.R, R2 = R * R;
+  const uint32_t* ph = phx + phi_index_x(lv, x, s);
+  s.ph[0] = ph[0];
+  s.ph[1] = ph[1];
+  s.ph[2] = ph[R];
+  s.ph[3] = ph[R + 1];
+  s.ph[4] = ph[R2];
+  s.ph[5] = ph[R2 + 1];
+  s.ph[6] = ph[R2 + R];
+  s.ph[7] = ph[R2 + R + 1];
 }
 
 __device__ __forceinline__ void finish_level_x(const LevelDev& lv, int fp16, const LevelFetchX& s, float& e0,

@@ -366,8 +366,11 @@ __device__ __forceinline__ void block_gemm_4x8(const float* __restrict__ act, co
 // loads in flight), the SH encoding and alpha_c (half 1), the diffuse colour
 // and tint of the variant (half 0), all into the [k][kF32Tile] FP32 tile;
 // invalid slots are zero.  Returns the ray index of the hit record.
+// kStaged: the offset tables of levels 0 .. p.phis_levels - 1 are read from
+// their shared-memory copies at sphi + p.phis_off[l].
+template <bool kStaged>
 __device__ __forceinline__ int64_t gather_tile_f32(const Params& p, uint32_t h, bool valid, int ray_slot, int half,
-                                                   float* act, float* dif) {
+                                                   float* act, float* dif, const uint32_t* sphi = nullptr) {
   if (!valid) {
     for (int k = half; k < p.d_in; k += 2) act[k * kF32Tile + ray_slot] = 0.0f;
     return 0;
@@ -377,16 +380,22 @@ __device__ __forceinline__ int64_t gather_tile_f32(const Params& p, uint32_t h, 
   float o[3], d[3], x[3];
   ray_of(p, ray, o, d);
   hit_unit_coords(p, o, d, __uint_as_float(rec.y), x);
+  auto fetch = [&](int l, LevelFetchX& f) {
+    if (kStaged && l < p.phis_levels)
+      fetch_phi_x_from(p.lv[l], sphi + p.phis_off[l], x, f);
+    else
+      fetch_phi_x(p.lv[l], x, f);
+  };
   LevelFetchX fa, fb;
-  if (half < p.L) fetch_phi_x(p.lv[half], x, fa);
+  if (half < p.L) fetch(half, fa);
   for (int l = half; l < p.L; l += 4) {  // levels half, half + 2, ... in pairs, no state copies
     float e0, e1;
-    if (l + 2 < p.L) fetch_phi_x(p.lv[l + 2], x, fb);
+    if (l + 2 < p.L) fetch(l + 2, fb);
     finish_level_x(p.lv[l], p.fp16, fa, e0, e1);
     act[(2 * l) * kF32Tile + ray_slot] = e0;
     act[(2 * l + 1) * kF32Tile + ray_slot] = e1;
     if (l + 2 >= p.L) break;
-    if (l + 4 < p.L) fetch_phi_x(p.lv[l + 4], x, fa);
+    if (l + 4 < p.L) fetch(l + 4, fa);
     finish_level_x(p.lv[l + 2], p.fp16, fb, e0, e1);
     act[(2 * (l + 2)) * kF32Tile + ray_slot] = e0;
     act[(2 * (l + 2) + 1) * kF32Tile + ray_slot] = e1;
@@ -434,7 +443,7 @@ __global__ void __launch_bounds__(kF32Threads, 3) k_shade_f32_tiled(const __grid
   for (uint32_t base = blockIdx.x * kF32Tile; base < total; base += gridDim.x * kF32Tile) {
     const uint32_t h = base + (uint32_t)ray_slot;
     const bool valid = h < total;
-    const int64_t ray = gather_tile_f32(p, h, valid, ray_slot, half, act, dif);
+    const int64_t ray = gather_tile_f32<false>(p, h, valid, ray_slot, half, act, dif);
     __syncthreads();
     float acc[4][8];
     block_gemm_4x8(act, W1T, din, r0, c0, c0 + 4, acc);
@@ -514,17 +523,33 @@ static constexpr int kWsLaunchRegs = 80, kWsGatherRegs = 64, kWsMlpRegs = 112;
 static_assert(kWsTeams * 256 * kWsGatherRegs + kWsMlp * kWsMlpRegs <= kWsThreads * kWsLaunchRegs,
               "register split exceeds the CTA's launch allocation");
 static_assert(kWsThreads * kWsLaunchRegs <= 65536, "launch allocation exceeds the register file");
+// Shared memory of one ws CTA with its staged offset tables.  The SM splits
+// its 256 KB between shared memory and L1 in steps; below the 196 KB step
+// (less the 1 KB the CTA reserves) about 60 KB of L1 stay for the fine
+// levels' tables.  On the full scene this stages levels 0-2 (0.3% faster
+// than none); staging level 3 as well crosses the step and measured 8%
+// slower.
+static constexpr size_t kWsPhiSmemLimit = 195 * 1024;
 static constexpr uint64_t kRingWaitLimitNs = 2000000000ull;  // default hand-over limit: 2 s; a tile takes microseconds
 
 // shared-memory floats of one ring slot: inputs [d_in][tile], diffuse
 // [4][tile], ray ids [tile]
 __host__ __device__ constexpr int ws_slot_floats(int din) { return (din + 5) * kF32Tile; }
+// Bytes before the staged offset tables: weights, hidden tile, ring, the
+// full/empty barriers and the staging barrier (padded to 16 bytes, so the
+// tables that follow start 16-byte aligned).
 __host__ __device__ constexpr size_t ws_smem_bytes(int din) {
   return (size_t)(din * 64 + 64 * 64 + 4 * 64 + 64 * kF32Tile + kWsSlots * ws_slot_floats(din)) * sizeof(float) +
-         2 * kWsSlots * sizeof(uint64_t);
+         (2 * kWsSlots + 2) * sizeof(uint64_t);
 }
 static_assert(ws_smem_bytes(2 * INOLF_MAX_LEVELS + 17) <= 227 * 1024,
               "the largest input tile (16 levels, alpha_c) must fit one CTA's shared memory");
+static_assert(ws_smem_bytes(0) % 16 == 0 && ws_smem_bytes(1) % 16 == 0, "staged tables must start 16-byte aligned");
+// The raw FP32 weights land in the ring before it carries tiles: the ring
+// holds them for every d_in >= 4 (d_in is at least 18: one level and the 16
+// direction coefficients).
+static_assert((size_t)kWsSlots * ws_slot_floats(4) >= (size_t)(4 * 64 + 64 * 64 + 4 * 64),
+              "ring too small for the weight blob");
 // column of neuron c in the permuted W^T rows: octet c / 8, float4 half (c / 4) & 1
 __device__ __forceinline__ int ws_wcol(int c) { return ((c >> 2) & 1) * 32 + (c >> 3) * 4 + (c & 3); }
 
@@ -554,23 +579,41 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_shade_f32_ws(const __grid_con
   const int slot_floats = ws_slot_floats(din);
   uint64_t* full = reinterpret_cast<uint64_t*>(ring + kWsSlots * slot_floats);
   uint64_t* empty = full + kWsSlots;
+  uint64_t* staged = empty + kWsSlots;                           // weights and tables landed
+  const uint32_t* sphi = reinterpret_cast<uint32_t*>(staged + 2);  // 16-byte aligned
   const int tid = threadIdx.x;
+  // Staging by the bulk-copy engine: the raw weight blob into the (still
+  // unused) ring, and the offset tables of levels 0 .. phis_levels - 1 to
+  // their place after the barriers, all completing on one barrier.
+  const uint32_t wbytes = (uint32_t)(din * 64 + 64 * 64 + 64 * 4) * 4u;
   if (tid == 0) {
     for (int s = 0; s < kWsSlots; ++s) {
       tc::mbar_init(&full[s], 256);
       tc::mbar_init(&empty[s], kWsMlp);
     }
+    tc::mbar_init(staged, 1);
     tc::fence_mbar_init();
+    tc::mbar_arrive_expect_tx(staged, wbytes + p.phis_off[p.phis_levels] * 4u);
+    tc::bulk_g2s(ring, p.w_f32, wbytes, staged);
+    for (int l = 0; l < p.phis_levels; ++l)
+      tc::bulk_g2s(const_cast<uint32_t*>(sphi) + p.phis_off[l], p.lv[l].phix,
+                   (p.phis_off[l + 1] - p.phis_off[l]) * 4u, staged);
+  }
+  __syncthreads();  // barrier initialised before anyone polls it
+  if (!tc::mbar_wait(staged, 0u, p.wait_ns)) {
+    if (tid == 0) atomicOr(p.counter + 1, INOLF_FLAG_WAIT_TIMEOUT);
+    tc::mbar_wait(staged, 0u, p.wait_ns);  // copies still in flight land before the CTA leaves
+    return;
   }
   {
-    const float* g = p.w_f32;  // W1^T [din][64]
+    const float* g = ring;  // W1^T [din][64]
     for (int k = tid; k < din * 64; k += kWsThreads) W1T[(k & ~63) + ws_wcol(k & 63)] = g[k];
     const float* g2 = g + din * 64;  // W2 [out][in]
     for (int k = tid; k < 64 * 64; k += kWsThreads) W2T[(k & 63) * 64 + ws_wcol(k >> 6)] = g2[k];
     const float* g3 = g2 + 64 * 64;  // W3^T [in][4]
     for (int k = tid; k < 64 * 4; k += kWsThreads) W3T[k] = g3[k];
   }
-  __syncthreads();
+  __syncthreads();  // the ring's weight copy is read before the gathers overwrite it
   const uint32_t total = *p.counter;
   const uint32_t n_tiles = (total + kF32Tile - 1) / kF32Tile;
   const uint32_t n_k = blockIdx.x < n_tiles ? (n_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0u;
@@ -592,7 +635,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_shade_f32_ws(const __grid_con
       float* dif = in + din * kF32Tile;
       uint32_t* rid = reinterpret_cast<uint32_t*>(dif + 4 * kF32Tile);
       const uint32_t h = (blockIdx.x + k * gridDim.x) * kF32Tile + (uint32_t)ray_slot;
-      const int64_t ray = gather_tile_f32(p, h, h < total, ray_slot, half, in, dif);
+      const int64_t ray = gather_tile_f32<true>(p, h, h < total, ray_slot, half, in, dif, sphi);
       if (half == 0) rid[ray_slot] = (uint32_t)ray;
       if (!(p.inject & INOLF_INJECT_RING_STALL)) tc::mbar_arrive(&full[s]);  // injected stall: never handed over
     }
@@ -816,18 +859,33 @@ inolf_status launch_render(const Object& obj, const RayBatch& rays, inolf_precis
     cudaGetLastError();
   });
   const int f32_grid = sm_count() * f32_ctas_dev[dev];
-  const size_t smem_ws = ws_smem_bytes(obj.d_in);
   static std::once_flag ws_once[kMaxDevices];
   static bool ws_ok_dev[kMaxDevices];  // compiled with the register count its split assumes
+  static size_t ws_smem_max_dev[kMaxDevices];
   std::call_once(ws_once[dev], [&] {
     cudaFuncAttributes fa{};
     ws_ok_dev[dev] = cudaFuncGetAttributes(&fa, k_shade_f32_ws) == cudaSuccess && fa.numRegs == kWsLaunchRegs;
-    const size_t mx = ws_smem_bytes(2 * INOLF_MAX_LEVELS + 17);
-    cudaFuncSetAttribute(k_shade_f32_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t mx = std::max((size_t)optin, ws_smem_bytes(2 * INOLF_MAX_LEVELS + 17)) - fa.sharedSizeBytes;
+    ws_smem_max_dev[dev] = cudaFuncSetAttribute(k_shade_f32_ws, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)mx) == cudaSuccess ? mx : ws_smem_bytes(2 * INOLF_MAX_LEVELS + 17);
     cudaGetLastError();
   });
 
   const bool ws_ok = ws_ok_dev[dev];
+  // The unwrapped offset tables of the coarsest levels go to shared memory
+  // while they fit beside the tiles (each padded to 16 bytes, as allocated).
+  size_t smem_ws = ws_smem_bytes(obj.d_in);
+  p.phis_levels = 0;
+  p.phis_off[0] = 0;
+  for (int l = 0; l < obj.L && ws_ok; ++l) {
+    const size_t R = (size_t)obj.lv[l].R, words = (R * R * R + 3) / 4 * 4;
+    if (smem_ws + (p.phis_off[l] + words) * 4 > std::min(ws_smem_max_dev[dev], kWsPhiSmemLimit)) break;
+    p.phis_off[l + 1] = p.phis_off[l] + (uint32_t)words;
+    p.phis_levels = l + 1;
+  }
+  smem_ws += (size_t)p.phis_off[p.phis_levels] * 4;
   // the hit counter restarts with every chunk; the failure flags (word 1)
   // accumulate over the call
   bool first_chunk = clear_flags;
