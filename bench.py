@@ -45,6 +45,9 @@ def _args():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--small", action="store_true", help="tiny scene, 1 view at 512x512 (profiling)")
     ap.add_argument("--views", type=int, default=N_VIEWS)
+    ap.add_argument("--levels", type=int, default=16,
+                    help="PSH levels of the full scene (N = 16 .. 16 * 2^(levels-1), at most 2048); the proxy "
+                         "mesh is the same at any count, so a small count keeps a trace profile's footprint small")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precisions", default="fp32,bf16,fp8")
     ap.add_argument("--no-serving", action="store_true")
@@ -157,16 +160,17 @@ def replica_throughput(units_per_rank, seconds_max, world):
     return units_per_rank * world / seconds_max
 
 
-def make_workload(small: bool, views: int):
+def make_workload(small: bool, views: int, levels: int = 16):
     from paper_2303_04086_gb300 import synth
     if small:
         scene = synth.tiny_scene(seed=0)
         cams = synth.ring_cameras(max(1, min(views, 4)), 3.0)
         return scene, cams, 512, 512, {"workload": "icosphere-1280tri L4 N16-128, %d view(s) 512x512" % len(cams)}
-    scene = synth.full_scene(seed=0)
+    top = min(2048, 16 << (levels - 1))
+    scene = synth.full_scene(seed=0, n_levels=levels, top=top)
     cams = synth.ring_cameras(views, RING_R)
-    desc = ("displaced geodesic sphere 200k tris, L16 PSH N16-2048 band 2 cells, F2 fp32, "
-            "MLP 48-64-64-4, %d ring views r=2.5 at 3840x2160" % views)
+    desc = ("displaced geodesic sphere 200k tris, L%d PSH N16-%d band 2 cells, F2 fp32, "
+            "MLP %d-64-64-4, %d ring views r=2.5 at 3840x2160" % (levels, top, 2 * levels + 16, views))
     return scene, cams, W4K, H4K, {"workload": desc}
 
 
@@ -178,11 +182,11 @@ def make_workload(small: bool, views: int):
 # hash of the kernel's sources; once they change the figure prints as null
 # until it is captured again.
 SHADE_SOURCES = ["render.cu", "kernels_common.cuh", "tc_ptx.cuh", "inolf_internal.h"]
-SHADE_COUNTERS = {"k_shade_f32": {"src_sha": "228081bf6ec2131f",
-                                   # (1.10 GB read + 64.47 MB written) / 4 010 637 hit rays
-                                   "dram_bytes_per_hit": (1.10e9 + 64.47e6) / 4010637,
-                                   # 58 025 794 sectors / 4 010 637 hit rays
-                                   "l2_sectors_per_hit": 58025794 / 4010637}}
+SHADE_COUNTERS = {"k_shade_f32": {"src_sha": "14fc496e3e363f8c",
+                                   # (1 105 263 360 B read + 64 690 432 B written) / 4 010 637 hit rays
+                                   "dram_bytes_per_hit": (1105263360 + 64690432) / 4010637,
+                                   # 58 983 362 sectors / 4 010 637 hit rays
+                                   "l2_sectors_per_hit": 58983362 / 4010637}}
 
 
 def shade_source_sha() -> str:
@@ -759,7 +763,7 @@ def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    scene, cams, W, H, cfg = make_workload(a.small, a.views)
+    scene, cams, W, H, cfg = make_workload(a.small, a.views, a.levels)
     import oracle
     oracle.build()
     orc = oracle.Oracle(scene)
@@ -783,7 +787,7 @@ def run_native(a):
     from paper_2303_04086_gb300 import build, inolf, synth
     rank, world, local = _dist_init(a.gpus)
     build.build()
-    scene, cams, W, H, cfg = make_workload(a.small, a.views)
+    scene, cams, W, H, cfg = make_workload(a.small, a.views, a.levels)
     t0 = time.time()
     hashes = inolf.build_hashes(scene, slot_slack=1.0 if a.small else SLOT_SLACK)
     obj = inolf.object_create(scene, hashes)
@@ -891,7 +895,7 @@ def run_native(a):
             # reported beside it
             byt = algorithmic_bytes_per_hit(scene) * hits_per_launch + 16 * hits_per_launch + 8 * hits_per_launch
             achieved = byt / avg_s / 1e9
-            cnt = shade_counters(top) if not a.small else {}
+            cnt = shade_counters(top) if not a.small and a.levels == 16 else {}
             dram = cnt.get("dram_bytes_per_hit")
             l2s = cnt.get("l2_sectors_per_hit")
             roof = {"kernel": top, "bound": "latency (dependent L1/L2 gather loads)", "achieved": achieved,

@@ -337,7 +337,9 @@ struct Builder {
       if (count <= kMaxLeaf) return leaf();
     }
     int32_t mid;
+    int split_axis = 0;  // the left child holds the lower centroids along this axis
     if (best_axis >= 0) {
+      split_axis = best_axis;
       const int a = best_axis;
       const float ext = cb.hi[a] - cb.lo[a];
       auto it = std::partition(idx.begin() + first, idx.begin() + first + count, [&](int32_t t) {
@@ -350,6 +352,7 @@ struct Builder {
     }
     if (mid == first || mid == first + count) {  // degenerate: median by (centroid x, id)
       mid = first + count / 2;
+      split_axis = 0;
       std::nth_element(idx.begin() + first, idx.begin() + mid, idx.begin() + first + count,
                        [&](int32_t x, int32_t y) { return cen[3 * x] < cen[3 * y] || (cen[3 * x] == cen[3 * y] && x < y); });
     }
@@ -357,7 +360,7 @@ struct Builder {
     nodes.resize(nodes.size() + 16);
     ChildRef l = make(first, mid - first, depth + 1);
     ChildRef r = make(mid, first + count - mid, depth + 1);
-    write_node(node, l, r);
+    write_node(node, l, r, split_axis);
     ref.index = node;
     ref.count = 0;
     return ref;
@@ -366,22 +369,24 @@ struct Builder {
   static float pad_lo(float v) { return (float)((double)v - 1e-5 * (1.0 + std::fabs((double)v))); }
   static float pad_hi(float v) { return (float)((double)v + 1e-5 * (1.0 + std::fabs((double)v))); }
 
-  void write_node(int32_t node, const ChildRef& l, const ChildRef& r) {
+  void write_node(int32_t node, const ChildRef& l, const ChildRef& r, int split_axis) {
     float* nd = &nodes[16 * (size_t)node];
     const ChildRef* c[2] = {&l, &r};
     // layout: [lx0 lx1 rx0 rx1] [ly0 ly1 ry0 ry1] [lz0 lz1 rz0 rz1] [l.index l.count r.index r.count]
+    // where each count word is (triangles of a leaf, 0 for an inner node) | split axis << 4
     for (int k = 0; k < 3; ++k)
       for (int s = 0; s < 2; ++s) {
         const Box& b = c[s]->box;
         if (b.empty() || c[s]->index < 0) {
-          nd[4 * k + 2 * s + 0] = INFINITY;   // lo > hi: never entered
+          nd[4 * k + 2 * s + 0] = INFINITY;   // lo > hi: never entered (the traversal's signed slab test relies on it)
           nd[4 * k + 2 * s + 1] = -INFINITY;
         } else {
           nd[4 * k + 2 * s + 0] = pad_lo(b.lo[k]);
           nd[4 * k + 2 * s + 1] = pad_hi(b.hi[k]);
         }
       }
-    int32_t meta[4] = {l.index, l.count, r.index, r.count};
+    static_assert(kMaxLeaf < 16, "leaf counts take the low 4 bits of a count word");
+    int32_t meta[4] = {l.index, l.count | (split_axis << 4), r.index, r.count | (split_axis << 4)};
     std::memcpy(nd + 12, meta, sizeof(meta));
   }
 };
@@ -690,7 +695,7 @@ extern "C" inolf_status inolf_object_create(const inolf_object_desc* desc, void*
     ChildRef root = b.make(0, nF);
     if (root.count > 0) {  // whole mesh is one leaf: root = (leaf, empty)
       ChildRef none;
-      b.write_node(0, root, none);
+      b.write_node(0, root, none, 0);
     } else {
       // make() appended the real root at index 1.. copy it into slot 0
       std::copy(b.nodes.begin() + 16 * (size_t)root.index, b.nodes.begin() + 16 * (size_t)root.index + 16,

@@ -209,13 +209,43 @@ __device__ __forceinline__ bool mt_hit(const float o[3], const float d[3], const
 // per axis, so each plane distance is one fused multiply-add (the boxes are
 // padded and the comparison against the best hit has slack, so the rounding
 // of this test never decides a result).
+// Three-operand minimum and maximum (one instruction each on sm_100 and
+// later; a NaN operand is ignored, as by fminf / fmaxf).
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+  float d;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+
 __device__ __forceinline__ float box_enter(float lox, float hix, float loy, float hiy, float loz, float hiz,
                                            const float oi[3], const float inv[3], float tmax) {
   const float ax = fmaf(lox, inv[0], -oi[0]), bx = fmaf(hix, inv[0], -oi[0]);
   const float ay = fmaf(loy, inv[1], -oi[1]), by = fmaf(hiy, inv[1], -oi[1]);
   const float az = fmaf(loz, inv[2], -oi[2]), bz = fmaf(hiz, inv[2], -oi[2]);
-  const float t0 = fmaxf(fmaxf(fminf(ax, bx), fminf(ay, by)), fmaxf(fminf(az, bz), 0.0f));
-  const float t1 = fminf(fminf(fmaxf(ax, bx), fmaxf(ay, by)), fminf(fmaxf(az, bz), tmax));
+  const float t0 = fmax3(fminf(ax, bx), fminf(ay, by), fmaxf(fminf(az, bz), 0.0f));
+  const float t1 = fmin3(fmaxf(ax, bx), fmaxf(ay, by), fminf(fmaxf(az, bz), tmax));
+  return t0 <= t1 ? t0 : INFINITY;
+}
+
+// The same test when the signs of the direction are known at compile time
+// (bit k of kSign set: d[k] has its sign bit set, so inv[k] < 0).  Since
+// lo <= hi and a rounded multiply-add is monotone in lo, the entry plane of
+// axis k is lo for inv[k] > 0 and hi for inv[k] < 0: the same plane that
+// fminf / fmaxf pick in box_enter, so both return the same value, with no
+// per-axis minimum or maximum.
+template <int kSign>
+__device__ __forceinline__ float box_enter_signed(float lox, float hix, float loy, float hiy, float loz, float hiz,
+                                                  const float oi[3], const float inv[3], float tmax) {
+  const float nx = fmaf((kSign & 1) ? hix : lox, inv[0], -oi[0]), fx = fmaf((kSign & 1) ? lox : hix, inv[0], -oi[0]);
+  const float ny = fmaf((kSign & 2) ? hiy : loy, inv[1], -oi[1]), fy = fmaf((kSign & 2) ? loy : hiy, inv[1], -oi[1]);
+  const float nz = fmaf((kSign & 4) ? hiz : loz, inv[2], -oi[2]), fz = fmaf((kSign & 4) ? loz : hiz, inv[2], -oi[2]);
+  const float t0 = fmax3(nx, ny, fmaxf(nz, 0.0f));
+  const float t1 = fmin3(fx, fy, fminf(fz, tmax));
   return t0 <= t1 ? t0 : INFINITY;
 }
 
@@ -247,7 +277,7 @@ __device__ __forceinline__ void closest_hit_bvh(const float4* __restrict__ nodes
       break;
     }
     const float lim = best_id < 0 ? INFINITY : best_t * 1.00002f + 1e-5f;
-    if (cur_cnt == 0) {
+    if ((cur_cnt & 15) == 0) {  // count words carry the parent's split axis above bit 4
       const float4 nx = __ldg(nodes + 4 * cur + 0);
       const float4 ny = __ldg(nodes + 4 * cur + 1);
       const float4 nz = __ldg(nodes + 4 * cur + 2);
@@ -275,7 +305,7 @@ __device__ __forceinline__ void closest_hit_bvh(const float4* __restrict__ nodes
         continue;
       }
     } else {
-      for (int32_t k = 0; k < cur_cnt; ++k) {
+      for (int32_t k = 0, n = cur_cnt & 15; k < n; ++k) {
         const float4 a = __ldg(tris + 3 * (cur + k) + 0);
         const float4 b = __ldg(tris + 3 * (cur + k) + 1);
         const float4 c = __ldg(tris + 3 * (cur + k) + 2);
@@ -320,11 +350,13 @@ __device__ __forceinline__ void closest_hit(const Params& p, const float o[3], c
 // be called by all 32 lanes of the warp.
 // kCount: also returns the warp's inner-node visits and triangle tests (the
 // same in every lane: the packet moves as one).
-template <bool kCount = false>
-__device__ __forceinline__ void closest_hit_packet(const float4* __restrict__ nodes, const float4* __restrict__ tris,
-                                                   uint32_t* err, bool active, const float o[3], const float d[3],
-                                                   int32_t& best_id, float& best_t, uint32_t* n_inner = nullptr,
-                                                   uint32_t* n_tests = nullptr) {
+// kSign < 8: every active lane's direction has the signs of kSign (bits as
+// in box_enter_signed); 8: the signs differ across the packet.
+template <bool kCount, int kSign>
+__device__ __forceinline__ void closest_hit_packet_s(const float4* __restrict__ nodes, const float4* __restrict__ tris,
+                                                     uint32_t* err, bool active, const float o[3], const float d[3],
+                                                     int32_t& best_id, float& best_t, uint32_t* n_inner,
+                                                     uint32_t* n_tests) {
   uint32_t visits = 0, tests = 0;
   float inv[3], oi[3];
 #pragma unroll
@@ -346,23 +378,41 @@ __device__ __forceinline__ void closest_hit_packet(const float4* __restrict__ no
       break;
     }
     const float lim = best_id < 0 ? INFINITY : best_t * 1.00002f + 1e-5f;
-    if (cur_cnt == 0) {
+    if ((cur_cnt & 15) == 0) {  // count words carry the parent's split axis above bit 4
       if (kCount) ++visits;
       const float4 nx = __ldg(nodes + 4 * cur + 0);
       const float4 ny = __ldg(nodes + 4 * cur + 1);
       const float4 nz = __ldg(nodes + 4 * cur + 2);
       const int4 meta = __ldg(reinterpret_cast<const int4*>(nodes) + 4 * cur + 3);
-      float tl = box_enter(nx.x, nx.y, ny.x, ny.y, nz.x, nz.y, oi, inv, lim);
-      float tr = box_enter(nx.z, nx.w, ny.z, ny.w, nz.z, nz.w, oi, inv, lim);
-      if (!active || meta.x < 0) tl = INFINITY;
-      if (!active || meta.z < 0) tr = INFINITY;
+      float tl, tr;
+      if constexpr (kSign < 8) {
+        // An empty child's box is stored inverted (lo = +inf, hi = -inf), so
+        // its entry plane is +inf and the signed test rejects it; a lane
+        // without a ray tests against a negative limit, which rejects every
+        // box.
+        const float lim_a = active ? lim : -1.0f;
+        tl = box_enter_signed<kSign>(nx.x, nx.y, ny.x, ny.y, nz.x, nz.y, oi, inv, lim_a);
+        tr = box_enter_signed<kSign>(nx.z, nx.w, ny.z, ny.w, nz.z, nz.w, oi, inv, lim_a);
+      } else {
+        tl = box_enter(nx.x, nx.y, ny.x, ny.y, nz.x, nz.y, oi, inv, lim);
+        tr = box_enter(nx.z, nx.w, ny.z, ny.w, nz.z, nz.w, oi, inv, lim);
+        if (!active || meta.x < 0) tl = INFINITY;
+        if (!active || meta.z < 0) tr = INFINITY;
+      }
       const bool hl = tl != INFINITY, hr = tr != INFINITY;
       const bool wl = __any_sync(0xffffffffu, hl), wr = __any_sync(0xffffffffu, hr);
       if (wl && wr) {
-        // the child most rays enter first goes first
-        const uint32_t first_l = __ballot_sync(0xffffffffu, hl && (!hr || tl <= tr));
-        const uint32_t first_r = __ballot_sync(0xffffffffu, hr && (!hl || tr < tl));
-        const bool lfirst = __popc(first_l) >= __popc(first_r);
+        bool lfirst;
+        if constexpr (kSign < 8) {
+          // the left child holds the lower centroids along the node's split
+          // axis: it goes first when the packet moves up that axis
+          lfirst = !((kSign >> ((meta.y >> 4) & 3)) & 1);
+        } else {
+          // the child most rays enter first goes first
+          const uint32_t first_l = __ballot_sync(0xffffffffu, hl && (!hr || tl <= tr));
+          const uint32_t first_r = __ballot_sync(0xffffffffu, hr && (!hl || tr < tl));
+          lfirst = __popc(first_l) >= __popc(first_r);
+        }
         if (sp < kStackDepth) {
           st_idx[sp] = lfirst ? meta.z : meta.x;
           st_cnt[sp] = lfirst ? meta.w : meta.y;
@@ -380,8 +430,8 @@ __device__ __forceinline__ void closest_hit_packet(const float4* __restrict__ no
         continue;
       }
     } else {
-      if (kCount) tests += (uint32_t)cur_cnt;
-      for (int32_t k = 0; k < cur_cnt; ++k) {
+      if (kCount) tests += (uint32_t)(cur_cnt & 15);
+      for (int32_t k = 0, n = cur_cnt & 15; k < n; ++k) {
         const float4 a = __ldg(tris + 3 * (cur + k) + 0);
         const float4 b = __ldg(tris + 3 * (cur + k) + 1);
         const float4 c = __ldg(tris + 3 * (cur + k) + 2);
@@ -411,6 +461,40 @@ __device__ __forceinline__ void closest_hit_packet(const float4* __restrict__ no
     *n_inner = visits;
     *n_tests = tests;
   }
+}
+
+// Dispatches the packet to the traversal specialised for its direction
+// signs when all its active rays share them (the usual case for a camera
+// tile: only tiles that a plane d[k] = 0 crosses take the general test).
+template <bool kCount = false>
+__device__ __forceinline__ void closest_hit_packet(const float4* __restrict__ nodes, const float4* __restrict__ tris,
+                                                   uint32_t* err, bool active, const float o[3], const float d[3],
+                                                   int32_t& best_id, float& best_t, uint32_t* n_inner = nullptr,
+                                                   uint32_t* n_tests = nullptr) {
+  const uint32_t sgn = (signbit(d[0]) ? 1u : 0u) | (signbit(d[1]) ? 2u : 0u) | (signbit(d[2]) ? 4u : 0u);
+  const uint32_t act = __ballot_sync(0xffffffffu, active);
+  uint32_t kind = 8u;
+  if (act) {
+    const uint32_t s0 = __shfl_sync(0xffffffffu, sgn, __ffs(act) - 1);
+    if (__all_sync(0xffffffffu, !active || sgn == s0)) kind = s0;
+  }
+#define INOLF_PACKET_CASE(k)                                                                               \
+  case k:                                                                                                  \
+    closest_hit_packet_s<kCount, k>(nodes, tris, err, active, o, d, best_id, best_t, n_inner, n_tests); \
+    break;
+  switch (kind) {
+    INOLF_PACKET_CASE(0)
+    INOLF_PACKET_CASE(1)
+    INOLF_PACKET_CASE(2)
+    INOLF_PACKET_CASE(3)
+    INOLF_PACKET_CASE(4)
+    INOLF_PACKET_CASE(5)
+    INOLF_PACKET_CASE(6)
+    INOLF_PACKET_CASE(7)
+    default:
+      closest_hit_packet_s<kCount, 8>(nodes, tris, err, active, o, d, best_id, best_t, n_inner, n_tests);
+  }
+#undef INOLF_PACKET_CASE
 }
 
 // Scene-unit coordinates of the hit point: P = o + t d, x = (P - lo) * scale.

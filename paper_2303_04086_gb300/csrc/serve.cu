@@ -432,7 +432,7 @@ __global__ void __launch_bounds__(kServeThreads, 2) k_serve(const __grid_constan
           if (c2 > 0.f && (b > 0.f || b * b < c2)) act = false;
         }
         if (!__any_sync(0xffffffffu, act)) continue;
-        closest_hit_packet(ob.nodes, ob.tris, &kp.st->err, act, ol, d, id, t);
+        closest_hit_packet_s<false, 8>(ob.nodes, ob.tris, &kp.st->err, act, ol, d, id, t, nullptr, nullptr);
         if (!act || id < 0) continue;
       }
       {
