@@ -372,12 +372,15 @@ __device__ __forceinline__ void closest_hit_packet_s(const float4* __restrict__ 
   float st_t[kStackDepth];      // this lane's entry distance (INFINITY: not wanted)
   int sp = 0;
   int32_t cur = 0, cur_cnt = 0;  // inner node 0
+  // This lane's limit on entry distances: its best t plus a relative slack
+  // (INFINITY before a hit); -1 for a lane without a ray, which every box
+  // test then rejects.  Changes only after a leaf.
+  float lim = active ? INFINITY : -1.0f;
   for (int32_t guard = 0;; ++guard) {
     if (guard > (1 << 22)) {  // warp-uniform
       atomicOr(err, INOLF_FLAG_TRAVERSAL_LIMIT);
       break;
     }
-    const float lim = best_id < 0 ? INFINITY : best_t * 1.00002f + 1e-5f;
     if ((cur_cnt & 15) == 0) {  // count words carry the parent's split axis above bit 4
       if (kCount) ++visits;
       const float4 nx = __ldg(nodes + 4 * cur + 0);
@@ -386,18 +389,15 @@ __device__ __forceinline__ void closest_hit_packet_s(const float4* __restrict__ 
       const int4 meta = __ldg(reinterpret_cast<const int4*>(nodes) + 4 * cur + 3);
       float tl, tr;
       if constexpr (kSign < 8) {
-        // An empty child's box is stored inverted (lo = +inf, hi = -inf), so
-        // its entry plane is +inf and the signed test rejects it; a lane
-        // without a ray tests against a negative limit, which rejects every
-        // box.
-        const float lim_a = active ? lim : -1.0f;
-        tl = box_enter_signed<kSign>(nx.x, nx.y, ny.x, ny.y, nz.x, nz.y, oi, inv, lim_a);
-        tr = box_enter_signed<kSign>(nx.z, nx.w, ny.z, ny.w, nz.z, nz.w, oi, inv, lim_a);
+        // an empty child's box is stored inverted (lo = +inf, hi = -inf): its
+        // entry plane is +inf, so the signed test rejects it
+        tl = box_enter_signed<kSign>(nx.x, nx.y, ny.x, ny.y, nz.x, nz.y, oi, inv, lim);
+        tr = box_enter_signed<kSign>(nx.z, nx.w, ny.z, ny.w, nz.z, nz.w, oi, inv, lim);
       } else {
         tl = box_enter(nx.x, nx.y, ny.x, ny.y, nz.x, nz.y, oi, inv, lim);
         tr = box_enter(nx.z, nx.w, ny.z, ny.w, nz.z, nz.w, oi, inv, lim);
-        if (!active || meta.x < 0) tl = INFINITY;
-        if (!active || meta.z < 0) tr = INFINITY;
+        if (meta.x < 0) tl = INFINITY;
+        if (meta.z < 0) tr = INFINITY;
       }
       const bool hl = tl != INFINITY, hr = tr != INFINITY;
       const bool wl = __any_sync(0xffffffffu, hl), wr = __any_sync(0xffffffffu, hr);
@@ -441,13 +441,13 @@ __device__ __forceinline__ void closest_hit_packet_s(const float4* __restrict__ 
           if (t < best_t || (t == best_t && id < best_id)) { best_t = t; best_id = id; }
         }
       }
+      if (best_id >= 0) lim = best_t * 1.00002f + 1e-5f;
     }
     // pop the next subtree that some ray of the warp still wants
     bool found = false;
     while (sp > 0) {
       --sp;
-      const float lim2 = best_id < 0 ? INFINITY : best_t * 1.00002f + 1e-5f;
-      if (__any_sync(0xffffffffu, st_t[sp] <= lim2)) {
+      if (__any_sync(0xffffffffu, st_t[sp] <= lim)) {
         cur = st_idx[sp];
         cur_cnt = st_cnt[sp];
         found = true;
