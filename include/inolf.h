@@ -193,8 +193,16 @@ inolf_status inolf_object_table_rows(const inolf_object* obj, int32_t level, int
 /* ------------------------------------------------------------------------ */
 
 /* Workspace bytes inolf_render / inolf_render_rays / inolf_march_rays need
- * for n_rays rays (a header plus 12 bytes per ray: the hit list and, for
- * density-cube objects, each hit's alpha_c). */
+ * for n_rays rays: a 256-byte header, 12 bytes per ray (the hit list and,
+ * for density-cube objects, each hit's alpha_c), and the operand tiles of
+ * the BF16 / FP8 shade, 128 bytes per ray for at most 4 Mi rays (512 MiB;
+ * the environment variable INOLF_TC_CHUNK_ROWS, read at every call, sets
+ * that row count) plus 256 bytes.  With these tiles the BF16 / FP8 shade
+ * runs as two kernels over sub-ranges of the hit list: one gathers and
+ * encodes the hits into the tiles, the other runs the MLP on the tensor
+ * cores.  A smaller workspace (down to the header and the hit list of one
+ * view, or of all rays for ray batches) is accepted; the shade then runs as
+ * one fused kernel with the same results. */
 size_t inolf_render_workspace_bytes(int64_t n_rays);
 
 /* Renders n_views pinhole views of W x H pixels.

@@ -41,6 +41,11 @@ struct Params {
   const void* tc_w;                   // blob used by this launch
   int32_t tc_k1;
   uint32_t tc_wbytes;
+  // split tensor-core shade: operand tiles of the hits [tc_h_begin,
+  // tc_h_end) in the workspace (NULL: the fused kernel runs instead)
+  uint8_t* tc_a;
+  uint64_t tc_a_bytes;
+  uint32_t tc_h_begin, tc_h_end;
   const float* fp8_w_scale;           // device [3]
   float fp8_act_scale[3];
   float shc[10];

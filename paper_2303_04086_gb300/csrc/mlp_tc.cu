@@ -44,6 +44,51 @@ static constexpr int kTcThreads = 256;
 static constexpr uint32_t kTmemCols = 128;  // 2 tiles x 64 FP32 columns
 static constexpr int kW3Rows = 16;          // W3 padded to the smallest N of an M = 128 MMA
 
+// Encodes hit h into its operand row (Sec. 4.1): the trilinear PSH features
+// of every level, then the SH view encoding and, for density-cube objects,
+// alpha_c; zero-padded to K1 columns.  Returns the hit's ray index.
+template <bool kFP8>
+__device__ __forceinline__ int64_t encode_hit(const Params& p, uint32_t h, uint32_t K1, RowWriter<kFP8>& rw) {
+  const uint2 rec = p.hits[h];
+  float o[3], d[3], x[3];
+  ray_of(p, rec.x, o, d);
+  hit_unit_coords(p, o, d, __uint_as_float(rec.y), x);
+  // levels in pairs: Phi loads of the next level in flight, no state copies
+  LevelFetchX fa, fb;
+  fetch_phi_x(p.lv[0], x, fa);
+  for (int l = 0; l < p.L; l += 2) {
+    float e0, e1;
+    if (l + 1 < p.L) fetch_phi_x(p.lv[l + 1], x, fb);
+    finish_level_x(p.lv[l], p.fp16, fa, e0, e1);
+    rw.push(e0, e1);
+    if (l + 1 >= p.L) break;
+    if (l + 2 < p.L) fetch_phi_x(p.lv[l + 2], x, fa);
+    finish_level_x(p.lv[l + 1], p.fp16, fb, e0, e1);
+    rw.push(e0, e1);
+  }
+  float sh[16];
+  sh16(p, d, sh);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) rw.push(sh[2 * i], sh[2 * i + 1]);
+  if (p.variant) rw.push(p.hit_alpha[h], 0.f);  // alpha_c, the last input of F_s (Eq. 5)
+  rw.pad_to(K1);
+  return rec.x;
+}
+
+// Writes the shaded colour of hit h (ray `ray`); density-cube objects add
+// the diffuse colour read at the hit point, c = c_d + tint c_s (Eq. 7).
+__device__ __forceinline__ void store_rgba(const Params& p, uint32_t h, int64_t ray, float4 rgba) {
+  if (p.variant) {
+    const uint2 rec = p.hits[h];
+    float o[3], d[3], x[3];
+    ray_of(p, ray, o, d);
+    hit_unit_coords(p, o, d, __uint_as_float(rec.y), x);
+    const float4 dc = cube_diffuse(p.cub, x);
+    rgba = make_float4(fmaf(dc.w, rgba.x, dc.x), fmaf(dc.w, rgba.y, dc.y), fmaf(dc.w, rgba.z, dc.z), rgba.w);
+  }
+  p.rgba[p.ray_base + ray] = rgba;
+}
+
 template <bool kFP8>
 __global__ void __launch_bounds__(kTcThreads, 4) k_shade_tc(const __grid_constant__ Params p) {
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -91,31 +136,8 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_shade_tc(const __grid_constan
     int64_t ray = 0;
     // ---- 1. gather + encode -> A1 row ----
     if (valid) {
-      const uint2 rec = p.hits[h];
-      ray = rec.x;
-      float o[3], d[3], x[3];
-      ray_of(p, ray, o, d);
-      hit_unit_coords(p, o, d, __uint_as_float(rec.y), x);
-      // levels in pairs: Phi loads of the next level in flight, no state copies
       RowWriter<kFP8> rw(A, row, chunks1, inv_sx);
-      LevelFetchX fa, fb;
-      fetch_phi_x(p.lv[0], x, fa);
-      for (int l = 0; l < p.L; l += 2) {
-        float e0, e1;
-        if (l + 1 < p.L) fetch_phi_x(p.lv[l + 1], x, fb);
-        finish_level_x(p.lv[l], p.fp16, fa, e0, e1);
-        rw.push(e0, e1);
-        if (l + 1 >= p.L) break;
-        if (l + 2 < p.L) fetch_phi_x(p.lv[l + 2], x, fa);
-        finish_level_x(p.lv[l + 1], p.fp16, fb, e0, e1);
-        rw.push(e0, e1);
-      }
-      float sh[16];
-      sh16(p, d, sh);
-#pragma unroll
-      for (int i = 0; i < 8; ++i) rw.push(sh[2 * i], sh[2 * i + 1]);
-      if (p.variant) rw.push(p.hit_alpha[h], 0.f);  // alpha_c, the last input of F_s (Eq. 5)
-      rw.pad_to(K1);
+      ray = encode_hit<kFP8>(p, h, K1, rw);
     } else {
       for (uint32_t c = 0; c < chunks1; ++c)
         *reinterpret_cast<uint4*>(A + tc::core_off(row, c, chunks1)) = make_uint4(0, 0, 0, 0);
@@ -125,22 +147,113 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_shade_tc(const __grid_constan
       bad = true;
       break;
     }
-    if (valid) {
-      if (p.variant) {  // c = c_d + tint c_s (Eq. 7), diffuse read at the hit point
-        const uint2 rec = p.hits[h];
-        float o[3], d[3], x[3];
-        ray_of(p, ray, o, d);
-        hit_unit_coords(p, o, d, __uint_as_float(rec.y), x);
-        const float4 dc = cube_diffuse(p.cub, x);
-        rgba = make_float4(fmaf(dc.w, rgba.x, dc.x), fmaf(dc.w, rgba.y, dc.y), fmaf(dc.w, rgba.z, dc.z), rgba.w);
-      }
-      p.rgba[p.ray_base + ray] = rgba;
-    }
+    if (valid) store_rgba(p, h, ray, rgba);
   }
   if (bad) {
     if (tid == 0) atomicOr(p.counter + 1, INOLF_FLAG_WAIT_TIMEOUT);
     // let MMAs still in flight finish: the failed wait already flipped `phase`,
     // so the phase in flight has parity phase ^ 1
+    tc::mbar_wait(&bars[1], phase ^ 1u, kWaitLimitNs);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after();
+    tc::tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Split tensor-core shade, used when the render workspace holds operand tiles
+// for a sub-range of the hit list.  k_encode_tc gathers and encodes the hits
+// [tc_h_begin, tc_h_end) into tiles in global memory, in the layout of the
+// MMA's A operand (128 rows per tile, K-major 8x16-byte core matrices, K1
+// columns); k_mlp_tc copies two tiles at a time into shared memory by bulk
+// copy and runs the three layers on the tensor cores.  The gather then runs
+// at the occupancy its registers allow: no operand tiles, tensor memory or
+// MLP barriers hold its warps.
+static constexpr int kEncThreads = 256;
+
+template <bool kFP8>
+__global__ void __launch_bounds__(kEncThreads, 4) k_encode_tc(const __grid_constant__ Params p) {
+  constexpr uint32_t ES = kFP8 ? 1u : 2u;
+  const uint32_t K1 = (uint32_t)p.tc_k1, chunks1 = K1 * ES / 16u, tile_gbytes = 128u * K1 * ES;
+  const float inv_sx = kFP8 ? 1.0f / p.fp8_act_scale[0] : 1.0f;
+  const uint32_t end = min(p.tc_h_end, *p.counter);  // launches past the last hit return at once
+  for (uint32_t h = p.tc_h_begin + blockIdx.x * kEncThreads + threadIdx.x; h < end; h += gridDim.x * kEncThreads) {
+    const uint32_t i = h - p.tc_h_begin;
+    RowWriter<kFP8> rw(p.tc_a + (size_t)(i >> 7) * tile_gbytes, i & 127u, chunks1, inv_sx);
+    encode_hit<kFP8>(p, h, K1, rw);
+  }
+}
+
+template <bool kFP8>
+__global__ void __launch_bounds__(kTcThreads, 4) k_mlp_tc(const __grid_constant__ Params p) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  // a range past the last hit: nothing to stage (uniform over the grid)
+  if (p.tc_h_begin >= *p.counter) return;
+  constexpr uint32_t ES = kFP8 ? 1u : 2u;
+  const uint32_t K1 = (uint32_t)p.tc_k1;
+  const uint32_t wbytes = p.tc_wbytes;
+  const uint32_t tile_gbytes = 128u * K1 * ES;  // one tile in global memory
+  uint8_t* sB1 = smem;
+  uint8_t* sB2 = smem + 64u * K1 * ES;
+  const uint8_t* sB3 = sB2 + 64u * 64u * ES;
+  uint8_t* sA = smem + ((wbytes + 1023u) & ~1023u);
+  constexpr uint32_t tile_bytes = 128u * 64u * ES;  // one tile in shared memory (room for 64 columns)
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + 2 * tile_bytes);  // [0] weights, [1] MMA, [2] tiles
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 3);
+
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (tid == 0) {
+    for (int b = 0; b < 3; ++b) tc::mbar_init(&bars[b], 1);
+    tc::fence_mbar_init();
+  }
+  __syncthreads();
+  if (warp == 0) tc::tmem_alloc(tslot, kTmemCols);
+  if (tid == 0) {
+    tc::mbar_arrive_expect_tx(&bars[0], wbytes);
+    tc::bulk_g2s(smem, p.tc_w, wbytes, &bars[0]);
+  }
+  const bool ok = tc::mbar_wait(&bars[0], 0, kWaitLimitNs);
+  tc::fence_before();
+  bool bad = __syncthreads_or(!ok);
+  tc::fence_after();
+  const uint32_t tmem = *tslot;
+  const TcScales sc = TcScales::make(kFP8, p.fp8_act_scale, p.fp8_w_scale);
+  uint32_t phase = 0, tphase = 0;
+  bool tiles_in_flight = false;
+  const uint32_t end = min(p.tc_h_end, *p.counter);
+
+  for (uint32_t base = p.tc_h_begin + blockIdx.x * kTcThreads; !bad && base < end;
+       base += gridDim.x * kTcThreads) {
+    const uint32_t t0 = (base - p.tc_h_begin) >> 7;  // first of the two tiles
+    if (tid == 0) {
+      tc::fence_async_smem();  // the previous pair's in-place writes precede the copy
+      tc::mbar_arrive_expect_tx(&bars[2], 2u * tile_gbytes);
+      tc::bulk_g2s(sA, p.tc_a + (size_t)t0 * tile_gbytes, tile_gbytes, &bars[2]);
+      tc::bulk_g2s(sA + tile_bytes, p.tc_a + (size_t)(t0 + 1u) * tile_gbytes, tile_gbytes, &bars[2]);
+    }
+    tiles_in_flight = true;
+    const bool landed = tc::mbar_wait(&bars[2], tphase, kWaitLimitNs);
+    tphase ^= 1u;
+    if (__syncthreads_or(!landed)) {
+      bad = true;
+      break;
+    }
+    tiles_in_flight = false;
+    float4 rgba;
+    if (!tc_mlp_run<kFP8>(sA, sB1, sB2, sB3, K1, tmem, &bars[1], phase, sc, rgba)) {
+      bad = true;
+      break;
+    }
+    const uint32_t h = base + (uint32_t)tid;
+    if (h < end) store_rgba(p, h, (int64_t)p.hits[h].x, rgba);
+  }
+  if (bad) {
+    if (tid == 0) atomicOr(p.counter + 1, INOLF_FLAG_WAIT_TIMEOUT);
+    // copies and MMAs still in flight finish before the CTA leaves; a failed
+    // wait already flipped its parity, so the one in flight has parity ^ 1
+    if (tiles_in_flight) tc::mbar_wait(&bars[2], tphase ^ 1u, kWaitLimitNs);
     tc::mbar_wait(&bars[1], phase ^ 1u, kWaitLimitNs);
   }
   __syncthreads();
@@ -341,6 +454,7 @@ inolf_status launch_shade_tc(const Params& p_in, inolf_precision prec, cudaStrea
   const int dev = device_index();
   if (dev < 0) return fail(INOLF_E_UNSUPPORTED, "k_shade_tc: no current device, or an index beyond 63");
   static int grid_bf16_dev[kMaxDevices], grid_fp8_dev[kMaxDevices];
+  static int grid_enc_dev[kMaxDevices][2], grid_mlp_dev[kMaxDevices][2];  // [precision: BF16, FP8]
   static std::once_flag once[kMaxDevices];
   std::call_once(once[dev], [&] {
     int sms = 1, regs_sm = 65536, smem_sm = 0;
@@ -367,10 +481,50 @@ inolf_status launch_shade_tc(const Params& p_in, inolf_precision prec, cudaStrea
     };
     grid_bf16 = sms * ctas_per_sm((const void*)k_shade_tc<false>, tc_smem_bytes(kMaxTcWeightBytes, false));
     grid_fp8 = sms * ctas_per_sm((const void*)k_shade_tc<true>, tc_smem_bytes(kMaxTcWeightBytes, true));
+    grid_mlp_dev[dev][0] = sms * ctas_per_sm((const void*)k_mlp_tc<false>, tc_smem_bytes(kMaxTcWeightBytes, false));
+    grid_mlp_dev[dev][1] = sms * ctas_per_sm((const void*)k_mlp_tc<true>, tc_smem_bytes(kMaxTcWeightBytes, true));
+    // the encode kernel holds neither shared nor tensor memory: registers decide
+    auto enc_ctas = [&](const void* fn) {
+      cudaFuncAttributes fa{};
+      cudaFuncGetAttributes(&fa, fn);
+      const int regs_warp = ((std::max(fa.numRegs, 1) * 32 + 255) / 256) * 256;
+      return std::max(1, std::min(regs_sm / (regs_warp * (kEncThreads / 32)), 2048 / kEncThreads));
+    };
+    grid_enc_dev[dev][0] = sms * enc_ctas((const void*)k_encode_tc<false>);
+    grid_enc_dev[dev][1] = sms * enc_ctas((const void*)k_encode_tc<true>);
     cudaGetLastError();
   });
   if (smem > (size_t)tc_smem_bytes(kMaxTcWeightBytes, fp8)) return fail(INOLF_E_INVALID, "tensor-core weights too large");
   const int grid = fp8 ? grid_fp8_dev[dev] : grid_bf16_dev[dev];
+  if (p.tc_a) {
+    // split path: sub-ranges of the hit list as large as the workspace's
+    // operand tiles hold (a multiple of the MLP kernel's 256 rows); the hit
+    // count is known on the device only, so the ranges span the chunk's ray
+    // count and launches past the last hit return at once
+    const uint64_t row_bytes = (uint64_t)p.tc_k1 * (fp8 ? 1u : 2u);
+    const uint64_t rows = std::min<uint64_t>(p.tc_a_bytes / row_bytes / 256u * 256u, 0x80000000ull);
+    if (rows < 256) return fail(INOLF_E_INVALID, "split shade: operand tile region smaller than 256 rows");
+    for (int64_t h0 = 0; h0 < p.n_rays; h0 += (int64_t)rows) {
+      Params q = p;
+      q.tc_h_begin = (uint32_t)h0;
+      q.tc_h_end = (uint32_t)std::min<int64_t>(h0 + (int64_t)rows, p.n_rays);
+      {
+        LaunchTimer lt(fp8 ? "k_encode_tc_fp8" : "k_encode_tc_bf16", st);
+        if (fp8) k_encode_tc<true><<<grid_enc_dev[dev][1], kEncThreads, 0, st>>>(q);
+        else k_encode_tc<false><<<grid_enc_dev[dev][0], kEncThreads, 0, st>>>(q);
+      }
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return fail(INOLF_E_CUDA, std::string("k_encode_tc: ") + cudaGetErrorString(e));
+      {
+        LaunchTimer lt(fp8 ? "k_mlp_tc_fp8" : "k_mlp_tc_bf16", st);
+        if (fp8) k_mlp_tc<true><<<grid_mlp_dev[dev][1], kTcThreads, smem, st>>>(q);
+        else k_mlp_tc<false><<<grid_mlp_dev[dev][0], kTcThreads, smem, st>>>(q);
+      }
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return fail(INOLF_E_CUDA, std::string("k_mlp_tc: ") + cudaGetErrorString(e));
+    }
+    return INOLF_OK;
+  }
   {
     LaunchTimer lt(fp8 ? "k_shade_tc_fp8" : "k_shade_tc_bf16", st);
     if (fp8) k_shade_tc<true><<<grid, kTcThreads, smem, st>>>(p);

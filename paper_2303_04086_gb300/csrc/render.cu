@@ -27,6 +27,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -714,7 +715,23 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_shade_f32_ws(const __grid_con
 // ---------------------------------------------------------------------------
 static constexpr size_t kWsHeader = 256;
 
-size_t workspace_bytes(int64_t n_rays) { return kWsHeader + (size_t)std::max<int64_t>(n_rays, 1) * 12; }
+// Operand tiles of the split tensor-core shade: 128 bytes per hit row (the
+// widest first-layer row, 64 BF16 inputs) for up to tc_chunk_rows() hits at
+// a time, plus 256 bytes of alignment slack.  4 Mi rows (512 MiB): 64 4K
+// views take about 95 encode/MLP launch pairs, as fast as 16 Mi rows and 5 %
+// faster than 1 Mi.  INOLF_TC_CHUNK_ROWS overrides it (read at every call;
+// below 256 the fused kernel runs).
+static size_t tc_chunk_rows() {
+  const char* e = std::getenv("INOLF_TC_CHUNK_ROWS");
+  return e ? (size_t)std::max(0ll, std::atoll(e)) : ((size_t)1 << 22);
+}
+static size_t tc_region_bytes(int64_t n_rays) {
+  const size_t n = ((size_t)std::max<int64_t>(n_rays, 1) + 255) / 256 * 256;
+  return std::min(n, tc_chunk_rows()) * 128 + 256;
+}
+size_t workspace_bytes(int64_t n_rays) {
+  return kWsHeader + (size_t)std::max<int64_t>(n_rays, 1) * 12 + tc_region_bytes(n_rays);
+}
 static size_t workspace_bytes_min() { return workspace_bytes(1); }
 
 std::atomic<int64_t> g_wait_ns{0};     // inolf_set_wait_limit_ns (0 = default)
@@ -826,7 +843,21 @@ inolf_status launch_render(const Object& obj, const RayBatch& rays, inolf_precis
     return fail(INOLF_E_INVALID, "render: FP8 needs activation scales (inolf_object_set_fp8_scales)");
   Params p{};
   fill_common(obj, p);
-  const int64_t cap = place_hit_list(obj, workspace, ws_bytes, p);
+  // The split tensor-core shade keeps its operand tiles at the end of the
+  // workspace when the workspace holds them beside one view's (or all the
+  // rays') hit records; otherwise the fused kernel runs.
+  size_t hit_ws = ws_bytes;
+  if (!encode && !amax && !hits_only && prec != INOLF_FP32 && tc_chunk_rows() >= 256) {
+    const int64_t n_call = rays.mode == 0 ? (int64_t)rays.n_views * rays.W * rays.H : rays.n;
+    const int64_t min_hits = rays.mode == 0 ? (int64_t)rays.W * rays.H : n_call;
+    const size_t a_bytes = tc_region_bytes(n_call);
+    if (ws_bytes >= kWsHeader + (size_t)min_hits * hit_bytes_per_ray(obj) + a_bytes) {
+      hit_ws = (ws_bytes - a_bytes + 255) / 256 * 256;
+      p.tc_a = (uint8_t*)workspace + hit_ws;
+      p.tc_a_bytes = (uint64_t)(ws_bytes - hit_ws);
+    }
+  }
+  const int64_t cap = place_hit_list(obj, workspace, hit_ws, p);
   uint32_t* counter = p.counter;
   p.mode = rays.mode;
   p.rgba = (float4*)rgba;
