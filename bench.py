@@ -182,11 +182,11 @@ def make_workload(small: bool, views: int, levels: int = 16):
 # hash of the kernel's sources; once they change the figure prints as null
 # until it is captured again.
 SHADE_SOURCES = ["render.cu", "kernels_common.cuh", "tc_ptx.cuh", "inolf_internal.h"]
-SHADE_COUNTERS = {"k_shade_f32": {"src_sha": "f0fece8f21e2fe6c",
-                                   # (1 107 057 408 B read + 64 699 904 B written) / 4 010 637 hit rays
-                                   "dram_bytes_per_hit": (1107057408 + 64699904) / 4010637,
-                                   # 58 949 640 sectors / 4 010 637 hit rays
-                                   "l2_sectors_per_hit": 58949640 / 4010637}}
+SHADE_COUNTERS = {"k_shade_f32": {"src_sha": "fc072ee43e256737",
+                                   # (1 106 912 256 B read + 64 595 968 B written) / 4 010 637 hit rays
+                                   "dram_bytes_per_hit": (1106912256 + 64595968) / 4010637,
+                                   # 59 006 194 sectors / 4 010 637 hit rays
+                                   "l2_sectors_per_hit": 59006194 / 4010637}}
 
 
 def shade_source_sha() -> str:
