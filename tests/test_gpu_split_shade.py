@@ -100,3 +100,38 @@ def test_split_equals_fused_density_cubes(torch_cuda, prec):
     assert (ref[..., 3] > 0).sum() > 1000
     for k, v in out.items():
         assert np.array_equal(v, ref), k
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_split_equals_fused_explicit_rays(torch_cuda, prec):
+    """Explicit rays (inolf_render_rays): the split path over one and over many
+    sub-ranges, the fused kernel, and the allocation-free entry point (its
+    fixed scratch) give the same colours."""
+    from paper_2303_04086_gb300 import inolf
+    import oracle
+    torch = torch_cuda
+    scene = synth.tiny_scene(seed=1, fp16=False)
+    obj = inolf.object_create(scene)
+    cams = synth.ring_cameras(2, 2.8)
+    W, H = 96, 80
+    if prec == "fp8":
+        inolf.calibrate_fp8(obj, cams[:1], W, H)
+    o, d = oracle.raygen(cams[1], W, H)
+    rng = np.random.default_rng(3)
+    idx = rng.permutation(len(o))[:5000]  # scattered rays, ragged count
+    o = torch.tensor(np.ascontiguousarray(o[idx]), dtype=torch.float32, device="cuda")
+    d = torch.tensor(np.ascontiguousarray(d[idx]), dtype=torch.float32, device="cuda")
+    n = o.shape[0]
+    out = {}
+    with _env(None):
+        out["default"] = inolf.render_rays(obj, o, d, prec).cpu().numpy()
+        small = torch.empty((12 * n + 256 + 15) // 16 * 4, dtype=torch.int32, device="cuda")
+        out["fused_small_ws"] = inolf.render_rays(obj, o, d, prec, workspace=small).cpu().numpy()
+        out["noalloc"] = inolf.render_rays_noalloc(obj, o, d, prec).cpu().numpy()
+    with _env(300):
+        out["split_many"] = inolf.render_rays(obj, o, d, prec).cpu().numpy()
+    torch.cuda.synchronize()
+    ref = out["default"]
+    assert (ref[:, 3] > 0).sum() > 1000
+    for k, v in out.items():
+        assert np.array_equal(v, ref), k
