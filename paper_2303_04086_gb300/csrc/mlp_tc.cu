@@ -57,19 +57,26 @@ __device__ __forceinline__ int64_t encode_hit(const Params& p, uint32_t h, uint3
   LevelFetchX fa, fb;
   fetch_phi_x(p.lv[0], x, fa);
   for (int l = 0; l < p.L; l += 2) {
-    float e0, e1;
+    float e0, e1, g0, g1;
     if (l + 1 < p.L) fetch_phi_x(p.lv[l + 1], x, fb);
     finish_level_x(p.lv[l], p.fp16, fa, e0, e1);
-    rw.push(e0, e1);
-    if (l + 1 >= p.L) break;
+    if (l + 1 >= p.L) {
+      rw.push(e0, e1);
+      break;
+    }
     if (l + 2 < p.L) fetch_phi_x(p.lv[l + 2], x, fa);
-    finish_level_x(p.lv[l + 1], p.fp16, fb, e0, e1);
-    rw.push(e0, e1);
+    finish_level_x(p.lv[l + 1], p.fp16, fb, g0, g1);
+    rw.push2(e0, e1, g0, g1);  // levels l, l + 1: columns 4 (l / 2) .. + 3
   }
   float sh[16];
   sh16(p, d, sh);
+  if ((p.L & 1) == 0) {
 #pragma unroll
-  for (int i = 0; i < 8; ++i) rw.push(sh[2 * i], sh[2 * i + 1]);
+    for (int i = 0; i < 4; ++i) rw.push2(sh[4 * i], sh[4 * i + 1], sh[4 * i + 2], sh[4 * i + 3]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) rw.push(sh[2 * i], sh[2 * i + 1]);
+  }
   if (p.variant) rw.push(p.hit_alpha[h], 0.f);  // alpha_c, the last input of F_s (Eq. 5)
   rw.pad_to(K1);
   return rec.x;

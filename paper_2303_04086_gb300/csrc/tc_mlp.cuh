@@ -72,6 +72,27 @@ struct RowWriter {
       if ((++n & 3u) == 0) flush((n >> 2) - 1u);
     }
   }
+  // two consecutive pairs at once; the count of pairs pushed so far must be
+  // even (the words then hold whole 32-bit column groups, so no shifting)
+  __device__ __forceinline__ void push2(float a0, float b0, float a1, float b1) {
+    if (kFP8) {
+      const uint32_t v =
+          (uint32_t)pack_fp8(a0 * inv_s, b0 * inv_s) | ((uint32_t)pack_fp8(a1 * inv_s, b1 * inv_s) << 16);
+      w0 = w1;
+      w1 = w2;
+      w2 = w3;
+      w3 = v;
+      n += 2;
+      if ((n & 7u) == 0) flush((n >> 3) - 1u);
+    } else {
+      w0 = w2;
+      w1 = w3;
+      w2 = pack_bf16(a0, b0);
+      w3 = pack_bf16(a1, b1);
+      n += 2;
+      if ((n & 3u) == 0) flush((n >> 2) - 1u);
+    }
+  }
   __device__ __forceinline__ void flush(uint32_t c) {
     *reinterpret_cast<uint4*>(A + tc::core_off(row, c, chunks)) = make_uint4(w0, w1, w2, w3);
   }
