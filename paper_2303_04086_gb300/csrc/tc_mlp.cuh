@@ -96,9 +96,19 @@ struct RowWriter {
   __device__ __forceinline__ void flush(uint32_t c) {
     *reinterpret_cast<uint4*>(A + tc::core_off(row, c, chunks)) = make_uint4(w0, w1, w2, w3);
   }
-  // zero pairs up to column K (a multiple of the chunk width)
+  // zero pairs up to column K (a multiple of the chunk width).  FP8 rows pad
+  // whole chunks (K rounds up to 32 columns): the open chunk is completed
+  // pair by pair, the chunks after it are stored as zeros at once.
   __device__ __forceinline__ void pad_to(uint32_t K) {
-    while (2u * n < K) push(0.f, 0.f);
+    if constexpr (kFP8) {
+      while ((n & 7u) != 0u) push(0.f, 0.f);
+      for (; 2u * n < K; n += 8u) {
+        w0 = w1 = w2 = w3 = 0u;
+        flush(n >> 3);
+      }
+    } else {
+      while (2u * n < K) push(0.f, 0.f);
+    }
   }
 };
 
