@@ -135,3 +135,29 @@ def test_split_equals_fused_explicit_rays(torch_cuda, prec):
     assert (ref[:, 3] > 0).sum() > 1000
     for k, v in out.items():
         assert np.array_equal(v, ref), k
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_split_with_no_hits_and_a_ragged_hit_count(torch_cuda, prec):
+    """A view with no hit at all (every encode / MLP launch returns at once)
+    beside a view with a few hits: misses are exact zeros, the failure flags
+    stay clear, and the hit view matches the fused kernel."""
+    from paper_2303_04086_gb300 import inolf
+    torch = torch_cuda
+    scene = synth.tiny_scene(seed=2, fp16=True)
+    obj = inolf.object_create(scene)
+    W, H = 120, 72
+    away = synth.camera((0.0, 0.0, 3.0), target=(0.0, 0.0, 6.0))  # looks away from the object
+    far = synth.camera((0.0, 0.0, 12.0))                          # the object covers a few pixels
+    cams = np.stack([away, far])
+    if prec == "fp8":
+        inolf.calibrate_fp8(obj, cams[1:], W, H)
+    with _env(None):
+        split = inolf.render(obj, cams, W, H, prec).cpu().numpy()
+        small = torch.empty((12 * 2 * W * H + 256 + 15) // 16 * 4, dtype=torch.int32, device="cuda")
+        fused = inolf.render(obj, cams, W, H, prec, workspace=small).cpu().numpy()
+    torch.cuda.synchronize()
+    assert np.all(split[0] == 0)
+    n_hit = int((split[1][..., 3] > 0).sum())
+    assert 0 < n_hit < 2000
+    assert np.array_equal(split, fused)
