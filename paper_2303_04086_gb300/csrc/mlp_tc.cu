@@ -241,6 +241,9 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_mlp_tc(const __grid_constant_
       tc::bulk_g2s(sA + tile_bytes, p.tc_a + (size_t)(t0 + 1u) * tile_gbytes, tile_gbytes, &bars[2]);
     }
     tiles_in_flight = true;
+    // the hit's ray index is loaded now, while the tiles and the MMAs are in flight
+    const uint32_t h = base + (uint32_t)tid;
+    const uint32_t ray = h < end ? p.hits[h].x : 0u;
     const bool landed = tc::mbar_wait(&bars[2], tphase, kWaitLimitNs);
     tphase ^= 1u;
     if (__syncthreads_or(!landed)) {
@@ -253,8 +256,7 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_mlp_tc(const __grid_constant_
       bad = true;
       break;
     }
-    const uint32_t h = base + (uint32_t)tid;
-    if (h < end) store_rgba(p, h, (int64_t)p.hits[h].x, rgba);
+    if (h < end) store_rgba(p, h, (int64_t)ray, rgba);
   }
   if (bad) {
     if (tid == 0) atomicOr(p.counter + 1, INOLF_FLAG_WAIT_TIMEOUT);
