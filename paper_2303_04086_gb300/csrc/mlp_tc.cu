@@ -47,9 +47,10 @@ static constexpr int kW3Rows = 16;          // W3 padded to the smallest N of an
 // Encodes hit h into its operand row (Sec. 4.1): the trilinear PSH features
 // of every level, then the SH view encoding and, for density-cube objects,
 // alpha_c; zero-padded to K1 columns.  Returns the hit's ray index.
+// rec: the hit record (ray, t bits) of hit h, loaded by the caller.
 template <bool kFP8>
-__device__ __forceinline__ int64_t encode_hit(const Params& p, uint32_t h, uint32_t K1, RowWriter<kFP8>& rw) {
-  const uint2 rec = p.hits[h];
+__device__ __forceinline__ int64_t encode_rec(const Params& p, uint2 rec, uint32_t h, uint32_t K1,
+                                              RowWriter<kFP8>& rw) {
   float o[3], d[3], x[3];
   ray_of(p, rec.x, o, d);
   hit_unit_coords(p, o, d, __uint_as_float(rec.y), x);
@@ -80,6 +81,11 @@ __device__ __forceinline__ int64_t encode_hit(const Params& p, uint32_t h, uint3
   if (p.variant) rw.push(p.hit_alpha[h], 0.f);  // alpha_c, the last input of F_s (Eq. 5)
   rw.pad_to(K1);
   return rec.x;
+}
+
+template <bool kFP8>
+__device__ __forceinline__ int64_t encode_hit(const Params& p, uint32_t h, uint32_t K1, RowWriter<kFP8>& rw) {
+  return encode_rec<kFP8>(p, p.hits[h], h, K1, rw);
 }
 
 // Writes the shaded colour of hit h (ray `ray`); density-cube objects add
@@ -186,10 +192,25 @@ __global__ void __launch_bounds__(kEncThreads, 4) k_encode_tc(const __grid_const
   const uint32_t K1 = (uint32_t)p.tc_k1, chunks1 = K1 * ES / 16u, tile_gbytes = 128u * K1 * ES;
   const float inv_sx = kFP8 ? 1.0f / p.fp8_act_scale[0] : 1.0f;
   const uint32_t end = min(p.tc_h_end, *p.counter);  // launches past the last hit return at once
-  for (uint32_t h = p.tc_h_begin + blockIdx.x * kEncThreads + threadIdx.x; h < end; h += gridDim.x * kEncThreads) {
-    const uint32_t i = h - p.tc_h_begin;
-    RowWriter<kFP8> rw(p.tc_a + (size_t)(i >> 7) * tile_gbytes, i & 127u, chunks1, inv_sx);
-    encode_hit<kFP8>(p, h, K1, rw);
+  const uint32_t stride = gridDim.x * kEncThreads;
+  uint32_t h = p.tc_h_begin + blockIdx.x * kEncThreads + threadIdx.x;
+  if constexpr (kFP8) {
+    // the next hit's record is loaded while this one is encoded (measured
+    // faster for FP8; the BF16 kernel spills with it and is not)
+    uint2 rec = h < end ? p.hits[h] : make_uint2(0u, 0u);
+    for (; h < end; h += stride) {
+      const uint2 next = h + stride < end ? p.hits[h + stride] : make_uint2(0u, 0u);
+      const uint32_t i = h - p.tc_h_begin;
+      RowWriter<kFP8> rw(p.tc_a + (size_t)(i >> 7) * tile_gbytes, i & 127u, chunks1, inv_sx);
+      encode_rec<kFP8>(p, rec, h, K1, rw);
+      rec = next;
+    }
+  } else {
+    for (; h < end; h += stride) {
+      const uint32_t i = h - p.tc_h_begin;
+      RowWriter<kFP8> rw(p.tc_a + (size_t)(i >> 7) * tile_gbytes, i & 127u, chunks1, inv_sx);
+      encode_hit<kFP8>(p, h, K1, rw);
+    }
   }
 }
 
