@@ -54,6 +54,26 @@ def test_render_rejects_bad_arguments_before_any_launch(lib):
     assert lib.inolf_set_fault_injection(0) == inolf.OK
 
 
+def test_render_workspace_size_follows_the_documented_layout(lib, monkeypatch):
+    # header + 12 bytes per ray + operand tiles of 128 bytes per ray for at
+    # most 4 Mi rays (+ 256 bytes of alignment slack); INOLF_TC_CHUNK_ROWS
+    # sets the row count, read at every call
+    monkeypatch.delenv("INOLF_TC_CHUNK_ROWS", raising=False)
+    lib.inolf_render_workspace_bytes.restype = ctypes.c_size_t
+    lib.inolf_render_workspace_bytes.argtypes = [ctypes.c_int64]
+
+    def expect(n, rows=1 << 22):
+        n1 = max(n, 1)
+        return 256 + 12 * n1 + min((n1 + 255) // 256 * 256, rows) * 128 + 256
+
+    for n in (0, 1, 1000, 300_000, 8_294_400, 530_841_600):
+        assert lib.inolf_render_workspace_bytes(n) == expect(n), n
+    monkeypatch.setenv("INOLF_TC_CHUNK_ROWS", "300")
+    assert lib.inolf_render_workspace_bytes(100_000) == expect(100_000, 300)
+    monkeypatch.setenv("INOLF_TC_CHUNK_ROWS", "0")
+    assert lib.inolf_render_workspace_bytes(100_000) == 256 + 12 * 100_000 + 256
+
+
 def _cube_desc_scene():
     from paper_2303_04086_gb300 import synth
     return synth.tiny_density_scene(seed=0)
