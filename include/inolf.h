@@ -94,6 +94,9 @@ typedef struct {
   int64_t n;          /* number of hashed points */
   uint32_t* phi;      /* host, r^3 entries, offset (x, y, z) packed x | y << 10 | z << 20 */
   uint32_t* slot_of;  /* host, n entries: h(p_i) linearised x + m (y + m z) */
+  int32_t* coords;    /* host, n x 3: the hashed points in input order (a copy owned by the
+                         handle); inolf_object_create reads them to lay out each level's
+                         corner bundles */
 } inolf_hash;
 
 /* Host-only, pure.  Builds a collision-free hash of n distinct integer points
@@ -169,8 +172,15 @@ typedef struct inolf_object inolf_object;
 
 /* Copies the description into library-owned device memory on the current
  * device (BVH built on the host, feature rows scattered into slot order).
+ * Per level it also lays out the corner bundles the shade kernels read: for
+ * every hashed vertex c (from the hash's `coords`), bundle row h(c) holds the
+ * feature rows of the 8 corners of the cell whose lowest corner is c, so one
+ * hit point costs one Phi entry and one 64-byte read (32 bytes for FP16
+ * tables) per level, half a cache line (Sec. 4.1).  The bundles are rebuilt
+ * by inolf_object_load_params.
  * Synchronous with respect to `stream` (returns after the uploads finish).
- * Errors: INOLF_E_INVALID, INOLF_E_OOM, INOLF_E_CUDA. */
+ * Errors: INOLF_E_INVALID (also: a hash with points but no coords),
+ * INOLF_E_OOM, INOLF_E_CUDA. */
 inolf_status inolf_object_create(const inolf_object_desc* desc, void* stream, inolf_object** out);
 void inolf_object_destroy(inolf_object* obj);
 

@@ -437,31 +437,53 @@ __global__ void k_tables_to_fp16(const float2* __restrict__ src, __half2* __rest
     dst[i] = __floats2half2_rn(src[i].x, src[i].y);
 }
 
-// Unwrapped table: row X + S (Y + S Z) of the S = 2m sided copy holds the
-// canonical row (X mod m) + m ((Y mod m) + m (Z mod m)).
+// Eq. 1 for a vertex p of the level (each coordinate in [0, N]): the slot
+// ((p mod m) + Phi[p mod r]) mod m per axis, linearised x + m (y + m z).
+__device__ __forceinline__ uint32_t psh_slot_of(const inolf::LevelDev& lv, uint32_t px, uint32_t py, uint32_t pz) {
+  const uint32_t m = (uint32_t)lv.m, r = (uint32_t)lv.r;
+  const uint32_t e = lv.phi[(px % r) + r * ((py % r) + r * (pz % r))];
+  uint32_t sx = px % m + (e & 1023u), sy = py % m + ((e >> 10) & 1023u), sz = pz % m + (e >> 20);
+  sx = sx >= m ? sx - m : sx;
+  sy = sy >= m ? sy - m : sy;
+  sz = sz >= m ? sz - m : sz;
+  return sx + m * (sy + m * sz);
+}
+
+// Corner bundles of one level: for every hashed vertex c (packed x | y << 21
+// | z << 42) whose coordinates are all below N, bundle row h(c) receives the
+// rows T[h(c + d)] of the 8 corners d of the cell above c (x fastest).
 template <class Row>
-__global__ void k_expand_table(const Row* __restrict__ src, Row* __restrict__ dst, uint32_t m, uint32_t S,
-                               uint64_t n) {
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t X = (uint32_t)(i % S), Y = (uint32_t)((i / S) % S), Z = (uint32_t)(i / ((uint64_t)S * S));
-    const uint32_t x = X >= m ? X - m : X, y = Y >= m ? Y - m : Y, z = Z >= m ? Z - m : Z;
-    dst[i] = src[x + (uint64_t)m * (y + (uint64_t)m * z)];
+__global__ void k_build_bundles(const uint64_t* __restrict__ pts, int64_t n, const inolf::LevelDev lv,
+                                Row* __restrict__ bundle) {
+  const Row* table = reinterpret_cast<const Row*>(lv.table);
+  const uint32_t N = (uint32_t)lv.N;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t pk = pts[i];
+    const uint32_t cx = (uint32_t)(pk & 0x1FFFFFu), cy = (uint32_t)((pk >> 21) & 0x1FFFFFu),
+                   cz = (uint32_t)((pk >> 42) & 0x1FFFFFu);
+    if (cx >= N || cy >= N || cz >= N) continue;  // no cell has c as its lowest corner
+    Row* out = bundle + 8 * (size_t)psh_slot_of(lv, cx, cy, cz);
+#pragma unroll
+    for (int cc = 0; cc < 8; ++cc)
+      out[cc] = table[psh_slot_of(lv, cx + (cc & 1), cy + ((cc >> 1) & 1), cz + (cc >> 2))];
   }
 }
 
 namespace inolf {
-inolf_status expand_level_table(Object& o, int l, void* stream) {
+inolf_status build_level_bundles(Object& o, int l, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   const LevelDev& lv = o.lv[l];
-  const uint64_t n = (uint64_t)lv.S * lv.S * lv.S;
-  if (o.fp16)
-    k_expand_table<__half2><<<1024, 256, 0, st>>>((const __half2*)lv.table, (__half2*)lv.tablex, (uint32_t)lv.m,
-                                                  (uint32_t)lv.S, n);
-  else
-    k_expand_table<float2><<<1024, 256, 0, st>>>((const float2*)lv.table, (float2*)lv.tablex, (uint32_t)lv.m,
-                                                 (uint32_t)lv.S, n);
+  const size_t rows = (size_t)lv.m * lv.m * lv.m * 8;
+  if (cudaMemsetAsync(const_cast<void*>(lv.bundle), 0, rows * (o.fp16 ? 4 : 8), st) != cudaSuccess)
+    return fail(INOLF_E_CUDA, "corner bundles: cudaMemsetAsync failed");
+  if (o.n_pts[l] > 0) {
+    if (o.fp16)
+      k_build_bundles<__half2><<<1024, 256, 0, st>>>(o.pts[l], o.n_pts[l], lv, (__half2*)lv.bundle);
+    else
+      k_build_bundles<float2><<<1024, 256, 0, st>>>(o.pts[l], o.n_pts[l], lv, (float2*)lv.bundle);
+  }
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return fail(INOLF_E_CUDA, std::string("k_expand_table: ") + cudaGetErrorString(e));
+  if (e != cudaSuccess) return fail(INOLF_E_CUDA, std::string("k_build_bundles: ") + cudaGetErrorString(e));
   return INOLF_OK;
 }
 }  // namespace inolf
@@ -485,7 +507,7 @@ extern "C" inolf_status inolf_object_load_params(inolf_object* obj, const float*
                  cudaSuccess) {
         return fail(INOLF_E_CUDA, "load_params: table copy failed");
       }
-      inolf_status es = inolf::expand_level_table(o, l, stream);
+      inolf_status es = inolf::build_level_bundles(o, l, stream);
       if (es != INOLF_OK) return es;
     }
   }

@@ -229,9 +229,11 @@ extern "C" inolf_status inolf_build_hash(const int32_t* coords, int64_t n, int32
       h->m = (int32_t)m; h->r = (int32_t)r; h->n = n;
       h->phi = (uint32_t*)std::malloc(sizeof(uint32_t) * res.phi.size());
       h->slot_of = (uint32_t*)std::malloc(sizeof(uint32_t) * (n > 0 ? n : 1));
-      if (!h->phi || !h->slot_of) { inolf_hash_free(h); return fail(INOLF_E_OOM, "inolf_build_hash: oom"); }
+      h->coords = (int32_t*)std::malloc(sizeof(int32_t) * 3 * (n > 0 ? n : 1));
+      if (!h->phi || !h->slot_of || !h->coords) { inolf_hash_free(h); return fail(INOLF_E_OOM, "inolf_build_hash: oom"); }
       std::memcpy(h->phi, res.phi.data(), sizeof(uint32_t) * res.phi.size());
       if (n) std::memcpy(h->slot_of, res.slot_of.data(), sizeof(uint32_t) * n);
+      if (n) std::memcpy(h->coords, coords, sizeof(int32_t) * 3 * n);
       *out = h;
       return INOLF_OK;
     }
@@ -246,6 +248,7 @@ extern "C" void inolf_hash_free(inolf_hash* h) {
   if (!h) return;
   std::free(h->phi);
   std::free(h->slot_of);
+  std::free(h->coords);
   std::free(h);
 }
 
@@ -433,7 +436,7 @@ static void destroy_object(Object& o) {
   f(o.nodes); f(o.tris); f(o.w_f32); f(o.w_bf16); f(o.w_fp8); f(o.w_scale_dev);
   f((void*)o.cub.grid); f((void*)o.cub.dens); f((void*)o.cub.diff); f((void*)o.cub.fdist); f((void*)o.cub.bdist);
   for (int l = 0; l < o.L; ++l) {
-    f((void*)o.lv[l].phi); f((void*)o.lv[l].table); f((void*)o.lv[l].phix); f((void*)o.lv[l].tablex);
+    f((void*)o.lv[l].phi); f((void*)o.lv[l].table); f((void*)o.lv[l].bundle); f((void*)o.pts[l]);
   }
   o = Object();
 }
@@ -628,10 +631,13 @@ extern "C" inolf_status inolf_object_create(const inolf_object_desc* desc, void*
     if (h->r >= 2048)
       return fail(INOLF_E_UNSUPPORTED, "inolf_object_create: offset-table side r = " + std::to_string(h->r) +
                                            " of level " + std::to_string(l) + " exceeds 2047");
-    if (h->m > kMaxUnwrappedM)
-      return fail(INOLF_E_UNSUPPORTED, "inolf_object_create: hash-table side m = " + std::to_string(h->m) +
-                                           " of level " + std::to_string(l) + " exceeds " +
-                                           std::to_string(kMaxUnwrappedM) + " (unwrapped tables are 2m per side)");
+    if (h->n > 0 && !h->coords)
+      return fail(INOLF_E_INVALID, "inolf_object_create: the hash of level " + std::to_string(l) +
+                                       " carries no coords (the corner bundles need the hashed points)");
+    for (int64_t i = 0; i < 3 * h->n; ++i)
+      if (h->coords[i] < 0 || h->coords[i] > D.resolution[l])
+        return fail(INOLF_E_INVALID, "inolf_object_create: a hashed point of level " + std::to_string(l) +
+                                         " lies outside [0, N]");
   }
   inolf_object* obj = new (std::nothrow) inolf_object();
   if (!obj) return fail(INOLF_E_OOM, "inolf_object_create: oom");
@@ -748,9 +754,13 @@ extern "C" inolf_status inolf_object_create(const inolf_object_desc* desc, void*
     const int64_t R3 = (int64_t)h->r * h->r * h->r;
     const int64_t M3 = (int64_t)h->m * h->m * h->m;
     o.rows[l] = M3;
+    // Phi padded with zeros to a multiple of 16 bytes, so that one bulk copy
+    // of the whole table (a multiple of 16 bytes) stays inside the allocation
+    const int64_t R3p = (R3 + 3) / 4 * 4;
     void* dphi = nullptr;
-    CUDA_TRY(cudaMalloc(&dphi, sizeof(uint32_t) * R3));
+    CUDA_TRY(cudaMalloc(&dphi, sizeof(uint32_t) * R3p));
     lv.phi = (const uint32_t*)dphi;
+    CUDA_TRY(cudaMemsetAsync(dphi, 0, sizeof(uint32_t) * R3p, st));
     CUDA_TRY(cudaMemcpyAsync(dphi, h->phi, sizeof(uint32_t) * R3, cudaMemcpyHostToDevice, st));
     const size_t row_bytes = o.fp16 ? 4 : 8;
     std::vector<uint8_t> table((size_t)M3 * row_bytes, 0);
@@ -769,34 +779,23 @@ extern "C" inolf_status inolf_object_create(const inolf_object_desc* desc, void*
     CUDA_TRY(cudaMalloc(&dt, table.size()));
     lv.table = dt;
     CUDA_TRY(cudaMemcpyAsync(dt, table.data(), table.size(), cudaMemcpyHostToDevice, st));
-    o.bytes += sizeof(uint32_t) * R3 + table.size();
-    // unwrapped copies for the shade kernels: Phi of side r + 1 with offsets
-    // linearised in the 2m-sided table, and the table itself expanded on the device
-    lv.S = 2 * lv.m;
-    lv.R = lv.r + 1;
+    o.bytes += sizeof(uint32_t) * R3p + table.size();
+    // the hashed points (packed x | y << 21 | z << 42) and the corner bundles
+    // built from them on the device
     {
-      const int64_t R = lv.R, r = lv.r, S = lv.S;
-      std::vector<uint32_t> px((size_t)(R * R * R));
-      for (int64_t c = 0; c < R; ++c)
-        for (int64_t b2 = 0; b2 < R; ++b2)
-          for (int64_t a = 0; a < R; ++a) {
-            const uint32_t e = h->phi[(a % r) + r * ((b2 % r) + r * (c % r))];
-            const uint32_t fx = e & 1023u, fy = (e >> 10) & 1023u, fz = e >> 20;
-            px[(size_t)(a + R * (b2 + R * c))] = (uint32_t)(fx + S * (fy + S * (int64_t)fz));
-          }
-      // padded with zeros to a multiple of 16 bytes, so that one bulk copy of
-      // the whole table (a multiple of 16 bytes) stays inside the allocation
-      px.resize((px.size() + 3) / 4 * 4, 0u);
-      void* dpx = nullptr;
-      CUDA_TRY(cudaMalloc(&dpx, px.size() * sizeof(uint32_t)));
-      lv.phix = (const uint32_t*)dpx;
-      CUDA_TRY(cudaMemcpyAsync(dpx, px.data(), px.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
-      const size_t xbytes = (size_t)S * S * S * row_bytes;
-      void* dtx = nullptr;
-      CUDA_TRY(cudaMalloc(&dtx, xbytes));
-      lv.tablex = dtx;
-      o.bytes += px.size() * sizeof(uint32_t) + xbytes;
-      inolf_status es = expand_level_table(o, l, stream);
+      std::vector<uint64_t> pk((size_t)std::max<int64_t>(h->n, 1), 0);
+      for (int64_t i = 0; i < h->n; ++i)
+        pk[(size_t)i] = (uint64_t)(uint32_t)h->coords[3 * i] | ((uint64_t)(uint32_t)h->coords[3 * i + 1] << 21) |
+                        ((uint64_t)(uint32_t)h->coords[3 * i + 2] << 42);
+      CUDA_TRY(cudaMalloc(&o.pts[l], pk.size() * sizeof(uint64_t)));
+      o.n_pts[l] = h->n;
+      CUDA_TRY(cudaMemcpyAsync(o.pts[l], pk.data(), pk.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+      const size_t bbytes = (size_t)M3 * 8 * row_bytes;
+      void* db = nullptr;
+      CUDA_TRY(cudaMalloc(&db, bbytes));
+      lv.bundle = db;
+      o.bytes += pk.size() * sizeof(uint64_t) + bbytes;
+      inolf_status es = build_level_bundles(o, l, stream);
       if (es != INOLF_OK) { destroy_object(o); delete obj; return es; }
       CUDA_TRY(cudaStreamSynchronize(st));
     }

@@ -41,19 +41,15 @@ struct LevelDev {
   uint32_t magic_r;       // the same for r
   const uint32_t* phi;    // r^3 packed offsets
   const void* table;      // m^3 rows of F=2 features: float2 (FP32) or __half2 (FP16)
-  // Unwrapped copies used by the shade kernels: the table repeated to side
-  // S = 2m (row X + S (Y + S Z) holds slot (X mod m, Y mod m, Z mod m)) and
-  // Phi repeated to side R = r + 1 with each offset stored linearised in the
-  // S-sided table, so corner c + d of a cell reads Phi at h1(c) + d and its
-  // features at h0(c) + d + phi without any wrap-around.
-  const uint32_t* phix;   // R^3 linear offsets phi_x + S (phi_y + S phi_z)
-  const void* tablex;     // S^3 rows, same row type as `table`
-  int32_t S, R;
+  // Corner bundles read by the shade kernels (Sec. 4.1: one memory request
+  // per sample point, half a cache line): row s = h(c) of the vertex c holds
+  // the feature rows T[h(c + d)] of the 8 corners d in {0,1}^3 (x fastest) of
+  // the cell whose lowest corner is c -- 64 bytes (FP32) or 32 bytes (FP16);
+  // rows of empty slots, and of vertices with a coordinate equal to N (no
+  // cell above them), are zero.  Derived from `table` (rebuilt whenever the
+  // table changes).
+  const void* bundle;     // m^3 rows of 8 x (float2 or __half2)
 };
-
-// Largest hash-table side the unwrapped layout supports: (2m)^3 rows must be
-// indexable with 32 bits.
-static constexpr int32_t kMaxUnwrappedM = 812;
 
 // Density and diffuse texture cubes as the kernels see them (Sec. 4.2).
 // grid[x + b (y + b z)] of a base cell is its cube's index, or -1 when no
@@ -85,6 +81,10 @@ struct Object {
   float bsphere[4] = {0, 0, 0, 0};  // proxy bounding sphere (centre, padded radius), object frame
   LevelDev lv[INOLF_MAX_LEVELS] = {};
   int64_t rows[INOLF_MAX_LEVELS] = {};
+  // the hashed vertices of each level, packed x | y << 21 | z << 42 (device),
+  // kept to rebuild the corner bundles when the tables change
+  uint64_t* pts[INOLF_MAX_LEVELS] = {};
+  int64_t n_pts[INOLF_MAX_LEVELS] = {};
   // BVH: nodes are 4 x float4 (child boxes x, y, z + child refs), triangles
   // 3 x float4 (v0 + id bits, e1, e2)
   void* nodes = nullptr;
@@ -153,8 +153,9 @@ inolf_status prepare_tc_weights(Object& obj, const float* w1, const float* w2, c
 inolf_status pack_weights_device(Object& obj, const float* w1, const float* w2, const float* w3, void* stream);
 inolf_status upload_weights(Object& obj, const float* w1, const float* w2, const float* w3, void* stream);
 
-// Fills level l's unwrapped table from its canonical table (backward.cu).
-inolf_status expand_level_table(Object& o, int l, void* stream);
+// Lays out level l's corner bundles from its table and hashed points
+// (backward.cu).
+inolf_status build_level_bundles(Object& o, int l, void* stream);
 
 // Backward over explicit rays (render.cu + backward.cu).
 inolf_status launch_backward_rays(const Object& obj, const float* o, const float* d, int64_t n, const float* d_rgba,

@@ -618,69 +618,69 @@ __device__ __forceinline__ void finish_level(const LevelDev& lv, int fp16, const
   e1 = fmaf(f[2], by1 - by0, by0);
 }
 
-// The same two halves of Eq. 1 on the unwrapped copies (see LevelDev): the
-// corner c + d of the cell reads Phi at h1(c) + d (no wrap, Phi is repeated to
-// side r + 1) and its features at h0(c) + d + phi in the table repeated to
-// side 2m, where phi is stored linearised -- one add per corner between the
-// two dependent loads.  The features are those of the canonical slots.
-struct LevelFetchX {
-  uint32_t ph[8];
-  uint32_t base;  // h0(c) linearised in the 2m-sided table
+// The same level fetch on the corner bundles (see LevelDev): Eq. 1 gives
+// the slot h(c) of the cell's lowest corner c, and bundle row h(c) holds the
+// feature rows of all 8 corners, so a level costs one Phi load and one
+// 64-byte (FP32) or 32-byte (FP16) read -- half a 128-byte cache line -- in
+// place of 8 Phi loads and 8 scattered row loads.  The rows are those of the
+// canonical slots h(c + d), so the result equals finish_level's.
+struct LevelFetchB {
+  uint32_t ph;     // packed Phi entry of h1(c) (in flight)
+  uint32_t h0[3];  // h0(c) per axis
   float f[3];
 };
 
-// Cell, fractions, h0 and the offset-table index q of corner 0 of x's cell.
-__device__ __forceinline__ uint32_t phi_index_x(const LevelDev& lv, const float x[3], LevelFetchX& s) {
+// Cell, fractions, h0(c) and the load of Phi[h1(c)] (Eq. 1, first half);
+// `phi` is lv.phi or a copy of it staged in shared memory.
+__device__ __forceinline__ void fetch_bundle_phi_from(const LevelDev& lv, const uint32_t* phi, const float x[3],
+                                                      LevelFetchB& s) {
   int32_t c[3];
   cell_of(lv, x, c, s.f);
-  const uint32_t S = (uint32_t)lv.S, R = (uint32_t)lv.R;
-  s.base = (uint32_t)mod_small(c[0], lv.m, lv.magic_m) +
-           S * ((uint32_t)mod_small(c[1], lv.m, lv.magic_m) + S * (uint32_t)mod_small(c[2], lv.m, lv.magic_m));
-  return (uint32_t)mod_small(c[0], lv.r, lv.magic_r) +
-         R * ((uint32_t)mod_small(c[1], lv.r, lv.magic_r) + R * (uint32_t)mod_small(c[2], lv.r, lv.magic_r));
+  const uint32_t r = (uint32_t)lv.r;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) s.h0[k] = (uint32_t)mod_small(c[k], lv.m, lv.magic_m);
+  const uint32_t q = (uint32_t)mod_small(c[0], lv.r, lv.magic_r) +
+                     r * ((uint32_t)mod_small(c[1], lv.r, lv.magic_r) + r * (uint32_t)mod_small(c[2], lv.r, lv.magic_r));
+  s.ph = phi[q];
 }
 
-__device__ __forceinline__ void fetch_phi_x(const LevelDev& lv, const float x[3], LevelFetchX& s) {
-  const uint32_t R = (uint32_t)lv.R, R2 = R * R;
-  const uint32_t* ph = lv.phix + phi_index_x(lv, x, s);
-  s.ph[0] = __ldg(ph);
-  s.ph[1] = __ldg(ph + 1);
-  s.ph[2] = __ldg(ph + R);
-  s.ph[3] = __ldg(ph + R + 1);
-  s.ph[4] = __ldg(ph + R2);
-  s.ph[5] = __ldg(ph + R2 + 1);
-  s.ph[6] = __ldg(ph + R2 + R);
-  s.ph[7] = __ldg(ph + R2 + R + 1);
+__device__ __forceinline__ void fetch_bundle_phi(const LevelDev& lv, const float x[3], LevelFetchB& s) {
+  int32_t c[3];
+  cell_of(lv, x, c, s.f);
+  const uint32_t r = (uint32_t)lv.r;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) s.h0[k] = (uint32_t)mod_small(c[k], lv.m, lv.magic_m);
+  const uint32_t q = (uint32_t)mod_small(c[0], lv.r, lv.magic_r) +
+                     r * ((uint32_t)mod_small(c[1], lv.r, lv.magic_r) + r * (uint32_t)mod_small(c[2], lv.r, lv.magic_r));
+  s.ph = __ldg(lv.phi + q);
 }
 
-// The same fetch from `phx`, a copy of lv.phix staged in shared memory.
-__device__ __forceinline__ void fetch_phi_x_from(const LevelDev& lv, const uint32_t* phx, const float x[3],
-                                                 LevelFetchX& s) {
-  const uint32_t R = (uint32_t)lv.R, R2 = R * R;
-  const uint32_t* ph = phx + phi_index_x(lv, x, s);
-  s.ph[0] = ph[0];
-  s.ph[1] = ph[1];
-  s.ph[2] = ph[R];
-  s.ph[3] = ph[R + 1];
-  s.ph[4] = ph[R2];
-  s.ph[5] = ph[R2 + 1];
-  s.ph[6] = ph[R2 + R];
-  s.ph[7] = ph[R2 + R + 1];
-}
-
-__device__ __forceinline__ void finish_level_x(const LevelDev& lv, int fp16, const LevelFetchX& s, float& e0,
-                                               float& e1) {
-  const uint32_t S = (uint32_t)lv.S, S2 = S * S;
-  const uint32_t off[8] = {0u, 1u, S, S + 1u, S2, S2 + 1u, S2 + S, S2 + S + 1u};
+// Second half of Eq. 1 for the lowest corner, the bundle read and the
+// trilinear interpolation (the same operations, in the same order, as
+// finish_level).
+__device__ __forceinline__ void finish_bundle(const LevelDev& lv, int fp16, const LevelFetchB& s, float& e0,
+                                              float& e1) {
+  const uint32_t um = (uint32_t)lv.m;
+  uint32_t sx = s.h0[0] + (s.ph & 1023u), sy = s.h0[1] + ((s.ph >> 10) & 1023u), sz = s.h0[2] + (s.ph >> 20);
+  sx = min(sx, sx - um);  // (h0 + phi) mod m, as in finish_level
+  sy = min(sy, sy - um);
+  sz = min(sz, sz - um);
+  const size_t slot = (size_t)(sx + um * (sy + um * sz));
   float2 v[8];
   if (fp16) {
-    const __half2* tb = reinterpret_cast<const __half2*>(lv.tablex) + s.base;
+    const uint4* b = reinterpret_cast<const uint4*>(lv.bundle) + 2 * slot;
+    const uint4 u0 = __ldg(b), u1 = __ldg(b + 1);
+    const uint32_t w[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
 #pragma unroll
-    for (int cc = 0; cc < 8; ++cc) v[cc] = __half22float2(__ldg(tb + (off[cc] + s.ph[cc])));
+    for (int cc = 0; cc < 8; ++cc) v[cc] = __half22float2(*reinterpret_cast<const __half2*>(&w[cc]));
   } else {
-    const float2* tb = reinterpret_cast<const float2*>(lv.tablex) + s.base;
+    const float4* b = reinterpret_cast<const float4*>(lv.bundle) + 4 * slot;
 #pragma unroll
-    for (int cc = 0; cc < 8; ++cc) v[cc] = __ldg(tb + (off[cc] + s.ph[cc]));
+    for (int k = 0; k < 4; ++k) {
+      const float4 u = __ldg(b + k);
+      v[2 * k] = make_float2(u.x, u.y);
+      v[2 * k + 1] = make_float2(u.z, u.w);
+    }
   }
   const float* f = s.f;
   float ax[4], bx[4];

@@ -54,19 +54,19 @@ __device__ __forceinline__ int64_t encode_rec(const Params& p, uint2 rec, uint32
   float o[3], d[3], x[3];
   ray_of(p, rec.x, o, d);
   hit_unit_coords(p, o, d, __uint_as_float(rec.y), x);
-  // levels in pairs: Phi loads of the next level in flight, no state copies
-  LevelFetchX fa, fb;
-  fetch_phi_x(p.lv[0], x, fa);
+  // levels in pairs: the Phi load of the next level in flight, no state copies
+  LevelFetchB fa, fb;
+  fetch_bundle_phi(p.lv[0], x, fa);
   for (int l = 0; l < p.L; l += 2) {
     float e0, e1, g0, g1;
-    if (l + 1 < p.L) fetch_phi_x(p.lv[l + 1], x, fb);
-    finish_level_x(p.lv[l], p.fp16, fa, e0, e1);
+    if (l + 1 < p.L) fetch_bundle_phi(p.lv[l + 1], x, fb);
+    finish_bundle(p.lv[l], p.fp16, fa, e0, e1);
     if (l + 1 >= p.L) {
       rw.push(e0, e1);
       break;
     }
-    if (l + 2 < p.L) fetch_phi_x(p.lv[l + 2], x, fa);
-    finish_level_x(p.lv[l + 1], p.fp16, fb, g0, g1);
+    if (l + 2 < p.L) fetch_bundle_phi(p.lv[l + 2], x, fa);
+    finish_bundle(p.lv[l + 1], p.fp16, fb, g0, g1);
     rw.push2(e0, e1, g0, g1);  // levels l, l + 1: columns 4 (l / 2) .. + 3
   }
   float sh[16];

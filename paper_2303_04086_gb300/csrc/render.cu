@@ -363,8 +363,8 @@ __device__ __forceinline__ void block_gemm_4x8(const float* __restrict__ act, co
 }
 
 // Input tile of one hit ray, written by its two gather threads (half 0 and
-// 1): features of levels half, half + 2, ... (each with the next level's Phi
-// loads in flight), the SH encoding and alpha_c (half 1), the diffuse colour
+// 1): features of levels half, half + 2, ... from the corner bundles (each
+// with the next level's Phi entry in flight), the SH encoding and alpha_c (half 1), the diffuse colour
 // and tint of the variant (half 0), all into the [k][kF32Tile] FP32 tile;
 // invalid slots are zero.  Returns the ray index of the hit record.
 // kStaged: the offset tables of levels 0 .. p.phis_levels - 1 are read from
@@ -381,23 +381,23 @@ __device__ __forceinline__ int64_t gather_tile_f32(const Params& p, uint32_t h, 
   float o[3], d[3], x[3];
   ray_of(p, ray, o, d);
   hit_unit_coords(p, o, d, __uint_as_float(rec.y), x);
-  auto fetch = [&](int l, LevelFetchX& f) {
+  auto fetch = [&](int l, LevelFetchB& f) {
     if (kStaged && l < p.phis_levels)
-      fetch_phi_x_from(p.lv[l], sphi + p.phis_off[l], x, f);
+      fetch_bundle_phi_from(p.lv[l], sphi + p.phis_off[l], x, f);
     else
-      fetch_phi_x(p.lv[l], x, f);
+      fetch_bundle_phi(p.lv[l], x, f);
   };
-  LevelFetchX fa, fb;
+  LevelFetchB fa, fb;
   if (half < p.L) fetch(half, fa);
   for (int l = half; l < p.L; l += 4) {  // levels half, half + 2, ... in pairs, no state copies
     float e0, e1;
     if (l + 2 < p.L) fetch(l + 2, fb);
-    finish_level_x(p.lv[l], p.fp16, fa, e0, e1);
+    finish_bundle(p.lv[l], p.fp16, fa, e0, e1);
     act[(2 * l) * kF32Tile + ray_slot] = e0;
     act[(2 * l + 1) * kF32Tile + ray_slot] = e1;
     if (l + 2 >= p.L) break;
     if (l + 4 < p.L) fetch(l + 4, fa);
-    finish_level_x(p.lv[l + 2], p.fp16, fb, e0, e1);
+    finish_bundle(p.lv[l + 2], p.fp16, fb, e0, e1);
     act[(2 * (l + 2)) * kF32Tile + ray_slot] = e0;
     act[(2 * (l + 2) + 1) * kF32Tile + ray_slot] = e1;
   }
@@ -597,7 +597,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_shade_f32_ws(const __grid_con
     tc::mbar_arrive_expect_tx(staged, wbytes + p.phis_off[p.phis_levels] * 4u);
     tc::bulk_g2s(ring, p.w_f32, wbytes, staged);
     for (int l = 0; l < p.phis_levels; ++l)
-      tc::bulk_g2s(const_cast<uint32_t*>(sphi) + p.phis_off[l], p.lv[l].phix,
+      tc::bulk_g2s(const_cast<uint32_t*>(sphi) + p.phis_off[l], p.lv[l].phi,
                    (p.phis_off[l + 1] - p.phis_off[l]) * 4u, staged);
   }
   __syncthreads();  // barrier initialised before anyone polls it
@@ -905,13 +905,13 @@ inolf_status launch_render(const Object& obj, const RayBatch& rays, inolf_precis
   });
 
   const bool ws_ok = ws_ok_dev[dev];
-  // The unwrapped offset tables of the coarsest levels go to shared memory
+  // The offset tables of the coarsest levels go to shared memory
   // while they fit beside the tiles (each padded to 16 bytes, as allocated).
   size_t smem_ws = ws_smem_bytes(obj.d_in);
   p.phis_levels = 0;
   p.phis_off[0] = 0;
   for (int l = 0; l < obj.L && ws_ok; ++l) {
-    const size_t R = (size_t)obj.lv[l].R, words = (R * R * R + 3) / 4 * 4;
+    const size_t r = (size_t)obj.lv[l].r, words = (r * r * r + 3) / 4 * 4;  // as allocated
     if (smem_ws + (p.phis_off[l] + words) * 4 > std::min(ws_smem_max_dev[dev], kWsPhiSmemLimit)) break;
     p.phis_off[l + 1] = p.phis_off[l] + (uint32_t)words;
     p.phis_levels = l + 1;

@@ -502,14 +502,14 @@ __global__ void __launch_bounds__(kServeThreads, 2) k_serve(const __grid_constan
           hit_unit_coords_ls(ob.lo, ob.scale, ol, d, ht[q], x3);
           float x[kCubes ? kServeMaxDin : kServeMaxDin - 1];
           {
-            LevelFetchX fa, fb;
-            fetch_phi_x(ob.lv[0], x3, fa);
-            for (int l = 0; l < ob.L; l += 2) {  // levels in pairs, the next level's Phi loads in flight
-              if (l + 1 < ob.L) fetch_phi_x(ob.lv[l + 1], x3, fb);
-              finish_level_x(ob.lv[l], ob.fp16, fa, x[2 * l], x[2 * l + 1]);
+            LevelFetchB fa, fb;
+            fetch_bundle_phi(ob.lv[0], x3, fa);
+            for (int l = 0; l < ob.L; l += 2) {  // levels in pairs, the next level's Phi entry in flight
+              if (l + 1 < ob.L) fetch_bundle_phi(ob.lv[l + 1], x3, fb);
+              finish_bundle(ob.lv[l], ob.fp16, fa, x[2 * l], x[2 * l + 1]);
               if (l + 1 >= ob.L) break;
-              if (l + 2 < ob.L) fetch_phi_x(ob.lv[l + 2], x3, fa);
-              finish_level_x(ob.lv[l + 1], ob.fp16, fb, x[2 * l + 2], x[2 * l + 3]);
+              if (l + 2 < ob.L) fetch_bundle_phi(ob.lv[l + 2], x3, fa);
+              finish_bundle(ob.lv[l + 1], ob.fp16, fb, x[2 * l + 2], x[2 * l + 3]);
             }
           }
           sh16c(kp.shc, d, x + 2 * ob.L);
@@ -559,16 +559,16 @@ __global__ void __launch_bounds__(kServeThreads, 2) k_serve(const __grid_constan
             for (int a = 0; a < 3; ++a) ol[a] = __fsub_rn(po[a], ob.T[a]);
             hit_unit_coords_ls(ob.lo, ob.scale, ol, pd, th, x3);
             {
-              LevelFetchX fa, fb;
-              fetch_phi_x(ob.lv[0], x3, fa);
-              for (int l = 0; l < ob.L; l += 2) {  // levels in pairs, the next level's Phi loads in flight
+              LevelFetchB fa, fb;
+              fetch_bundle_phi(ob.lv[0], x3, fa);
+              for (int l = 0; l < ob.L; l += 2) {  // levels in pairs, the next level's Phi entry in flight
                 float e0, e1;
-                if (l + 1 < ob.L) fetch_phi_x(ob.lv[l + 1], x3, fb);
-                finish_level_x(ob.lv[l], ob.fp16, fa, e0, e1);
+                if (l + 1 < ob.L) fetch_bundle_phi(ob.lv[l + 1], x3, fb);
+                finish_bundle(ob.lv[l], ob.fp16, fa, e0, e1);
                 store_pair<false>(A, row, 2u * l, chunks1, e0, e1, 1.f);
                 if (l + 1 >= ob.L) break;
-                if (l + 2 < ob.L) fetch_phi_x(ob.lv[l + 2], x3, fa);
-                finish_level_x(ob.lv[l + 1], ob.fp16, fb, e0, e1);
+                if (l + 2 < ob.L) fetch_bundle_phi(ob.lv[l + 2], x3, fa);
+                finish_bundle(ob.lv[l + 1], ob.fp16, fb, e0, e1);
                 store_pair<false>(A, row, 2u * (l + 1), chunks1, e0, e1, 1.f);
               }
             }

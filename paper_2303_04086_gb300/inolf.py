@@ -43,7 +43,8 @@ class HashParams(ctypes.Structure):
 
 class HashStruct(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int32), ("r", ctypes.c_int32), ("n", ctypes.c_int64),
-                ("phi", ctypes.POINTER(ctypes.c_uint32)), ("slot_of", ctypes.POINTER(ctypes.c_uint32))]
+                ("phi", ctypes.POINTER(ctypes.c_uint32)), ("slot_of", ctypes.POINTER(ctypes.c_uint32)),
+                ("coords", ctypes.POINTER(ctypes.c_int32))]
 
 
 class CubesDesc(ctypes.Structure):

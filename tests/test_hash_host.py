@@ -39,6 +39,15 @@ def test_hash_tiny_scene_levels(tiny, level):
     assert np.array_equal(table[oracle.psh_slots(h.phi, h.m, h.r, c)], tiny.features[level])
 
 
+def test_hash_carries_its_points(tiny):
+    # object creation lays out the corner bundles from the points the hash
+    # keeps: they must be the input points, in input order
+    c = synth.unpack_keys(tiny.keys[1])
+    h = inolf.build_hash(c, tiny.resolutions[1])
+    got = np.ctypeslib.as_array(h._h.contents.coords, shape=(h.n * 3,)).reshape(-1, 3)
+    assert np.array_equal(got, c.astype(np.int32))
+
+
 def test_hash_is_deterministic(tiny):
     c = synth.unpack_keys(tiny.keys[2])
     a = inolf.build_hash(c, tiny.resolutions[2])
