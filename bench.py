@@ -213,9 +213,12 @@ def algorithmic_bytes_per_hit(scene) -> int:
 
 
 def kernel_stats() -> dict:
-    """The library's per-kernel launch statistics, with the split tensor-core
-    shade (k_encode_tc_* gathers and encodes, k_mlp_tc_* runs the MLP) also
-    summed under k_shade_tc_*, the name of the fused kernel it replaces."""
+    """The library's per-kernel launch statistics, with the split BF16 / FP8
+    tensor-core shade (k_encode_tc_* gathers and encodes, k_mlp_tc_* runs the
+    MLP) also summed under k_shade_tc_*, the name of the fused kernel it
+    replaces.  The FP32 split shade (k_encode_tc_f32, k_mlp_tc_f32) stays as
+    two entries: the roofline line takes the dominant kernel of the FP32
+    step, so each must stand on its own."""
     from paper_2303_04086_gb300 import inolf
     st = inolf.stats_read()
     for prec in ("bf16", "fp8"):
@@ -234,6 +237,26 @@ def mlp_flops_per_hit(scene) -> int:
     return 2 * (64 * scene.d_in + 64 * 64 + 4 * 64)
 
 
+def tf32_k1(scene) -> int:
+    return (scene.d_in + 7) // 8 * 8
+
+
+def tf32_row_bytes(scene) -> int:
+    # one FP32 layer-1 operand row of the split shade
+    return 4 * tf32_k1(scene)
+
+
+def tf32x3_flops_per_hit(scene) -> int:
+    # tensor-core flops the split-TF32 MLP issues per hit: three products per
+    # layer, layer 1 padded to K1 columns, layer 3 to 16 outputs
+    return 3 * 2 * (64 * tf32_k1(scene) + 64 * 64 + 16 * 64)
+
+
+def encode_bytes_per_hit(scene) -> int:
+    # the gather's algorithmic bytes, the hit record read, the operand row written
+    return algorithmic_bytes_per_hit(scene) + 8 + tf32_row_bytes(scene)
+
+
 def kernel_rooflines(kernels, scene, n_rays, n_hit, steps, peaks):
     """Every kernel of a timed run against its roofline: the shade kernels'
     algorithmic gather + output bytes against the measured HBM copy bandwidth
@@ -250,7 +273,23 @@ def kernel_rooflines(kernels, scene, n_rays, n_hit, steps, peaks):
             continue
         sec = st["ms"] / 1e3
         per_step_launches = max(1, st["launches"] // max(1, steps))
-        if name.startswith("k_shade"):
+        if name == "k_encode_tc_f32":
+            byt = encode_bytes_per_hit(scene) * n_hit * steps
+            out[name] = {"gbs": byt / sec / 1e9, "frac_hbm": byt / sec / 1e9 / hbm,
+                         "frac_hbm_basis": "algorithmic gather bytes (every corner row and Phi entry) + the hit "
+                                           "record read + the FP32 operand row written, per second over the HBM "
+                                           "copy rate; L1 and L2 serve most of the gather, so it can exceed 1",
+                         "bound": "latency (dependent L1/L2 gather loads)", "launches_per_step": per_step_launches}
+        elif name == "k_mlp_tc_f32":
+            fl = tf32x3_flops_per_hit(scene) * n_hit * steps
+            byt = (tf32_row_bytes(scene) + 16 + 8) * n_hit * steps
+            out[name] = {"tensor_tflops": fl / sec / 1e12, "frac_tf32_peak": fl / sec / 1e12 / (0.5 * bf16),
+                         "tf32_peak_tflops": 0.5 * bf16,
+                         "tf32_peak_basis": "measured BF16 burst x 0.5, the nominal dense TF32 / BF16 ratio",
+                         "mlp_tflops": mlp_flops_per_hit(scene) * n_hit * steps / sec / 1e12,
+                         "gbs": byt / sec / 1e9, "frac_hbm": byt / sec / 1e9 / hbm,
+                         "launches_per_step": per_step_launches}
+        elif name.startswith("k_shade"):
             byt = (algorithmic_bytes_per_hit(scene) + 24) * n_hit * steps
             fl = mlp_flops_per_hit(scene) * n_hit * steps
             out[name] = {"gbs": byt / sec / 1e9, "frac_hbm": byt / sec / 1e9 / hbm,
@@ -908,7 +947,29 @@ def run_native(a):
         avg_s = st["ms"] / 1e3 / st["launches"]
         hits_per_launch = n_hit / max(1, st["launches"] // a.steps) if a.steps else n_hit
         peak = peaks.get("hbm_gbs", 6800.0)
-        if top.startswith("k_shade"):
+        if top == "k_encode_tc_f32":
+            byt = encode_bytes_per_hit(scene) * hits_per_launch
+            achieved = byt / avg_s / 1e9
+            cnt = shade_counters(top) if not a.small and a.levels == 16 else {}
+            dram = cnt.get("dram_bytes_per_hit")
+            l2s = cnt.get("l2_sectors_per_hit")
+            roof = {"kernel": top, "bound": "latency (dependent L1/L2 gather loads)", "achieved": achieved,
+                    "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": "measured",
+                    "traffic": dram * hits_per_launch if dram else None,
+                    "algorithmic_bytes_per_launch": byt,
+                    "frac_algorithmic_of_hbm": achieved / peak,
+                    "frac_dram_of_hbm": dram * hits_per_launch / avg_s / 1e9 / peak if dram else None,
+                    "l2_sectors_per_launch": l2s * hits_per_launch if l2s else None,
+                    "frac_l2_served_of_l2_random_probe": None,
+                    "counters_src_sha": shade_source_sha()}
+        elif top == "k_mlp_tc_f32":
+            fl = tf32x3_flops_per_hit(scene) * hits_per_launch
+            tpk = 0.5 * peaks.get("bf16_tflops", 1900.0)
+            achieved = fl / avg_s / 1e12
+            roof = {"kernel": top, "bound": "tensor", "achieved": achieved, "peak": tpk, "unit": "TFLOP/s",
+                    "frac": achieved / tpk, "peak_source": "measured BF16 burst x 0.5 (nominal TF32 / BF16 ratio)",
+                    "traffic": None, "flops_per_launch": fl}
+        elif top.startswith("k_shade"):
             # the gather's algorithmic bytes over the measured HBM copy rate (the
             # contract's fraction); the kernel is bound by the latency of its
             # dependent L1/L2 gathers, so the DRAM bytes it actually moves and

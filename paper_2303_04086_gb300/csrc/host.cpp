@@ -433,7 +433,7 @@ inolf_status upload_weights(Object& o, const float* w1, const float* w2, const f
 
 static void destroy_object(Object& o) {
   auto f = [](void* p) { if (p) cudaFree(p); };
-  f(o.nodes); f(o.tris); f(o.w_f32); f(o.w_bf16); f(o.w_fp8); f(o.w_scale_dev);
+  f(o.nodes); f(o.tris); f(o.w_f32); f(o.w_bf16); f(o.w_fp8); f(o.w_tf32); f(o.w_scale_dev);
   f((void*)o.cub.grid); f((void*)o.cub.dens); f((void*)o.cub.diff); f((void*)o.cub.fdist); f((void*)o.cub.bdist);
   for (int l = 0; l < o.L; ++l) {
     f((void*)o.lv[l].phi); f((void*)o.lv[l].table); f((void*)o.lv[l].bundle); f((void*)o.pts[l]);

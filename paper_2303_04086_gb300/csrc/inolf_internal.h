@@ -96,8 +96,9 @@ struct Object {
   // BF16 / FP8 operands for the tensor-core MLP (K-major rows, see mlp kernels)
   void* w_bf16 = nullptr;
   void* w_fp8 = nullptr;
-  int32_t tc_k1_bf16 = 0, tc_k1_fp8 = 0;
-  uint32_t tc_bytes_bf16 = 0, tc_bytes_fp8 = 0;
+  void* w_tf32 = nullptr;  // FP32 weights as split-TF32 operands (hi then lo per layer)
+  int32_t tc_k1_bf16 = 0, tc_k1_fp8 = 0, tc_k1_tf32 = 0;
+  uint32_t tc_bytes_bf16 = 0, tc_bytes_fp8 = 0, tc_bytes_tf32 = 0;
   float fp8_w_scale[3] = {0, 0, 0};  // host copy of the FP8 weight scales (refreshed on demand)
   float* w_scale_dev = nullptr;       // device copy, read by the kernels
   float fp8_act_scale[3] = {0, 0, 0};

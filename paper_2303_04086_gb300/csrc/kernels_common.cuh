@@ -36,8 +36,9 @@ struct Params {
   const float* w_f32;
   const void* w_bf16;
   const void* w_fp8;
-  int32_t tc_k1_bf16, tc_k1_fp8;      // padded input width of the tensor-core layer 1
-  uint32_t tc_bytes_bf16, tc_bytes_fp8;
+  const void* w_tf32;                 // FP32 weights split into TF32 hi / lo operands
+  int32_t tc_k1_bf16, tc_k1_fp8, tc_k1_tf32;  // padded input width of the tensor-core layer 1
+  uint32_t tc_bytes_bf16, tc_bytes_fp8, tc_bytes_tf32;
   const void* tc_w;                   // blob used by this launch
   int32_t tc_k1;
   uint32_t tc_wbytes;

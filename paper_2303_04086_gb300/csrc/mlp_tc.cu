@@ -48,9 +48,9 @@ static constexpr int kW3Rows = 16;          // W3 padded to the smallest N of an
 // of every level, then the SH view encoding and, for density-cube objects,
 // alpha_c; zero-padded to K1 columns.  Returns the hit's ray index.
 // rec: the hit record (ray, t bits) of hit h, loaded by the caller.
-template <bool kFP8>
+template <int kOp>
 __device__ __forceinline__ int64_t encode_rec(const Params& p, uint2 rec, uint32_t h, uint32_t K1,
-                                              RowWriter<kFP8>& rw) {
+                                              RowWriter<kOp>& rw) {
   float o[3], d[3], x[3];
   ray_of(p, rec.x, o, d);
   hit_unit_coords(p, o, d, __uint_as_float(rec.y), x);
@@ -83,9 +83,9 @@ __device__ __forceinline__ int64_t encode_rec(const Params& p, uint2 rec, uint32
   return rec.x;
 }
 
-template <bool kFP8>
-__device__ __forceinline__ int64_t encode_hit(const Params& p, uint32_t h, uint32_t K1, RowWriter<kFP8>& rw) {
-  return encode_rec<kFP8>(p, p.hits[h], h, K1, rw);
+template <int kOp>
+__device__ __forceinline__ int64_t encode_hit(const Params& p, uint32_t h, uint32_t K1, RowWriter<kOp>& rw) {
+  return encode_rec<kOp>(p, p.hits[h], h, K1, rw);
 }
 
 // Writes the shaded colour of hit h (ray `ray`); density-cube objects add
@@ -186,9 +186,10 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_shade_tc(const __grid_constan
 // MLP barriers hold its warps.
 static constexpr int kEncThreads = 256;
 
-template <bool kFP8>
+template <int kOp>
 __global__ void __launch_bounds__(kEncThreads, 4) k_encode_tc(const __grid_constant__ Params p) {
-  constexpr uint32_t ES = kFP8 ? 1u : 2u;
+  constexpr bool kFP8 = kOp == kOpFP8;
+  constexpr uint32_t ES = op_bytes<kOp>();
   const uint32_t K1 = (uint32_t)p.tc_k1, chunks1 = K1 * ES / 16u, tile_gbytes = 128u * K1 * ES;
   const float inv_sx = kFP8 ? 1.0f / p.fp8_act_scale[0] : 1.0f;
   const uint32_t end = min(p.tc_h_end, *p.counter);  // launches past the last hit return at once
@@ -201,15 +202,15 @@ __global__ void __launch_bounds__(kEncThreads, 4) k_encode_tc(const __grid_const
     for (; h < end; h += stride) {
       const uint2 next = h + stride < end ? p.hits[h + stride] : make_uint2(0u, 0u);
       const uint32_t i = h - p.tc_h_begin;
-      RowWriter<kFP8> rw(p.tc_a + (size_t)(i >> 7) * tile_gbytes, i & 127u, chunks1, inv_sx);
-      encode_rec<kFP8>(p, rec, h, K1, rw);
+      RowWriter<kOp> rw(p.tc_a + (size_t)(i >> 7) * tile_gbytes, i & 127u, chunks1, inv_sx);
+      encode_rec<kOp>(p, rec, h, K1, rw);
       rec = next;
     }
   } else {
     for (; h < end; h += stride) {
       const uint32_t i = h - p.tc_h_begin;
-      RowWriter<kFP8> rw(p.tc_a + (size_t)(i >> 7) * tile_gbytes, i & 127u, chunks1, inv_sx);
-      encode_hit<kFP8>(p, h, K1, rw);
+      RowWriter<kOp> rw(p.tc_a + (size_t)(i >> 7) * tile_gbytes, i & 127u, chunks1, inv_sx);
+      encode_hit<kOp>(p, h, K1, rw);
     }
   }
 }
@@ -293,10 +294,138 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_mlp_tc(const __grid_constant_
   }
 }
 
+// FP32 path of the split shade: the tiles hold raw FP32 layer-1 inputs
+// (written by k_encode_tc<kOpF32>).  A CTA runs two independent pipelines of
+// 128 threads, each over its own 128-row tiles with its own hi / lo buffers,
+// mbarriers, 64 tensor-memory columns and named barrier, so that one
+// pipeline's MMAs overlap the other's tile copy, split and epilogues.  Per
+// tile: one bulk copy into the hi buffer, the split into TF32 hi / lo parts
+// in place, and the three layers as split-TF32 products (tc_mlp_run_tf32).
+// The weights, split on the host, arrive by one bulk copy.  One CTA per SM
+// (about 200 KB of shared memory).
+static constexpr uint32_t kTf32TileBytes = 128u * 64u * 4u;
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tf32(const __grid_constant__ Params p) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  if (p.tc_h_begin >= *p.counter) return;  // a range past the last hit (uniform over the grid)
+  const uint32_t K1 = (uint32_t)p.tc_k1;
+  const uint32_t wbytes = p.tc_wbytes;
+  const uint32_t tile_gbytes = 128u * K1 * 4u;
+  uint8_t* sA = smem + ((wbytes + 1023u) & ~1023u);  // per pipeline: hi buffer, lo buffer
+  // [0] weights; pipeline q: [1 + 2 q] its MMAs, [2 + 2 q] its tile copy
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + 4u * kTf32TileBytes);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 5);
+
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const uint32_t pipe = (uint32_t)tid >> 7, row = (uint32_t)tid & 127u;
+  const bool lead = row == 0u;
+  if (tid == 0) {
+    for (int b = 0; b < 5; ++b) tc::mbar_init(&bars[b], 1);
+    tc::fence_mbar_init();
+  }
+  __syncthreads();
+  if (warp == 0) tc::tmem_alloc(tslot, kTmemCols);
+  if (tid == 0) {
+    tc::mbar_arrive_expect_tx(&bars[0], wbytes);
+    tc::bulk_g2s(smem, p.tc_w, wbytes, &bars[0]);
+  }
+  const bool ok = tc::mbar_wait(&bars[0], 0, kWaitLimitNs);
+  tc::fence_before();
+  bool bad = __syncthreads_or(!ok);
+  tc::fence_after();
+  const uint32_t tmem = *tslot + pipe * 64u;
+  uint8_t* Ah = sA + pipe * 2u * kTf32TileBytes;
+  uint8_t* Al = Ah + kTf32TileBytes;
+  uint64_t* mbar = &bars[1 + 2 * pipe];
+  uint64_t* tbar = &bars[2 + 2 * pipe];
+  const uint32_t bid = 1u + pipe;
+  uint32_t phase = 0, tphase = 0;
+  bool tile_in_flight = false;
+  const uint32_t end = min(p.tc_h_end, *p.counter);
+
+  for (uint32_t base = p.tc_h_begin + (blockIdx.x * 2u + pipe) * 128u; !bad && base < end;
+       base += gridDim.x * 256u) {
+    const uint32_t t0 = (base - p.tc_h_begin) >> 7;
+    if (lead) {
+      tc::fence_async_smem();  // the previous tile's in-place writes precede the copy
+      tc::mbar_arrive_expect_tx(tbar, tile_gbytes);
+      tc::bulk_g2s(Ah, p.tc_a + (size_t)t0 * tile_gbytes, tile_gbytes, tbar);
+    }
+    tile_in_flight = true;
+    const uint32_t h = base + row;
+    const uint32_t ray = h < end ? p.hits[h].x : 0u;
+    const bool landed = tc::mbar_wait(tbar, tphase, kWaitLimitNs);
+    tphase ^= 1u;
+    if (pipe_or(bid, !landed)) {
+      bad = true;
+      break;
+    }
+    tile_in_flight = false;
+    float4 rgba;
+    if (!tc_mlp_run_tf32(Ah, Al, smem, K1, tmem, lead, bid, mbar, phase, rgba)) {
+      bad = true;
+      break;
+    }
+    if (h < end) store_rgba(p, h, (int64_t)ray, rgba);
+  }
+  if (bad) {
+    if (lead) atomicOr(p.counter + 1, INOLF_FLAG_WAIT_TIMEOUT);
+    // the pipeline's copy and MMAs still in flight finish before the CTA
+    // leaves; a failed wait already flipped its parity
+    if (tile_in_flight) tc::mbar_wait(tbar, tphase ^ 1u, kWaitLimitNs);
+    tc::mbar_wait(mbar, phase ^ 1u, kWaitLimitNs);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after();
+    tc::tmem_dealloc(*tslot, kTmemCols);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 static uint32_t round_up(uint32_t v, uint32_t m) { return (v + m - 1) / m * m; }
+
+// Split-TF32 weight blob: [W1 hi | W1 lo | W2 hi | W2 lo | W3 hi | W3 lo],
+// W1 64 x K1 (columns from din on zero), W2 64 x 64, W3 16 x 64 (rows 4..15
+// zero), each K-major in core matrices of 8 rows x 4 FP32 values; hi =
+// tf32(w), lo = tf32(w - hi).  Returns the offset of element (n, k) of a
+// matrix with `chunks` 16-byte chunks per row.
+static inline uint32_t tf32_off(uint32_t n, uint32_t k, uint32_t chunks) {
+  return tc::core_off(n, k / 4, chunks) + (k % 4) * 4;
+}
+static void tf32_split_host(float w, uint32_t& hi, uint32_t& lo) {
+  uint32_t u;
+  std::memcpy(&u, &w, 4);
+  hi = tf32_rna_bits(u);
+  float h, r;
+  std::memcpy(&h, &hi, 4);
+  r = w - h;
+  std::memcpy(&u, &r, 4);
+  lo = tf32_rna_bits(u);
+}
+static std::vector<uint8_t> tf32_blob_host(const float* w1, const float* w2, const float* w3, int din, uint32_t K1) {
+  const int H = INOLF_HIDDEN, O = INOLF_OUT;
+  const size_t m1 = (size_t)H * K1 * 4, m2 = (size_t)H * H * 4, m3 = (size_t)kW3Rows * H * 4;
+  std::vector<uint8_t> blob(2 * (m1 + m2 + m3), 0);
+  auto put = [&](uint8_t* hi_base, size_t lo_delta, uint32_t n, uint32_t k, uint32_t chunks, float w) {
+    uint32_t hi, lo;
+    tf32_split_host(w, hi, lo);
+    std::memcpy(hi_base + tf32_off(n, k, chunks), &hi, 4);
+    std::memcpy(hi_base + lo_delta + tf32_off(n, k, chunks), &lo, 4);
+  };
+  uint8_t* b1 = blob.data();
+  uint8_t* b2 = b1 + 2 * m1;
+  uint8_t* b3 = b2 + 2 * m2;
+  for (int n = 0; n < H; ++n)
+    for (int k = 0; k < din; ++k) put(b1, m1, n, k, K1 / 4, w1[(size_t)n * din + k]);
+  for (int n = 0; n < H; ++n)
+    for (int k = 0; k < H; ++k) put(b2, m2, n, k, 16, w2[(size_t)n * H + k]);
+  for (int n = 0; n < O; ++n)
+    for (int k = 0; k < H; ++k) put(b3, m3, n, k, 16, w3[(size_t)n * H + k]);
+  return blob;
+}
 
 // Weight blob in the operand layout (K-major core matrices, rows = output
 // neurons): [W1: 64 x K1][W2: 64 x 64][W3: 16 x 64, rows 4..15 zero]
@@ -338,6 +467,20 @@ inolf_status prepare_tc_weights(Object& obj, const float* w1, const float* w2, c
       return fail(INOLF_E_CUDA, "upload bf16 weights");
     obj.tc_k1_bf16 = (int32_t)K1;
     obj.tc_bytes_bf16 = (uint32_t)blob.size();
+  }
+  // ---- FP32 as split TF32: per layer the hi parts, then the lo parts ----
+  {
+    const uint32_t K1 = round_up((uint32_t)din, 8);
+    const std::vector<uint8_t> blob = tf32_blob_host(w1, w2, w3, din, K1);
+    if (!obj.w_tf32) {
+      if (cudaMalloc(&obj.w_tf32, blob.size()) != cudaSuccess) return fail(INOLF_E_OOM, "cudaMalloc tf32 weights");
+      obj.bytes += blob.size();
+    }
+    if (cudaMemcpyAsync(obj.w_tf32, blob.data(), blob.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return fail(INOLF_E_CUDA, "upload tf32 weights");
+    obj.tc_k1_tf32 = (int32_t)K1;
+    obj.tc_bytes_tf32 = (uint32_t)blob.size();
   }
   // ---- FP8 e4m3, per-tensor scales amax / 448 ----
   {
@@ -394,9 +537,18 @@ __device__ float block_amax(const float* w, int n, float* red) {
   return m;
 }
 
+__device__ __forceinline__ void tf32_put(uint8_t* hi_base, size_t lo_delta, uint32_t n, uint32_t k, uint32_t chunks,
+                                         float w) {
+  const uint32_t hi = tf32_rna_bits(__float_as_uint(w));
+  const uint32_t lo = tf32_rna_bits(__float_as_uint(w - __uint_as_float(hi)));
+  const uint32_t off = tc::core_off(n, k / 4, chunks) + (k % 4) * 4;
+  *reinterpret_cast<uint32_t*>(hi_base + off) = hi;
+  *reinterpret_cast<uint32_t*>(hi_base + lo_delta + off) = lo;
+}
+
 __global__ void k_pack_weights(const float* __restrict__ w1, const float* __restrict__ w2,
-                               const float* __restrict__ w3, int din, uint32_t K1b, uint32_t K1f, float* f32,
-                               uint8_t* bf16, uint8_t* fp8, float* scales) {
+                               const float* __restrict__ w3, int din, uint32_t K1b, uint32_t K1f, uint32_t K1t,
+                               float* f32, uint8_t* bf16, uint8_t* fp8, uint8_t* tf32, float* scales) {
   constexpr int H = INOLF_HIDDEN, O = INOLF_OUT;
   __shared__ float red[32];
   const float a1 = block_amax(w1, H * din, red), a2 = block_amax(w2, H * H, red), a3 = block_amax(w3, O * H, red);
@@ -452,14 +604,27 @@ __global__ void k_pack_weights(const float* __restrict__ w1, const float* __rest
     const int n = i / H, k = i - n * H;
     f3[tc::core_off(n, k / 16, 4) + (k % 16)] = n < O ? q(w3[i], s3) : (uint8_t)0;
   }
+  // split TF32: [W1 hi | W1 lo (64 x K1t, zero padded) | W2 hi | W2 lo | W3 hi | W3 lo (16 rows)]
+  const size_t m1 = (size_t)H * K1t * 4, m2 = (size_t)H * H * 4, m3 = (size_t)kW3Rows * H * 4;
+  for (int i = tid; i < H * (int)K1t; i += nt) {
+    const int n = i / (int)K1t, k = i - n * (int)K1t;
+    tf32_put(tf32, m1, n, k, K1t / 4, k < din ? w1[n * din + k] : 0.0f);
+  }
+  uint8_t* t2 = tf32 + 2 * m1;
+  for (int i = tid; i < H * H; i += nt) tf32_put(t2, m2, i / H, i % H, 16, w2[i]);
+  uint8_t* t3 = t2 + 2 * m2;
+  for (int i = tid; i < kW3Rows * H; i += nt) {
+    const int n = i / H, k = i - n * H;
+    tf32_put(t3, m3, n, k, 16, n < O ? w3[i] : 0.0f);
+  }
 }
 
 inolf_status pack_weights_device(Object& obj, const float* w1, const float* w2, const float* w3, void* stream) {
-  if (!obj.w_f32 || !obj.w_bf16 || !obj.w_fp8 || !obj.w_scale_dev)
+  if (!obj.w_f32 || !obj.w_bf16 || !obj.w_fp8 || !obj.w_tf32 || !obj.w_scale_dev)
     return fail(INOLF_E_INVALID, "pack_weights_device: object weights not allocated");
-  k_pack_weights<<<1, 1024, 0, (cudaStream_t)stream>>>(w1, w2, w3, obj.d_in, (uint32_t)obj.tc_k1_bf16,
-                                                      (uint32_t)obj.tc_k1_fp8, obj.w_f32, (uint8_t*)obj.w_bf16,
-                                                      (uint8_t*)obj.w_fp8, obj.w_scale_dev);
+  k_pack_weights<<<1, 1024, 0, (cudaStream_t)stream>>>(
+      w1, w2, w3, obj.d_in, (uint32_t)obj.tc_k1_bf16, (uint32_t)obj.tc_k1_fp8, (uint32_t)obj.tc_k1_tf32, obj.w_f32,
+      (uint8_t*)obj.w_bf16, (uint8_t*)obj.w_fp8, (uint8_t*)obj.w_tf32, obj.w_scale_dev);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(INOLF_E_CUDA, std::string("k_pack_weights: ") + cudaGetErrorString(e));
   return INOLF_OK;
@@ -473,18 +638,25 @@ static size_t tc_smem_bytes(uint32_t wbytes, bool fp8) {
   return ((wbytes + 1023u) & ~1023u) + 2 * tile + 64;
 }
 
+// Largest split-TF32 weight blob (K1 = 64) and the shared memory of
+// k_mlp_tf32: the blob, hi and lo buffers of two tiles, three mbarriers and
+// the tensor-memory slot.
+static constexpr uint32_t kMaxTf32WeightBytes = 2u * (64u * 64u + 64u * 64u + 16u * 64u) * 4u;
+static size_t tf32_smem_bytes(uint32_t wbytes) { return ((wbytes + 1023u) & ~1023u) + 4u * kTf32TileBytes + 64; }
+
 inolf_status launch_shade_tc(const Params& p_in, inolf_precision prec, cudaStream_t st) {
-  const bool fp8 = prec == INOLF_FP8;
+  const bool fp8 = prec == INOLF_FP8, f32 = prec == INOLF_FP32;
   Params p = p_in;
-  p.tc_w = fp8 ? p.w_fp8 : p.w_bf16;
-  p.tc_k1 = fp8 ? p.tc_k1_fp8 : p.tc_k1_bf16;
-  p.tc_wbytes = fp8 ? p.tc_bytes_fp8 : p.tc_bytes_bf16;
+  p.tc_w = f32 ? p.w_tf32 : (fp8 ? p.w_fp8 : p.w_bf16);
+  p.tc_k1 = f32 ? p.tc_k1_tf32 : (fp8 ? p.tc_k1_fp8 : p.tc_k1_bf16);
+  p.tc_wbytes = f32 ? p.tc_bytes_tf32 : (fp8 ? p.tc_bytes_fp8 : p.tc_bytes_bf16);
   if (!p.tc_w || p.tc_wbytes == 0 || (p.tc_wbytes & 15u)) return fail(INOLF_E_INVALID, "tensor-core weights missing");
-  const size_t smem = tc_smem_bytes(p.tc_wbytes, fp8);
+  if (f32 && !p.tc_a) return fail(INOLF_E_INVALID, "FP32 tensor-core shade: no operand tiles in the workspace");
+  const size_t smem = f32 ? tf32_smem_bytes(p.tc_wbytes) : tc_smem_bytes(p.tc_wbytes, fp8);
   const int dev = device_index();
   if (dev < 0) return fail(INOLF_E_UNSUPPORTED, "k_shade_tc: no current device, or an index beyond 63");
   static int grid_bf16_dev[kMaxDevices], grid_fp8_dev[kMaxDevices];
-  static int grid_enc_dev[kMaxDevices][2], grid_mlp_dev[kMaxDevices][2];  // [precision: BF16, FP8]
+  static int grid_enc_dev[kMaxDevices][3], grid_mlp_dev[kMaxDevices][3];  // [operand kind: BF16, FP8, FP32]
   static std::once_flag once[kMaxDevices];
   std::call_once(once[dev], [&] {
     int sms = 1, regs_sm = 65536, smem_sm = 0;
@@ -520,18 +692,21 @@ inolf_status launch_shade_tc(const Params& p_in, inolf_precision prec, cudaStrea
       const int regs_warp = ((std::max(fa.numRegs, 1) * 32 + 255) / 256) * 256;
       return std::max(1, std::min(regs_sm / (regs_warp * (kEncThreads / 32)), 2048 / kEncThreads));
     };
-    grid_enc_dev[dev][0] = sms * enc_ctas((const void*)k_encode_tc<false>);
-    grid_enc_dev[dev][1] = sms * enc_ctas((const void*)k_encode_tc<true>);
+    grid_mlp_dev[dev][2] = sms * ctas_per_sm((const void*)k_mlp_tf32, tf32_smem_bytes(kMaxTf32WeightBytes));
+    grid_enc_dev[dev][0] = sms * enc_ctas((const void*)k_encode_tc<kOpBF16>);
+    grid_enc_dev[dev][1] = sms * enc_ctas((const void*)k_encode_tc<kOpFP8>);
+    grid_enc_dev[dev][2] = sms * enc_ctas((const void*)k_encode_tc<kOpF32>);
     cudaGetLastError();
   });
-  if (smem > (size_t)tc_smem_bytes(kMaxTcWeightBytes, fp8)) return fail(INOLF_E_INVALID, "tensor-core weights too large");
+  if (smem > (f32 ? tf32_smem_bytes(kMaxTf32WeightBytes) : tc_smem_bytes(kMaxTcWeightBytes, fp8)))
+    return fail(INOLF_E_INVALID, "tensor-core weights too large");
   const int grid = fp8 ? grid_fp8_dev[dev] : grid_bf16_dev[dev];
   if (p.tc_a) {
     // split path: sub-ranges of the hit list as large as the workspace's
     // operand tiles hold (a multiple of the MLP kernel's 256 rows); the hit
     // count is known on the device only, so the ranges span the chunk's ray
     // count and launches past the last hit return at once
-    const uint64_t row_bytes = (uint64_t)p.tc_k1 * (fp8 ? 1u : 2u);
+    const uint64_t row_bytes = (uint64_t)p.tc_k1 * (f32 ? 4u : (fp8 ? 1u : 2u));
     const uint64_t rows = std::min<uint64_t>(p.tc_a_bytes / row_bytes / 256u * 256u, 0x80000000ull);
     if (rows < 256) return fail(INOLF_E_INVALID, "split shade: operand tile region smaller than 256 rows");
     for (int64_t h0 = 0; h0 < p.n_rays; h0 += (int64_t)rows) {
@@ -539,15 +714,17 @@ inolf_status launch_shade_tc(const Params& p_in, inolf_precision prec, cudaStrea
       q.tc_h_begin = (uint32_t)h0;
       q.tc_h_end = (uint32_t)std::min<int64_t>(h0 + (int64_t)rows, p.n_rays);
       {
-        LaunchTimer lt(fp8 ? "k_encode_tc_fp8" : "k_encode_tc_bf16", st);
-        if (fp8) k_encode_tc<true><<<grid_enc_dev[dev][1], kEncThreads, 0, st>>>(q);
-        else k_encode_tc<false><<<grid_enc_dev[dev][0], kEncThreads, 0, st>>>(q);
+        LaunchTimer lt(f32 ? "k_encode_tc_f32" : (fp8 ? "k_encode_tc_fp8" : "k_encode_tc_bf16"), st);
+        if (f32) k_encode_tc<kOpF32><<<grid_enc_dev[dev][2], kEncThreads, 0, st>>>(q);
+        else if (fp8) k_encode_tc<kOpFP8><<<grid_enc_dev[dev][1], kEncThreads, 0, st>>>(q);
+        else k_encode_tc<kOpBF16><<<grid_enc_dev[dev][0], kEncThreads, 0, st>>>(q);
       }
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return fail(INOLF_E_CUDA, std::string("k_encode_tc: ") + cudaGetErrorString(e));
       {
-        LaunchTimer lt(fp8 ? "k_mlp_tc_fp8" : "k_mlp_tc_bf16", st);
-        if (fp8) k_mlp_tc<true><<<grid_mlp_dev[dev][1], kTcThreads, smem, st>>>(q);
+        LaunchTimer lt(f32 ? "k_mlp_tc_f32" : (fp8 ? "k_mlp_tc_fp8" : "k_mlp_tc_bf16"), st);
+        if (f32) k_mlp_tf32<<<grid_mlp_dev[dev][2], kTcThreads, smem, st>>>(q);
+        else if (fp8) k_mlp_tc<true><<<grid_mlp_dev[dev][1], kTcThreads, smem, st>>>(q);
         else k_mlp_tc<false><<<grid_mlp_dev[dev][0], kTcThreads, smem, st>>>(q);
       }
       e = cudaGetLastError();

@@ -766,6 +766,9 @@ static void fill_common(const Object& obj, Params& p) {
   p.w_f32 = obj.w_f32;
   p.w_bf16 = obj.w_bf16;
   p.w_fp8 = obj.w_fp8;
+  p.w_tf32 = obj.w_tf32;
+  p.tc_k1_tf32 = obj.tc_k1_tf32;
+  p.tc_bytes_tf32 = obj.tc_bytes_tf32;
   p.tc_k1_bf16 = obj.tc_k1_bf16;
   p.tc_k1_fp8 = obj.tc_k1_fp8;
   p.tc_bytes_bf16 = obj.tc_bytes_bf16;
@@ -844,14 +847,21 @@ inolf_status launch_render(const Object& obj, const RayBatch& rays, inolf_precis
   Params p{};
   fill_common(obj, p);
   // The split tensor-core shade keeps its operand tiles at the end of the
-  // workspace when the workspace holds them beside one view's (or all the
-  // rays') hit records; otherwise the fused kernel runs.
+  // workspace beside one view's (or all the rays') hit records: the full
+  // tile region when the workspace holds it, else what the hit records
+  // leave, as long as that is at least 256 rows of this precision;
+  // otherwise the fused kernel (BF16 / FP8) or the FP32 SIMT kernel runs.
   size_t hit_ws = ws_bytes;
-  if (!encode && !amax && !hits_only && prec != INOLF_FP32 && tc_chunk_rows() >= 256) {
+  if (!encode && !amax && !hits_only && tc_chunk_rows() >= 256) {
     const int64_t n_call = rays.mode == 0 ? (int64_t)rays.n_views * rays.W * rays.H : rays.n;
     const int64_t min_hits = rays.mode == 0 ? (int64_t)rays.W * rays.H : n_call;
-    const size_t a_bytes = tc_region_bytes(n_call);
-    if (ws_bytes >= kWsHeader + (size_t)min_hits * hit_bytes_per_ray(obj) + a_bytes) {
+    const size_t hits_min = kWsHeader + (size_t)min_hits * hit_bytes_per_ray(obj);
+    size_t a_bytes = tc_region_bytes(n_call);
+    if (ws_bytes < hits_min + a_bytes && ws_bytes > hits_min) a_bytes = (ws_bytes - hits_min) / 256 * 256;
+    const size_t row_bytes = prec == INOLF_FP32 ? 4u * (size_t)obj.tc_k1_tf32
+                             : prec == INOLF_FP8 ? (size_t)obj.tc_k1_fp8
+                                                 : 2u * (size_t)obj.tc_k1_bf16;
+    if (ws_bytes >= hits_min + a_bytes && row_bytes > 0 && a_bytes >= 256 + 256 * row_bytes) {
       hit_ws = (ws_bytes - a_bytes + 255) / 256 * 256;
       p.tc_a = (uint8_t*)workspace + hit_ws;
       p.tc_a_bytes = (uint64_t)(ws_bytes - hit_ws);
@@ -952,7 +962,7 @@ inolf_status launch_render(const Object& obj, const RayBatch& rays, inolf_precis
       k_shade_f32<kAmax><<<shade_grid, 128, smem_f32, st>>>(p);
       return check_launch("k_shade_amax");
     }
-    if (prec == INOLF_FP32) {
+    if (prec == INOLF_FP32 && !p.tc_a) {
       {
         LaunchTimer lt("k_shade_f32", st);
         if (ws_ok) k_shade_f32_ws<<<sm_count(), kWsThreads, smem_ws, st>>>(p);

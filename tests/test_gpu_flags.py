@@ -7,7 +7,11 @@ INOLF_FLAG_WAIT_TIMEOUT and returns.  The flag must be visible through
 inolf_workspace_flags for the asynchronous calls, turned into INOLF_E_TIMEOUT
 by the calls that synchronise (inolf_render_host, the allocation-free entry
 point), and the context must stay usable: the next call, without injection,
-matches the oracle with its flags clear."""
+matches the oracle with its flags clear.  The FP32 shade runs on the CUDA
+cores (k_shade_f32_ws) only when the workspace carries no operand tiles, so
+the injected calls switch the tiles off (INOLF_TC_CHUNK_ROWS=0)."""
+import os
+
 import numpy as np
 import pytest
 
@@ -31,6 +35,8 @@ def test_wait_timeout_is_reported_and_the_context_survives(env, tiny_oracle, tin
     rgba = torch.empty((1, H, W, 4), device="cuda")
     checking = inolf._check_flags
     inolf.check_device_flags(False)
+    old_rows = os.environ.get("INOLF_TC_CHUNK_ROWS")
+    os.environ["INOLF_TC_CHUNK_ROWS"] = "0"
     try:
         inolf.set_wait_limit_ns(1_000_000)  # 1 ms
         inolf.set_fault_injection(inolf.INJECT_RING_STALL)
@@ -51,6 +57,10 @@ def test_wait_timeout_is_reported_and_the_context_survives(env, tiny_oracle, tin
         inolf.set_fault_injection(0)
         inolf.set_wait_limit_ns(0)
         inolf.check_device_flags(checking)
+        if old_rows is None:
+            os.environ.pop("INOLF_TC_CHUNK_ROWS", None)
+        else:
+            os.environ["INOLF_TC_CHUNK_ROWS"] = old_rows
     # the context is intact: the same render, without injection, is right
     tri = torch.empty((1, H, W), dtype=torch.int32, device="cuda")
     inolf.render(obj, tiny_cam[None], W, H, "fp32", rgba_out=rgba, tri_out=tri, workspace=ws)

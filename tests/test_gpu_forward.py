@@ -69,11 +69,21 @@ def test_ragged_sizes_and_views(torch_cuda, tiny, tiny_obj, tiny_oracle, W, H, n
 
 
 def test_small_workspace_chunks_views(torch_cuda, tiny, tiny_obj, tiny_oracle):
+    # a workspace for 2 of the 7 views: the views are rendered in chunks, and
+    # the FP32 shade runs on the CUDA cores because the workspace has no room
+    # for operand tiles; with the full workspace it runs on the tensor cores
+    # (split TF32).  Hits are bit-exact either way, colours agree within the
+    # split-TF32 tolerance and both meet the FP32 bar against the oracle.
     from paper_2303_04086_gb300 import inolf
     cams = synth.ring_cameras(7, 3.0)
     full, tri_f, t_f = _render(inolf, tiny_obj, cams, 40, 30)
     part, tri_p, t_p = _render(inolf, tiny_obj, cams, 40, 30, ws_rays=40 * 30 * 2)  # 2 views per chunk
-    assert np.array_equal(tri_f, tri_p) and np.array_equal(full, part)
+    assert np.array_equal(tri_f, tri_p) and np.array_equal(t_f.view(np.int32), t_p.view(np.int32))
+    assert np.abs(full - part).max() <= 2e-5
+    for v in range(len(cams)):
+        ref = tiny_oracle.render_pixels(cams[v], 40, 30)
+        assert np.abs(part[v].reshape(-1, 4) - ref["rgba"]).max() <= RGBA_TOL
+        assert np.abs(full[v].reshape(-1, 4) - ref["rgba"]).max() <= RGBA_TOL
 
 
 def _random_rays(n, seed, inside_frac=0.1):

@@ -5,7 +5,10 @@ the same MMAs and epilogues, so their frames must agree bit for bit:
   - split with the default workspace (one sub-range per launch chunk);
   - split with sub-ranges of a few hundred rows (many ranges, a ragged last
     range, launches past the last hit);
-  - fused, with a workspace holding only the header and the hit list;
+  - a small workspace (room for the hit records of the whole call only):
+    renders take one view per chunk with the operand tiles that one view's
+    hit records leave room for, explicit rays run fused (no room for 256
+    rows of tiles);
   - fused, with the operand tiles switched off (INOLF_TC_CHUNK_ROWS=0).
 Mesh objects and density-cube objects (alpha_c input, c = c_d + tint c_s)
 are both covered; the accuracy of these paths against the oracle is checked
@@ -57,7 +60,7 @@ def _frames(torch, inolf, obj, cams, W, H, prec):
     with _env(None):
         out["split"] = inolf.render(obj, cams, W, H, prec).cpu().numpy()
         small = torch.empty((hit_bytes + 15) // 16 * 4, dtype=torch.int32, device="cuda")
-        out["fused_small_ws"] = inolf.render(obj, cams, W, H, prec, workspace=small).cpu().numpy()
+        out["small_ws"] = inolf.render(obj, cams, W, H, prec, workspace=small).cpu().numpy()
     with _env(300):  # tiles for 300 rows of 128 B: ranges of 512 (BF16) or 1024 (FP8) hits
         out["split_many"] = inolf.render(obj, cams, W, H, prec).cpu().numpy()
     with _env(0):
@@ -126,7 +129,7 @@ def test_split_equals_fused_explicit_rays(torch_cuda, prec):
     with _env(None):
         out["default"] = inolf.render_rays(obj, o, d, prec).cpu().numpy()
         small = torch.empty((12 * n + 256 + 15) // 16 * 4, dtype=torch.int32, device="cuda")
-        out["fused_small_ws"] = inolf.render_rays(obj, o, d, prec, workspace=small).cpu().numpy()
+        out["small_ws"] = inolf.render_rays(obj, o, d, prec, workspace=small).cpu().numpy()
         out["noalloc"] = inolf.render_rays_noalloc(obj, o, d, prec).cpu().numpy()
     with _env(300):
         out["split_many"] = inolf.render_rays(obj, o, d, prec).cpu().numpy()
