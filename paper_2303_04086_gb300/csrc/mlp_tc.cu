@@ -342,16 +342,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tf32(const __grid_constan
   uint32_t phase = 0, tphase = 0;
   bool tile_in_flight = false;
   const uint32_t end = min(p.tc_h_end, *p.counter);
-
-  for (uint32_t base = p.tc_h_begin + (blockIdx.x * 2u + pipe) * 128u; !bad && base < end;
-       base += gridDim.x * 256u) {
-    const uint32_t t0 = (base - p.tc_h_begin) >> 7;
-    if (lead) {
-      tc::fence_async_smem();  // the previous tile's in-place writes precede the copy
-      tc::mbar_arrive_expect_tx(tbar, tile_gbytes);
-      tc::bulk_g2s(Ah, p.tc_a + (size_t)t0 * tile_gbytes, tile_gbytes, tbar);
-    }
+  const uint32_t step = gridDim.x * 256u;
+  // lead thread: copy of the tile at hit `b` into Ah, and a prefetch of the
+  // pipeline's tile after it into L2
+  auto issue_copy = [&](uint32_t b) {
+    tc::fence_async_smem();  // earlier in-place writes to Ah precede the copy
+    tc::mbar_arrive_expect_tx(tbar, tile_gbytes);
+    tc::bulk_g2s(Ah, p.tc_a + (size_t)((b - p.tc_h_begin) >> 7) * tile_gbytes, tile_gbytes, tbar);
+    if (b + step < end) tc::bulk_prefetch_l2(p.tc_a + (size_t)((b + step - p.tc_h_begin) >> 7) * tile_gbytes, tile_gbytes);
+  };
+  uint32_t base = p.tc_h_begin + (blockIdx.x * 2u + pipe) * 128u;
+  if (!bad && base < end) {
+    if (lead) issue_copy(base);
     tile_in_flight = true;
+  }
+  for (; !bad && base < end; base += step) {
     const uint32_t h = base + row;
     const uint32_t ray = h < end ? p.hits[h].x : 0u;
     const bool landed = tc::mbar_wait(tbar, tphase, kWaitLimitNs);
@@ -361,11 +366,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tf32(const __grid_constan
       break;
     }
     tile_in_flight = false;
+    const bool more = base + step < end;
     float4 rgba;
-    if (!tc_mlp_run_tf32(Ah, Al, smem, K1, tmem, lead, bid, mbar, phase, rgba)) {
+    // the next tile's copy starts as soon as the last layer's MMAs have
+    // read this tile's operands, ahead of the output epilogue
+    if (!tc_mlp_run_tf32(Ah, Al, smem, K1, tmem, lead, bid, mbar, phase, rgba, [&] {
+          if (lead && more) issue_copy(base + step);
+        })) {
       bad = true;
       break;
     }
+    tile_in_flight = more;
     if (h < end) store_rgba(p, h, (int64_t)ray, rgba);
   }
   if (bad) {

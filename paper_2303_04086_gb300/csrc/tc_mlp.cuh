@@ -290,11 +290,14 @@ __device__ __forceinline__ bool pipe_or(uint32_t id, bool v) {
 // 64 x 64, W3 16 x 64 (rows 4..15 zero), each K-major in 8-row x 16-byte
 // core matrices.  tmem: the pipeline's 64 accumulator columns; `lead` (the
 // pipeline's first thread) issues its MMAs and commits them to `bar`; `bid`
-// is its named barrier.  Returns false (uniformly in the pipeline) when an
-// MMA completion wait ran out.
+// is its named barrier.  after_last_mma() runs in every thread of the
+// pipeline once the last layer's MMAs have completed: Ah and Al are free
+// from then on (the caller starts the next tile's copy there).  Returns
+// false (uniformly in the pipeline) when an MMA completion wait ran out.
+template <class AfterLastMma>
 __device__ __forceinline__ bool tc_mlp_run_tf32(uint8_t* Ah, uint8_t* Al, const uint8_t* sB, uint32_t K1,
                                                 uint32_t tmem, bool lead, uint32_t bid, uint64_t* bar,
-                                                uint32_t& phase, float4& out) {
+                                                uint32_t& phase, float4& out, AfterLastMma&& after_last_mma) {
   const uint32_t chunks1 = K1 / 4u, chunks2 = 16u;
   const uint8_t* sB1h = sB;
   const uint8_t* sB1l = sB1h + 64u * K1 * 4u;
@@ -368,6 +371,7 @@ __device__ __forceinline__ bool tc_mlp_run_tf32(uint8_t* Ah, uint8_t* Al, const 
   if (!mma(sB2h, sB2l, chunks2, id)) return false;  // D2 = A2 W2^T
   next_input();                                      // A3
   if (!mma(sB3h, sB3l, chunks2, id3)) return false; // D3 = A3 W3^T (columns 0..3)
+  after_last_mma();
   float v[16];
   tc::tmem_ld16(tmem + lane_base, v);
   out = make_float4(sigmoidf_(v[0]), sigmoidf_(v[1]), sigmoidf_(v[2]), sigmoidf_(v[3]));

@@ -164,6 +164,12 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
+// Bulk prefetch of `bytes` (multiple of 16, address 16-byte aligned) from
+// global memory into L2, without a completion mechanism.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // Byte offset of 16-byte chunk c of row r in a K-major no-swizzle operand
 // tile with `chunks` 16-byte chunks per row (lbo = 128, sbo = chunks * 128).
 __host__ __device__ __forceinline__ uint32_t core_off(uint32_t r, uint32_t c, uint32_t chunks) {
