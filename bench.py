@@ -294,8 +294,8 @@ def kernel_rooflines(kernels, scene, n_rays, n_hit, steps, peaks):
             fl = mlp_flops_per_hit(scene) * n_hit * steps
             out[name] = {"gbs": byt / sec / 1e9, "frac_hbm": byt / sec / 1e9 / hbm,
                          "frac_hbm_basis": "algorithmic bytes (every corner row and Phi entry, 1 560 B per hit) "
-                                           "per second over the HBM copy rate; L1 and L2 serve most of them "
-                                           "(DRAM about 292 B per hit by ncu), so it can exceed 1",
+                                           "per second over the HBM copy rate; L1 and L2 serve most of them, "
+                                           "so it can exceed 1",
                          "mlp_tflops": fl / sec / 1e12, "frac_mlp_peak": fl / sec / 1e12 / mlp_peak.get(name, bf16),
                          "mlp_peak_tflops": mlp_peak.get(name, bf16), "launches_per_step": per_step_launches}
         else:

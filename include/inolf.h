@@ -66,7 +66,9 @@ typedef int inolf_status;
 #define INOLF_N_SH 16
 
 typedef enum {
-  INOLF_FP32 = 0, /* FP32 SIMT MLP */
+  INOLF_FP32 = 0, /* FP32 MLP: on the tensor cores as split TF32 (each FP32 operand as a TF32
+                     hi and lo part, three products per step, FP32 accumulation: FP32-level
+                     accuracy) when the workspace holds operand tiles, else on the CUDA cores */
   INOLF_BF16 = 1, /* BF16 weights/activations, FP32 accumulation (tensor cores) */
   INOLF_FP8 = 2   /* FP8 e4m3 weights/activations with per-tensor scales, FP32 accumulation */
 } inolf_precision;
@@ -205,14 +207,18 @@ inolf_status inolf_object_table_rows(const inolf_object* obj, int32_t level, int
 /* Workspace bytes inolf_render / inolf_render_rays / inolf_march_rays need
  * for n_rays rays: a 256-byte header, 12 bytes per ray (the hit list and,
  * for density-cube objects, each hit's alpha_c), and the operand tiles of
- * the BF16 / FP8 shade, 128 bytes per ray for at most 4 Mi rays (512 MiB;
+ * the tensor-core shade, 128 bytes per ray for at most 4 Mi rays (512 MiB;
  * the environment variable INOLF_TC_CHUNK_ROWS, read at every call, sets
- * that row count) plus 256 bytes.  With these tiles the BF16 / FP8 shade
- * runs as two kernels over sub-ranges of the hit list: one gathers and
- * encodes the hits into the tiles, the other runs the MLP on the tensor
- * cores.  A smaller workspace (down to the header and the hit list of one
- * view, or of all rays for ray batches) is accepted; the shade then runs as
- * one fused kernel with the same results. */
+ * that row count) plus 256 bytes.  With these tiles the shade runs as two
+ * kernels over sub-ranges of the hit list: one gathers and encodes the hits
+ * into the tiles (rows of 2 d_in bytes BF16, d_in rounded up to 32 bytes
+ * FP8, 4 d_in rounded up to 8 columns FP32), the other runs the MLP on the
+ * tensor cores.  A smaller workspace (down to the header and the hit list of
+ * one view, or of all rays for ray batches) is accepted: the tiles then take
+ * what one view's hit records leave, if that is at least 256 rows; with less
+ * room the BF16 / FP8 shade runs as one fused kernel with the same results
+ * and the FP32 shade on the CUDA cores (within 2e-5 of the tensor-core
+ * result, both within the FP32 bar of 1e-4 against the FP64 reference). */
 size_t inolf_render_workspace_bytes(int64_t n_rays);
 
 /* Renders n_views pinhole views of W x H pixels.
