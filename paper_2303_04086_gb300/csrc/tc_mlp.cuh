@@ -335,28 +335,24 @@ __device__ __forceinline__ bool tc_mlp_run_tf32(uint8_t* Ah, uint8_t* Al, const 
   // this thread's TMEM row (64 columns) -> ReLU -> hi / lo parts of the next
   // layer's A operand row, in place
   auto next_input = [&]() {
-#pragma unroll 1
-    for (uint32_t c = 0; c < 4; ++c) {
-      float v[16];
-      tc::tmem_ld16(tmem + lane_base + c * 16u, v);
+    float v[64];
+    tc::tmem_ld64(tmem + lane_base, v);  // the whole row, one load and one wait
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const uint4 x = make_uint4(__float_as_uint(fmaxf(v[4 * q], 0.f)), __float_as_uint(fmaxf(v[4 * q + 1], 0.f)),
-                                   __float_as_uint(fmaxf(v[4 * q + 2], 0.f)),
-                                   __float_as_uint(fmaxf(v[4 * q + 3], 0.f)));
-        uint4 hi, lo;
-        split_tf32(x, hi, lo);
-        const uint32_t off = tc::core_off(row, 4u * c + (uint32_t)q, chunks2);
-        *reinterpret_cast<uint4*>(Ah + off) = hi;
-        *reinterpret_cast<uint4*>(Al + off) = lo;
-      }
+    for (uint32_t q = 0; q < 16; ++q) {
+      const uint4 x = make_uint4(__float_as_uint(fmaxf(v[4 * q], 0.f)), __float_as_uint(fmaxf(v[4 * q + 1], 0.f)),
+                                 __float_as_uint(fmaxf(v[4 * q + 2], 0.f)), __float_as_uint(fmaxf(v[4 * q + 3], 0.f)));
+      uint4 hi, lo;
+      split_tf32(x, hi, lo);
+      const uint32_t off = tc::core_off(row, q, chunks2);
+      *reinterpret_cast<uint4*>(Ah + off) = hi;
+      *reinterpret_cast<uint4*>(Al + off) = lo;
     }
     tc::fence_before();
     tc::fence_async_smem();
     pipe_sync(bid);
   };
-  // layer-1 input: split this thread's raw FP32 row in place
-#pragma unroll 1
+  // layer-1 input: split this thread's raw FP32 row in place (chunks1 is even)
+#pragma unroll 2
   for (uint32_t c = 0; c < chunks1; ++c) {
     const uint32_t off = tc::core_off(row, c, chunks1);
     uint4 hi, lo;
