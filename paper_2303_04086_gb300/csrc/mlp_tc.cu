@@ -1,8 +1,11 @@
-// Tensor-core shade kernel: the gather of k_shade_f32 followed by the MLP F_s
-// (Eq. 3) on the 5th-generation tensor cores, with BF16 or FP8-e4m3 operands
-// and FP32 accumulation in tensor memory.
+// Tensor-core shade: the corner-bundle gather followed by the MLP F_s (Eq. 3)
+// on the 5th-generation tensor cores, with BF16 or FP8-e4m3 operands, or FP32
+// operands as split TF32, and FP32 accumulation in tensor memory.  With
+// operand tiles in the render workspace the shade runs as k_encode_tc
+// (gather + encode into the tiles) and k_mlp_tc / k_mlp_tf32 (the MLP over
+// bulk-copied tiles); without them BF16 / FP8 run as the fused k_shade_tc.
 //
-// One CTA = 256 threads = two tiles of 128 hit rays.  Per tile pair:
+// k_shade_tc: one CTA = 256 threads = two tiles of 128 hit rays.  Per tile pair:
 //   1. every thread gathers its ray's encoding (Sec. 4.1: 16 corner features
 //      of the PSH levels, trilinear) and SH view encoding, quantises it and
 //      writes its row of the A operand (K-major, 8x16-byte core matrices);

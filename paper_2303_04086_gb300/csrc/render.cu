@@ -6,15 +6,18 @@
 //            lexicographic (t, triangle id) minimum), then warp-ballot
 //            compaction of the hitting rays into a dense hit list
 //            (one global atomic per CTA).  Misses write RGBA = 0.
-//   k_shade  persistent over the hit list in tiles of 128 hit rays: the
-//            Sec. 4.1 grid vertex of the hit point on every level, Eq. 1
-//            perfect-hash slots of the 8 voxel corners, feature gather,
+//   shade    over the hit list: the Sec. 4.1 grid cell of the hit point on
+//            every level, its 8 corner features (one Eq. 1 slot of the lowest
+//            corner and one corner-bundle read per level in the render
+//            kernels; Eq. 1 slots of all 8 corners in the per-ray kernel),
 //            trilinear interpolation, SH view encoding and the MLP F_s of
-//            Eq. 3 with weights resident in shared memory.  FP32:
-//            k_shade_f32_ws (gather and MLP on separate warps; k_shade_f32_tiled
-//            where the register split cannot be used); per-ray k_shade_f32
-//            for stage outputs and FP8 calibration.  Tensor-core variants of
-//            the MLP live in mlp_tc.cu.
+//            Eq. 3.  With operand tiles in the workspace every precision runs
+//            on the tensor cores as an encode kernel and an MLP kernel
+//            (mlp_tc.cu; FP32 as split TF32).  Without them: the fused BF16 /
+//            FP8 kernel (mlp_tc.cu), or FP32 on the CUDA cores in this file:
+//            k_shade_f32_ws (gather and MLP on separate warps;
+//            k_shade_f32_tiled where the register split cannot be used).
+//            The per-ray k_shade_f32 serves stage outputs and FP8 calibration.
 //
 // The FP32 steps that decide integers (ray generation, triangle test, hit
 // point, cell index) are written with explicit round-to-nearest intrinsics
