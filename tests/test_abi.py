@@ -162,3 +162,26 @@ def test_cube_descriptions_are_checked_on_the_host(lib, case):
 
     st = _create_status(scene, mutate_desc=desc, mutate_cubes=cubes)
     assert st == inolf.E_INVALID, (case, st, inolf.last_error())
+
+
+@pytest.mark.parametrize("case", ["no_coords", "coord_above_N", "negative_coord"])
+def test_hashed_points_are_checked_on_the_host(lib, case):
+    # the corner bundles are laid out from the points each hash carries:
+    # a hash without them, or with a point outside [0, N], is refused before
+    # any device call
+    from paper_2303_04086_gb300 import inolf
+    scene = _cube_desc_scene()
+
+    def mutate(d):
+        h = ctypes.cast(d.hashes, ctypes.POINTER(ctypes.POINTER(inolf.HashStruct)))[1].contents
+        if case == "no_coords":
+            h.coords = None
+        elif case == "coord_above_N":
+            h.coords[4] = int(scene.resolutions[1]) + 1
+        else:
+            h.coords[0] = -1
+
+    st = _create_status(scene, mutate_desc=mutate)
+    assert st == inolf.E_INVALID
+    msg = inolf.last_error()
+    assert ("coords" in msg) if case == "no_coords" else ("outside [0, N]" in msg)
